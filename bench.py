@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the condensed spectral-element Helmholtz solver on GB300.
+
+One step = one full solve (Algorithm 4 of the paper): transformed condensed
+load, CG with the BT preconditioner to a relative residual of 1e-10, interior
+recovery, on the graded-mesh workload N = n_e p^3 ~ 1.68e7 (default p = 8 on
+32^3 elements, aspect ratio 128, lambda = 0, manufactured right-hand side plus
+seeded U[-1,1] noise).  Inputs are synthetic; f is resident in HBM when the
+timed region starts.
+
+Prints one JSON line (rank 0).  `value` is solve time per unknown (s/DOF,
+lower is better) over all ranks; every rank solves its own replica of the
+workload (weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--p 8] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import sem_inputs as si  # noqa: E402
+
+METRIC = "condensed-operator GDOF/s; PCG s/DOF to 1e-10, chosen form vs plain FP64 on GB300"
+UNIT = "s/DOF"
+# FP64 ceiling of the GB300: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_BYTES = 129e6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--p", type=int, default=8, choices=list(si.SCALE_DEGREES))
+    ap.add_argument("--ar", type=float, default=128.0)
+    ap.add_argument("--lam", type=float, default=0.0)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        busy = [x for x in sm if smax is None or x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def node_field(x, y, z, w: si.Workload, seed: int):
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    f = si.manufactured_f(X, Y, Z, w.lam)
+    if w.noise:
+        f = f + si.node_noise(X.size, seed).reshape(X.shape)
+    return np.ascontiguousarray(f.ravel())
+
+
+def apply_flops(w: si.Workload) -> float:
+    """Algorithmic FP64 flops of one condensed-operator application: the
+    multiplication counts of Table 3 (TPT: 13 n^3 + 68 n^2 per element), each
+    with its addition."""
+    n = w.p - 1
+    return 2.0 * (13 * n ** 3 + 68 * n ** 2) * w.n_elements
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (the baseline; test infrastructure timed as it stands)
+# --------------------------------------------------------------------------
+def oracle_sample(w: si.Workload, iterations: int, target_s: float = 12.0):
+    """Times the oracle on a slab of the workload's mesh: condensed load, one
+    CG iteration (operator application + vector updates) and the interior
+    recovery, then scales to the full element count and `iterations`."""
+    from oracle import local
+    from oracle.mesh import Mesh
+    hx, hy, hz = w.widths()
+    mz_s = 1
+    t_est = None
+    while True:
+        ms = Mesh(w.p, hx, hy, hz[:mz_s])
+        X, Y, Z = ms.coords()
+        f = si.manufactured_f(X, Y, Z, w.lam).ravel()
+        uB = si.random_vector(ms.n_skeleton, 1)
+        t0 = time.perf_counter()
+        fh = local.condensed_rhs(ms, w.lam, f)
+        t1 = time.perf_counter()
+        v = local.apply_condensed(ms, w.lam, uB)
+        r = fh - 0.5 * v                      # CG vector work of one iteration
+        z = r * 1.0
+        _ = float(r @ z) + float(uB @ v)
+        uB2 = uB + 0.5 * z
+        t2 = time.perf_counter()
+        local.recover_interior(ms, w.lam, f, uB2)
+        t3 = time.perf_counter()
+        t_est = (t1 - t0, t2 - t1, t3 - t2)
+        total = sum(t_est)
+        if total * 2 > target_s or mz_s >= w.m[2]:
+            break
+        mz_s = min(w.m[2], max(mz_s + 1, int(mz_s * min(4.0, target_s / max(total, 1e-3) / 2))))
+    scale = w.m[2] / mz_s
+    t_full = scale * (t_est[0] + t_est[2] + iterations * t_est[1])
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": t_full / w.dofs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"NumPy FP64 oracle (element-local tier) on the {w.m[0]}x{w.m[1]}x{mz_s} slab of the "
+                       f"{w.m[0]}x{w.m[1]}x{w.m[2]} mesh: condensed load {t_est[0]:.2f}s, one CG iteration "
+                       f"{t_est[1]:.2f}s, recovery {t_est[2]:.2f}s; scaled x{scale:g} to the full mesh and to "
+                       f"{iterations} CG iterations"),
+            "sample_s": sum(t_est)}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def our_arm(args, rank, world, local_rank):
+    import torch
+
+    from paper_1601_08179_gb300 import build, sem
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    w = si.scale_workload(args.p, ar=args.ar, lam=args.lam)
+    seed = w.seed + 1000 * rank
+    hx, hy, hz = w.widths()
+    t0 = time.perf_counter()
+    ctx = sem.sem_setup(w.p, hx, hy, hz, w.lam)
+    setup_s = time.perf_counter() - t0
+    x, y, z = sem.sem_node_coords(ctx)
+    f_host = node_field(x, y, z, w, seed)
+    f = torch.from_numpy(f_host).cuda()
+    u = torch.empty_like(f)
+    sem.sem_profile_enable(ctx, True)
+    for _ in range(args.warmup):
+        sem.sem_solve(ctx, f, u)
+    sem.sem_profile_read(ctx, reset=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = sem.sem_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            infos.append(sem.sem_solve(ctx, f, u))
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = sem.sem_launch_count() - launches0
+    step_s = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    step_s = max_over_ranks(step_s, world)
+    apply_ms, apply_n = sem.sem_profile_read(ctx, reset=True)
+    apply_avg_s = apply_ms / 1e3 / max(apply_n, 1)
+
+    # end to end through the host-buffer entry point: H2D f, solve, D2H u
+    e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
+    e2e_s = None
+    if e2e_steps > 0:
+        f_pin = torch.from_numpy(f_host).pin_memory().numpy()
+        u_pin = torch.empty(f_host.size, dtype=torch.float64).pin_memory().numpy()
+        sem.sem_solve_host(ctx, f_pin, u_pin)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sem.sem_solve_host(ctx, f_pin, u_pin)
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+
+    iters = infos[-1]["iters"]
+    flops = apply_flops(w)
+    achieved = flops / apply_avg_s / 1e12
+    out = {
+        "metric": METRIC,
+        "value": step_s / (w.dofs * world),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_s * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "dofs_per_gpu": w.dofs,
+                   "skeleton_unknowns": ctx.nb, "lambda": w.lam, "aspect_ratio": w.ar, "rtol": 1e-10,
+                   "precision": "fp64", "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (solve working set > 129 MB)"},
+        "solve": {"iters": iters, "rel_res": infos[-1]["rel_res"], "setup_s": setup_s,
+                  "s_per_iteration": step_s / max(iters, 1)},
+        "operator": {"gdof_s": w.dofs / apply_avg_s / 1e9, "apply_ms": apply_avg_s * 1e3,
+                     "timed_launches": apply_n, "dtype": "f64"},
+        "roofline": {"kernel": "k_tpt_apply<double>", "bound": "alu", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_source": "FP64 FMA units x SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                     "flops_per_launch": flops},
+        "e2e": {"value": e2e_s / (w.dofs * world) if e2e_s else None, "unit": UNIT,
+                "h2d_bytes_per_step": f_host.nbytes, "d2h_bytes_per_step": f_host.nbytes},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ref_iters = reference_iterations(w)
+        out["cpu_baseline"] = oracle_sample(w, ref_iters if ref_iters is not None else iters)
+        if ref_iters is None:
+            out["cpu_baseline"]["sample"] += " (iteration count of this GPU solve; no oracle solve recorded)"
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def reference_iterations(w: si.Workload):
+    """CG iterations to 1e-10 of the oracle's own solve of this workload, as
+    recorded by `python -m oracle.reference_solve` (None if not recorded)."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{w.name}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return int(json.load(fh)["iterations_to_1e-10"])
+
+
+def reference_arm(args, rank, world):
+    """The oracle, timed as it stands on the host cores, per step one bounded
+    sample of the same workload, scaled by the iteration count of the
+    oracle's own full solve of this workload (tests/golden)."""
+    if rank != 0:
+        return
+    w = si.scale_workload(args.p, ar=args.ar, lam=args.lam)
+    iters = reference_iterations(w)
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no oracle solve recorded for {w.name}; "
+                          f"run python -m oracle.reference_solve {w.p}"}), flush=True)
+        return
+    samples = []
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample(w, iters, target_s=6.0)
+        if i >= args.warmup:
+            samples.append(s)
+    v = statistics.median(s["value"] for s in samples)
+    last = samples[-1]
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": statistics.median(s["sample_s"] for s in samples) * 1e3,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "dofs_per_gpu": w.dofs,
+                      "lambda": w.lam, "aspect_ratio": w.ar, "rtol": 1e-10, "precision": "fp64"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_setup()
+    try:
+        if args.impl == "reference":
+            reference_arm(args, rank, world)
+        else:
+            our_arm(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * sem.h -- C ABI of the GB300 (sm_103a) statically condensed spectral-element
+ * Helmholtz solver.
+ *
+ * Problem (Sec. 3, Eq. helmholtz_equation):  lambda u - Laplace u = f on the box
+ * [0, sum hx] x [0, sum hy] x [0, sum hz], lambda >= 0, homogeneous Dirichlet
+ * boundary values, discretised by a Cartesian mesh of mx * my * mz hexahedral
+ * spectral elements of degree p on Gauss-Lobatto-Legendre (GLL) nodes.  Element
+ * (ex, ey, ez) has widths (hx[ex], hy[ey], hz[ez]).
+ *
+ * The library applies the statically condensed operator
+ *     Hhat = H_BB - H_BI H_II^-1 H_IB          (Sec. 4, Eq. condensation_system)
+ * element by element in the transformed, factorised form of Sec. 6 (Table 2 and
+ * Eq. east_east_primary_part_transformed), inside a conjugate-gradient solver
+ * with the block preconditioner that is diagonal in the transformed system
+ * (solver "BT", Sec. 8), and recovers the interior unknowns by fast
+ * diagonalisation (Algorithm 4).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * n = p - 1.  Global nodes form the grid Nx x Ny x Nz with Nx = mx p + 1 (etc.);
+ * a "full nodal field" is a double array of Nx*Ny*Nz values, x fastest:
+ * index gx + Nx (gy + Ny gz).
+ *
+ * A "skeleton vector" holds one value per node on element boundaries, packed
+ * entity by entity (length N_B from sem_skeleton_size):
+ *   1. x-faces (f, ey, ez), f in 0..mx: (mx+1) my mz faces, n*n values each,
+ *      local (j, k) in 1..n, j fastest; node (f p, ey p + j, ez p + k)
+ *   2. y-faces (ex, f, ez): mx (my+1) mz faces, local (i, k), i fastest
+ *   3. z-faces (ex, ey, f): mx my (mz+1) faces, local (i, j), i fastest
+ *   4. x-edges (ex, vy, vz): mx (my+1)(mz+1) edges, n values, local i
+ *   5. y-edges (vx, ey, vz): (mx+1) my (mz+1) edges, local j
+ *   6. z-edges (vx, vy, ez): (mx+1)(my+1) mz edges, local k
+ *   7. vertices (vx, vy, vz): (mx+1)(my+1)(mz+1)
+ * Within each block the first entity index is fastest.  Entities on the domain
+ * boundary are present and held at zero: inputs there are ignored, outputs
+ * there are written as zero.
+ *
+ * Spaces (sem_space): NODAL skeleton vectors are nodal values (or, for loads
+ * and residuals, nodal load vectors).  TRANSFORMED vectors are those of Sec. 6:
+ * with S_II from the generalised eigenproblem K_II V = M_II V Lambda,
+ * V^T M_II V = I, S_II = V^T (eigenvalues ascending, each column of V scaled so
+ * that its first entry is positive), a solution-like vector transforms as
+ * u~ = T^-T u and a load-like vector as F~ = T F, where T applies S_II (x) S_II to
+ * every face, S_II to every edge and 1 to every vertex.
+ *
+ * Memory and ownership: every vector argument is a caller-owned DEVICE pointer
+ * (CUDA global memory of the current device), 8-byte aligned, unless the name
+ * says host.  The library never frees caller memory.  A context owns its
+ * precomputed tables and solver scratch on the device it was created on.  A
+ * context is not thread-safe: use one context per host thread.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Operator, load and recovery calls are asynchronous on that stream.  sem_solve
+ * returns after the solution is written (it synchronises to read its
+ * convergence state).
+ *
+ * Errors: no exception crosses the ABI.  Arguments are checked before any
+ * launch (SEM_EINVAL); CUDA failures return SEM_ECUDA; sem_last_error() gives
+ * a human-readable message for the calling thread's last failure.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sem_ctx sem_ctx;
+
+typedef enum {
+  SEM_OK = 0,
+  SEM_EINVAL = 1,     /* invalid argument (checked before any launch) */
+  SEM_ENOMEM = 2,     /* device or host allocation failed */
+  SEM_ECUDA = 3,      /* a CUDA call or kernel launch failed */
+  SEM_ENOCONV = 4,    /* solver hit maxit; the best iterate is still written */
+  SEM_EBREAKDOWN = 5, /* CG breakdown: p^T A p <= 0 or not finite (e.g. NaN input) */
+  SEM_ENOTSUP = 6     /* option not supported by this build */
+} sem_status;
+
+typedef enum { SEM_SPACE_NODAL = 0, SEM_SPACE_TRANSFORMED = 1 } sem_space;
+
+typedef enum {
+  SEM_PREC_FP64 = 0,  /* FP64 everywhere */
+  SEM_PREC_MIXED = 1  /* FP32 inner CG inside FP64 iterative refinement */
+} sem_precision;
+
+/* Solver options.  Fill with sem_default_opts before changing fields. */
+typedef struct {
+  double rtol;        /* stop when ||r||_2 <= rtol ||b||_2 in the transformed
+                         condensed space, b the condensed load (= ||r_0||_2 for a
+                         zero start) (default 1e-10) */
+  int maxit;          /* CG iteration cap, all refinement steps together (default 50000) */
+  int precision;      /* sem_precision (default SEM_PREC_FP64) */
+  int check_every;    /* CG iterations per device-side batch between host
+                         convergence checks (default 16) */
+  double inner_rtol;  /* MIXED: residual reduction of each FP32 inner solve (default 1e-4) */
+  int max_refine;     /* MIXED: cap on FP64 refinement steps (default 40) */
+} sem_opts;
+
+/* Result of a solve. */
+typedef struct {
+  int iters;          /* CG iterations (sum over refinement steps for MIXED) */
+  int refinements;    /* FP64 refinement steps (MIXED), 0 for FP64 */
+  double rel_res;     /* final ||r||_2 / ||b||_2, FP64, transformed condensed space */
+  double t_solve_s;   /* wall time of the solve, host clock, seconds */
+} sem_info;
+
+/* Fills *opts with the defaults listed above. */
+void sem_default_opts(sem_opts* opts);
+
+/* Creates a context (Sec. 3 problem statement; setup of Sec. 5-6 and the
+ * diagonal of the transformed condensed operator, Sec. 8).
+ *   p in [2, 32]; mx, my, mz >= 1; hx[mx], hy[my], hz[mz]: HOST arrays of
+ *   positive finite element widths; lambda >= 0 and finite; opts may be NULL.
+ * Computes on the host the 1D GLL basis, the generalised eigenpairs and the
+ * transformed stiffness vectors, then on the device per element-width class
+ * the metric coefficients (Eq. metriccoeffelement), D^-1 (Eq. hii_diagonal)
+ * and the diagonal preconditioner.  Allocates all device scratch.  On success
+ * *out owns everything; release it with sem_destroy.  Uses the current CUDA
+ * device; synchronises before returning. */
+sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz,
+                     const double* hx, const double* hy, const double* hz,
+                     double lambda, const sem_opts* opts);
+
+/* Changes lambda (the paper's time-step dependent Helmholtz parameter, Sec. 8)
+ * and recomputes D^-1 and the preconditioner.  Synchronous. */
+sem_status sem_set_lambda(sem_ctx* ctx, double lambda);
+
+/* Replaces the solver options of an existing context (NULL = defaults). */
+sem_status sem_set_opts(sem_ctx* ctx, const sem_opts* opts);
+
+/* N_B, the packed skeleton length (see the layout above). */
+sem_status sem_skeleton_size(const sem_ctx* ctx, long long* nb);
+
+/* Number of global nodes Nx*Ny*Nz of a full nodal field. */
+sem_status sem_grid_size(const sem_ctx* ctx, long long* n_nodes);
+
+/* Global node coordinates along each axis, HOST arrays of length Nx, Ny, Nz
+ * (element offsets plus the GLL points mapped to each element). */
+sem_status sem_node_coords(const sem_ctx* ctx, double* x, double* y, double* z);
+
+/* 1D basis used by the context, HOST arrays: gll_x[p+1], gll_w[p+1],
+ * lambda_1d[n] (ascending) and V[n*n] row-major (V[r*n + c] = entry r of
+ * eigenvector c), canonical signs as described above.  Any pointer may be NULL. */
+sem_status sem_get_basis(const sem_ctx* ctx, double* gll_x, double* gll_w,
+                         double* lambda_1d, double* V);
+
+/* v_B = Rhat Hhat Rhat^T u_B on the skeleton (Sec. 4 operator, assembled).
+ * NODAL: u and v are nodal skeleton vectors (v is a load vector).
+ * TRANSFORMED: v~ = T Hhat T^T u~, the operator the CG iterates on.
+ * uB, vB: device, length N_B, must not overlap.  Asynchronous on stream. */
+sem_status sem_apply_condensed(sem_ctx* ctx, const double* uB, double* vB,
+                               sem_space space, void* stream);
+
+/* Condensed load fhat = sum_e Rhat_e (F_B - H_BI H_II^-1 F_I) (Algorithm 1,
+ * first loop; Algorithm 4 in the TRANSFORMED space), with F_e the GLL-quadrature
+ * load of the nodal field f: F_e = (h1 h2 h3 / 8) (w (x) w (x) w) o f_e.
+ * f: device full nodal field; fB: device skeleton vector.  Asynchronous. */
+sem_status sem_condense_rhs(sem_ctx* ctx, const double* f, double* fB,
+                            sem_space space, void* stream);
+
+/* Diagonal of the assembled transformed condensed operator T Hhat T^T (the
+ * BT preconditioner is its inverse, Sec. 8).  diag: device skeleton vector;
+ * Dirichlet entries are written as zero.  Asynchronous. */
+sem_status sem_precond_diag(sem_ctx* ctx, double* diag, void* stream);
+
+/* Interior recovery (Algorithm 4, second loop): u_I = H_II^-1 (F_I - H_IB u_B)
+ * per element, back-transformed, written with the skeleton values into the
+ * full nodal field u.  uB is a skeleton solution in `space`.  f, u: device full
+ * nodal fields (u is fully overwritten, Dirichlet nodes with 0).  Asynchronous. */
+sem_status sem_recover_interior(sem_ctx* ctx, const double* f, const double* uB,
+                                sem_space space, double* u, void* stream);
+
+/* Full solve (Algorithm 4): condense the load, CG with the BT preconditioner
+ * to opts.rtol, recover the interior.  f, u: device full nodal fields; u0:
+ * optional device skeleton start vector in NODAL space (NULL = 0); info may be
+ * NULL.  Returns SEM_ENOCONV / SEM_EBREAKDOWN with u still written. */
+sem_status sem_solve(sem_ctx* ctx, const double* f, double* u, const double* u0,
+                     sem_info* info, void* stream);
+
+/* sem_solve on HOST arrays f_host, u_host (full nodal fields): copies f to the
+ * device, solves, copies u back, all on `stream`; returns when u_host is
+ * written.  Pinned host memory gives the fastest copies. */
+sem_status sem_solve_host(sem_ctx* ctx, const double* f_host, double* u_host,
+                          sem_info* info, void* stream);
+
+/* Transform of a skeleton vector between spaces (see "Spaces" above):
+ * kind 0: u~ = T^-T u (solution, nodal -> transformed)
+ * kind 1: u  = T^T u~ (solution, transformed -> nodal)
+ * kind 2: F~ = T F    (load, nodal -> transformed)
+ * kind 3: F  = T^-1 F~ (load, transformed -> nodal)
+ * in, out: device, length N_B, may alias.  Asynchronous. */
+sem_status sem_transform_skeleton(sem_ctx* ctx, const double* in, double* out,
+                                  int kind, void* stream);
+
+/* Skeleton <-> full nodal field: pack gathers the skeleton nodes of u_full into
+ * uB; unpack writes uB into the skeleton nodes of u_full (other nodes are left
+ * untouched).  Device pointers.  Asynchronous. */
+sem_status sem_pack_skeleton(sem_ctx* ctx, const double* u_full, double* uB, void* stream);
+sem_status sem_unpack_skeleton(sem_ctx* ctx, const double* uB, double* u_full, void* stream);
+
+/* Kernel timing inside sem_solve.  While enabled, every launch of the condensed
+ * operator kernel inside the solver's CG iteration is bracketed by CUDA events
+ * on the stream it runs on; sem_profile_read returns the summed device time
+ * (milliseconds) and the number of timed launches since the last reset.
+ * Enabling or disabling rebuilds the captured iteration graph. */
+sem_status sem_profile_enable(sem_ctx* ctx, int enable);
+sem_status sem_profile_read(sem_ctx* ctx, double* apply_ms, long long* apply_launches, int reset);
+
+/* Number of kernel launches this library has issued in this process (graph
+ * launches count each kernel node).  Monotone. */
+long long sem_launch_count(void);
+
+/* Releases every device and host resource of the context (NULL is a no-op). */
+void sem_destroy(sem_ctx* ctx);
+
+/* Static description of a status code. */
+const char* sem_status_string(sem_status s);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* sem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

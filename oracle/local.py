@@ -175,3 +175,48 @@ def rhs_full(mesh: Mesh, f_full: np.ndarray) -> np.ndarray:
         vg += np.bincount(g.ravel(), weights=_local_rhs(mesh, f_full, g, ex, ey, ez).ravel(),
                           minlength=mesh.n_global)
     return vg
+
+
+def transformed_diagonal(mesh: Mesh, lam: float, chunk_probes: int = 2048) -> np.ndarray:
+    """Diagonal of the assembled transformed condensed operator T Ahat T^T.
+
+    The diagonal of a sum is the sum of the element diagonals.  For an element
+    and a boundary node b, the element entry is psi_b^T Hhat_e psi_b with
+    psi_b = T_e^T e_b, which is supported on b's entity: an outer product of
+    two eigenvectors on a face, one eigenvector on an edge, a unit value at a
+    vertex.  Elements of equal widths share their diagonal, so each width
+    class is probed once, then the class diagonals are scatter-added.
+    """
+    p, q = mesh.p, mesh.p + 1
+    _, V = eigenbasis(p)
+    S = np.eye(q)
+    S[1:p, 1:p] = V.T                               # S = diag(1, S_II, 1)
+    c, b, a = np.meshgrid(np.arange(q), np.arange(q), np.arange(q), indexing="ij")
+    inner = ((a > 0) & (a < p) & (b > 0) & (b < p) & (c > 0) & (c < p)).ravel()
+    bidx = np.flatnonzero(~inner)
+    ab, bb, cb = a.ravel()[bidx], b.ravel()[bidx], c.ravel()[bidx]
+    widths = mesh.elem_widths
+    keys, inv = np.unique(widths, axis=0, return_inverse=True)
+    inv = inv.ravel()
+    dclass = np.zeros((len(keys), len(bidx)))
+    for ci, h in enumerate(keys):
+        d = metric(h[0], h[1], h[2], lam)[None, :]
+        for s0 in range(0, len(bidx), chunk_probes):
+            sel = slice(s0, min(len(bidx), s0 + chunk_probes))
+            P = len(bidx[sel])
+            # psi = (S^T (x) S^T (x) S^T) e_b: row b of S in every direction
+            psi = (S[cb[sel]][:, :, None, None] * S[bb[sel]][:, None, :, None]
+                   * S[ab[sel]][:, None, None, :])
+            dd = np.repeat(d, P, axis=0)
+            Y = H_apply(p, dd, psi)
+            Z = np.zeros_like(psi)
+            Z[:, 1:-1, 1:-1, 1:-1] = HII_solve(p, dd, _interior(Y))
+            out = _zero_interior(Y - H_apply(p, dd, Z))
+            dclass[ci, sel] = np.einsum("pcba,pcba->p", psi, out)
+    diag = np.zeros(mesh.n_global)
+    slot_vals = dclass[inv]                                   # (n_e, n_boundary)
+    for e0, e1 in _chunks(mesh):
+        g, _, _, _ = _l2g(mesh, e0, e1)
+        gb = g.reshape(e1 - e0, -1)[:, bidx]
+        diag += np.bincount(gb.ravel(), weights=slot_vals[e0:e1].ravel(), minlength=mesh.n_global)
+    return np.where(mesh.skeleton_free, diag[mesh.pack_map], 0.0)

@@ -10,7 +10,7 @@ from __future__ import annotations
 import numpy as np
 
 
-def pcg(apply, b, pdiag=None, rtol=1e-10, maxit=100000, x0=None):
+def pcg(apply, b, pdiag=None, rtol=1e-10, maxit=100000, x0=None, callback=None):
     """Solve A x = b.  ``apply(v)`` returns A v; ``pdiag`` is the diagonal of
     the preconditioner P ~ A^-1 (None: unpreconditioned).
 
@@ -37,6 +37,8 @@ def pcg(apply, b, pdiag=None, rtol=1e-10, maxit=100000, x0=None):
         it += 1
         rel = float(np.linalg.norm(r)) / r0
         hist.append(rel)
+        if callback is not None:
+            callback(it, rel)
         if rel <= rtol:
             break
         z = r * pdiag if pdiag is not None else r

@@ -1,0 +1,690 @@
+// C ABI of the condensed spectral-element Helmholtz library (include/sem.h).
+//
+// The context owns: the 1D basis (host), per-width-class tables (device),
+// transform matrices, the BT preconditioner, CG vectors and scratch.  The
+// FP64 solve follows Algorithm 4 of the paper:
+//   1. transformed condensed load  fhat~ = T F_B - H~_BI D^-1 F~_I
+//   2. CG on Hhat~ with the diagonal (block-Jacobi) preconditioner, batches of
+//      iterations captured in a CUDA graph; the convergence test runs on the
+//      device and the host reads one small status record per batch;
+//   3. interior recovery u_I = (V(x)V(x)V) D^-1 (F~_I - H~_IB u~_B) and the
+//      nodal skeleton u_B = T^T u~_B.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sem.h"
+#include "sem_internal.h"
+#include "sem_kernels.cuh"
+
+namespace {
+
+thread_local std::string t_err;
+
+sem_status fail(sem_status s, const std::string& msg) {
+  t_err = msg;
+  return s;
+}
+
+#define SEM_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (call);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return fail(SEM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));       \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+}  // namespace
+
+struct sem_ctx {
+  int device = 0;
+  SemGeom g{};
+  SemHost1D h1;
+  double lambda = 0.0;
+  sem_opts opts{};
+  std::vector<double> hx, hy, hz;
+  std::vector<double> uxw, uyw, uzw;
+  std::vector<int> clsx, clsy, clsz;
+  std::vector<double> xc, yc, zc;      // node coordinates per axis
+
+  int* d_cls = nullptr;                // [mx + my + mz]
+  double* d_uw = nullptr;              // [ux + uy + uz] distinct widths
+  double* d_dcoef = nullptr;
+  double* d_dinv = nullptr;
+  double* d_mats = nullptr;            // 4 n*n: S_II, V, V^T M_II, M_II V
+  double* d_mass = nullptr;            // [Nx + Ny + Nz] assembled 1D lumped masses
+  double* d_P = nullptr;               // BT preconditioner (inverse diagonal)
+  double *d_x = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_b = nullptr;
+  double *d_t1 = nullptr, *d_t2 = nullptr;
+  double *d_c0 = nullptr, *d_c1 = nullptr, *d_FtI = nullptr;   // interior cubes
+  double* d_partials = nullptr;
+  PcgState* d_st = nullptr;
+  PcgState* h_st = nullptr;            // pinned
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  bool graph_prof = false;
+  bool prof = false;                   // time operator launches inside the CG graph
+  std::vector<cudaEvent_t> pev;        // 2 per captured iteration
+  double prof_ms = 0.0;
+  long long prof_count = 0;
+  SemClassTables<double> tab{};
+
+  const double* mat(int k) const { return d_mats + (size_t)k * g.n * g.n; }
+};
+
+namespace {
+
+constexpr size_t kPartials = 1 << 17;
+
+void build_classes(const std::vector<double>& h, std::vector<double>* uw, std::vector<int>* cls) {
+  std::map<double, int> seen;
+  cls->resize(h.size());
+  uw->clear();
+  for (size_t i = 0; i < h.size(); ++i) {
+    auto it = seen.find(h[i]);
+    if (it == seen.end()) {
+      int id = (int)uw->size();
+      seen[h[i]] = id;
+      uw->push_back(h[i]);
+      (*cls)[i] = id;
+    } else {
+      (*cls)[i] = it->second;
+    }
+  }
+}
+
+// 1D assembled lumped mass: m[e p + a] += (h_e / 2) w_a; node coordinates.
+void axis_mass_coords(int p, const std::vector<double>& h, const std::vector<double>& xg,
+                      const std::vector<double>& w, std::vector<double>* m, std::vector<double>* x) {
+  const size_t N = h.size() * p + 1;
+  m->assign(N, 0.0);
+  x->assign(N, 0.0);
+  double X0 = 0.0;
+  for (size_t e = 0; e < h.size(); ++e) {
+    for (int a = 0; a <= p; ++a) {
+      (*m)[e * p + a] += 0.5 * h[e] * w[a];
+      if (a < p) (*x)[e * p + a] = X0 + 0.5 * h[e] * (xg[a] + 1.0);
+    }
+    X0 += h[e];
+  }
+  (*x)[N - 1] = X0;
+}
+
+bool valid_widths(const double* h, int m) {
+  if (h == nullptr) return false;
+  for (int i = 0; i < m; ++i)
+    if (!(h[i] > 0.0) || !std::isfinite(h[i])) return false;
+  return true;
+}
+
+sem_status compute_tables(sem_ctx* c, cudaStream_t s) {
+  const SemGeom& g = c->g;
+  launch_class_tables(g, c->h1.basis, c->d_uw, c->d_uw + g.ux, c->d_uw + g.ux + g.uy, c->lambda, c->d_dcoef,
+                      c->d_dinv, s);
+  SEM_CUDA(cudaGetLastError());
+  SEM_CUDA(cudaMemsetAsync(c->d_t1, 0, sizeof(double) * g.nb, s));
+  launch_precond_diag(g, c->h1.basis, c->tab, c->d_t1, s);
+  launch_invert_diag(g, c->d_t1, c->d_P, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status ensure_cubes(sem_ctx* c) {
+  if (c->d_c0 != nullptr) return SEM_OK;
+  const size_t n3 = (size_t)c->g.nelem * c->g.n * c->g.n * c->g.n;
+  if (dalloc(&c->d_c0, n3) != cudaSuccess || dalloc(&c->d_c1, n3) != cudaSuccess ||
+      dalloc(&c->d_FtI, n3) != cudaSuccess)
+    return fail(SEM_ENOMEM, "cannot allocate element interior scratch");
+  return SEM_OK;
+}
+
+// fhat~ into out (transformed).  Leaves F~_I in d_FtI for the recovery.
+sem_status condense_rhs_t(sem_ctx* c, const double* f, double* out, cudaStream_t s) {
+  sem_status st = ensure_cubes(c);
+  if (st != SEM_OK) return st;
+  const SemGeom& g = c->g;
+  const double *mx = c->d_mass, *my = mx + g.Nx, *mz = my + g.Ny;
+  launch_load_skeleton(g, mx, my, mz, f, c->d_t1, s);
+  launch_skel_transform(g, c->mat(0), c->d_t1, out, s);
+  launch_interior_load(g, mx, my, mz, f, c->d_c0, s);
+  launch_mode(g, c->mat(0), 0, c->d_c0, c->d_c1, nullptr, s);
+  launch_mode(g, c->mat(0), 1, c->d_c1, c->d_c0, nullptr, s);
+  launch_mode(g, c->mat(0), 2, c->d_c0, c->d_FtI, nullptr, s);
+  launch_condense_faces(g, c->h1.basis, c->tab, c->d_FtI, out, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+// Interior recovery from a transformed skeleton solution ut; d_FtI must hold F~_I.
+sem_status recover_t(sem_ctx* c, const double* ut, double* u, cudaStream_t s) {
+  const SemGeom& g = c->g;
+  launch_recover_expand(g, c->h1.basis, c->tab, c->d_FtI, ut, c->d_c0, s);
+  launch_mode(g, c->mat(1), 0, c->d_c0, c->d_c1, nullptr, s);
+  launch_mode(g, c->mat(1), 1, c->d_c1, c->d_c0, nullptr, s);
+  launch_mode(g, c->mat(1), 2, c->d_c0, nullptr, u, s);
+  launch_skel_transform(g, c->mat(1), ut, c->d_t2, s);
+  launch_unpack(g, c->d_t2, u, 1, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
+  SEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * c->g.nb, s));
+  launch_tpt_apply_f64(c->g, c->h1.basis, c->tab, x, y, nullptr, nullptr, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status build_graph(sem_ctx* c) {
+  if (c->graph != nullptr && c->graph_iters == c->opts.check_every && c->graph_prof == c->prof) return SEM_OK;
+  if (c->prof && (int)c->pev.size() < 2 * c->opts.check_every) {
+    while ((int)c->pev.size() < 2 * c->opts.check_every) {
+      cudaEvent_t ev;
+      SEM_CUDA(cudaEventCreate(&ev));
+      c->pev.push_back(ev);
+    }
+  }
+  if (c->graph != nullptr) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  const SemGeom& g = c->g;
+  cudaGraph_t graph;
+  SEM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  const long long before = sem_launch_total();
+  for (int it = 0; it < c->opts.check_every; ++it) {
+    // external event-record nodes: recorded at every replay, usable for timing
+    if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it], c->stream, cudaEventRecordExternal);
+    launch_tpt_apply_f64(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, c->stream);
+    if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it + 1], c->stream, cudaEventRecordExternal);
+    launch_pcg_update(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, c->stream);
+    launch_pcg_dir(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, c->stream);
+  }
+  sem_count_launch(-(sem_launch_total() - before));   // counted at replay instead
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  c->graph_iters = c->opts.check_every;
+  c->graph_prof = c->prof;
+  return SEM_OK;
+}
+
+// CG on the transformed condensed system: d_b -> d_x.  warm: d_x holds x0.
+sem_status pcg_fp64(sem_ctx* c, bool warm, sem_info* info) {
+  const SemGeom& g = c->g;
+  cudaStream_t s = c->stream;
+  if (warm) {
+    sem_status st = apply_t(c, c->d_x, c->d_q, s);
+    if (st != SEM_OK) return st;
+  }
+  launch_pcg_init(g.nb, c->d_b, c->d_r, c->d_p, c->d_q, c->d_x, c->d_P, c->d_partials, c->d_st, c->opts.rtol,
+                  c->opts.maxit, warm ? 1 : 0, s);
+  SEM_CUDA(cudaGetLastError());
+  sem_status st = build_graph(c);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  const int max_batches = c->opts.maxit / c->opts.check_every + 2;
+  for (int b = 0; b < max_batches && c->h_st->done == 0; ++b) {
+    const int it0 = c->h_st->iter;
+    SEM_CUDA(cudaGraphLaunch(c->graph, s));
+    sem_count_launch(3LL * c->graph_iters);
+    SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    if (c->graph_prof) {
+      // operator launches that did work in this batch (later ones exit at once)
+      int worked = c->h_st->iter - it0 + (c->h_st->done == 2 ? 1 : 0);
+      if (worked > c->graph_iters) worked = c->graph_iters;
+      for (int it = 0; it < worked; ++it) {
+        float ms = 0.f;
+        SEM_CUDA(cudaEventElapsedTime(&ms, c->pev[2 * it], c->pev[2 * it + 1]));
+        c->prof_ms += ms;
+        c->prof_count += 1;
+      }
+    }
+  }
+  const PcgState& h = *c->h_st;
+  if (info) {
+    info->iters += h.iter;
+    info->rel_res = h.rr0 > 0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+  }
+  if (h.done == 2) return fail(SEM_EBREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite values)");
+  if (h.done != 1) return fail(SEM_ENOCONV, "CG reached maxit without meeting rtol");
+  return SEM_OK;
+}
+
+void free_ctx(sem_ctx* c) {
+  if (c == nullptr) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  void* ptrs[] = {c->d_cls, c->d_uw, c->d_dcoef, c->d_dinv, c->d_mats, c->d_mass, c->d_P, c->d_x, c->d_r,
+                  c->d_p, c->d_q, c->d_b, c->d_t1, c->d_t2, c->d_c0, c->d_c1, c->d_FtI, c->d_partials, c->d_st};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  for (cudaEvent_t ev : c->pev) cudaEventDestroy(ev);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  cudaSetDevice(prev);
+  delete c;
+}
+
+sem_status check_ctx(const sem_ctx* c) {
+  if (c == nullptr) return fail(SEM_EINVAL, "null context");
+  return SEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sem_default_opts(sem_opts* o) {
+  if (o == nullptr) return;
+  o->rtol = 1e-10;
+  o->maxit = 50000;
+  o->precision = SEM_PREC_FP64;
+  o->check_every = 16;
+  o->inner_rtol = 1e-4;
+  o->max_refine = 40;
+}
+
+static sem_status check_opts(const sem_opts* o) {
+  if (!(o->rtol > 0.0 && o->rtol < 1.0)) return fail(SEM_EINVAL, "rtol must be in (0, 1)");
+  if (o->maxit < 1) return fail(SEM_EINVAL, "maxit must be >= 1");
+  if (o->check_every < 1 || o->check_every > 1024) return fail(SEM_EINVAL, "check_every must be in [1, 1024]");
+  if (o->precision != SEM_PREC_FP64 && o->precision != SEM_PREC_MIXED) return fail(SEM_EINVAL, "unknown precision");
+  if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0)) return fail(SEM_EINVAL, "inner_rtol must be in (0, 1)");
+  if (o->max_refine < 1) return fail(SEM_EINVAL, "max_refine must be >= 1");
+  return SEM_OK;
+}
+
+sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double* hx, const double* hy,
+                     const double* hz, double lambda, const sem_opts* opts) {
+  t_err.clear();
+  if (out == nullptr) return fail(SEM_EINVAL, "out is null");
+  *out = nullptr;
+  if (p < 2 || p > 32) return fail(SEM_EINVAL, "p must be in [2, 32]");
+  if (mx < 1 || my < 1 || mz < 1) return fail(SEM_EINVAL, "element counts must be >= 1");
+  if (!valid_widths(hx, mx) || !valid_widths(hy, my) || !valid_widths(hz, mz))
+    return fail(SEM_EINVAL, "element widths must be positive and finite");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(SEM_EINVAL, "lambda must be finite and >= 0");
+  sem_opts o;
+  sem_default_opts(&o);
+  if (opts) o = *opts;
+  sem_status vs = check_opts(&o);
+  if (vs != SEM_OK) return vs;
+
+  sem_ctx* c = new sem_ctx();
+  cudaGetDevice(&c->device);
+  c->opts = o;
+  c->lambda = lambda;
+  std::string err;
+  if (!sem_build_1d(p, &c->h1, &err)) {
+    delete c;
+    return fail(SEM_EINVAL, err);
+  }
+  c->hx.assign(hx, hx + mx);
+  c->hy.assign(hy, hy + my);
+  c->hz.assign(hz, hz + mz);
+  build_classes(c->hx, &c->uxw, &c->clsx);
+  build_classes(c->hy, &c->uyw, &c->clsy);
+  build_classes(c->hz, &c->uzw, &c->clsz);
+  SemGeom& g = c->g;
+  const int n = p - 1;
+  g.p = p;
+  g.n = n;
+  g.mx = mx;
+  g.my = my;
+  g.mz = mz;
+  g.ux = (int)c->uxw.size();
+  g.uy = (int)c->uyw.size();
+  g.uz = (int)c->uzw.size();
+  g.nelem = (long long)mx * my * mz;
+  const long long n2 = (long long)n * n;
+  const long long cnt[7] = {(long long)(mx + 1) * my * mz * n2,       (long long)mx * (my + 1) * mz * n2,
+                            (long long)mx * my * (mz + 1) * n2,       (long long)mx * (my + 1) * (mz + 1) * n,
+                            (long long)(mx + 1) * my * (mz + 1) * n,  (long long)(mx + 1) * (my + 1) * mz * n,
+                            (long long)(mx + 1) * (my + 1) * (mz + 1)};
+  g.off[0] = 0;
+  for (int b = 0; b < 7; ++b) g.off[b + 1] = g.off[b] + cnt[b];
+  g.nb = g.off[7];
+  g.Nx = (long long)mx * p + 1;
+  g.Ny = (long long)my * p + 1;
+  g.Nz = (long long)mz * p + 1;
+
+  std::vector<double> mass, mxv, myv, mzv;
+  axis_mass_coords(p, c->hx, c->h1.x, c->h1.w, &mxv, &c->xc);
+  axis_mass_coords(p, c->hy, c->h1.x, c->h1.w, &myv, &c->yc);
+  axis_mass_coords(p, c->hz, c->h1.x, c->h1.w, &mzv, &c->zc);
+  mass.insert(mass.end(), mxv.begin(), mxv.end());
+  mass.insert(mass.end(), myv.begin(), myv.end());
+  mass.insert(mass.end(), mzv.begin(), mzv.end());
+
+  // transform matrices, row-major n x n
+  std::vector<double> mats(4 * n2);
+  const std::vector<double>& V = c->h1.V;
+  for (int r = 0; r < n; ++r)
+    for (int q = 0; q < n; ++q) {
+      mats[0 * n2 + r * n + q] = V[q * n + r];                      // S_II = V^T
+      mats[1 * n2 + r * n + q] = V[r * n + q];                      // V
+      mats[2 * n2 + r * n + q] = V[q * n + r] * c->h1.w[q + 1];     // S_II^-T = V^T M_II
+      mats[3 * n2 + r * n + q] = c->h1.w[r + 1] * V[r * n + q];     // S_II^-1 = M_II V
+    }
+
+  const long long ncls = (long long)g.ux * g.uy * g.uz;
+  std::vector<int> cls;
+  cls.insert(cls.end(), c->clsx.begin(), c->clsx.end());
+  cls.insert(cls.end(), c->clsy.begin(), c->clsy.end());
+  cls.insert(cls.end(), c->clsz.begin(), c->clsz.end());
+  std::vector<double> uw;
+  uw.insert(uw.end(), c->uxw.begin(), c->uxw.end());
+  uw.insert(uw.end(), c->uyw.begin(), c->uyw.end());
+  uw.insert(uw.end(), c->uzw.begin(), c->uzw.end());
+
+  bool ok = dalloc(&c->d_cls, cls.size()) == cudaSuccess && dalloc(&c->d_uw, uw.size()) == cudaSuccess &&
+            dalloc(&c->d_dcoef, ncls * 4) == cudaSuccess && dalloc(&c->d_dinv, ncls * n2 * n) == cudaSuccess &&
+            dalloc(&c->d_mats, mats.size()) == cudaSuccess && dalloc(&c->d_mass, mass.size()) == cudaSuccess &&
+            dalloc(&c->d_P, g.nb) == cudaSuccess && dalloc(&c->d_x, g.nb) == cudaSuccess &&
+            dalloc(&c->d_r, g.nb) == cudaSuccess && dalloc(&c->d_p, g.nb) == cudaSuccess &&
+            dalloc(&c->d_q, g.nb) == cudaSuccess && dalloc(&c->d_b, g.nb) == cudaSuccess &&
+            dalloc(&c->d_t1, g.nb) == cudaSuccess && dalloc(&c->d_t2, g.nb) == cudaSuccess &&
+            dalloc(&c->d_partials, kPartials) == cudaSuccess && dalloc(&c->d_st, 1) == cudaSuccess &&
+            cudaMallocHost((void**)&c->h_st, sizeof(PcgState)) == cudaSuccess;
+  if (!ok) {
+    free_ctx(c);
+    return fail(SEM_ENOMEM, "device allocation failed in sem_setup");
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+  cudaStream_t s = c->stream;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cls, cls.data(), cls.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_uw, uw.data(), uw.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mats, mats.data(), mats.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mass, mass.data(), mass.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_st, 0, sizeof(PcgState), s);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return fail(SEM_ECUDA, std::string("sem_setup: ") + cudaGetErrorString(e));
+  }
+  c->tab.cls_x = c->d_cls;
+  c->tab.cls_y = c->d_cls + mx;
+  c->tab.cls_z = c->d_cls + mx + my;
+  c->tab.dcoef = c->d_dcoef;
+  c->tab.dinv = c->d_dinv;
+  sem_status st = compute_tables(c, s);
+  if (st == SEM_OK) {
+    // warm the operator kernel's attributes outside any graph capture
+    st = apply_t(c, c->d_P, c->d_t2, s);
+  }
+  if (st == SEM_OK) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = fail(SEM_ECUDA, std::string("sem_setup: ") + cudaGetErrorString(e));
+  }
+  if (st != SEM_OK) {
+    std::string keep = t_err;
+    free_ctx(c);
+    t_err = keep;
+    return st;
+  }
+  *out = c;
+  return SEM_OK;
+}
+
+sem_status sem_set_lambda(sem_ctx* c, double lambda) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(SEM_EINVAL, "lambda must be finite and >= 0");
+  c->lambda = lambda;
+  sem_status st = compute_tables(c, c->stream);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(cudaStreamSynchronize(c->stream));
+  return SEM_OK;
+}
+
+sem_status sem_set_opts(sem_ctx* c, const sem_opts* opts) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  sem_opts o;
+  sem_default_opts(&o);
+  if (opts) o = *opts;
+  sem_status vs = check_opts(&o);
+  if (vs != SEM_OK) return vs;
+  c->opts = o;
+  return SEM_OK;
+}
+
+sem_status sem_skeleton_size(const sem_ctx* c, long long* nb) {
+  if (c == nullptr || nb == nullptr) return fail(SEM_EINVAL, "null argument");
+  *nb = c->g.nb;
+  return SEM_OK;
+}
+
+sem_status sem_grid_size(const sem_ctx* c, long long* n) {
+  if (c == nullptr || n == nullptr) return fail(SEM_EINVAL, "null argument");
+  *n = c->g.Nx * c->g.Ny * c->g.Nz;
+  return SEM_OK;
+}
+
+sem_status sem_node_coords(const sem_ctx* c, double* x, double* y, double* z) {
+  if (c == nullptr || x == nullptr || y == nullptr || z == nullptr) return fail(SEM_EINVAL, "null argument");
+  std::memcpy(x, c->xc.data(), c->xc.size() * sizeof(double));
+  std::memcpy(y, c->yc.data(), c->yc.size() * sizeof(double));
+  std::memcpy(z, c->zc.data(), c->zc.size() * sizeof(double));
+  return SEM_OK;
+}
+
+sem_status sem_get_basis(const sem_ctx* c, double* gx, double* gw, double* lam, double* V) {
+  if (c == nullptr) return fail(SEM_EINVAL, "null context");
+  const SemHost1D& h = c->h1;
+  if (gx) std::memcpy(gx, h.x.data(), h.x.size() * sizeof(double));
+  if (gw) std::memcpy(gw, h.w.data(), h.w.size() * sizeof(double));
+  if (lam) std::memcpy(lam, h.lam.data(), h.lam.size() * sizeof(double));
+  if (V) std::memcpy(V, h.V.data(), h.V.size() * sizeof(double));
+  return SEM_OK;
+}
+
+sem_status sem_apply_condensed(sem_ctx* c, const double* uB, double* vB, sem_space space, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (uB == nullptr || vB == nullptr) return fail(SEM_EINVAL, "null vector");
+  if (uB == vB) return fail(SEM_EINVAL, "uB and vB must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (space == SEM_SPACE_TRANSFORMED) return apply_t(c, uB, vB, s);
+  if (space != SEM_SPACE_NODAL) return fail(SEM_EINVAL, "unknown space");
+  launch_skel_transform(c->g, c->mat(2), uB, c->d_t1, s);
+  sem_status st = apply_t(c, c->d_t1, c->d_t2, s);
+  if (st != SEM_OK) return st;
+  launch_skel_transform(c->g, c->mat(3), c->d_t2, vB, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status sem_condense_rhs(sem_ctx* c, const double* f, double* fB, sem_space space, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (f == nullptr || fB == nullptr) return fail(SEM_EINVAL, "null vector");
+  if (space != SEM_SPACE_NODAL && space != SEM_SPACE_TRANSFORMED) return fail(SEM_EINVAL, "unknown space");
+  cudaStream_t s = (cudaStream_t)stream;
+  sem_status st = condense_rhs_t(c, f, fB, s);
+  if (st != SEM_OK) return st;
+  if (space == SEM_SPACE_NODAL) {
+    launch_skel_transform(c->g, c->mat(3), fB, fB, s);
+    SEM_CUDA(cudaGetLastError());
+  }
+  return SEM_OK;
+}
+
+sem_status sem_precond_diag(sem_ctx* c, double* diag, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (diag == nullptr) return fail(SEM_EINVAL, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  SEM_CUDA(cudaMemsetAsync(diag, 0, sizeof(double) * c->g.nb, s));
+  launch_precond_diag(c->g, c->h1.basis, c->tab, diag, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status sem_recover_interior(sem_ctx* c, const double* f, const double* uB, sem_space space, double* u,
+                                void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (f == nullptr || uB == nullptr || u == nullptr) return fail(SEM_EINVAL, "null vector");
+  if (space != SEM_SPACE_NODAL && space != SEM_SPACE_TRANSFORMED) return fail(SEM_EINVAL, "unknown space");
+  cudaStream_t s = (cudaStream_t)stream;
+  // F~_I for this f (the condensed load itself is discarded)
+  sem_status st = condense_rhs_t(c, f, c->d_b, s);
+  if (st != SEM_OK) return st;
+  const double* ut = uB;
+  if (space == SEM_SPACE_NODAL) {
+    launch_skel_transform(c->g, c->mat(2), uB, c->d_x, s);
+    ut = c->d_x;
+  }
+  return recover_t(c, ut, u, s);
+}
+
+sem_status sem_solve(sem_ctx* c, const double* f, double* u, const double* u0, sem_info* info, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (f == nullptr || u == nullptr) return fail(SEM_EINVAL, "null vector");
+  if (c->opts.precision != SEM_PREC_FP64) return fail(SEM_ENOTSUP, "precision mode not available");
+  const auto t0 = std::chrono::steady_clock::now();
+  if (info) std::memset(info, 0, sizeof(*info));
+  cudaStream_t us = (cudaStream_t)stream;
+  SEM_CUDA(cudaEventRecord(c->ev_in, us));
+  SEM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  cudaStream_t s = c->stream;
+  sem_status st = condense_rhs_t(c, f, c->d_b, s);
+  if (st != SEM_OK) return st;
+  if (u0) launch_skel_transform(c->g, c->mat(2), u0, c->d_x, s);
+  sem_status cg = pcg_fp64(c, u0 != nullptr, info);
+  if (cg != SEM_OK && cg != SEM_ENOCONV && cg != SEM_EBREAKDOWN) return cg;
+  std::string cg_err = t_err;
+  st = recover_t(c, c->d_x, u, s);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(cudaEventRecord(c->ev_out, s));
+  SEM_CUDA(cudaStreamWaitEvent(us, c->ev_out, 0));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  if (info) info->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  t_err = cg_err;
+  return cg;
+}
+
+sem_status sem_solve_host(sem_ctx* c, const double* f_host, double* u_host, sem_info* info, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (f_host == nullptr || u_host == nullptr) return fail(SEM_EINVAL, "null vector");
+  const size_t bytes = sizeof(double) * (size_t)(c->g.Nx * c->g.Ny * c->g.Nz);
+  cudaStream_t us = (cudaStream_t)stream;
+  double *df = nullptr, *du = nullptr;
+  if (cudaMalloc((void**)&df, bytes) != cudaSuccess || cudaMalloc((void**)&du, bytes) != cudaSuccess) {
+    if (df) cudaFree(df);
+    return fail(SEM_ENOMEM, "cannot allocate device fields");
+  }
+  sem_status st = SEM_OK;
+  cudaError_t e = cudaMemcpyAsync(df, f_host, bytes, cudaMemcpyHostToDevice, us);
+  if (e != cudaSuccess) st = fail(SEM_ECUDA, cudaGetErrorString(e));
+  if (st == SEM_OK) st = sem_solve(c, df, du, nullptr, info, stream);
+  std::string keep = t_err;
+  if (st == SEM_OK || st == SEM_ENOCONV || st == SEM_EBREAKDOWN) {
+    e = cudaMemcpyAsync(u_host, du, bytes, cudaMemcpyDeviceToHost, us);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+    if (e != cudaSuccess) {
+      st = fail(SEM_ECUDA, cudaGetErrorString(e));
+      keep = t_err;
+    }
+  }
+  cudaFree(df);
+  cudaFree(du);
+  t_err = keep;
+  return st;
+}
+
+sem_status sem_transform_skeleton(sem_ctx* c, const double* in, double* out, int kind, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (in == nullptr || out == nullptr) return fail(SEM_EINVAL, "null vector");
+  if (kind < 0 || kind > 3) return fail(SEM_EINVAL, "kind must be 0..3");
+  static const int mat_of_kind[4] = {2, 1, 0, 3};
+  launch_skel_transform(c->g, c->mat(mat_of_kind[kind]), in, out, (cudaStream_t)stream);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status sem_pack_skeleton(sem_ctx* c, const double* u_full, double* uB, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (u_full == nullptr || uB == nullptr) return fail(SEM_EINVAL, "null vector");
+  launch_pack(c->g, u_full, uB, (cudaStream_t)stream);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status sem_unpack_skeleton(sem_ctx* c, const double* uB, double* u_full, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (u_full == nullptr || uB == nullptr) return fail(SEM_EINVAL, "null vector");
+  launch_unpack(c->g, uB, u_full, 0, (cudaStream_t)stream);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status sem_profile_enable(sem_ctx* c, int enable) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  c->prof = enable != 0;
+  return SEM_OK;
+}
+
+sem_status sem_profile_read(sem_ctx* c, double* apply_ms, long long* apply_launches, int reset) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (apply_ms) *apply_ms = c->prof_ms;
+  if (apply_launches) *apply_launches = c->prof_count;
+  if (reset) {
+    c->prof_ms = 0.0;
+    c->prof_count = 0;
+  }
+  return SEM_OK;
+}
+
+long long sem_launch_count(void) { return sem_launch_total(); }
+
+void sem_destroy(sem_ctx* c) { free_ctx(c); }
+
+const char* sem_status_string(sem_status s) {
+  switch (s) {
+    case SEM_OK: return "ok";
+    case SEM_EINVAL: return "invalid argument";
+    case SEM_ENOMEM: return "out of memory";
+    case SEM_ECUDA: return "CUDA error";
+    case SEM_ENOCONV: return "not converged";
+    case SEM_EBREAKDOWN: return "CG breakdown";
+    case SEM_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+const char* sem_last_error(void) { return t_err.c_str(); }
+
+}  // extern "C"

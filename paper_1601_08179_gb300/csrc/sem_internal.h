@@ -1,0 +1,77 @@
+// Internal declarations of the sm_103a condensed spectral-element library.
+// Shared by the host setup, the kernels and the C-ABI layer; not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#define SEM_MAXN 32   // interior nodes per direction, n = p - 1 <= 31
+
+// Geometry of the Cartesian mesh and the packed skeleton layout (see sem.h).
+struct SemGeom {
+  int p, n, mx, my, mz;
+  int ux, uy, uz;        // distinct element widths per axis (width classes)
+  long long nelem;
+  long long off[8];      // block offsets: xf, yf, zf, xe, ye, ze, v, end(=N_B)
+  long long nb;
+  long long Nx, Ny, Nz;  // global nodal grid
+};
+
+// Transformed 1D operators of Sec. 6 (passed by value to kernels).
+//  lam   : eigenvalues Lambda of (K_II, M_II), ascending
+//  k0, kp: K~_{I0} = S_II K_{I0}, K~_{Ip} = S_II K_{Ip}
+//  Kss   : K~ corner entries [0][0], [0][p], [p][0], [p][p]
+//  w0    : GLL end weight M_00 = M_pp
+struct SemBasis {
+  int n;
+  double w0;
+  double K[2][2];
+  double lam[SEM_MAXN];
+  double k[2][SEM_MAXN];
+};
+
+// Host-side 1D data computed at setup.
+struct SemHost1D {
+  int p;
+  std::vector<double> x, w;          // GLL nodes and weights (p+1)
+  std::vector<double> K;             // stiffness (p+1)^2 row-major
+  std::vector<double> lam;           // n
+  std::vector<double> V;             // n*n, V[r*n+c]: entry r of eigenvector c
+  SemBasis basis;
+};
+
+// Per-element-width-class tables on the device.
+template <typename T>
+struct SemClassTables {
+  const int* cls_x;   // [mx] class index of hx[ex]
+  const int* cls_y;   // [my]
+  const int* cls_z;   // [mz]
+  const T* dcoef;     // [ncls][4] metric coefficients d0..d3
+  const T* dinv;      // [ncls][n^3] D^-1, index (k n + j) n + i
+};
+
+// Device-resident CG scalars (one per solve in flight).
+struct PcgState {
+  double rho;        // r^T z of the current iterate
+  double rho_new;
+  double pq;         // p^T A p
+  double rr;         // r^T r
+  double rr0;        // b^T b, reference of the stopping rule
+  double alpha, beta;
+  double tol2;       // rtol^2 * rr0 (stop when rr <= tol2)
+  int iter;          // iterations done
+  int done;          // 1: converged, 2: breakdown, 3: maxit
+  int maxit;
+  int pad;
+  unsigned int counter[4];  // last-block reduction tickets
+};
+
+// ---- host helpers (sem_host.cpp) ----
+bool sem_build_1d(int p, SemHost1D* out, std::string* err);
+
+// ---- launch helpers (sem_kernels.cu) ----
+void sem_count_launch(long long k = 1);
+long long sem_launch_total();

@@ -1,0 +1,1048 @@
+// sm_103a kernels of the statically condensed spectral-element Helmholtz solver.
+//
+// The hot kernel is k_tpt_apply: the assembled transformed condensed operator
+//   v~ = sum_e Rhat_e (H~_BB - H~_BI D^-1 H~_IB) Rhat_e^T u~
+// evaluated element by element (Sec. 6):
+//   * condensed part, Table 2: expand the six faces into the interior
+//     eigenspace with d * K~_{I0} / K~_{Ip} (rank-1 per face and line), scale by
+//     D^-1 (Eq. hii_diagonal), contract back with d * K~_{0I} / K~_{pI};
+//     13 n^3 multiplications (Table 3);
+//   * primary part H~_BB: the restriction of
+//     H~ = d0 M~(x)M~(x)M~ + d1 M~(x)M~(x)K~ + d2 M~(x)K~(x)M~ + d3 K~(x)M~(x)M~
+//     to the skeleton, with M~ = diag(w0, I, w0) and K~ = S K S^T, whose face
+//     self-blocks are diagonal (Eq. east_east_primary_part_transformed); only
+//     1D lines that lie in a face or an edge couple different entities;
+//   * gather R^T and scatter-add R over faces (2 elements), edges (4) and
+//     vertices (8) with FP64 reductions in L2 (red.global.add.f64).
+// The per-element working set (faces, edges, vertices, a slab of the n^3
+// eigenspace cube) lives in shared memory; nothing per element touches HBM
+// except the skeleton values and the per-width-class D^-1 table (L2 resident).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+
+#include "sem_kernels.cuh"
+
+static std::atomic<long long> g_launches{0};
+void sem_count_launch(long long k) { g_launches += k; }
+long long sem_launch_total() { return g_launches.load(); }
+
+namespace {
+
+constexpr int kVecThreads = 256;
+constexpr int kApplyThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Mesh helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void elem_coords(const SemGeom& g, long long e, int* ex, int* ey, int* ez) {
+  *ex = (int)(e % g.mx);
+  long long r = e / g.mx;
+  *ey = (int)(r % g.my);
+  *ez = (int)(r / g.my);
+}
+
+// Face slot 0..5 = (dir, side): 0 w, 1 e, 2 s, 3 n, 4 b, 5 t.
+__device__ __forceinline__ long long face_base(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
+  const int d = slot >> 1, s = slot & 1;
+  const long long n2 = (long long)g.n * g.n;
+  if (d == 0) {
+    const int f = ex + s;
+    *dir = (f == 0 || f == g.mx);
+    return g.off[0] + (f + (long long)(g.mx + 1) * (ey + (long long)g.my * ez)) * n2;
+  }
+  if (d == 1) {
+    const int f = ey + s;
+    *dir = (f == 0 || f == g.my);
+    return g.off[1] + (ex + (long long)g.mx * (f + (long long)(g.my + 1) * ez)) * n2;
+  }
+  const int f = ez + s;
+  *dir = (f == 0 || f == g.mz);
+  return g.off[2] + (ex + (long long)g.mx * (ey + (long long)g.my * f)) * n2;
+}
+
+// Edge slot 0..11: group = slot >> 2 (0 x-edges Ex[sb][sc], 1 y-edges Ey[sa][sc],
+// 2 z-edges Ez[sa][sb]); the two side bits are slot & 1 and (slot >> 1) & 1.
+__device__ __forceinline__ long long edge_base(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
+  const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+  if (grp == 0) {
+    const int vy = ey + s1, vz = ez + s2;
+    *dir = (vy == 0 || vy == g.my || vz == 0 || vz == g.mz);
+    return g.off[3] + (ex + (long long)g.mx * (vy + (long long)(g.my + 1) * vz)) * g.n;
+  }
+  if (grp == 1) {
+    const int vx = ex + s1, vz = ez + s2;
+    *dir = (vx == 0 || vx == g.mx || vz == 0 || vz == g.mz);
+    return g.off[4] + (vx + (long long)(g.mx + 1) * (ey + (long long)g.my * vz)) * g.n;
+  }
+  const int vx = ex + s1, vy = ey + s2;
+  *dir = (vx == 0 || vx == g.mx || vy == 0 || vy == g.my);
+  return g.off[5] + (vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * ez)) * g.n;
+}
+
+// Vertex slot 0..7 = sa + 2 sb + 4 sc.
+__device__ __forceinline__ long long vert_index(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
+  const int vx = ex + (slot & 1), vy = ey + ((slot >> 1) & 1), vz = ez + (slot >> 2);
+  *dir = (vx == 0 || vx == g.mx || vy == 0 || vy == g.my || vz == 0 || vz == g.mz);
+  return g.off[6] + vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * vz);
+}
+
+template <typename T>
+__device__ __forceinline__ int elem_class(const SemGeom& g, const SemClassTables<T>& t, int ex, int ey, int ez) {
+  return t.cls_x[ex] + g.ux * (t.cls_y[ey] + g.uy * t.cls_z[ez]);
+}
+
+// Global node (gx, gy, gz) of packed skeleton entry idx.
+__device__ __forceinline__ void skel_node(const SemGeom& g, long long idx, long long* gx, long long* gy,
+                                          long long* gz) {
+  const int p = g.p, n = g.n;
+  const long long n2 = (long long)n * n;
+  int b = 0;
+  while (b < 6 && idx >= g.off[b + 1]) ++b;
+  const long long loc = idx - g.off[b];
+  if (b < 3) {
+    const long long ent = loc / n2, r = loc - ent * n2;
+    const int fast = (int)(r % n) + 1, slow = (int)(r / n) + 1;
+    if (b == 0) {
+      const long long f = ent % (g.mx + 1), t = ent / (g.mx + 1);
+      *gx = f * p; *gy = (t % g.my) * p + fast; *gz = (t / g.my) * p + slow;
+    } else if (b == 1) {
+      const long long ex = ent % g.mx, t = ent / g.mx;
+      *gx = ex * p + fast; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p + slow;
+    } else {
+      const long long ex = ent % g.mx, t = ent / g.mx;
+      *gx = ex * p + fast; *gy = (t % g.my) * p + slow; *gz = (t / g.my) * p;
+    }
+  } else if (b < 6) {
+    const long long ent = loc / n;
+    const int l = (int)(loc - ent * n) + 1;
+    if (b == 3) {
+      const long long ex = ent % g.mx, t = ent / g.mx;
+      *gx = ex * p + l; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p;
+    } else if (b == 4) {
+      const long long vx = ent % (g.mx + 1), t = ent / (g.mx + 1);
+      *gx = vx * p; *gy = (t % g.my) * p + l; *gz = (t / g.my) * p;
+    } else {
+      const long long vx = ent % (g.mx + 1), t = ent / (g.mx + 1);
+      *gx = vx * p; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p + l;
+    }
+  } else {
+    const long long vx = loc % (g.mx + 1), t = loc / (g.mx + 1);
+    *gx = vx * p; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p;
+  }
+}
+
+__device__ __forceinline__ bool node_on_boundary(const SemGeom& g, long long gx, long long gy, long long gz) {
+  return gx == 0 || gx == g.Nx - 1 || gy == 0 || gy == g.Ny - 1 || gz == 0 || gz == g.Nz - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction + last-block finalisation
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k * 32 + wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < nw ? sh[k * 32 + lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;   // valid in thread 0
+    }
+  }
+  __syncthreads();
+}
+
+// Writes this block's NV sums to partials[k * G + block]; the last block to
+// arrive sums all partials in a fixed order and returns true with the totals
+// in tot (valid in thread 0).
+template <int NV>
+__device__ bool reduce_grid(double (&v)[NV], double* partials, unsigned int* counter, double (&tot)[NV]) {
+  __shared__ double sh[NV * 32];
+  __shared__ bool last;
+  block_sum<NV>(v, sh);
+  const unsigned G = gridDim.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * G + blockIdx.x] = v[k];
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    last = (t == G - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    s[k] = 0.0;
+    for (unsigned i = threadIdx.x; i < G; i += blockDim.x) s[k] += __ldcg(partials + k * G + i);
+  }
+  block_sum<NV>(s, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = s[k];
+    *counter = 0u;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Per-width-class tables: d (Eq. metriccoeffelement) and D^-1 (Eq. hii_diagonal)
+// ---------------------------------------------------------------------------
+__global__ void k_class_tables(SemGeom g, SemBasis b, const double* __restrict__ wx,
+                               const double* __restrict__ wy, const double* __restrict__ wz,
+                               double lambda, double* __restrict__ dcoef, double* __restrict__ dinv) {
+  const int n = g.n;
+  const long long n3 = (long long)n * n * n;
+  const long long ncls = (long long)g.ux * g.uy * g.uz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncls * (n3 + 4);
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = t / (n3 + 4), r = t - c * (n3 + 4);
+    const int cx = (int)(c % g.ux), cy = (int)((c / g.ux) % g.uy), cz = (int)(c / ((long long)g.ux * g.uy));
+    const double h1 = wx[cx], h2 = wy[cy], h3 = wz[cz];
+    const double J = h1 * h2 * h3 / 8.0;
+    const double d0 = J * lambda, d1 = J * 4.0 / (h1 * h1), d2 = J * 4.0 / (h2 * h2), d3 = J * 4.0 / (h3 * h3);
+    if (r < 4) {
+      dcoef[c * 4 + r] = r == 0 ? d0 : (r == 1 ? d1 : (r == 2 ? d2 : d3));
+    } else {
+      const long long q = r - 4;
+      const int i = (int)(q % n), j = (int)((q / n) % n), k = (int)(q / ((long long)n * n));
+      dinv[c * n3 + q] = 1.0 / (d0 + d1 * b.lam[i] + d2 * b.lam[j] + d3 * b.lam[k]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused transformed condensed operator
+// ---------------------------------------------------------------------------
+// Per-element coefficient arrays (offsets inside the sk / co regions):
+//   skd [dir][side][i] = d_{dir+1} k_side[i]          condensed expansion/contraction
+//   skw [dir][side][i] = d_{dir+1} w0 k_side[i]       lines inside a face
+//   skww[dir][side][i] = d_{dir+1} w0^2 k_side[i]     lines along an edge
+//   lw  [dir][i]       = d_{dir+1} w0 Lambda_i        face diagonal
+//   lww [dir][i]       = d_{dir+1} w0^2 Lambda_i      edge diagonal
+//   co: cF[6] = d0 w0 + d K_ss, cO[6] = d K_so, eS[6] = d w0 K_ss, eO[6] = d w0 K_so,
+//       vS[6] = d w0^2 K_ss, vO[6] = d w0^2 K_so (index dir*2+side), d0 w0^2, d0 w0^3
+template <typename T>
+__device__ __forceinline__ void elem_coeffs(const SemBasis& b, const T* dd, T* sk, T* co, int n, int t) {
+  const double w0 = b.w0;
+  const double d[4] = {(double)dd[0], (double)dd[1], (double)dd[2], (double)dd[3]};
+  if (t < 18 * n) {
+    const int which = t / (6 * n), r = t - which * 6 * n, ds = r / n, i = r - ds * n;
+    const int dir = ds >> 1, side = ds & 1;
+    const double sc = which == 0 ? 1.0 : (which == 1 ? w0 : w0 * w0);
+    sk[t] = (T)(d[dir + 1] * sc * b.k[side][i]);
+  } else if (t < 24 * n) {
+    const int r = t - 18 * n, which = r / (3 * n), q = r - which * 3 * n, dir = q / n, i = q - dir * n;
+    sk[t] = (T)(d[dir + 1] * (which == 0 ? w0 : w0 * w0) * b.lam[i]);
+  } else if (t < 24 * n + 40) {
+    const int c = t - 24 * n;
+    double v = 0.0;
+    if (c < 36) {
+      const int grp = c / 6, ds = c - grp * 6, dir = ds >> 1, side = ds & 1;
+      const double dv = d[dir + 1], Kss = b.K[side][side], Kso = b.K[side][1 - side];
+      switch (grp) {
+        case 0: v = d[0] * w0 + dv * Kss; break;
+        case 1: v = dv * Kso; break;
+        case 2: v = dv * w0 * Kss; break;
+        case 3: v = dv * w0 * Kso; break;
+        case 4: v = dv * w0 * w0 * Kss; break;
+        default: v = dv * w0 * w0 * Kso; break;
+      }
+    } else if (c == 36) {
+      v = d[0] * w0 * w0;
+    } else if (c == 37) {
+      v = d[0] * w0 * w0 * w0;
+    }
+    co[c] = (T)v;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+k_tpt_apply(SemGeom g, SemBasis b, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
+            int epb, int ks, double* __restrict__ partials, PcgState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (st != nullptr && st->done) return;
+
+  const int n = g.n, n2 = n * n;
+  const ElemLayout L = elem_layout(n, ks);
+  int* s_cls = reinterpret_cast<int*>(smem_raw);                          // [epb]
+  T* s_dd = reinterpret_cast<T*>(smem_raw + apply_hdr_cls_bytes(epb));     // [epb][4]
+  T* base = reinterpret_cast<T*>(smem_raw + apply_hdr_bytes(epb, sizeof(T)));
+  const int per_load = 6 * n2 + 12 * n + 8;
+  const long long ntiles = (g.nelem + epb - 1) / epb;
+  double dot = 0.0;
+
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long e0 = tile * epb;
+    // --- element classes and metric coefficients
+    for (int t = threadIdx.x; t < epb; t += blockDim.x) {
+      const long long e = e0 + t;
+      int c = 0;
+      if (e < g.nelem) {
+        int ex, ey, ez;
+        elem_coords(g, e, &ex, &ey, &ez);
+        c = elem_class(g, tab, ex, ey, ez);
+      }
+      s_cls[t] = c;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s_dd[t * 4 + k] = tab.dcoef[c * 4 + k];
+    }
+    __syncthreads();
+    // --- gather R^T: faces, edges, vertices (Dirichlet entities read as 0)
+    for (int t = threadIdx.x; t < epb * per_load; t += blockDim.x) {
+      const int el = t / per_load, r = t - el * per_load;
+      const long long e = e0 + el;
+      T val = T(0);
+      if (e < g.nelem) {
+        int ex, ey, ez;
+        elem_coords(g, e, &ex, &ey, &ez);
+        bool dir;
+        long long gi;
+        if (r < 6 * n2) {
+          const int slot = r / n2;
+          gi = face_base(g, ex, ey, ez, slot, &dir) + (r - slot * n2);
+        } else if (r < 6 * n2 + 12 * n) {
+          const int q = r - 6 * n2, slot = q / n;
+          gi = edge_base(g, ex, ey, ez, slot, &dir) + (q - slot * n);
+        } else {
+          gi = vert_index(g, ex, ey, ez, r - 6 * n2 - 12 * n, &dir);
+        }
+        if (!dir) val = u[gi];
+      }
+      T* E = base + el * L.size;
+      if (r < 6 * n2) E[L.F + r] = val;
+      else if (r < 6 * n2 + 12 * n) E[L.E + (r - 6 * n2)] = val;
+      else E[L.Vt + (r - 6 * n2 - 12 * n)] = val;
+    }
+    // --- per-element scaled coefficient vectors
+    const int per_co = 24 * n + 40;
+    for (int t = threadIdx.x; t < epb * per_co; t += blockDim.x) {
+      const int el = t / per_co, r = t - el * per_co;
+      T* E = base + el * L.size;
+      elem_coeffs<T>(b, s_dd + 4 * el, E + L.sk, E + L.co, n, r);
+    }
+    __syncthreads();
+
+    // --- condensed part, slab by slab of the eigenspace cube (Table 2)
+    for (int k0 = 0; k0 < n; k0 += ks) {
+      const int kn = min(ks, n - k0);
+      const int per_cube = kn * n2;
+      for (int t = threadIdx.x; t < epb * per_cube; t += blockDim.x) {
+        const int el = t / per_cube, r = t - el * per_cube;
+        const int kk = r / n2, ji = r - kk * n2, j = ji / n, i = ji - j * n, k = k0 + kk;
+        T* E = base + el * L.size;
+        const T* F = E + L.F;
+        const T* skd = E + L.sk;
+        T x = skd[0 * n + i] * F[0 * n2 + k * n + j];
+        x = fma(skd[1 * n + i], F[1 * n2 + k * n + j], x);
+        x = fma(skd[2 * n + j], F[2 * n2 + k * n + i], x);
+        x = fma(skd[3 * n + j], F[3 * n2 + k * n + i], x);
+        x = fma(skd[4 * n + k], F[4 * n2 + j * n + i], x);
+        x = fma(skd[5 * n + k], F[5 * n2 + j * n + i], x);
+        const T di = __ldg(tab.dinv + (long long)s_cls[el] * n2 * n + (long long)k * n2 + ji);
+        E[L.cube + r] = di * x;
+      }
+      __syncthreads();
+      const int per_con = 4 * kn * n + 2 * n2;
+      for (int t = threadIdx.x; t < epb * per_con; t += blockDim.x) {
+        const int el = t / per_con, r = t - el * per_con;
+        T* E = base + el * L.size;
+        const T* C = E + L.cube;
+        const T* skd = E + L.sk;
+        T* Acc = E + L.Acc;
+        if (r < 2 * kn * n) {          // w / e: sum over i
+          const int side = r / (kn * n), q = r - side * kn * n, kk = q / n, j = q - kk * n;
+          const T* kv = skd + side * n;
+          const T* row = C + kk * n2 + j * n;
+          T s = T(0);
+          for (int i = 0; i < n; ++i) s = fma(kv[i], row[i], s);
+          Acc[side * n2 + (k0 + kk) * n + j] = s;
+        } else if (r < 4 * kn * n) {   // s / n: sum over j
+          const int q0 = r - 2 * kn * n, side = q0 / (kn * n), q = q0 - side * kn * n;
+          const int kk = q / n, i = q - kk * n;
+          const T* kv = skd + (2 + side) * n;
+          const T* col = C + kk * n2 + i;
+          T s = T(0);
+          for (int j = 0; j < n; ++j) s = fma(kv[j], col[j * n], s);
+          Acc[(2 + side) * n2 + (k0 + kk) * n + i] = s;
+        } else {                       // b / t: sum over k, accumulated over slabs
+          const int q0 = r - 4 * kn * n, side = q0 / n2, ji = q0 - side * n2;
+          const T* kv = skd + (4 + side) * n + k0;
+          const T* col = C + ji;
+          T s = k0 == 0 ? T(0) : Acc[(4 + side) * n2 + ji];
+          for (int kk = 0; kk < kn; ++kk) s = fma(kv[kk], col[kk * n2], s);
+          Acc[(4 + side) * n2 + ji] = s;
+        }
+      }
+      __syncthreads();
+    }
+
+    // --- primary part minus condensed part, scatter-add R
+    for (int t = threadIdx.x; t < epb * per_load; t += blockDim.x) {
+      const int el = t / per_load, r = t - el * per_load;
+      const long long e = e0 + el;
+      if (e >= g.nelem) continue;
+      int ex, ey, ez;
+      elem_coords(g, e, &ex, &ey, &ez);
+      const T* E = base + el * L.size;
+      const T* F = E + L.F;
+      const T* Ed = E + L.E;
+      const T* Vt = E + L.Vt;
+      const T* skw = E + L.sk + 6 * n;
+      const T* skww = E + L.sk + 12 * n;
+      const T* lw = E + L.sk + 18 * n;
+      const T* lww = E + L.sk + 21 * n;
+      const T* co = E + L.co;
+      const T* cF = co, *cO = co + 6, *eS = co + 12, *eO = co + 18, *vS = co + 24, *vO = co + 30;
+      T out, uval;
+      bool dir;
+      long long gi;
+      if (r < 6 * n2) {
+        const int slot = r / n2, idx = r - slot * n2, dd = slot >> 1, s = slot & 1;
+        const int slow = idx / n, fast = idx - slow * n;
+        gi = face_base(g, ex, ey, ez, slot, &dir) + idx;
+        uval = F[r];
+        const T uo = F[(slot ^ 1) * n2 + idx];
+        // edges bounding this face that carry its in-face lines; see the
+        // per-direction formulas in the header comment of this function
+        if (dd == 0) {          // x-face (j = fast, k = slow)
+          const int j = fast, k = slow;
+          const T* Ez0 = Ed + (8 + s + 0) * n;   // Ez[sa=s][sb=0]
+          const T* Ez1 = Ed + (8 + s + 2) * n;   // Ez[s][1]
+          const T* Ey0 = Ed + (4 + s + 0) * n;   // Ey[sa=s][sc=0]
+          const T* Ey1 = Ed + (4 + s + 2) * n;   // Ey[s][1]
+          out = (cF[slot] + lw[n + j] + lw[2 * n + k]) * uval + cO[slot] * uo;
+          out = fma(skw[2 * n + j], Ez0[k], out);
+          out = fma(skw[3 * n + j], Ez1[k], out);
+          out = fma(skw[4 * n + k], Ey0[j], out);
+          out = fma(skw[5 * n + k], Ey1[j], out);
+        } else if (dd == 1) {   // y-face (i = fast, k = slow)
+          const int i = fast, k = slow;
+          const T* Ez0 = Ed + (8 + 0 + 2 * s) * n;   // Ez[sa=0][sb=s]
+          const T* Ez1 = Ed + (8 + 1 + 2 * s) * n;   // Ez[1][s]
+          const T* Ex0 = Ed + (0 + s + 0) * n;       // Ex[sb=s][sc=0]
+          const T* Ex1 = Ed + (0 + s + 2) * n;       // Ex[s][1]
+          out = (cF[slot] + lw[i] + lw[2 * n + k]) * uval + cO[slot] * uo;
+          out = fma(skw[0 * n + i], Ez0[k], out);
+          out = fma(skw[1 * n + i], Ez1[k], out);
+          out = fma(skw[4 * n + k], Ex0[i], out);
+          out = fma(skw[5 * n + k], Ex1[i], out);
+        } else {                // z-face (i = fast, j = slow)
+          const int i = fast, j = slow;
+          const T* Ey0 = Ed + (4 + 0 + 2 * s) * n;   // Ey[sa=0][sc=s]
+          const T* Ey1 = Ed + (4 + 1 + 2 * s) * n;   // Ey[1][s]
+          const T* Ex0 = Ed + (0 + 0 + 2 * s) * n;   // Ex[sb=0][sc=s]
+          const T* Ex1 = Ed + (0 + 1 + 2 * s) * n;   // Ex[1][s]
+          out = (cF[slot] + lw[i] + lw[n + j]) * uval + cO[slot] * uo;
+          out = fma(skw[0 * n + i], Ey0[j], out);
+          out = fma(skw[1 * n + i], Ey1[j], out);
+          out = fma(skw[2 * n + j], Ex0[i], out);
+          out = fma(skw[3 * n + j], Ex1[i], out);
+        }
+        out -= E[L.Acc + r];
+      } else if (r < 6 * n2 + 12 * n) {
+        const int q = r - 6 * n2, slot = q / n, l = q - slot * n;
+        const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+        gi = edge_base(g, ex, ey, ez, slot, &dir) + l;
+        uval = Ed[q];
+        if (grp == 0) {         // x-edge Ex[sb=s1][sc=s2], index i = l
+          const int sb = s1, sc = s2, i = l;
+          const T* Fz = F + (4 + sc) * n2;   // z-face sc, [j][i]
+          const T* Fy = F + (2 + sb) * n2;   // y-face sb, [k][i]
+          out = (co[36] + lww[i] + eS[2 + sb] + eS[4 + sc]) * uval;
+          out = fma(skww[0 * n + i], Vt[0 + 2 * sb + 4 * sc], out);
+          out = fma(skww[1 * n + i], Vt[1 + 2 * sb + 4 * sc], out);
+          const T* kb = skw + (2 + sb) * n;
+          const T* kc = skw + (4 + sc) * n;
+          for (int m = 0; m < n; ++m) out = fma(kb[m], Fz[m * n + i], out);
+          for (int m = 0; m < n; ++m) out = fma(kc[m], Fy[m * n + i], out);
+          out = fma(eO[2 + sb], Ed[(0 + (1 - sb) + 2 * sc) * n + i], out);
+          out = fma(eO[4 + sc], Ed[(0 + sb + 2 * (1 - sc)) * n + i], out);
+        } else if (grp == 1) {  // y-edge Ey[sa=s1][sc=s2], index j = l
+          const int sa = s1, sc = s2, j = l;
+          const T* Fz = F + (4 + sc) * n2;   // [j][i]
+          const T* Fx = F + (0 + sa) * n2;   // [k][j]
+          out = (co[36] + lww[n + j] + eS[0 + sa] + eS[4 + sc]) * uval;
+          out = fma(skww[2 * n + j], Vt[sa + 0 + 4 * sc], out);
+          out = fma(skww[3 * n + j], Vt[sa + 2 + 4 * sc], out);
+          const T* ka = skw + (0 + sa) * n;
+          const T* kc = skw + (4 + sc) * n;
+          for (int m = 0; m < n; ++m) out = fma(ka[m], Fz[j * n + m], out);
+          for (int m = 0; m < n; ++m) out = fma(kc[m], Fx[m * n + j], out);
+          out = fma(eO[0 + sa], Ed[(4 + (1 - sa) + 2 * sc) * n + j], out);
+          out = fma(eO[4 + sc], Ed[(4 + sa + 2 * (1 - sc)) * n + j], out);
+        } else {                // z-edge Ez[sa=s1][sb=s2], index k = l
+          const int sa = s1, sb = s2, k = l;
+          const T* Fy = F + (2 + sb) * n2;   // [k][i]
+          const T* Fx = F + (0 + sa) * n2;   // [k][j]
+          out = (co[36] + lww[2 * n + k] + eS[0 + sa] + eS[2 + sb]) * uval;
+          out = fma(skww[4 * n + k], Vt[sa + 2 * sb + 0], out);
+          out = fma(skww[5 * n + k], Vt[sa + 2 * sb + 4], out);
+          const T* ka = skw + (0 + sa) * n;
+          const T* kb = skw + (2 + sb) * n;
+          for (int m = 0; m < n; ++m) out = fma(ka[m], Fy[k * n + m], out);
+          for (int m = 0; m < n; ++m) out = fma(kb[m], Fx[k * n + m], out);
+          out = fma(eO[0 + sa], Ed[(8 + (1 - sa) + 2 * sb) * n + k], out);
+          out = fma(eO[2 + sb], Ed[(8 + sa + 2 * (1 - sb)) * n + k], out);
+        }
+      } else {
+        const int slot = r - 6 * n2 - 12 * n;
+        const int sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
+        gi = vert_index(g, ex, ey, ez, slot, &dir);
+        uval = Vt[slot];
+        out = (co[37] + vS[0 + sa] + vS[2 + sb] + vS[4 + sc]) * uval;
+        const T* ka = skww + (0 + sa) * n;
+        const T* kb = skww + (2 + sb) * n;
+        const T* kc = skww + (4 + sc) * n;
+        const T* ex_ = Ed + (0 + sb + 2 * sc) * n;    // Ex[sb][sc]
+        const T* ey_ = Ed + (4 + sa + 2 * sc) * n;    // Ey[sa][sc]
+        const T* ez_ = Ed + (8 + sa + 2 * sb) * n;    // Ez[sa][sb]
+        for (int m = 0; m < n; ++m) out = fma(ka[m], ex_[m], out);
+        for (int m = 0; m < n; ++m) out = fma(kb[m], ey_[m], out);
+        for (int m = 0; m < n; ++m) out = fma(kc[m], ez_[m], out);
+        out = fma(vO[0 + sa], Vt[slot ^ 1], out);
+        out = fma(vO[2 + sb], Vt[slot ^ 2], out);
+        out = fma(vO[4 + sc], Vt[slot ^ 4], out);
+      }
+      if (!dir) {
+        atomicAdd(v + gi, out);
+        dot += (double)uval * (double)out;
+      }
+    }
+    __syncthreads();
+  }
+
+  if (st != nullptr) {
+    double vals[1] = {dot}, tot[1];
+    if (reduce_grid<1>(vals, partials, &st->counter[0], tot) && threadIdx.x == 0) {
+      const double pq = tot[0];
+      st->pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        st->done = 2;
+      } else {
+        st->alpha = st->rho / pq;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal of the assembled transformed condensed operator (BT preconditioner)
+// ---------------------------------------------------------------------------
+// Face (dir, side) entry: d0 w0 + d K_ss + w0 (d' Lambda + d'' Lambda) (primary,
+// Eq. east_east_primary_part_transformed) minus d^2 sum_t k_side[t]^2 D^-1 over
+// the line into the interior (condensed self term).  Edge entry: the edge's
+// primary diagonal (edges do not couple to the interior).  Vertex: primary.
+__global__ void k_precond_diag(SemGeom g, SemBasis b, SemClassTables<double> tab, double* __restrict__ diag) {
+  const int n = g.n, n2 = n * n;
+  const int per = 6 * n2 + 12 * n + 8;
+  const double w0 = b.w0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.nelem * per;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / per;
+    const int r = (int)(t - e * per);
+    int ex, ey, ez;
+    elem_coords(g, e, &ex, &ey, &ez);
+    const int c = elem_class(g, tab, ex, ey, ez);
+    const double d[4] = {tab.dcoef[c * 4], tab.dcoef[c * 4 + 1], tab.dcoef[c * 4 + 2], tab.dcoef[c * 4 + 3]};
+    const double* Dinv = tab.dinv + (long long)c * n2 * n;
+    bool dir;
+    long long gi;
+    double val;
+    if (r < 6 * n2) {
+      const int slot = r / n2, idx = r - slot * n2, dd = slot >> 1, s = slot & 1;
+      const int slow = idx / n, fast = idx - slow * n;
+      gi = face_base(g, ex, ey, ez, slot, &dir) + idx;
+      const double* ks = b.k[s];
+      double cond = 0.0;
+      if (dd == 0) {      // (j, k) = (fast, slow), line over i
+        for (int i = 0; i < n; ++i) cond += ks[i] * ks[i] * Dinv[(slow * n + fast) * n + i];
+        val = d[0] * w0 + d[1] * b.K[s][s] + w0 * (d[2] * b.lam[fast] + d[3] * b.lam[slow]) - d[1] * d[1] * cond;
+      } else if (dd == 1) {  // (i, k), line over j
+        for (int j = 0; j < n; ++j) cond += ks[j] * ks[j] * Dinv[(slow * n + j) * n + fast];
+        val = d[0] * w0 + d[2] * b.K[s][s] + w0 * (d[1] * b.lam[fast] + d[3] * b.lam[slow]) - d[2] * d[2] * cond;
+      } else {               // (i, j), line over k
+        for (int k = 0; k < n; ++k) cond += ks[k] * ks[k] * Dinv[(k * n + slow) * n + fast];
+        val = d[0] * w0 + d[3] * b.K[s][s] + w0 * (d[1] * b.lam[fast] + d[2] * b.lam[slow]) - d[3] * d[3] * cond;
+      }
+    } else if (r < 6 * n2 + 12 * n) {
+      const int q = r - 6 * n2, slot = q / n, l = q - slot * n;
+      const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+      gi = edge_base(g, ex, ey, ez, slot, &dir) + l;
+      // along-edge direction gets d w0^2 Lambda; the two transverse directions d w0 K_ss
+      const int da = grp, t1 = grp == 0 ? 1 : 0, t2 = grp == 2 ? 1 : 2;
+      val = d[0] * w0 * w0 + d[da + 1] * w0 * w0 * b.lam[l] + d[t1 + 1] * w0 * b.K[s1][s1] +
+            d[t2 + 1] * w0 * b.K[s2][s2];
+    } else {
+      const int slot = r - 6 * n2 - 12 * n;
+      const int sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
+      gi = vert_index(g, ex, ey, ez, slot, &dir);
+      val = d[0] * w0 * w0 * w0 + w0 * w0 * (d[1] * b.K[sa][sa] + d[2] * b.K[sb][sb] + d[3] * b.K[sc][sc]);
+    }
+    if (!dir) atomicAdd(diag + gi, val);
+  }
+}
+
+__global__ void k_invert_diag(long long nb, const double* __restrict__ diag, double* __restrict__ P) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    const double d = diag[i];
+    P[i] = d != 0.0 ? 1.0 / d : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Skeleton transform: faces A U A^T, edges A u (in place allowed)
+// ---------------------------------------------------------------------------
+__global__ void k_skel_faces(SemGeom g, const double* __restrict__ A, const double* in, double* out, int fpb) {
+  extern __shared__ double sh[];
+  const int n = g.n, n2 = n * n;
+  double* sA = sh;
+  double* sU = sh + n2;            // [fpb][n2]
+  double* sT = sU + fpb * n2;      // [fpb][n2]
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) sA[t] = A[t];
+  const long long nfaces = (g.off[3] - g.off[0]) / n2;
+  for (long long f0 = (long long)blockIdx.x * fpb; f0 < nfaces; f0 += (long long)gridDim.x * fpb) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < fpb * n2; t += blockDim.x) {
+      const long long f = f0 + t / n2;
+      sU[t] = f < nfaces ? in[g.off[0] + f * n2 + (t % n2)] : 0.0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < fpb * n2; t += blockDim.x) {   // T = U A^T
+      const int fl = t / n2, r = t - fl * n2, row = r / n, col = r - row * n;
+      const double* U = sU + fl * n2 + row * n;
+      double s = 0.0;
+      for (int c = 0; c < n; ++c) s = fma(U[c], sA[col * n + c], s);
+      sT[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < fpb * n2; t += blockDim.x) {   // A T
+      const int fl = t / n2, r = t - fl * n2, row = r / n, col = r - row * n;
+      const long long f = f0 + fl;
+      if (f >= nfaces) continue;
+      const double* Tm = sT + fl * n2 + col;
+      double s = 0.0;
+      for (int c = 0; c < n; ++c) s = fma(sA[row * n + c], Tm[c * n], s);
+      out[g.off[0] + f * n2 + r] = s;
+    }
+  }
+}
+
+__global__ void k_skel_edges(SemGeom g, const double* __restrict__ A, const double* in, double* out, int epb) {
+  extern __shared__ double sh[];
+  const int n = g.n;
+  double* sA = sh;
+  double* sU = sh + n * n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sA[t] = A[t];
+  const long long nedges = (g.off[6] - g.off[3]) / n;
+  for (long long e0 = (long long)blockIdx.x * epb; e0 < nedges; e0 += (long long)gridDim.x * epb) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < epb * n; t += blockDim.x) {
+      const long long e = e0 + t / n;
+      sU[t] = e < nedges ? in[g.off[3] + e * n + (t % n)] : 0.0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < epb * n; t += blockDim.x) {
+      const int el = t / n, row = t - el * n;
+      const long long e = e0 + el;
+      if (e >= nedges) continue;
+      double s = 0.0;
+      for (int c = 0; c < n; ++c) s = fma(sA[row * n + c], sU[el * n + c], s);
+      out[g.off[3] + e * n + row] = s;
+    }
+  }
+}
+
+__global__ void k_copy_range(const double* in, double* out, long long a, long long b) {
+  for (long long i = a + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b; i += (long long)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+// ---------------------------------------------------------------------------
+// Pack / unpack, lumped-mass loads, interior cubes
+// ---------------------------------------------------------------------------
+// Assembled lumped mass at a node factorises over the axes: m(gx) m(gy) m(gz)
+// with m(g) = sum over the 1D elements containing g of (h_e / 2) w_local.
+__global__ void k_pack(SemGeom g, const double* __restrict__ full, double* __restrict__ uB,
+                       const double* __restrict__ mxs, const double* __restrict__ mys,
+                       const double* __restrict__ mzs, int zero_dirichlet) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nb; i += (long long)gridDim.x * blockDim.x) {
+    long long gx, gy, gz;
+    skel_node(g, i, &gx, &gy, &gz);
+    double v = full[gx + g.Nx * (gy + g.Ny * gz)];
+    if (mxs != nullptr) v *= mxs[gx] * mys[gy] * mzs[gz];
+    if (zero_dirichlet && node_on_boundary(g, gx, gy, gz)) v = 0.0;
+    uB[i] = v;
+  }
+}
+
+__global__ void k_unpack(SemGeom g, const double* __restrict__ uB, double* __restrict__ full, int zero_dirichlet) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nb; i += (long long)gridDim.x * blockDim.x) {
+    long long gx, gy, gz;
+    skel_node(g, i, &gx, &gy, &gz);
+    const bool bnd = zero_dirichlet && node_on_boundary(g, gx, gy, gz);
+    full[gx + g.Nx * (gy + g.Ny * gz)] = bnd ? 0.0 : uB[i];
+  }
+}
+
+__global__ void k_interior_load(SemGeom g, const double* __restrict__ mxs, const double* __restrict__ mys,
+                                const double* __restrict__ mzs, const double* __restrict__ f, double* __restrict__ X) {
+  const int n = g.n, p = g.p;
+  const long long n3 = (long long)n * n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.nelem * n3; t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / n3;
+    const long long r = t - e * n3;
+    const int i = (int)(r % n), j = (int)((r / n) % n), k = (int)(r / ((long long)n * n));
+    int ex, ey, ez;
+    elem_coords(g, e, &ex, &ey, &ez);
+    const long long gx = (long long)ex * p + i + 1, gy = (long long)ey * p + j + 1, gz = (long long)ez * p + k + 1;
+    X[t] = mxs[gx] * mys[gy] * mzs[gz] * f[gx + g.Nx * (gy + g.Ny * gz)];
+  }
+}
+
+__global__ void k_mode(SemGeom g, const double* __restrict__ A, int axis, const double* __restrict__ in,
+                       double* __restrict__ out, double* __restrict__ grid) {
+  __shared__ double sA[SEM_MAXN * SEM_MAXN];
+  const int n = g.n, p = g.p;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) sA[t] = A[t];
+  __syncthreads();
+  const long long n3 = (long long)n * n * n;
+  const int stride = axis == 0 ? 1 : (axis == 1 ? n : n * n);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.nelem * n3; t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / n3;
+    const long long r = t - e * n3;
+    const int i = (int)(r % n), j = (int)((r / n) % n), k = (int)(r / ((long long)n * n));
+    const int row = axis == 0 ? i : (axis == 1 ? j : k);
+    const double* line = in + (t - (long long)row * stride);
+    const double* Ar = sA + row * n;
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s = fma(Ar[c], line[(long long)c * stride], s);
+    if (grid != nullptr) {
+      int ex, ey, ez;
+      elem_coords(g, e, &ex, &ey, &ez);
+      const long long gx = (long long)ex * p + i + 1, gy = (long long)ey * p + j + 1, gz = (long long)ez * p + k + 1;
+      grid[gx + g.Nx * (gy + g.Ny * gz)] = s;
+    } else {
+      out[t] = s;
+    }
+  }
+}
+
+// fhat~ faces -= d k_side . (D^-1 Ft_I) along the line into the interior.
+__global__ void k_condense_faces(SemGeom g, SemBasis b, SemClassTables<double> tab, const double* __restrict__ FtI,
+                                 double* __restrict__ out) {
+  const int n = g.n, n2 = n * n;
+  const long long n3 = (long long)n2 * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.nelem * 6 * n2; t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / (6 * n2);
+    const int r = (int)(t - e * 6 * n2);
+    const int slot = r / n2, idx = r - slot * n2, dd = slot >> 1, s = slot & 1;
+    const int slow = idx / n, fast = idx - slow * n;
+    int ex, ey, ez;
+    elem_coords(g, e, &ex, &ey, &ez);
+    bool dir;
+    const long long gi = face_base(g, ex, ey, ez, slot, &dir) + idx;
+    if (dir) continue;
+    const int c = elem_class(g, tab, ex, ey, ez);
+    const double* Dinv = tab.dinv + (long long)c * n3;
+    const double* X = FtI + e * n3;
+    const double* ks = b.k[s];
+    double acc = 0.0;
+    long long off0, stride;
+    if (dd == 0) { off0 = (long long)(slow * n + fast) * n; stride = 1; }
+    else if (dd == 1) { off0 = (long long)slow * n2 + fast; stride = n; }
+    else { off0 = (long long)slow * n + fast; stride = n2; }
+    for (int m = 0; m < n; ++m) {
+      const long long q = off0 + m * stride;
+      acc = fma(ks[m], Dinv[q] * X[q], acc);
+    }
+    atomicAdd(out + gi, -tab.dcoef[c * 4 + 1 + dd] * acc);
+  }
+}
+
+// Z = D^-1 (Ft_I - H~_IB u~_B): expansion of the six faces (Table 2).
+__global__ void k_recover_expand(SemGeom g, SemBasis b, SemClassTables<double> tab, const double* __restrict__ FtI,
+                                 const double* __restrict__ uB, double* __restrict__ Z) {
+  const int n = g.n, n2 = n * n;
+  const long long n3 = (long long)n2 * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.nelem * n3; t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / n3;
+    const int r = (int)(t - e * n3);
+    const int i = r % n, j = (r / n) % n, k = r / n2;
+    int ex, ey, ez;
+    elem_coords(g, e, &ex, &ey, &ez);
+    const int c = elem_class(g, tab, ex, ey, ez);
+    const double* d = tab.dcoef + c * 4;
+    double acc = 0.0;
+    for (int slot = 0; slot < 6; ++slot) {
+      bool dir;
+      const long long fb = face_base(g, ex, ey, ez, slot, &dir);
+      if (dir) continue;
+      const int dd = slot >> 1, s = slot & 1;
+      double kv, uv;
+      if (dd == 0) { kv = b.k[s][i]; uv = uB[fb + k * n + j]; }
+      else if (dd == 1) { kv = b.k[s][j]; uv = uB[fb + k * n + i]; }
+      else { kv = b.k[s][k]; uv = uB[fb + j * n + i]; }
+      acc = fma(d[1 + dd] * kv, uv, acc);
+    }
+    Z[t] = tab.dinv[(long long)c * n3 + r] * (FtI[t] - acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CG vector kernels
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVecThreads)
+k_pcg_init(long long nb, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ p,
+           double* __restrict__ q, double* __restrict__ x, const double* __restrict__ P,
+           double* __restrict__ partials, PcgState* st, double rtol, int maxit, int keep_x, int have_q) {
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double ri = have_q ? bi - q[i] : bi;
+    const double zi = P[i] * ri;
+    r[i] = ri;
+    p[i] = zi;
+    q[i] = 0.0;
+    if (!keep_x) x[i] = 0.0;
+    rz = fma(ri, zi, rz);
+    rr = fma(ri, ri, rr);
+    bb = fma(bi, bi, bb);
+  }
+  // the stopping rule is relative to ||b|| (= ||r_0|| for a zero start)
+  double v[3] = {rz, rr, bb}, tot[3];
+  if (reduce_grid<3>(v, partials, &st->counter[1], tot) && threadIdx.x == 0) {
+    st->rho = tot[0];
+    st->rr = tot[1];
+    st->rr0 = tot[2];
+    st->tol2 = rtol * rtol * tot[2];
+    st->iter = 0;
+    st->maxit = maxit;
+    st->alpha = st->beta = 0.0;
+    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) st->done = 2;
+    else if (tot[1] <= st->tol2) st->done = 1;
+    else st->done = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+k_pcg_update(long long nb, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+             const double* __restrict__ q, const double* __restrict__ P, double* __restrict__ partials,
+             PcgState* st) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  double rz = 0.0, rr = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    rz = fma(ri, P[i] * ri, rz);
+    rr = fma(ri, ri, rr);
+  }
+  double v[2] = {rz, rr}, tot[2];
+  if (reduce_grid<2>(v, partials, &st->counter[2], tot) && threadIdx.x == 0) {
+    const int it = st->iter + 1;
+    st->iter = it;
+    st->rho_new = tot[0];
+    st->rr = tot[1];
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) {
+      st->done = 2;
+    } else if (tot[1] <= st->tol2) {
+      st->done = 1;
+    } else if (it >= st->maxit) {
+      st->done = 3;
+    } else {
+      st->beta = tot[0] / st->rho;
+      st->rho = tot[0];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+k_pcg_dir(long long nb, const double* __restrict__ r, double* __restrict__ p, double* __restrict__ q,
+          const double* __restrict__ P, PcgState* st) {
+  if (st->done) return;
+  const double beta = st->beta;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    p[i] = fma(beta, p[i], P[i] * r[i]);
+    q[i] = 0.0;
+  }
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 152;
+  }
+  return g_num_sms;
+}
+
+int grid_for(long long work, int threads, int per_sm = 8) {
+  long long b = (work + threads - 1) / threads;
+  long long cap = (long long)num_sms() * per_sm;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+int sem_vec_blocks() { return num_sms() * 4; }
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+ApplyConfig sem_apply_config(int n, size_t elem_bytes) {
+  ApplyConfig c;
+  c.threads = kApplyThreads;
+  const int n2 = n * n;
+  // slab depth: whole cube when it fits in ~64 KB of shared memory
+  const size_t budget = 64 * 1024;
+  int ks = n;
+  while (ks > 1 && (size_t)elem_layout(n, ks).size * elem_bytes > budget + (size_t)(12 * n2) * elem_bytes) ks = (ks + 1) / 2;
+  c.ks = ks;
+  // elements per block: enough cube work for the block
+  int per = n2 * n > 6 * n2 + 12 * n + 8 ? n2 * n : 6 * n2 + 12 * n + 8;
+  int epb = (kApplyThreads + per - 1) / per;
+  if (epb < 1) epb = 1;
+  if (epb > 32) epb = 32;
+  c.epb = epb;
+  const ElemLayout L = elem_layout(n, ks);
+  c.smem = apply_hdr_bytes(epb, elem_bytes) + (size_t)epb * L.size * elem_bytes;
+  return c;
+}
+
+void launch_tpt_apply_f64(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
+                          const double* x, double* y, double* partials, PcgState* st, cudaStream_t s) {
+  const ApplyConfig c = sem_apply_config(g.n, sizeof(double));
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_tpt_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply<double>, c.threads, c.smem);
+  if (occ < 1) occ = 1;
+  const long long ntiles = (g.nelem + c.epb - 1) / c.epb;
+  long long grid = (long long)num_sms() * occ;
+  if (grid > ntiles) grid = ntiles;
+  k_tpt_apply<double><<<(int)grid, c.threads, c.smem, s>>>(g, b, t, x, y, c.epb, c.ks, partials, st);
+  sem_count_launch();
+}
+
+void launch_class_tables(const SemGeom& g, const SemBasis& b, const double* ux_w, const double* uy_w,
+                         const double* uz_w, double lambda, double* dcoef, double* dinv, cudaStream_t s) {
+  const long long ncls = (long long)g.ux * g.uy * g.uz;
+  const long long work = ncls * ((long long)g.n * g.n * g.n + 4);
+  k_class_tables<<<grid_for(work, 256, 16), 256, 0, s>>>(g, b, ux_w, uy_w, uz_w, lambda, dcoef, dinv);
+  sem_count_launch();
+}
+
+void launch_precond_diag(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t, double* diag,
+                         cudaStream_t s) {
+  const long long work = g.nelem * (6LL * g.n * g.n + 12LL * g.n + 8);
+  k_precond_diag<<<grid_for(work, 256, 16), 256, 0, s>>>(g, b, t, diag);
+  sem_count_launch();
+}
+
+void launch_invert_diag(const SemGeom& g, const double* diag, double* P, cudaStream_t s) {
+  k_invert_diag<<<grid_for(g.nb, 256), 256, 0, s>>>(g.nb, diag, P);
+  sem_count_launch();
+}
+
+void launch_skel_transform(const SemGeom& g, const double* A, const double* in, double* out, cudaStream_t s) {
+  const int n = g.n, n2 = n * n;
+  const long long nfaces = (g.off[3] - g.off[0]) / n2;
+  int fpb = 256 / n2;
+  if (fpb < 1) fpb = 1;
+  size_t smf = (size_t)(n2 + 2 * fpb * n2) * sizeof(double);
+  k_skel_faces<<<grid_for(nfaces, fpb, 16), 256, smf, s>>>(g, A, in, out, fpb);
+  const long long nedges = (g.off[6] - g.off[3]) / n;
+  int epb = 256 / n;
+  if (epb < 1) epb = 1;
+  size_t sme = (size_t)(n2 + epb * n) * sizeof(double);
+  k_skel_edges<<<grid_for(nedges, epb, 16), 256, sme, s>>>(g, A, in, out, epb);
+  sem_count_launch(2);
+  if (in != out) {
+    k_copy_range<<<grid_for(g.nb - g.off[6], 256), 256, 0, s>>>(in, out, g.off[6], g.nb);
+    sem_count_launch();
+  }
+}
+
+void launch_load_skeleton(const SemGeom& g, const double* mxs, const double* mys, const double* mzs,
+                          const double* f, double* out, cudaStream_t s) {
+  k_pack<<<grid_for(g.nb, 256), 256, 0, s>>>(g, f, out, mxs, mys, mzs, 1);
+  sem_count_launch();
+}
+
+void launch_interior_load(const SemGeom& g, const double* mxs, const double* mys, const double* mzs,
+                          const double* f, double* X, cudaStream_t s) {
+  const long long work = g.nelem * (long long)g.n * g.n * g.n;
+  k_interior_load<<<grid_for(work, 256, 16), 256, 0, s>>>(g, mxs, mys, mzs, f, X);
+  sem_count_launch();
+}
+
+void launch_mode(const SemGeom& g, const double* A, int axis, const double* in, double* out, double* grid,
+                 cudaStream_t s) {
+  const long long work = g.nelem * (long long)g.n * g.n * g.n;
+  k_mode<<<grid_for(work, 256, 16), 256, 0, s>>>(g, A, axis, in, out, grid);
+  sem_count_launch();
+}
+
+void launch_condense_faces(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
+                           const double* FtI, double* out, cudaStream_t s) {
+  const long long work = g.nelem * 6LL * g.n * g.n;
+  k_condense_faces<<<grid_for(work, 256, 16), 256, 0, s>>>(g, b, t, FtI, out);
+  sem_count_launch();
+}
+
+void launch_recover_expand(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
+                           const double* FtI, const double* uB, double* Z, cudaStream_t s) {
+  const long long work = g.nelem * (long long)g.n * g.n * g.n;
+  k_recover_expand<<<grid_for(work, 256, 16), 256, 0, s>>>(g, b, t, FtI, uB, Z);
+  sem_count_launch();
+}
+
+void launch_pack(const SemGeom& g, const double* full, double* uB, cudaStream_t s) {
+  k_pack<<<grid_for(g.nb, 256), 256, 0, s>>>(g, full, uB, nullptr, nullptr, nullptr, 0);
+  sem_count_launch();
+}
+
+void launch_unpack(const SemGeom& g, const double* uB, double* full, int zero_dirichlet, cudaStream_t s) {
+  k_unpack<<<grid_for(g.nb, 256), 256, 0, s>>>(g, uB, full, zero_dirichlet);
+  sem_count_launch();
+}
+
+void launch_pcg_init(long long nb, const double* b, double* r, double* p, double* q, double* x,
+                     const double* P, double* partials, PcgState* st, double rtol, int maxit, int keep_x,
+                     cudaStream_t s) {
+  k_pcg_init<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, b, r, p, q, x, P, partials, st, rtol, maxit, keep_x,
+                                                      keep_x);
+  sem_count_launch();
+}
+
+void launch_pcg_update(long long nb, double* x, double* r, const double* p, const double* q, const double* P,
+                       double* partials, PcgState* st, cudaStream_t s) {
+  k_pcg_update<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, r, p, q, P, partials, st);
+  sem_count_launch();
+}
+
+void launch_pcg_dir(long long nb, const double* r, double* p, double* q, const double* P, PcgState* st,
+                    cudaStream_t s) {
+  k_pcg_dir<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, p, q, P, st);
+  sem_count_launch();
+}

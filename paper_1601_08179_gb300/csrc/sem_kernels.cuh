@@ -1,0 +1,102 @@
+// Kernel launchers of the sm_103a condensed spectral-element library.
+#pragma once
+
+#include "sem_internal.h"
+
+// Layout of one element's working set in shared memory (units of T).
+struct ElemLayout {
+  int F, Acc, E, Vt, sk, co, cube, size;
+};
+
+inline __host__ __device__ ElemLayout elem_layout(int n, int ks) {
+  const int n2 = n * n;
+  ElemLayout L;
+  L.F = 0;                  // 6 faces, n^2 each
+  L.Acc = 6 * n2;           // 6 condensed face contractions
+  L.E = 12 * n2;            // 12 edges, n each
+  L.Vt = L.E + 12 * n;      // 8 vertices
+  L.sk = L.Vt + 8;          // skd, skw, skww [3][2][n]; lw, lww [3][n]
+  L.co = L.sk + 24 * n;     // 40 scalars
+  L.cube = L.co + 40;       // ks * n^2 slab of the eigenspace cube
+  L.size = L.cube + ks * n2;
+  L.size = (L.size + 1) & ~1;
+  return L;
+}
+
+// Shared-memory header of the operator kernel: element classes, then metric
+// coefficients, each padded to 16 bytes.
+inline __host__ __device__ size_t apply_hdr_cls_bytes(int epb) { return ((size_t)epb * 4 + 15) & ~size_t(15); }
+inline __host__ __device__ size_t apply_hdr_bytes(int epb, size_t elem_bytes) {
+  return apply_hdr_cls_bytes(epb) + (((size_t)epb * 4 * elem_bytes + 15) & ~size_t(15));
+}
+
+// Launch configuration of the fused operator kernel for degree p.
+struct ApplyConfig {
+  int epb;      // elements per block
+  int ks;       // eigenspace slab depth (k planes held at once)
+  int threads;
+  size_t smem;  // dynamic shared memory bytes
+};
+ApplyConfig sem_apply_config(int n, size_t elem_bytes);
+
+// y = Hhat~ x on the skeleton (transformed space).  y must be zero on entry.
+// If st != nullptr: also x^T y -> st->pq, alpha = rho / pq (CG step).
+void launch_tpt_apply_f64(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
+                          const double* x, double* y, double* partials, PcgState* st,
+                          cudaStream_t s);
+
+void launch_class_tables(const SemGeom& g, const SemBasis& b, const double* ux_w, const double* uy_w,
+                         const double* uz_w, double lambda, double* dcoef, double* dinv,
+                         cudaStream_t s);
+
+// diag of the assembled transformed condensed operator (atomics into diag, zeroed).
+void launch_precond_diag(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
+                         double* diag, cudaStream_t s);
+// P = 1/diag on free entries, 0 on Dirichlet entries (diag in, P out; may alias).
+void launch_invert_diag(const SemGeom& g, const double* diag, double* P, cudaStream_t s);
+
+// Entity-wise skeleton transform with the n x n matrix A (device, row-major):
+// faces U -> A U A^T, edges u -> A u, vertices copied.  in may alias out.
+void launch_skel_transform(const SemGeom& g, const double* A, const double* in, double* out,
+                           cudaStream_t s);
+
+// Lumped-mass loads.  The assembled GLL mass at global node (gx, gy, gz) is
+// mxs[gx] mys[gy] mzs[gz] (a product of 1D assembled masses).
+// Skeleton: out[i] = mass * f at skeleton node i, 0 on Dirichlet entries.
+void launch_load_skeleton(const SemGeom& g, const double* mxs, const double* mys, const double* mzs,
+                          const double* f, double* out, cudaStream_t s);
+// Interior cubes X[e][k][j][i] = mass * f at the element's interior nodes.
+void launch_interior_load(const SemGeom& g, const double* mxs, const double* mys, const double* mzs,
+                          const double* f, double* X, cudaStream_t s);
+
+// Mode product along `axis` (0: i, 1: j, 2: k) of all interior cubes with the
+// n x n matrix A: out[.. r ..] = sum_c A[r][c] in[.. c ..].  If grid != nullptr
+// the result is written to the interior nodes of the full nodal field instead.
+void launch_mode(const SemGeom& g, const double* A, int axis, const double* in, double* out,
+                 double* grid, cudaStream_t s);
+
+// Condensed-load correction: Z = D^-1 Ft_I per element; out faces -= d k . Z.
+void launch_condense_faces(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
+                           const double* FtI, double* out, cudaStream_t s);
+
+// Recovery: Z = D^-1 (Ft_I - H~_IB u~_B) per element (transformed interior).
+void launch_recover_expand(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
+                           const double* FtI, const double* uB, double* Z, cudaStream_t s);
+
+void launch_pack(const SemGeom& g, const double* full, double* uB, cudaStream_t s);
+// Writes skeleton values into the full field; zero_dirichlet writes 0 at
+// domain-boundary nodes instead of the input value.
+void launch_unpack(const SemGeom& g, const double* uB, double* full, int zero_dirichlet, cudaStream_t s);
+
+// ---- CG vector kernels (FP64) ----
+// r = b - q (q may be null: r = b); z = P r; p = z; x = 0 unless keep_x; q = 0;
+// rho = r.z, rr0 = r.r, tol2 = rtol^2 rr0.
+void launch_pcg_init(long long nb, const double* b, double* r, double* p, double* q, double* x,
+                     const double* P, double* partials, PcgState* st, double rtol, int maxit,
+                     int keep_x, cudaStream_t s);
+void launch_pcg_update(long long nb, double* x, double* r, const double* p, const double* q,
+                       const double* P, double* partials, PcgState* st, cudaStream_t s);
+void launch_pcg_dir(long long nb, const double* r, double* p, double* q, const double* P,
+                    PcgState* st, cudaStream_t s);
+
+int sem_vec_blocks();

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C ABI in include/sem.h (libsemgb.so).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+functions keep the C names (sem_setup, sem_apply_condensed, ...); device
+vectors are torch CUDA float64 tensors, host vectors NumPy float64 arrays.
+Streams default to torch's current stream on the tensors' device.
+
+If the library has not been built, loading fails loudly: there is no CPU or
+Python fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsemgb.so")
+
+SEM_OK, SEM_EINVAL, SEM_ENOMEM, SEM_ECUDA, SEM_ENOCONV, SEM_EBREAKDOWN, SEM_ENOTSUP = range(7)
+SPACE_NODAL, SPACE_TRANSFORMED = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+# sem_transform_skeleton kinds
+SOLUTION_TO_T, SOLUTION_FROM_T, LOAD_TO_T, LOAD_FROM_T = 0, 1, 2, 3
+
+
+class SemError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class sem_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int)]
+
+
+class sem_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refinements", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("t_solve_s", ctypes.c_double)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Loads libsemgb.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1601_08179_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "sem_default_opts": (None, [ctypes.POINTER(sem_opts)]),
+        "sem_setup": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     _D, _D, _D, ctypes.c_double, ctypes.POINTER(sem_opts)]),
+        "sem_set_lambda": (ctypes.c_int, [_P, ctypes.c_double]),
+        "sem_set_opts": (ctypes.c_int, [_P, ctypes.POINTER(sem_opts)]),
+        "sem_skeleton_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+        "sem_grid_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+        "sem_node_coords": (ctypes.c_int, [_P, _D, _D, _D]),
+        "sem_get_basis": (ctypes.c_int, [_P, _D, _D, _D, _D]),
+        "sem_apply_condensed": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+        "sem_condense_rhs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+        "sem_precond_diag": (ctypes.c_int, [_P, _P, _P]),
+        "sem_recover_interior": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
+        "sem_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(sem_info), _P]),
+        "sem_solve_host": (ctypes.c_int, [_P, _D, _D, ctypes.POINTER(sem_info), _P]),
+        "sem_transform_skeleton": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+        "sem_pack_skeleton": (ctypes.c_int, [_P, _P, _P, _P]),
+        "sem_unpack_skeleton": (ctypes.c_int, [_P, _P, _P, _P]),
+        "sem_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+        "sem_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                            ctypes.c_int]),
+        "sem_launch_count": (ctypes.c_longlong, []),
+        "sem_destroy": (None, [_P]),
+        "sem_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "sem_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the entry points the binding expects the library to export."""
+    return ["sem_default_opts", "sem_setup", "sem_set_lambda", "sem_set_opts", "sem_skeleton_size",
+            "sem_grid_size", "sem_node_coords", "sem_get_basis", "sem_apply_condensed", "sem_condense_rhs",
+            "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
+            "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_profile_enable",
+            "sem_profile_read", "sem_launch_count",
+            "sem_destroy", "sem_status_string", "sem_last_error"]
+
+
+def _check(status: int, allow=()):
+    if status == SEM_OK or status in allow:
+        return status
+    msg = lib().sem_last_error().decode() or lib().sem_status_string(status).decode()
+    raise SemError(status, msg)
+
+
+def _dptr(t, n=None, name="tensor"):
+    """Device pointer of a contiguous CUDA float64 torch tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float64")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream, ref=None):
+    import torch
+    if stream is None:
+        dev = ref.device if ref is not None else None
+        stream = torch.cuda.current_stream(dev)
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _host(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_D)
+
+
+def default_opts(**kw) -> sem_opts:
+    o = sem_opts()
+    lib().sem_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class SemContext:
+    """Handle returned by sem_setup (owns the C context)."""
+    handle: ctypes.c_void_p
+    p: int
+    m: tuple
+    nb: int
+    n_nodes: int
+    grid_shape: tuple
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().sem_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def sem_setup(p, hx, hy, hz, lam, opts: sem_opts | None = None) -> SemContext:
+    hx, phx = _host(hx)
+    hy, phy = _host(hy)
+    hz, phz = _host(hz)
+    h = ctypes.c_void_p()
+    _check(lib().sem_setup(ctypes.byref(h), int(p), len(hx), len(hy), len(hz), phx, phy, phz, float(lam),
+                           ctypes.byref(opts) if opts is not None else None))
+    nb, nn = ctypes.c_longlong(), ctypes.c_longlong()
+    lib().sem_skeleton_size(h, ctypes.byref(nb))
+    lib().sem_grid_size(h, ctypes.byref(nn))
+    shape = (len(hz) * p + 1, len(hy) * p + 1, len(hx) * p + 1)
+    return SemContext(h, int(p), (len(hx), len(hy), len(hz)), nb.value, nn.value, shape)
+
+
+def sem_set_lambda(ctx: SemContext, lam: float):
+    _check(lib().sem_set_lambda(ctx.handle, float(lam)))
+
+
+def sem_set_opts(ctx: SemContext, opts: sem_opts | None):
+    _check(lib().sem_set_opts(ctx.handle, ctypes.byref(opts) if opts is not None else None))
+
+
+def sem_node_coords(ctx: SemContext):
+    nz, ny, nx = ctx.grid_shape
+    x, y, z = np.empty(nx), np.empty(ny), np.empty(nz)
+    _check(lib().sem_node_coords(ctx.handle, x.ctypes.data_as(_D), y.ctypes.data_as(_D), z.ctypes.data_as(_D)))
+    return x, y, z
+
+
+def sem_get_basis(ctx: SemContext):
+    p, n = ctx.p, ctx.p - 1
+    gx, gw, lam, V = np.empty(p + 1), np.empty(p + 1), np.empty(n), np.empty(n * n)
+    _check(lib().sem_get_basis(ctx.handle, gx.ctypes.data_as(_D), gw.ctypes.data_as(_D), lam.ctypes.data_as(_D),
+                               V.ctypes.data_as(_D)))
+    return gx, gw, lam, V.reshape(n, n)
+
+
+def sem_apply_condensed(ctx: SemContext, uB, vB, space=SPACE_TRANSFORMED, stream=None):
+    _check(lib().sem_apply_condensed(ctx.handle, _dptr(uB, ctx.nb, "uB"), _dptr(vB, ctx.nb, "vB"), int(space),
+                                     _stream(stream, uB)))
+
+
+def sem_condense_rhs(ctx: SemContext, f, fB, space=SPACE_TRANSFORMED, stream=None):
+    _check(lib().sem_condense_rhs(ctx.handle, _dptr(f, ctx.n_nodes, "f"), _dptr(fB, ctx.nb, "fB"), int(space),
+                                  _stream(stream, f)))
+
+
+def sem_precond_diag(ctx: SemContext, diag, stream=None):
+    _check(lib().sem_precond_diag(ctx.handle, _dptr(diag, ctx.nb, "diag"), _stream(stream, diag)))
+
+
+def sem_recover_interior(ctx: SemContext, f, uB, u, space=SPACE_TRANSFORMED, stream=None):
+    _check(lib().sem_recover_interior(ctx.handle, _dptr(f, ctx.n_nodes, "f"), _dptr(uB, ctx.nb, "uB"), int(space),
+                                      _dptr(u, ctx.n_nodes, "u"), _stream(stream, f)))
+
+
+def sem_solve(ctx: SemContext, f, u, u0=None, stream=None, check=True) -> dict:
+    info = sem_info()
+    st = lib().sem_solve(ctx.handle, _dptr(f, ctx.n_nodes, "f"), _dptr(u, ctx.n_nodes, "u"),
+                         _dptr(u0, ctx.nb, "u0") if u0 is not None else None, ctypes.byref(info),
+                         _stream(stream, f))
+    if check:
+        _check(st)
+    return dict(status=st, iters=info.iters, refinements=info.refinements, rel_res=info.rel_res,
+                t_solve_s=info.t_solve_s)
+
+
+def sem_solve_host(ctx: SemContext, f_host: np.ndarray, u_host: np.ndarray, stream=None, check=True) -> dict:
+    if f_host.dtype != np.float64 or not f_host.flags.c_contiguous or f_host.size != ctx.n_nodes:
+        raise TypeError("f_host must be a contiguous float64 array of the grid size")
+    if u_host.dtype != np.float64 or not u_host.flags.c_contiguous or u_host.size != ctx.n_nodes:
+        raise TypeError("u_host must be a contiguous float64 array of the grid size")
+    info = sem_info()
+    st = lib().sem_solve_host(ctx.handle, f_host.ctypes.data_as(_D), u_host.ctypes.data_as(_D), ctypes.byref(info),
+                              _stream(stream))
+    if check:
+        _check(st)
+    return dict(status=st, iters=info.iters, refinements=info.refinements, rel_res=info.rel_res,
+                t_solve_s=info.t_solve_s)
+
+
+def sem_transform_skeleton(ctx: SemContext, inp, out, kind: int, stream=None):
+    _check(lib().sem_transform_skeleton(ctx.handle, _dptr(inp, ctx.nb, "in"), _dptr(out, ctx.nb, "out"), int(kind),
+                                        _stream(stream, inp)))
+
+
+def sem_pack_skeleton(ctx: SemContext, u_full, uB, stream=None):
+    _check(lib().sem_pack_skeleton(ctx.handle, _dptr(u_full, ctx.n_nodes, "u_full"), _dptr(uB, ctx.nb, "uB"),
+                                   _stream(stream, u_full)))
+
+
+def sem_unpack_skeleton(ctx: SemContext, uB, u_full, stream=None):
+    _check(lib().sem_unpack_skeleton(ctx.handle, _dptr(uB, ctx.nb, "uB"), _dptr(u_full, ctx.n_nodes, "u_full"),
+                                     _stream(stream, uB)))
+
+
+def sem_profile_enable(ctx: SemContext, enable: bool = True):
+    _check(lib().sem_profile_enable(ctx.handle, 1 if enable else 0))
+
+
+def sem_profile_read(ctx: SemContext, reset: bool = False):
+    """(summed device milliseconds, number of timed operator launches)."""
+    ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib().sem_profile_read(ctx.handle, ctypes.byref(ms), ctypes.byref(cnt), 1 if reset else 0))
+    return ms.value, cnt.value
+
+
+def sem_launch_count() -> int:
+    return int(lib().sem_launch_count())

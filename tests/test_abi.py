@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/sem.h; argument checks reject bad input before any CUDA call.  CPU only."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1601_08179_gb300 import build, sem
+    build.build()
+    return sem.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sem.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sem_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_expected_entry_points():
+    names = _declared()
+    for must in ("sem_setup", "sem_apply_condensed", "sem_solve", "sem_recover_interior"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    from paper_1601_08179_gb300 import sem
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert set(sem.exported_symbols()) <= set(_declared())
+
+
+def test_argument_checks_without_gpu(L):
+    from paper_1601_08179_gb300 import sem
+    D = sem._D
+    h = ctypes.c_void_p()
+    ok = np.ones(2)
+    bad = np.array([1.0, -1.0])
+    nan = np.array([1.0, np.nan])
+    cases = [
+        (1, ok, ok, ok, 1.0), (33, ok, ok, ok, 1.0), (4, bad, ok, ok, 1.0),
+        (4, ok, nan, ok, 1.0), (4, ok, ok, ok, -1.0), (4, ok, ok, ok, float("inf")),
+    ]
+    for p, hx, hy, hz, lam in cases:
+        st = L.sem_setup(ctypes.byref(h), p, 2, 2, 2, hx.ctypes.data_as(D), hy.ctypes.data_as(D),
+                         hz.ctypes.data_as(D), lam, None)
+        assert st == sem.SEM_EINVAL, (p, lam)
+        assert L.sem_last_error().decode()
+    st = L.sem_setup(ctypes.byref(h), 4, 0, 2, 2, ok.ctypes.data_as(D), ok.ctypes.data_as(D),
+                     ok.ctypes.data_as(D), 1.0, None)
+    assert st == sem.SEM_EINVAL
+    o = sem.default_opts(rtol=2.0)
+    st = L.sem_setup(ctypes.byref(h), 4, 2, 2, 2, ok.ctypes.data_as(D), ok.ctypes.data_as(D),
+                     ok.ctypes.data_as(D), 1.0, ctypes.byref(o))
+    assert st == sem.SEM_EINVAL
+    # null context
+    assert L.sem_apply_condensed(None, None, None, 0, None) == sem.SEM_EINVAL
+    assert L.sem_status_string(sem.SEM_ENOCONV) == b"not converged"
+    L.sem_destroy(None)
+
+
+def test_default_opts(L):
+    from paper_1601_08179_gb300 import sem
+    o = sem.default_opts()
+    assert o.rtol == 1e-10 and o.precision == sem.PREC_FP64 and o.check_every > 0
