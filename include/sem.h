@@ -173,7 +173,11 @@ sem_status sem_recover_interior(sem_ctx* ctx, const double* f, const double* uB,
                                 sem_space space, double* u, void* stream);
 
 /* Full solve (Algorithm 4): condense the load, CG with the BT preconditioner
- * to opts.rtol, recover the interior.  f, u: device full nodal fields; u0:
+ * to opts.rtol, recover the interior.  With opts.precision = SEM_PREC_MIXED the
+ * CG runs in FP32 (FP32 operator, vectors and preconditioner) inside FP64
+ * iterative refinement: each step solves A c = r_k/||r_k|| to opts.inner_rtol
+ * and updates x += ||r_k|| c with the residual r = b - A x recomputed by the
+ * FP64 operator; the stopping rule is the FP64 residual.  f, u: device full nodal fields; u0:
  * optional device skeleton start vector in NODAL space (NULL = 0); info may be
  * NULL.  Returns SEM_ENOCONV / SEM_EBREAKDOWN with u still written. */
 sem_status sem_solve(sem_ctx* ctx, const double* f, double* u, const double* u0,
@@ -199,6 +203,12 @@ sem_status sem_transform_skeleton(sem_ctx* ctx, const double* in, double* out,
  * untouched).  Device pointers.  Asynchronous. */
 sem_status sem_pack_skeleton(sem_ctx* ctx, const double* u_full, double* uB, void* stream);
 sem_status sem_unpack_skeleton(sem_ctx* ctx, const double* uB, double* u_full, void* stream);
+
+/* Residual history of the last MIXED solve: rel_res[k] = ||b - A x_k|| / ||b||
+ * (FP64, transformed condensed space) before refinement step k and after the
+ * last one; *count = number of entries (up to max_refine + 1).  HOST array of
+ * `capacity` entries; at most `capacity` are written. */
+sem_status sem_refine_history(const sem_ctx* ctx, double* rel_res, int capacity, int* count);
 
 /* Kernel timing inside sem_solve.  While enabled, every launch of the condensed
  * operator kernel inside the solver's CG iteration is bracketed by CUDA events

@@ -83,6 +83,17 @@ struct sem_ctx {
   long long prof_count = 0;
   SemClassTables<double> tab{};
 
+  // mixed precision (FP32 inner CG), allocated on first use
+  float *d_dcoef_f = nullptr, *d_dinv_f = nullptr, *d_P32 = nullptr;
+  float *d_b32 = nullptr, *d_x32 = nullptr, *d_r32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr;
+  PcgState* d_st32 = nullptr;
+  SemClassTables<float> tab_f{};
+  cudaGraphExec_t graph32 = nullptr;
+  int graph32_iters = 0;
+  bool graph32_prof = false;
+  std::vector<cudaEvent_t> pev32;
+  std::vector<double> refine_hist;     // ||b - A x_k|| / ||b|| after each refinement step
+
   const double* mat(int k) const { return d_mats + (size_t)k * g.n * g.n; }
 };
 
@@ -131,6 +142,8 @@ bool valid_widths(const double* h, int m) {
   return true;
 }
 
+sem_status cast_tables_f32(sem_ctx* c, cudaStream_t s);
+
 sem_status compute_tables(sem_ctx* c, cudaStream_t s) {
   const SemGeom& g = c->g;
   launch_class_tables(g, c->h1.basis, c->d_uw, c->d_uw + g.ux, c->d_uw + g.ux + g.uy, c->lambda, c->d_dcoef,
@@ -139,6 +152,43 @@ sem_status compute_tables(sem_ctx* c, cudaStream_t s) {
   SEM_CUDA(cudaMemsetAsync(c->d_t1, 0, sizeof(double) * g.nb, s));
   launch_precond_diag(g, c->h1.basis, c->tab, c->d_t1, s);
   launch_invert_diag(g, c->d_t1, c->d_P, s);
+  SEM_CUDA(cudaGetLastError());
+  if (c->d_st32 != nullptr) return cast_tables_f32(c, s);
+  return SEM_OK;
+}
+
+sem_status cast_tables_f32(sem_ctx* c, cudaStream_t s) {
+  const SemGeom& g = c->g;
+  const long long ncls = (long long)g.ux * g.uy * g.uz;
+  launch_cast_f32(ncls * 4, c->d_dcoef, c->d_dcoef_f, s);
+  launch_cast_f32(ncls * (long long)g.n * g.n * g.n, c->d_dinv, c->d_dinv_f, s);
+  launch_cast_f32(g.nb, c->d_P, c->d_P32, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status ensure_mixed(sem_ctx* c) {
+  if (c->d_st32 != nullptr) return SEM_OK;
+  const SemGeom& g = c->g;
+  const long long ncls = (long long)g.ux * g.uy * g.uz;
+  bool ok = dalloc(&c->d_dcoef_f, ncls * 4) == cudaSuccess &&
+            dalloc(&c->d_dinv_f, ncls * (long long)g.n * g.n * g.n) == cudaSuccess &&
+            dalloc(&c->d_P32, g.nb) == cudaSuccess && dalloc(&c->d_b32, g.nb) == cudaSuccess &&
+            dalloc(&c->d_x32, g.nb) == cudaSuccess && dalloc(&c->d_r32, g.nb) == cudaSuccess &&
+            dalloc(&c->d_p32, g.nb) == cudaSuccess && dalloc(&c->d_q32, g.nb) == cudaSuccess &&
+            dalloc(&c->d_st32, 1) == cudaSuccess;
+  if (!ok) return fail(SEM_ENOMEM, "cannot allocate mixed-precision buffers");
+  SEM_CUDA(cudaMemsetAsync(c->d_st32, 0, sizeof(PcgState), c->stream));
+  c->tab_f.cls_x = c->tab.cls_x;
+  c->tab_f.cls_y = c->tab.cls_y;
+  c->tab_f.cls_z = c->tab.cls_z;
+  c->tab_f.dcoef = c->d_dcoef_f;
+  c->tab_f.dinv = c->d_dinv_f;
+  sem_status st = cast_tables_f32(c, c->stream);
+  if (st != SEM_OK) return st;
+  // operator kernel attributes outside any capture
+  SEM_CUDA(cudaMemsetAsync(c->d_q32, 0, sizeof(float) * g.nb, c->stream));
+  launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_P32, c->d_q32, nullptr, nullptr, c->stream);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -269,12 +319,133 @@ sem_status pcg_fp64(sem_ctx* c, bool warm, sem_info* info) {
   return SEM_OK;
 }
 
+sem_status build_graph32(sem_ctx* c) {
+  if (c->graph32 != nullptr && c->graph32_iters == c->opts.check_every && c->graph32_prof == c->prof) return SEM_OK;
+  while (c->prof && (int)c->pev32.size() < 2 * c->opts.check_every) {
+    cudaEvent_t ev;
+    SEM_CUDA(cudaEventCreate(&ev));
+    c->pev32.push_back(ev);
+  }
+  if (c->graph32 != nullptr) {
+    cudaGraphExecDestroy(c->graph32);
+    c->graph32 = nullptr;
+  }
+  const SemGeom& g = c->g;
+  cudaGraph_t graph;
+  SEM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  const long long before = sem_launch_total();
+  for (int it = 0; it < c->opts.check_every; ++it) {
+    if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it], c->stream, cudaEventRecordExternal);
+    launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, c->stream);
+    if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it + 1], c->stream, cudaEventRecordExternal);
+    launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32,
+                             c->stream);
+    launch_pcg_dir<float>(g.nb, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, c->stream);
+  }
+  sem_count_launch(-(sem_launch_total() - before));
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph32, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  c->graph32_iters = c->opts.check_every;
+  c->graph32_prof = c->prof;
+  return SEM_OK;
+}
+
+// Iterative refinement: x_{k+1} = x_k + ||r_k|| c_k, where c_k solves
+// A c = r_k / ||r_k|| by FP32 CG to a relative residual inner_rtol, and
+// r_{k+1} = b - A x_{k+1} is formed with the FP64 operator.  d_b -> d_x.
+sem_status pcg_mixed(sem_ctx* c, bool warm, sem_info* info) {
+  const SemGeom& g = c->g;
+  cudaStream_t s = c->stream;
+  sem_status st = ensure_mixed(c);
+  if (st != SEM_OK) return st;
+  st = build_graph32(c);
+  if (st != SEM_OK) return st;
+  c->refine_hist.clear();
+  if (warm) {
+    st = apply_t(c, c->d_x, c->d_q, s);
+  } else {
+    SEM_CUDA(cudaMemsetAsync(c->d_x, 0, sizeof(double) * g.nb, s));
+    SEM_CUDA(cudaMemsetAsync(c->d_q, 0, sizeof(double) * g.nb, s));
+  }
+  if (st != SEM_OK) return st;
+  // ||b|| as the reference of the stopping rule
+  SEM_CUDA(cudaMemsetAsync(c->d_t2, 0, sizeof(double) * g.nb, s));
+  launch_ir_residual(g.nb, c->d_b, c->d_t2, c->d_r, c->d_partials, c->d_st, s);
+  SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  const double bb = c->h_st->rr;
+  launch_ir_residual(g.nb, c->d_b, c->d_q, c->d_r, c->d_partials, c->d_st, s);
+  int total = 0, refinements = 0;
+  double rel = 1.0, prev = 1e300;
+  sem_status result = SEM_ENOCONV;
+  for (;;) {
+    SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    const double rr = c->h_st->rr;
+    if (!std::isfinite(rr)) { result = SEM_EBREAKDOWN; break; }
+    rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    c->refine_hist.push_back(rel);
+    if (rel <= c->opts.rtol) { result = SEM_OK; break; }
+    if (refinements >= c->opts.max_refine || total >= c->opts.maxit) break;
+    if (!(rel < 0.9 * prev)) break;   // refinement stagnated at the FP32 accuracy limit
+    prev = rel;
+    const double norm = std::sqrt(rr);
+    launch_scale_to_f32(g.nb, c->d_r, 1.0 / norm, c->d_b32, s);
+    launch_pcg_init<float>(g.nb, c->d_b32, c->d_r32, c->d_p32, c->d_q32, c->d_x32, c->d_P32, c->d_partials,
+                           c->d_st32, c->opts.inner_rtol, c->opts.maxit - total, 0, s);
+    SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < c->opts.maxit / c->opts.check_every + 2 && c->h_st->done == 0; ++b) {
+      const int it0 = c->h_st->iter;
+      SEM_CUDA(cudaGraphLaunch(c->graph32, s));
+      sem_count_launch(3LL * c->graph32_iters);
+      SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+      SEM_CUDA(cudaStreamSynchronize(s));
+      if (c->graph32_prof) {
+        int worked = c->h_st->iter - it0 + (c->h_st->done == 2 ? 1 : 0);
+        if (worked > c->graph32_iters) worked = c->graph32_iters;
+        for (int it = 0; it < worked; ++it) {
+          float ms = 0.f;
+          SEM_CUDA(cudaEventElapsedTime(&ms, c->pev32[2 * it], c->pev32[2 * it + 1]));
+          c->prof_ms += ms;
+          c->prof_count += 1;
+        }
+      }
+    }
+    const int inner = c->h_st->iter;
+    total += inner;
+    ++refinements;
+    if (c->h_st->done == 2 && inner == 0) { result = SEM_EBREAKDOWN; break; }
+    launch_ir_update(g.nb, c->d_x, c->d_x32, norm, s);
+    st = apply_t(c, c->d_x, c->d_q, s);
+    if (st != SEM_OK) return st;
+    launch_ir_residual(g.nb, c->d_b, c->d_q, c->d_r, c->d_partials, c->d_st, s);
+    SEM_CUDA(cudaGetLastError());
+  }
+  if (info) {
+    info->iters += total;
+    info->refinements = refinements;
+    info->rel_res = rel;
+  }
+  if (result == SEM_EBREAKDOWN) return fail(result, "CG breakdown or non-finite residual in the refinement");
+  if (result != SEM_OK) return fail(result, "refinement did not reach rtol (maxit, max_refine or stagnation)");
+  return SEM_OK;
+}
+
 void free_ctx(sem_ctx* c) {
   if (c == nullptr) return;
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph32) cudaGraphExecDestroy(c->graph32);
+  void* ptrs32[] = {c->d_dcoef_f, c->d_dinv_f, c->d_P32, c->d_b32, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_st32};
+  for (void* p : ptrs32)
+    if (p) cudaFree(p);
+  for (cudaEvent_t ev : c->pev32) cudaEventDestroy(ev);
   void* ptrs[] = {c->d_cls, c->d_uw, c->d_dcoef, c->d_dinv, c->d_mats, c->d_mass, c->d_P, c->d_x, c->d_r,
                   c->d_p, c->d_q, c->d_b, c->d_t1, c->d_t2, c->d_c0, c->d_c1, c->d_FtI, c->d_partials, c->d_st};
   for (void* p : ptrs)
@@ -567,7 +738,6 @@ sem_status sem_solve(sem_ctx* c, const double* f, double* u, const double* u0, s
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   if (f == nullptr || u == nullptr) return fail(SEM_EINVAL, "null vector");
-  if (c->opts.precision != SEM_PREC_FP64) return fail(SEM_ENOTSUP, "precision mode not available");
   const auto t0 = std::chrono::steady_clock::now();
   if (info) std::memset(info, 0, sizeof(*info));
   cudaStream_t us = (cudaStream_t)stream;
@@ -577,7 +747,8 @@ sem_status sem_solve(sem_ctx* c, const double* f, double* u, const double* u0, s
   sem_status st = condense_rhs_t(c, f, c->d_b, s);
   if (st != SEM_OK) return st;
   if (u0) launch_skel_transform(c->g, c->mat(2), u0, c->d_x, s);
-  sem_status cg = pcg_fp64(c, u0 != nullptr, info);
+  sem_status cg = c->opts.precision == SEM_PREC_MIXED ? pcg_mixed(c, u0 != nullptr, info)
+                                                     : pcg_fp64(c, u0 != nullptr, info);
   if (cg != SEM_OK && cg != SEM_ENOCONV && cg != SEM_EBREAKDOWN) return cg;
   std::string cg_err = t_err;
   st = recover_t(c, c->d_x, u, s);
@@ -665,6 +836,15 @@ sem_status sem_profile_read(sem_ctx* c, double* apply_ms, long long* apply_launc
     c->prof_ms = 0.0;
     c->prof_count = 0;
   }
+  return SEM_OK;
+}
+
+sem_status sem_refine_history(const sem_ctx* c, double* rel_res, int capacity, int* count) {
+  if (c == nullptr || count == nullptr || (capacity > 0 && rel_res == nullptr))
+    return fail(SEM_EINVAL, "null argument");
+  const int n = (int)c->refine_hist.size();
+  *count = n;
+  for (int i = 0; i < n && i < capacity; ++i) rel_res[i] = c->refine_hist[i];
   return SEM_OK;
 }
 

@@ -803,25 +803,28 @@ __global__ void k_recover_expand(SemGeom g, SemBasis b, SemClassTables<double> t
 // ---------------------------------------------------------------------------
 // CG vector kernels
 // ---------------------------------------------------------------------------
+// Per-thread partial sums are kept in T (FP32 for the inner solver, whose
+// scalars need only FP32 accuracy) and combined across the grid in FP64.
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-k_pcg_init(long long nb, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ p,
-           double* __restrict__ q, double* __restrict__ x, const double* __restrict__ P,
+k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restrict__ p,
+           T* __restrict__ q, T* __restrict__ x, const T* __restrict__ P,
            double* __restrict__ partials, PcgState* st, double rtol, int maxit, int keep_x, int have_q) {
-  double rz = 0.0, rr = 0.0, bb = 0.0;
+  T rz = T(0), rr = T(0), bb = T(0);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
-    const double bi = b[i];
-    const double ri = have_q ? bi - q[i] : bi;
-    const double zi = P[i] * ri;
+    const T bi = b[i];
+    const T ri = have_q ? bi - q[i] : bi;
+    const T zi = P[i] * ri;
     r[i] = ri;
     p[i] = zi;
-    q[i] = 0.0;
-    if (!keep_x) x[i] = 0.0;
+    q[i] = T(0);
+    if (!keep_x) x[i] = T(0);
     rz = fma(ri, zi, rz);
     rr = fma(ri, ri, rr);
     bb = fma(bi, bi, bb);
   }
   // the stopping rule is relative to ||b|| (= ||r_0|| for a zero start)
-  double v[3] = {rz, rr, bb}, tot[3];
+  double v[3] = {(double)rz, (double)rr, (double)bb}, tot[3];
   if (reduce_grid<3>(v, partials, &st->counter[1], tot) && threadIdx.x == 0) {
     st->rho = tot[0];
     st->rr = tot[1];
@@ -836,21 +839,22 @@ k_pcg_init(long long nb, const double* __restrict__ b, double* __restrict__ r, d
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-k_pcg_update(long long nb, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-             const double* __restrict__ q, const double* __restrict__ P, double* __restrict__ partials,
+k_pcg_update(long long nb, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+             const T* __restrict__ q, const T* __restrict__ P, double* __restrict__ partials,
              PcgState* st) {
   if (st->done) return;
-  const double alpha = st->alpha;
-  double rz = 0.0, rr = 0.0;
+  const T alpha = (T)st->alpha;
+  T rz = T(0), rr = T(0);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
-    const double ri = fma(-alpha, q[i], r[i]);
+    const T ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
     rz = fma(ri, P[i] * ri, rz);
     rr = fma(ri, ri, rr);
   }
-  double v[2] = {rz, rr}, tot[2];
+  double v[2] = {(double)rz, (double)rr}, tot[2];
   if (reduce_grid<2>(v, partials, &st->counter[2], tot) && threadIdx.x == 0) {
     const int it = st->iter + 1;
     st->iter = it;
@@ -869,15 +873,44 @@ k_pcg_update(long long nb, double* __restrict__ x, double* __restrict__ r, const
   }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-k_pcg_dir(long long nb, const double* __restrict__ r, double* __restrict__ p, double* __restrict__ q,
-          const double* __restrict__ P, PcgState* st) {
+k_pcg_dir(long long nb, const T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
+          const T* __restrict__ P, PcgState* st) {
   if (st->done) return;
-  const double beta = st->beta;
+  const T beta = (T)st->beta;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
     p[i] = fma(beta, p[i], P[i] * r[i]);
-    q[i] = 0.0;
+    q[i] = T(0);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Iterative refinement (FP64 outer loop around the FP32 inner CG)
+// ---------------------------------------------------------------------------
+// r = b - Ax (FP64), rr = r.r -> st->rr; r32 = r * scale is written later.
+__global__ void __launch_bounds__(kVecThreads)
+k_ir_residual(long long nb, const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
+              double* __restrict__ partials, PcgState* st) {
+  double rr = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = b[i] - Ax[i];
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+  }
+  double v[1] = {rr}, tot[1];
+  if (reduce_grid<1>(v, partials, &st->counter[3], tot) && threadIdx.x == 0) st->rr = tot[0];
+}
+
+__global__ void k_scale_to_f32(long long nb, const double* __restrict__ in, double scale, float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)(in[i] * scale);
+}
+
+// x += scale * (double) c
+__global__ void k_ir_update(long long nb, double* __restrict__ x, const float* __restrict__ c, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(scale, (double)c[i], x[i]);
 }
 
 int g_num_sms = 0;
@@ -926,21 +959,36 @@ ApplyConfig sem_apply_config(int n, size_t elem_bytes) {
   return c;
 }
 
-void launch_tpt_apply_f64(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
-                          const double* x, double* y, double* partials, PcgState* st, cudaStream_t s) {
-  const ApplyConfig c = sem_apply_config(g.n, sizeof(double));
+template <typename T>
+void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
+                      double* partials, PcgState* st, cudaStream_t s) {
+  const ApplyConfig c = sem_apply_config(g.n, sizeof(T));
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tpt_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_tpt_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply<double>, c.threads, c.smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply<T>, c.threads, c.smem);
   if (occ < 1) occ = 1;
   const long long ntiles = (g.nelem + c.epb - 1) / c.epb;
   long long grid = (long long)num_sms() * occ;
   if (grid > ntiles) grid = ntiles;
-  k_tpt_apply<double><<<(int)grid, c.threads, c.smem, s>>>(g, b, t, x, y, c.epb, c.ks, partials, st);
+  k_tpt_apply<T><<<(int)grid, c.threads, c.smem, s>>>(g, b, t, x, y, c.epb, c.ks, partials, st);
+  sem_count_launch();
+}
+template void launch_tpt_apply<double>(const SemGeom&, const SemBasis&, const SemClassTables<double>&,
+                                       const double*, double*, double*, PcgState*, cudaStream_t);
+template void launch_tpt_apply<float>(const SemGeom&, const SemBasis&, const SemClassTables<float>&,
+                                      const float*, float*, double*, PcgState*, cudaStream_t);
+
+void launch_tpt_apply_f64(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t, const double* x,
+                          double* y, double* partials, PcgState* st, cudaStream_t s) {
+  launch_tpt_apply<double>(g, b, t, x, y, partials, st, s);
+}
+
+void launch_cast_f32(long long n, const double* in, float* out, cudaStream_t s) {
+  k_scale_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, in, 1.0, out);
   sem_count_launch();
 }
 
@@ -1027,22 +1075,48 @@ void launch_unpack(const SemGeom& g, const double* uB, double* full, int zero_di
   sem_count_launch();
 }
 
-void launch_pcg_init(long long nb, const double* b, double* r, double* p, double* q, double* x,
-                     const double* P, double* partials, PcgState* st, double rtol, int maxit, int keep_x,
-                     cudaStream_t s) {
-  k_pcg_init<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, b, r, p, q, x, P, partials, st, rtol, maxit, keep_x,
-                                                      keep_x);
+template <typename T>
+void launch_pcg_init(long long nb, const T* b, T* r, T* p, T* q, T* x, const T* P, double* partials,
+                     PcgState* st, double rtol, int maxit, int keep_x, cudaStream_t s) {
+  k_pcg_init<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, b, r, p, q, x, P, partials, st, rtol, maxit, keep_x,
+                                                         keep_x);
   sem_count_launch();
 }
 
-void launch_pcg_update(long long nb, double* x, double* r, const double* p, const double* q, const double* P,
-                       double* partials, PcgState* st, cudaStream_t s) {
-  k_pcg_update<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, r, p, q, P, partials, st);
+template <typename T>
+void launch_pcg_update(long long nb, T* x, T* r, const T* p, const T* q, const T* P, double* partials,
+                       PcgState* st, cudaStream_t s) {
+  k_pcg_update<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, r, p, q, P, partials, st);
   sem_count_launch();
 }
 
-void launch_pcg_dir(long long nb, const double* r, double* p, double* q, const double* P, PcgState* st,
-                    cudaStream_t s) {
-  k_pcg_dir<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, p, q, P, st);
+template <typename T>
+void launch_pcg_dir(long long nb, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s) {
+  k_pcg_dir<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, p, q, P, st);
+  sem_count_launch();
+}
+
+#define SEM_INST_VEC(T)                                                                                       \
+  template void launch_pcg_init<T>(long long, const T*, T*, T*, T*, T*, const T*, double*, PcgState*, double, \
+                                   int, int, cudaStream_t);                                                   \
+  template void launch_pcg_update<T>(long long, T*, T*, const T*, const T*, const T*, double*, PcgState*,     \
+                                     cudaStream_t);                                                           \
+  template void launch_pcg_dir<T>(long long, const T*, T*, T*, const T*, PcgState*, cudaStream_t);
+SEM_INST_VEC(double)
+SEM_INST_VEC(float)
+
+void launch_ir_residual(long long nb, const double* b, const double* Ax, double* r, double* partials,
+                        PcgState* st, cudaStream_t s) {
+  k_ir_residual<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, b, Ax, r, partials, st);
+  sem_count_launch();
+}
+
+void launch_scale_to_f32(long long n, const double* in, double scale, float* out, cudaStream_t s) {
+  k_scale_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, in, scale, out);
+  sem_count_launch();
+}
+
+void launch_ir_update(long long nb, double* x, const float* c, double scale, cudaStream_t s) {
+  k_ir_update<<<grid_for(nb, 256), 256, 0, s>>>(nb, x, c, scale);
   sem_count_launch();
 }

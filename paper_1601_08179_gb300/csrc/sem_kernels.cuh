@@ -88,15 +88,31 @@ void launch_pack(const SemGeom& g, const double* full, double* uB, cudaStream_t 
 // domain-boundary nodes instead of the input value.
 void launch_unpack(const SemGeom& g, const double* uB, double* full, int zero_dirichlet, cudaStream_t s);
 
-// ---- CG vector kernels (FP64) ----
-// r = b - q (q may be null: r = b); z = P r; p = z; x = 0 unless keep_x; q = 0;
-// rho = r.z, rr0 = r.r, tol2 = rtol^2 rr0.
-void launch_pcg_init(long long nb, const double* b, double* r, double* p, double* q, double* x,
-                     const double* P, double* partials, PcgState* st, double rtol, int maxit,
-                     int keep_x, cudaStream_t s);
-void launch_pcg_update(long long nb, double* x, double* r, const double* p, const double* q,
-                       const double* P, double* partials, PcgState* st, cudaStream_t s);
-void launch_pcg_dir(long long nb, const double* r, double* p, double* q, const double* P,
-                    PcgState* st, cudaStream_t s);
+// ---- CG vector kernels (T = double, or float for the inner solver) ----
+// r = b - q (keep_x: q = A x0 on entry) else r = b and x = 0; z = P r; p = z;
+// q = 0; rho = r.z, rr = r.r, rr0 = b.b, tol2 = rtol^2 rr0.
+template <typename T>
+void launch_pcg_init(long long nb, const T* b, T* r, T* p, T* q, T* x, const T* P, double* partials,
+                     PcgState* st, double rtol, int maxit, int keep_x, cudaStream_t s);
+// alpha from st: x += alpha p, r -= alpha q; rho_new = r.P r, rr = r.r; convergence test.
+template <typename T>
+void launch_pcg_update(long long nb, T* x, T* r, const T* p, const T* q, const T* P, double* partials,
+                       PcgState* st, cudaStream_t s);
+// p = P r + beta p, q = 0.
+template <typename T>
+void launch_pcg_dir(long long nb, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s);
+
+// Generic operator launcher (T = double or float tables and vectors).
+template <typename T>
+void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
+                      double* partials, PcgState* st, cudaStream_t s);
+
+// Iterative refinement: r = b - Ax and st->rr = r.r (FP64); out = (float)(in * scale);
+// x += scale * c.
+void launch_ir_residual(long long nb, const double* b, const double* Ax, double* r, double* partials,
+                        PcgState* st, cudaStream_t s);
+void launch_scale_to_f32(long long n, const double* in, double scale, float* out, cudaStream_t s);
+void launch_ir_update(long long nb, double* x, const float* c, double scale, cudaStream_t s);
+void launch_cast_f32(long long n, const double* in, float* out, cudaStream_t s);
 
 int sem_vec_blocks();

@@ -74,6 +74,7 @@ def lib():
         "sem_transform_skeleton": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
         "sem_pack_skeleton": (ctypes.c_int, [_P, _P, _P, _P]),
         "sem_unpack_skeleton": (ctypes.c_int, [_P, _P, _P, _P]),
+        "sem_refine_history": (ctypes.c_int, [_P, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "sem_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
         "sem_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                             ctypes.c_int]),
@@ -95,7 +96,8 @@ def exported_symbols():
     return ["sem_default_opts", "sem_setup", "sem_set_lambda", "sem_set_opts", "sem_skeleton_size",
             "sem_grid_size", "sem_node_coords", "sem_get_basis", "sem_apply_condensed", "sem_condense_rhs",
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
-            "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_profile_enable",
+            "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
+            "sem_profile_enable",
             "sem_profile_read", "sem_launch_count",
             "sem_destroy", "sem_status_string", "sem_last_error"]
 
@@ -253,6 +255,14 @@ def sem_pack_skeleton(ctx: SemContext, u_full, uB, stream=None):
 def sem_unpack_skeleton(ctx: SemContext, uB, u_full, stream=None):
     _check(lib().sem_unpack_skeleton(ctx.handle, _dptr(uB, ctx.nb, "uB"), _dptr(u_full, ctx.n_nodes, "u_full"),
                                      _stream(stream, uB)))
+
+
+def sem_refine_history(ctx: SemContext):
+    """Relative FP64 residuals of the last mixed-precision solve, per refinement step."""
+    buf = np.empty(256)
+    cnt = ctypes.c_int()
+    _check(lib().sem_refine_history(ctx.handle, buf.ctypes.data_as(_D), len(buf), ctypes.byref(cnt)))
+    return buf[:min(cnt.value, len(buf))].copy()
 
 
 def sem_profile_enable(ctx: SemContext, enable: bool = True):
