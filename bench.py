@@ -36,6 +36,19 @@ METRIC = "condensed-operator GDOF/s; PCG s/DOF to 1e-10, chosen form vs plain FP
 UNIT = "s/DOF"
 # FP64 ceiling of the GB300: 152 SMs x 2 DFMA/clock x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 ceiling: 152 SMs x 128 FMA/clock x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0     # fallback figure for a GB300 copy
+
+
+HBM_GBS = _measured_hbm()
 L2_BYTES = 129e6
 
 
@@ -50,6 +63,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
+                    help="'both': time the plain FP64 solve and the mixed-precision solve (the headline)")
     return ap.parse_args()
 
 
@@ -198,6 +213,35 @@ def oracle_sample(w: si.Workload, iterations: int, target_s: float = 12.0):
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def time_solves(sem, ctx, f, u, steps, warmup, world, local_rank):
+    """Times `steps` solves after `warmup`, CUDA events on the caller's stream,
+    clocks sampled during the timed region.  Returns a dict."""
+    import torch
+    sem.sem_profile_enable(ctx, True)
+    for _ in range(warmup):
+        sem.sem_solve(ctx, f, u)
+    sem.sem_profile_read(ctx, reset=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = sem.sem_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            infos.append(sem.sem_solve(ctx, f, u))
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = sem.sem_launch_count() - launches0
+    step_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / steps, world)
+    apply_ms, apply_n = sem.sem_profile_read(ctx, reset=True)
+    return {"step_s": step_s, "info": infos[-1], "apply_s": apply_ms / 1e3 / max(apply_n, 1),
+            "apply_n": apply_n, "launches": launches, "clocks": clk.summary()}
+
+
 def our_arm(args, rank, world, local_rank):
     import torch
 
@@ -215,29 +259,18 @@ def our_arm(args, rank, world, local_rank):
     f_host = node_field(x, y, z, w, seed)
     f = torch.from_numpy(f_host).cuda()
     u = torch.empty_like(f)
-    sem.sem_profile_enable(ctx, True)
-    for _ in range(args.warmup):
-        sem.sem_solve(ctx, f, u)
-    sem.sem_profile_read(ctx, reset=True)
-    torch.cuda.synchronize()
-    barrier(world)
-    launches0 = sem.sem_launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    infos = []
-    with ClockSampler(local_rank) as clk:
-        torch.cuda.synchronize()
-        ev0.record()
-        for _ in range(args.steps):
-            infos.append(sem.sem_solve(ctx, f, u))
-        ev1.record()
-        torch.cuda.synchronize()
-    barrier(world)
-    launches = sem.sem_launch_count() - launches0
-    step_s = ev0.elapsed_time(ev1) / 1e3 / args.steps
-    step_s = max_over_ranks(step_s, world)
-    apply_ms, apply_n = sem.sem_profile_read(ctx, reset=True)
-    apply_avg_s = apply_ms / 1e3 / max(apply_n, 1)
+
+    forms = {"fp64": sem.default_opts(), "mixed": sem.default_opts(precision=sem.PREC_MIXED)}
+    order = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    res = {}
+    for form in order:
+        sem.sem_set_opts(ctx, forms[form])
+        res[form] = time_solves(sem, ctx, f, u, args.steps, args.warmup, world, local_rank)
+        if form == "mixed":
+            res[form]["refine_hist"] = [float(v) for v in sem.sem_refine_history(ctx)]
+    head = order[-1]          # the chosen form: mixed unless only fp64 was asked for
+    r = res[head]
+    sem.sem_set_opts(ctx, forms[head])
 
     # end to end through the host-buffer entry point: H2D f, solve, D2H u
     e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
@@ -253,45 +286,73 @@ def our_arm(args, rank, world, local_rank):
             sem.sem_solve_host(ctx, f_pin, u_pin)
         e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
 
-    iters = infos[-1]["iters"]
     flops = apply_flops(w)
-    achieved = flops / apply_avg_s / 1e12
+    nb = ctx.nb
+    if head == "fp64":
+        achieved = flops / r["apply_s"] / 1e12
+        roof = {"kernel": "k_tpt_apply<double>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA units x SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "flops_per_launch": flops}
+    else:
+        # FP32 operator: flops and bytes both near their ridge; report the
+        # bound whose floor is larger
+        t_alu = flops / (FP32_PEAK_TFLOPS * 1e12)
+        t_hbm = 8.0 * nb / (HBM_GBS * 1e9)
+        if t_alu >= t_hbm:
+            achieved = flops / r["apply_s"] / 1e12
+            roof = {"kernel": "k_tpt_apply<float>", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "FP32 FMA units x SM clock (152 SMs x 128 FMA/clk x 2.07 GHz)",
+                    "flops_per_launch": flops}
+        else:
+            achieved = 8.0 * nb / r["apply_s"] / 1e9
+            roof = {"kernel": "k_tpt_apply<float>", "bound": "hbm", "achieved": achieved, "peak": HBM_GBS,
+                    "unit": "GB/s", "frac": achieved / HBM_GBS, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)", "bytes_per_launch": 8.0 * nb}
     out = {
         "metric": METRIC,
-        "value": step_s / (w.dofs * world),
+        "value": r["step_s"] / (w.dofs * world),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": step_s * 1e3,
+        "ms_per_step": r["step_s"] * 1e3,
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if head == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "dofs_per_gpu": w.dofs,
-                   "skeleton_unknowns": ctx.nb, "lambda": w.lam, "aspect_ratio": w.ar, "rtol": 1e-10,
-                   "precision": "fp64", "parallelism": f"replicas{world}",
+                   "skeleton_unknowns": nb, "lambda": w.lam, "aspect_ratio": w.ar, "rtol": 1e-10,
+                   "precision": head, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (solve working set > 129 MB)"},
-        "solve": {"iters": iters, "rel_res": infos[-1]["rel_res"], "setup_s": setup_s,
-                  "s_per_iteration": step_s / max(iters, 1)},
-        "operator": {"gdof_s": w.dofs / apply_avg_s / 1e9, "apply_ms": apply_avg_s * 1e3,
-                     "timed_launches": apply_n, "dtype": "f64"},
-        "roofline": {"kernel": "k_tpt_apply<double>", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None,
-                     "peak_source": "FP64 FMA units x SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                     "flops_per_launch": flops},
+        "solve": {"iters": r["info"]["iters"], "refinements": r["info"]["refinements"],
+                  "rel_res": r["info"]["rel_res"], "setup_s": setup_s},
+        "operator": {"gdof_s": w.dofs / r["apply_s"] / 1e9, "apply_ms": r["apply_s"] * 1e3,
+                     "timed_launches": r["apply_n"], "dtype": "f64" if head == "fp64" else "f32"},
+        "roofline": roof,
         "e2e": {"value": e2e_s / (w.dofs * world) if e2e_s else None, "unit": UNIT,
                 "h2d_bytes_per_step": f_host.nbytes, "d2h_bytes_per_step": f_host.nbytes},
-        "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
     }
+    if "mixed" in res:
+        out["solve"]["refine_hist"] = res["mixed"]["refine_hist"]
+    if "fp64" in res and head != "fp64":
+        p64 = res["fp64"]
+        out["fp64"] = {"value": p64["step_s"] / (w.dofs * world), "ms_per_step": p64["step_s"] * 1e3,
+                       "iters": p64["info"]["iters"], "operator_gdof_s": w.dofs / p64["apply_s"] / 1e9,
+                       "operator_ms": p64["apply_s"] * 1e3,
+                       "operator_frac_fp64_peak": flops / p64["apply_s"] / 1e12 / FP64_PEAK_TFLOPS,
+                       "clocks": p64["clocks"]}
+        out["speedup_vs_fp64"] = p64["step_s"] / r["step_s"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_iters = reference_iterations(w)
+        iters = res["fp64"]["info"]["iters"] if "fp64" in res else r["info"]["iters"]
         out["cpu_baseline"] = oracle_sample(w, ref_iters if ref_iters is not None else iters)
         if ref_iters is None:
-            out["cpu_baseline"]["sample"] += " (iteration count of this GPU solve; no oracle solve recorded)"
+            out["cpu_baseline"]["sample"] += " (iteration count of this GPU FP64 solve; no oracle solve recorded)"
     if rank == 0:
         print(json.dumps(out), flush=True)
 
