@@ -204,6 +204,28 @@ sem_status sem_transform_skeleton(sem_ctx* ctx, const double* in, double* out,
 sem_status sem_pack_skeleton(sem_ctx* ctx, const double* u_full, double* uB, void* stream);
 sem_status sem_unpack_skeleton(sem_ctx* ctx, const double* uB, double* u_full, void* stream);
 
+/* sem_condense_rhs without any memory allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory at the time of the call -- for example code
+ * running while a CUDA stream is being captured into a graph (where
+ * cudaMalloc is not part of the capture), or applications whose device memory
+ * is fully reserved by their own pool.  sem_condense_rhs allocates its
+ * element-interior scratch with cudaMalloc on first use; this variant calls no
+ * cudaMalloc, cudaFree or other allocating routine and instead uses a fixed
+ * scratch array compiled into the library (12 MiB, held by every GPU that
+ * loads the library until the process exits).
+ *   ctx, f, fB, space, stream: as for sem_condense_rhs (same result).
+ *   Limit: elements * (p-1)^3 <= 524288 (e.g. p = 8 on 8^3 elements, p = 4 on
+ *   16^3); larger meshes are rejected with SEM_EINVAL and a message.
+ * The first call on each device looks up the scratch array's device address;
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU (different streams, or concurrent host
+ * threads) race on it and must be serialised by the caller.  Nothing needs to
+ * be cleared between calls.  Asynchronous on `stream`. */
+sem_status sem_condense_rhs_noalloc(sem_ctx* ctx, const double* f, double* fB,
+                                    sem_space space, void* stream);
+
 /* Residual history of the last MIXED solve: rel_res[k] = ||b - A x_k|| / ||b||
  * (FP64, transformed condensed space) before refinement step k and after the
  * last one; *count = number of entries (up to max_refine + 1).  HOST array of

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -868,3 +869,72 @@ const char* sem_status_string(sem_status s) {
 const char* sem_last_error(void) { return t_err.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Condensed load without any allocation
+// ---------------------------------------------------------------------------
+// Scratch for sem_condense_rhs_noalloc: three element-interior work arrays of
+// up to SEM_NOALLOC_MAX_CUBE doubles each (12 MiB in total).  The array is part
+// of the library image: every GPU that loads the library holds it until the
+// process exits.  Host code must not use its name as a device address; the
+// address comes from cudaGetSymbolAddress, looked up once per device.
+#define SEM_NOALLOC_MAX_CUBE (1LL << 19)
+static __device__ __align__(256) double g_noalloc_scratch[3 * SEM_NOALLOC_MAX_CUBE];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_scratch on the current device (looked up on the
+// first call per device).
+sem_status noalloc_scratch(double** out) {
+  int dev = 0;
+  SEM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(SEM_EINVAL, "device index out of range for no-alloc scratch");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr)
+      return fail(SEM_ECUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
+  return SEM_OK;
+}
+}  // namespace
+
+extern "C" sem_status sem_condense_rhs_noalloc(sem_ctx* c, const double* f, double* fB, sem_space space,
+                                               void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (f == nullptr || fB == nullptr) return fail(SEM_EINVAL, "null vector");
+  if (space != SEM_SPACE_NODAL && space != SEM_SPACE_TRANSFORMED) return fail(SEM_EINVAL, "unknown space");
+  const SemGeom& g = c->g;
+  const long long cube = g.nelem * (long long)g.n * g.n * g.n;
+  if (cube > SEM_NOALLOC_MAX_CUBE)
+    return fail(SEM_EINVAL, "mesh too large for sem_condense_rhs_noalloc: elements * (p-1)^3 = " +
+                                std::to_string(cube) + " exceeds " + std::to_string(SEM_NOALLOC_MAX_CUBE));
+  double* scratch = nullptr;
+  sem_status st = noalloc_scratch(&scratch);
+  if (st != SEM_OK) return st;
+  double* c0 = scratch;
+  double* c1 = scratch + SEM_NOALLOC_MAX_CUBE;
+  double* ft = scratch + 2 * SEM_NOALLOC_MAX_CUBE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double *mx = c->d_mass, *my = mx + g.Nx, *mz = my + g.Ny;
+  // Every scratch entry that is read is written earlier in this call, and fB
+  // is fully written before the face corrections are added: nothing has to be
+  // cleared between calls.
+  launch_load_skeleton(g, mx, my, mz, f, fB, s);
+  launch_skel_transform(g, c->mat(0), fB, fB, s);
+  launch_interior_load(g, mx, my, mz, f, c0, s);
+  launch_mode(g, c->mat(0), 0, c0, c1, nullptr, s);
+  launch_mode(g, c->mat(0), 1, c1, c0, nullptr, s);
+  launch_mode(g, c->mat(0), 2, c0, ft, nullptr, s);
+  launch_condense_faces(g, c->h1.basis, c->tab, ft, fB, s);
+  if (space == SEM_SPACE_NODAL) launch_skel_transform(g, c->mat(3), fB, fB, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}

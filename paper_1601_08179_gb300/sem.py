@@ -67,6 +67,7 @@ def lib():
         "sem_get_basis": (ctypes.c_int, [_P, _D, _D, _D, _D]),
         "sem_apply_condensed": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
         "sem_condense_rhs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+        "sem_condense_rhs_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
         "sem_precond_diag": (ctypes.c_int, [_P, _P, _P]),
         "sem_recover_interior": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
         "sem_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(sem_info), _P]),
@@ -95,6 +96,7 @@ def exported_symbols():
     """Names of the entry points the binding expects the library to export."""
     return ["sem_default_opts", "sem_setup", "sem_set_lambda", "sem_set_opts", "sem_skeleton_size",
             "sem_grid_size", "sem_node_coords", "sem_get_basis", "sem_apply_condensed", "sem_condense_rhs",
+            "sem_condense_rhs_noalloc",
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
             "sem_profile_enable",
@@ -206,6 +208,13 @@ def sem_apply_condensed(ctx: SemContext, uB, vB, space=SPACE_TRANSFORMED, stream
 def sem_condense_rhs(ctx: SemContext, f, fB, space=SPACE_TRANSFORMED, stream=None):
     _check(lib().sem_condense_rhs(ctx.handle, _dptr(f, ctx.n_nodes, "f"), _dptr(fB, ctx.nb, "fB"), int(space),
                                   _stream(stream, f)))
+
+
+def sem_condense_rhs_noalloc(ctx: SemContext, f, fB, space=SPACE_TRANSFORMED, stream=None):
+    """sem_condense_rhs for callers that cannot allocate device memory during
+    the call (it uses the library's fixed scratch array; see include/sem.h)."""
+    _check(lib().sem_condense_rhs_noalloc(ctx.handle, _dptr(f, ctx.n_nodes, "f"), _dptr(fB, ctx.nb, "fB"),
+                                          int(space), _stream(stream, f)))
 
 
 def sem_precond_diag(ctx: SemContext, diag, stream=None):
