@@ -64,6 +64,8 @@ struct sem_ctx {
   double* d_uw = nullptr;              // [ux + uy + uz] distinct widths
   double* d_dcoef = nullptr;
   double* d_dinv = nullptr;
+  double* d_coef = nullptr;            // per-class operator coefficient blocks (FP64)
+  float* d_coef_f = nullptr;           // the same in FP32 (mixed precision)
   double* d_mats = nullptr;            // 4 n*n: S_II, V, V^T M_II, M_II V
   double* d_mass = nullptr;            // [Nx + Ny + Nz] assembled 1D lumped masses
   double* d_P = nullptr;               // BT preconditioner (inverse diagonal)
@@ -149,6 +151,7 @@ sem_status compute_tables(sem_ctx* c, cudaStream_t s) {
   const SemGeom& g = c->g;
   launch_class_tables(g, c->h1.basis, c->d_uw, c->d_uw + g.ux, c->d_uw + g.ux + g.uy, c->lambda, c->d_dcoef,
                       c->d_dinv, s);
+  launch_class_coeffs<double>(g, c->h1.basis, c->d_dcoef, c->d_dinv, c->d_coef, s);
   SEM_CUDA(cudaGetLastError());
   SEM_CUDA(cudaMemsetAsync(c->d_t1, 0, sizeof(double) * g.nb, s));
   launch_precond_diag(g, c->h1.basis, c->tab, c->d_t1, s);
@@ -163,6 +166,7 @@ sem_status cast_tables_f32(sem_ctx* c, cudaStream_t s) {
   const long long ncls = (long long)g.ux * g.uy * g.uz;
   launch_cast_f32(ncls * 4, c->d_dcoef, c->d_dcoef_f, s);
   launch_cast_f32(ncls * (long long)g.n * g.n * g.n, c->d_dinv, c->d_dinv_f, s);
+  launch_class_coeffs<float>(g, c->h1.basis, c->d_dcoef, c->d_dinv, c->d_coef_f, s);
   launch_cast_f32(g.nb, c->d_P, c->d_P32, s);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
@@ -177,7 +181,8 @@ sem_status ensure_mixed(sem_ctx* c) {
             dalloc(&c->d_P32, g.nb) == cudaSuccess && dalloc(&c->d_b32, g.nb) == cudaSuccess &&
             dalloc(&c->d_x32, g.nb) == cudaSuccess && dalloc(&c->d_r32, g.nb) == cudaSuccess &&
             dalloc(&c->d_p32, g.nb) == cudaSuccess && dalloc(&c->d_q32, g.nb) == cudaSuccess &&
-            dalloc(&c->d_st32, 1) == cudaSuccess;
+            dalloc(&c->d_st32, 1) == cudaSuccess &&
+            dalloc(&c->d_coef_f, ncls * coef_offsets(g.n).stride) == cudaSuccess;
   if (!ok) return fail(SEM_ENOMEM, "cannot allocate mixed-precision buffers");
   SEM_CUDA(cudaMemsetAsync(c->d_st32, 0, sizeof(PcgState), c->stream));
   c->tab_f.cls_x = c->tab.cls_x;
@@ -185,6 +190,8 @@ sem_status ensure_mixed(sem_ctx* c) {
   c->tab_f.cls_z = c->tab.cls_z;
   c->tab_f.dcoef = c->d_dcoef_f;
   c->tab_f.dinv = c->d_dinv_f;
+  c->tab_f.coef = c->d_coef_f;
+  c->tab_f.coef_stride = coef_offsets(g.n).stride;
   sem_status st = cast_tables_f32(c, c->stream);
   if (st != SEM_OK) return st;
   // operator kernel attributes outside any capture
@@ -235,7 +242,7 @@ sem_status recover_t(sem_ctx* c, const double* ut, double* u, cudaStream_t s) {
 
 sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
   SEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * c->g.nb, s));
-  launch_tpt_apply_f64(c->g, c->h1.basis, c->tab, x, y, nullptr, nullptr, s);
+  launch_tpt_apply<double>(c->g, c->h1.basis, c->tab, x, y, nullptr, nullptr, s);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -260,7 +267,7 @@ sem_status build_graph(sem_ctx* c) {
   for (int it = 0; it < c->opts.check_every; ++it) {
     // external event-record nodes: recorded at every replay, usable for timing
     if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it], c->stream, cudaEventRecordExternal);
-    launch_tpt_apply_f64(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, c->stream);
+    launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, c->stream);
     if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it + 1], c->stream, cudaEventRecordExternal);
     launch_pcg_update(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, c->stream);
     launch_pcg_dir(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, c->stream);
@@ -443,7 +450,8 @@ void free_ctx(sem_ctx* c) {
   cudaSetDevice(c->device);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->graph32) cudaGraphExecDestroy(c->graph32);
-  void* ptrs32[] = {c->d_dcoef_f, c->d_dinv_f, c->d_P32, c->d_b32, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_st32};
+  void* ptrs32[] = {c->d_dcoef_f, c->d_dinv_f, c->d_P32, c->d_b32, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_st32,
+                    c->d_coef_f, c->d_coef};
   for (void* p : ptrs32)
     if (p) cudaFree(p);
   for (cudaEvent_t ev : c->pev32) cudaEventDestroy(ev);
@@ -531,6 +539,7 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
   g.uy = (int)c->uyw.size();
   g.uz = (int)c->uzw.size();
   g.nelem = (long long)mx * my * mz;
+  g.slow = (g.ux >= g.uy && g.ux >= g.uz && g.ux > 1) ? 0 : ((g.uy >= g.uz && g.uy > 1) ? 1 : 2);
   const long long n2 = (long long)n * n;
   const long long cnt[7] = {(long long)(mx + 1) * my * mz * n2,       (long long)mx * (my + 1) * mz * n2,
                             (long long)mx * my * (mz + 1) * n2,       (long long)mx * (my + 1) * (mz + 1) * n,
@@ -539,6 +548,10 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
   g.off[0] = 0;
   for (int b = 0; b < 7; ++b) g.off[b + 1] = g.off[b] + cnt[b];
   g.nb = g.off[7];
+  if (g.nb >= (1LL << 31)) {
+    delete c;
+    return fail(SEM_ENOTSUP, "skeleton too large: N_B must be below 2^31");
+  }
   g.Nx = (long long)mx * p + 1;
   g.Ny = (long long)my * p + 1;
   g.Nz = (long long)mz * p + 1;
@@ -574,6 +587,7 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
 
   bool ok = dalloc(&c->d_cls, cls.size()) == cudaSuccess && dalloc(&c->d_uw, uw.size()) == cudaSuccess &&
             dalloc(&c->d_dcoef, ncls * 4) == cudaSuccess && dalloc(&c->d_dinv, ncls * n2 * n) == cudaSuccess &&
+            dalloc(&c->d_coef, ncls * coef_offsets(n).stride) == cudaSuccess &&
             dalloc(&c->d_mats, mats.size()) == cudaSuccess && dalloc(&c->d_mass, mass.size()) == cudaSuccess &&
             dalloc(&c->d_P, g.nb) == cudaSuccess && dalloc(&c->d_x, g.nb) == cudaSuccess &&
             dalloc(&c->d_r, g.nb) == cudaSuccess && dalloc(&c->d_p, g.nb) == cudaSuccess &&
@@ -603,6 +617,8 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
   c->tab.cls_z = c->d_cls + mx + my;
   c->tab.dcoef = c->d_dcoef;
   c->tab.dinv = c->d_dinv;
+  c->tab.coef = c->d_coef;
+  c->tab.coef_stride = coef_offsets(n).stride;
   sem_status st = compute_tables(c, s);
   if (st == SEM_OK) {
     // warm the operator kernel's attributes outside any graph capture

@@ -1,0 +1,506 @@
+// The transformed condensed operator, fused over gather, primary part,
+// condensed part and scatter (Sec. 6 of the paper).
+//
+//   v~ = sum_e Rhat_e (H~_BB - H~_BI D^-1 H~_IB) Rhat_e^T u~
+//
+// * Condensed part (Table 2): the six faces are expanded into the interior
+//   eigenspace with d K~_{I0}, d K~_{Ip} (one rank-1 term per face and line),
+//   scaled by D^-1 (Eq. hii_diagonal) and contracted back with d K~_{0I},
+//   d K~_{pI}: 6 n^3 + n^3 + 6 n^3 multiply-adds (Table 3's 13 n^3).
+// * Primary part H~_BB: the restriction of
+//   H~ = d0 M~(x)M~(x)M~ + d1 M~(x)M~(x)K~ + d2 M~(x)K~(x)M~ + d3 K~(x)M~(x)M~
+//   to the skeleton, M~ = diag(w0, I, w0), K~ = S K S^T.  Face self-blocks are
+//   diagonal (Eq. east_east_primary_part_transformed); only 1D lines lying in
+//   a face or along an edge couple different entities.
+// * Gather R^T and scatter-add R: faces have 2 contributions, edges 4,
+//   vertices 8 (reductions in L2 with red.global.add).
+//
+// GB300 mapping: one CTA works on a tile of `epb` elements held entirely in
+// shared memory (faces, edges, vertices, outputs, a k-slab of the n^3 cube).
+// Entity offsets are computed once per element, coefficient vectors come from
+// per-width-class tables (reloaded only when the class changes: elements are
+// visited with the most-graded axis slowest, and each CTA takes a contiguous
+// range of tiles), and every item loop is uniform in its branch so warps stay
+// converged.  The degree is a template parameter for the common p.
+#include <cuda_runtime.h>
+
+#include "sem_device.cuh"
+#include "sem_kernels.cuh"
+
+using namespace semdev;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kHdrInts = 28;   // per element: class, loaded class, 6 + 12 + 8 entity offsets
+
+// Shared-memory layout of one element (units of T).
+struct ElemSm {
+  int F, Acc, E, Eo, Vt, Vo, C, cube, size;
+};
+
+__host__ __device__ inline ElemSm elem_sm(int n, int ks) {
+  const int n2 = n * n;
+  ElemSm L;
+  L.F = 0;
+  L.Acc = 6 * n2;
+  L.E = 12 * n2;
+  L.Eo = L.E + 12 * n;
+  L.Vt = L.Eo + 12 * n;
+  L.Vo = L.Vt + 8;
+  L.C = L.Vo + 8;
+  L.cube = L.C + 18 * n + 24;
+  L.size = (L.cube + ks * n2 + 3) & ~3;
+  return L;
+}
+
+__host__ __device__ inline size_t hdr_bytes(int epb) { return ((size_t)epb * kHdrInts * 4 + 31) & ~size_t(31); }
+
+// Element visiting order: the axis with the most width classes is slowest, so
+// consecutive elements of a CTA share their class tables.
+__device__ __forceinline__ void elem_of(const SemGeom& g, long long e, int* ex, int* ey, int* ez) {
+  if (g.slow == 0) {
+    const long long r = e % ((long long)g.my * g.mz);
+    *ex = (int)(e / ((long long)g.my * g.mz));
+    *ey = (int)(r % g.my);
+    *ez = (int)(r / g.my);
+  } else if (g.slow == 1) {
+    const long long r = e % ((long long)g.mx * g.mz);
+    *ey = (int)(e / ((long long)g.mx * g.mz));
+    *ex = (int)(r % g.mx);
+    *ez = (int)(r / g.mx);
+  } else {
+    elem_coords(g, e, ex, ey, ez);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-class coefficient blocks
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_class_coeffs(SemGeom g, SemBasis b, const double* __restrict__ dcoef,
+                               const double* __restrict__ dinv, T* __restrict__ coef) {
+  const int n = g.n, n2 = n * n;
+  const CoefOffsets o = coef_offsets(n);
+  const long long ncls = (long long)g.ux * g.uy * g.uz;
+  const double w0 = b.w0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncls * o.stride;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = t / o.stride;
+    const int r = (int)(t - c * o.stride);
+    const double* d = dcoef + c * 4;
+    double v = 0.0;
+    if (r < 18 * n) {                       // skd, skw, skww
+      const int which = r / (6 * n), q = r - which * 6 * n, ds = q / n, i = q - ds * n;
+      const double sc = which == 0 ? 1.0 : (which == 1 ? w0 : w0 * w0);
+      v = d[(ds >> 1) + 1] * sc * b.k[ds & 1][i];
+    } else if (r < 18 * n + 18) {           // cO, eO, vO
+      const int q = r - 18 * n, which = q / 6, ds = q - which * 6, s = ds & 1;
+      const double sc = which == 0 ? 1.0 : (which == 1 ? w0 : w0 * w0);
+      v = d[(ds >> 1) + 1] * sc * b.K[s][1 - s];
+    } else if (r < o.fdiag) {
+      v = 0.0;
+    } else if (r < o.ediag) {               // face diagonals
+      const int q = r - o.fdiag, slot = q / n2, idx = q - slot * n2, dd = slot >> 1, s = slot & 1;
+      const int slow = idx / n, fast = idx - slow * n;
+      const double Kss = b.K[s][s];
+      if (dd == 0) v = d[0] * w0 + d[1] * Kss + w0 * (d[2] * b.lam[fast] + d[3] * b.lam[slow]);
+      else if (dd == 1) v = d[0] * w0 + d[2] * Kss + w0 * (d[1] * b.lam[fast] + d[3] * b.lam[slow]);
+      else v = d[0] * w0 + d[3] * Kss + w0 * (d[1] * b.lam[fast] + d[2] * b.lam[slow]);
+    } else if (r < o.vdiag) {               // edge diagonals
+      const int q = r - o.ediag, slot = q / n, l = q - slot * n;
+      const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+      const int t1 = grp == 0 ? 1 : 0, t2 = grp == 2 ? 1 : 2;
+      v = d[0] * w0 * w0 + d[grp + 1] * w0 * w0 * b.lam[l] + d[t1 + 1] * w0 * b.K[s1][s1] +
+          d[t2 + 1] * w0 * b.K[s2][s2];
+    } else if (r < o.vdiag + 8) {           // vertex diagonals
+      const int slot = r - o.vdiag, sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
+      v = d[0] * w0 * w0 * w0 + w0 * w0 * (d[1] * b.K[sa][sa] + d[2] * b.K[sb][sb] + d[3] * b.K[sc][sc]);
+    } else if (r >= o.ndinv && r < o.ndinv + n2 * n) {
+      v = -dinv[c * n2 * n + (r - o.ndinv)];
+    }
+    coef[t] = (T)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The operator kernel
+// ---------------------------------------------------------------------------
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads)
+k_tpt_apply(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v, int epb, int ks,
+            double* __restrict__ partials, PcgState* st) {
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  if (st != nullptr && st->done) return;
+  const int n = NC > 0 ? NC : g.n;
+  const int n2 = n * n;
+  const ElemSm L = elem_sm(n, ks);
+  const CoefOffsets co = coef_offsets(n);
+  int* hdr = reinterpret_cast<int*>(smem_raw);                 // [epb][kHdrInts]
+  T* elems = reinterpret_cast<T*>(smem_raw + hdr_bytes(epb));
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  for (int t = tid; t < epb; t += nt) hdr[t * kHdrInts + 1] = -1;   // no class loaded yet
+  const long long ntiles = (g.nelem + epb - 1) / epb;
+  const long long t_begin = ntiles * blockIdx.x / gridDim.x;
+  const long long t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  T dot = T(0);
+
+  for (long long tile = t_begin; tile < t_end; ++tile) {
+    const long long e0 = tile * epb;
+    __syncthreads();
+    // ---- element headers: class and entity offsets (-1 on the Dirichlet boundary)
+    for (int t = tid; t < epb * 26; t += nt) {
+      const int el = t / 26, r = t - el * 26;
+      const long long e = e0 + el;
+      int* h = hdr + el * kHdrInts;
+      if (e >= g.nelem) {
+        if (r == 0) h[0] = -2;
+        h[2 + r] = -1;
+        continue;
+      }
+      int ex, ey, ez;
+      elem_of(g, e, &ex, &ey, &ez);
+      bool dir;
+      long long off;
+      if (r < 6) off = face_base(g, ex, ey, ez, r, &dir);
+      else if (r < 18) off = edge_base(g, ex, ey, ez, r - 6, &dir);
+      else off = vert_index(g, ex, ey, ez, r - 18, &dir);
+      h[2 + r] = dir ? -1 : (int)off;
+      if (r == 0) h[0] = elem_class(g, tab, ex, ey, ez);
+    }
+    __syncthreads();
+    // ---- gather R^T and the class coefficient vectors
+    for (int t = tid; t < epb * 6 * n2; t += nt) {
+      const int el = t / (6 * n2), r = t - el * 6 * n2, slot = r / n2, idx = r - slot * n2;
+      const int off = hdr[el * kHdrInts + 2 + slot];
+      elems[el * L.size + L.F + r] = off >= 0 ? u[off + idx] : T(0);
+    }
+    for (int t = tid; t < epb * 12 * n; t += nt) {
+      const int el = t / (12 * n), r = t - el * 12 * n, slot = r / n, l = r - slot * n;
+      const int off = hdr[el * kHdrInts + 8 + slot];
+      elems[el * L.size + L.E + r] = off >= 0 ? u[off + l] : T(0);
+    }
+    for (int t = tid; t < epb * 8; t += nt) {
+      const int el = t >> 3, r = t & 7;
+      const int off = hdr[el * kHdrInts + 20 + r];
+      elems[el * L.size + L.Vt + r] = off >= 0 ? u[off] : T(0);
+    }
+    for (int t = tid; t < epb * (18 * n + 18); t += nt) {
+      const int el = t / (18 * n + 18), r = t - el * (18 * n + 18);
+      const int* h = hdr + el * kHdrInts;
+      if (h[0] >= 0 && h[0] != h[1]) elems[el * L.size + L.C + r] = tab.coef[(long long)h[0] * co.stride + r];
+    }
+    __syncthreads();
+    for (int t = tid; t < epb; t += nt) hdr[t * kHdrInts + 1] = hdr[t * kHdrInts];
+
+    // ---- primary part on faces -> Acc (one loop per direction: uniform branches)
+#pragma unroll 1
+    for (int dd = 0; dd < 3; ++dd) {
+      for (int t = tid; t < epb * 2 * n2; t += nt) {
+        const int el = t / (2 * n2), r = t - el * 2 * n2, s = r / n2, idx = r - s * n2;
+        const int slow = idx / n, fast = idx - slow * n;
+        T* E = elems + el * L.size;
+        const int cls = hdr[el * kHdrInts];
+        if (cls < 0) continue;
+        const T* F = E + L.F;
+        const T* Ed = E + L.E;
+        const T* skw = E + L.C + 6 * n;
+        const T* cO = E + L.C + 18 * n;
+        const int slot = 2 * dd + s;
+        const T diag = __ldg(tab.coef + (long long)cls * co.stride + co.fdiag + slot * n2 + idx);
+        T out = diag * F[slot * n2 + idx];
+        out = fma(cO[slot], F[(slot ^ 1) * n2 + idx], out);
+        if (dd == 0) {          // x-face, (j, k) = (fast, slow)
+          const int j = fast, k = slow;
+          out = fma(skw[2 * n + j], Ed[(8 + s) * n + k], out);        // Ez[s][0]
+          out = fma(skw[3 * n + j], Ed[(10 + s) * n + k], out);       // Ez[s][1]
+          out = fma(skw[4 * n + k], Ed[(4 + s) * n + j], out);        // Ey[s][0]
+          out = fma(skw[5 * n + k], Ed[(6 + s) * n + j], out);        // Ey[s][1]
+        } else if (dd == 1) {   // y-face, (i, k)
+          const int i = fast, k = slow;
+          out = fma(skw[0 * n + i], Ed[(8 + 2 * s) * n + k], out);    // Ez[0][s]
+          out = fma(skw[1 * n + i], Ed[(9 + 2 * s) * n + k], out);    // Ez[1][s]
+          out = fma(skw[4 * n + k], Ed[(0 + s) * n + i], out);        // Ex[s][0]
+          out = fma(skw[5 * n + k], Ed[(2 + s) * n + i], out);        // Ex[s][1]
+        } else {                // z-face, (i, j)
+          const int i = fast, j = slow;
+          out = fma(skw[0 * n + i], Ed[(4 + 2 * s) * n + j], out);    // Ey[0][s]
+          out = fma(skw[1 * n + i], Ed[(5 + 2 * s) * n + j], out);    // Ey[1][s]
+          out = fma(skw[2 * n + j], Ed[(0 + 2 * s) * n + i], out);    // Ex[0][s]
+          out = fma(skw[3 * n + j], Ed[(1 + 2 * s) * n + i], out);    // Ex[1][s]
+        }
+        E[L.Acc + slot * n2 + idx] = out;
+      }
+    }
+    // ---- primary part on edges -> Eo
+#pragma unroll 1
+    for (int grp = 0; grp < 3; ++grp) {
+      for (int t = tid; t < epb * 4 * n; t += nt) {
+        const int el = t / (4 * n), r = t - el * 4 * n, q = r / n, l = r - q * n;
+        const int s1 = q & 1, s2 = q >> 1, slot = 4 * grp + q;
+        T* E = elems + el * L.size;
+        const int cls = hdr[el * kHdrInts];
+        if (cls < 0) continue;
+        const T* F = E + L.F;
+        const T* Ed = E + L.E;
+        const T* Vt = E + L.Vt;
+        const T* skw = E + L.C + 6 * n;
+        const T* skww = E + L.C + 12 * n;
+        const T* eO = E + L.C + 18 * n + 6;
+        const T diag = __ldg(tab.coef + (long long)cls * co.stride + co.ediag + slot * n + l);
+        T out = diag * Ed[slot * n + l];
+        if (grp == 0) {         // x-edge Ex[sb][sc], index i
+          const int sb = s1, sc = s2, i = l;
+          out = fma(skww[i], Vt[2 * sb + 4 * sc], out);
+          out = fma(skww[n + i], Vt[1 + 2 * sb + 4 * sc], out);
+          const T* kb = skw + (2 + sb) * n;
+          const T* kc = skw + (4 + sc) * n;
+          const T* Fz = F + (4 + sc) * n2 + i;
+          const T* Fy = F + (2 + sb) * n2 + i;
+#pragma unroll 4
+          for (int m = 0; m < n; ++m) out = fma(kb[m], Fz[m * n], out);
+#pragma unroll 4
+          for (int m = 0; m < n; ++m) out = fma(kc[m], Fy[m * n], out);
+          out = fma(eO[2 + sb], Ed[((1 - sb) + 2 * sc) * n + i], out);
+          out = fma(eO[4 + sc], Ed[(sb + 2 * (1 - sc)) * n + i], out);
+        } else if (grp == 1) {  // y-edge Ey[sa][sc], index j
+          const int sa = s1, sc = s2, j = l;
+          out = fma(skww[2 * n + j], Vt[sa + 4 * sc], out);
+          out = fma(skww[3 * n + j], Vt[sa + 2 + 4 * sc], out);
+          const T* ka = skw + sa * n;
+          const T* kc = skw + (4 + sc) * n;
+          const T* Fz = F + (4 + sc) * n2 + j * n;
+          const T* Fx = F + sa * n2 + j;
+#pragma unroll 4
+          for (int m = 0; m < n; ++m) out = fma(ka[m], Fz[m], out);
+#pragma unroll 4
+          for (int m = 0; m < n; ++m) out = fma(kc[m], Fx[m * n], out);
+          out = fma(eO[sa], Ed[(4 + (1 - sa) + 2 * sc) * n + j], out);
+          out = fma(eO[4 + sc], Ed[(4 + sa + 2 * (1 - sc)) * n + j], out);
+        } else {                // z-edge Ez[sa][sb], index k
+          const int sa = s1, sb = s2, k = l;
+          out = fma(skww[4 * n + k], Vt[sa + 2 * sb], out);
+          out = fma(skww[5 * n + k], Vt[sa + 2 * sb + 4], out);
+          const T* ka = skw + sa * n;
+          const T* kb = skw + (2 + sb) * n;
+          const T* Fy = F + (2 + sb) * n2 + k * n;
+          const T* Fx = F + sa * n2 + k * n;
+#pragma unroll 4
+          for (int m = 0; m < n; ++m) out = fma(ka[m], Fy[m], out);
+#pragma unroll 4
+          for (int m = 0; m < n; ++m) out = fma(kb[m], Fx[m], out);
+          out = fma(eO[sa], Ed[(8 + (1 - sa) + 2 * sb) * n + k], out);
+          out = fma(eO[2 + sb], Ed[(8 + sa + 2 * (1 - sb)) * n + k], out);
+        }
+        E[L.Eo + slot * n + l] = out;
+      }
+    }
+    // ---- primary part at vertices -> Vo
+    for (int t = tid; t < epb * 8; t += nt) {
+      const int el = t >> 3, slot = t & 7;
+      const int sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
+      T* E = elems + el * L.size;
+      const int cls = hdr[el * kHdrInts];
+      if (cls < 0) continue;
+      const T* Ed = E + L.E;
+      const T* Vt = E + L.Vt;
+      const T* skww = E + L.C + 12 * n;
+      const T* vO = E + L.C + 18 * n + 12;
+      const T diag = __ldg(tab.coef + (long long)cls * co.stride + co.vdiag + slot);
+      T out = diag * Vt[slot];
+      const T* ka = skww + sa * n;
+      const T* kb = skww + (2 + sb) * n;
+      const T* kc = skww + (4 + sc) * n;
+      const T* exl = Ed + (sb + 2 * sc) * n;
+      const T* eyl = Ed + (4 + sa + 2 * sc) * n;
+      const T* ezl = Ed + (8 + sa + 2 * sb) * n;
+      for (int m = 0; m < n; ++m) out = fma(ka[m], exl[m], out);
+      for (int m = 0; m < n; ++m) out = fma(kb[m], eyl[m], out);
+      for (int m = 0; m < n; ++m) out = fma(kc[m], ezl[m], out);
+      out = fma(vO[sa], Vt[slot ^ 1], out);
+      out = fma(vO[2 + sb], Vt[slot ^ 2], out);
+      out = fma(vO[4 + sc], Vt[slot ^ 4], out);
+      E[L.Vo + slot] = out;
+    }
+
+    // ---- condensed part, one k-slab of the eigenspace cube at a time
+    for (int k0 = 0; k0 < n; k0 += ks) {
+      const int kn = min(ks, n - k0);
+      const int per = kn * n2;
+      for (int t = tid; t < epb * per; t += nt) {       // expansion and -D^-1 (Table 2)
+        const int el = t / per, r = t - el * per;
+        const int kk = r / n2, ji = r - kk * n2, j = ji / n, i = ji - j * n, k = k0 + kk;
+        T* E = elems + el * L.size;
+        const int cls = hdr[el * kHdrInts];
+        const T* F = E + L.F;
+        const T* skd = E + L.C;
+        T x = skd[i] * F[k * n + j];
+        x = fma(skd[n + i], F[n2 + k * n + j], x);
+        x = fma(skd[2 * n + j], F[2 * n2 + k * n + i], x);
+        x = fma(skd[3 * n + j], F[3 * n2 + k * n + i], x);
+        x = fma(skd[4 * n + k], F[4 * n2 + ji], x);
+        x = fma(skd[5 * n + k], F[5 * n2 + ji], x);
+        const T nd = cls >= 0 ? __ldg(tab.coef + (long long)cls * co.stride + co.ndinv + k * n2 + ji) : T(0);
+        E[L.cube + r] = nd * x;
+      }
+      __syncthreads();
+      // contractions back to the faces, accumulated onto the primary part
+      for (int t = tid; t < epb * 2 * kn * n; t += nt) {   // w / e: sum over i
+        const int el = t / (2 * kn * n), r = t - el * 2 * kn * n, s = r / (kn * n), q = r - s * kn * n;
+        const int kk = q / n, j = q - kk * n;
+        T* E = elems + el * L.size;
+        const T* kv = E + L.C + s * n;
+        const T* row = E + L.cube + kk * n2 + j * n;
+        T acc = E[L.Acc + s * n2 + (k0 + kk) * n + j];
+#pragma unroll 8
+        for (int i = 0; i < n; ++i) acc = fma(kv[i], row[i], acc);
+        E[L.Acc + s * n2 + (k0 + kk) * n + j] = acc;
+      }
+      for (int t = tid; t < epb * 2 * kn * n; t += nt) {   // s / n: sum over j
+        const int el = t / (2 * kn * n), r = t - el * 2 * kn * n, s = r / (kn * n), q = r - s * kn * n;
+        const int kk = q / n, i = q - kk * n;
+        T* E = elems + el * L.size;
+        const T* kv = E + L.C + (2 + s) * n;
+        const T* col = E + L.cube + kk * n2 + i;
+        T acc = E[L.Acc + (2 + s) * n2 + (k0 + kk) * n + i];
+#pragma unroll 8
+        for (int j = 0; j < n; ++j) acc = fma(kv[j], col[j * n], acc);
+        E[L.Acc + (2 + s) * n2 + (k0 + kk) * n + i] = acc;
+      }
+      for (int t = tid; t < epb * 2 * n2; t += nt) {       // b / t: sum over the slab's k
+        const int el = t / (2 * n2), r = t - el * 2 * n2, s = r / n2, ji = r - s * n2;
+        T* E = elems + el * L.size;
+        const T* kv = E + L.C + (4 + s) * n + k0;
+        const T* col = E + L.cube + ji;
+        T acc = E[L.Acc + (4 + s) * n2 + ji];
+        for (int kk = 0; kk < kn; ++kk) acc = fma(kv[kk], col[kk * n2], acc);
+        E[L.Acc + (4 + s) * n2 + ji] = acc;
+      }
+      __syncthreads();
+    }
+
+    // ---- scatter R and the element share of x^T (A x)
+    for (int t = tid; t < epb * 6 * n2; t += nt) {
+      const int el = t / (6 * n2), r = t - el * 6 * n2, slot = r / n2, idx = r - slot * n2;
+      const int off = hdr[el * kHdrInts + 2 + slot];
+      if (off < 0) continue;
+      const T* E = elems + el * L.size;
+      const T o = E[L.Acc + r];
+      atomicAdd(v + off + idx, o);
+      dot = fma(E[L.F + r], o, dot);
+    }
+    for (int t = tid; t < epb * 12 * n; t += nt) {
+      const int el = t / (12 * n), r = t - el * 12 * n, slot = r / n, l = r - slot * n;
+      const int off = hdr[el * kHdrInts + 8 + slot];
+      if (off < 0) continue;
+      const T* E = elems + el * L.size;
+      const T o = E[L.Eo + r];
+      atomicAdd(v + off + l, o);
+      dot = fma(E[L.E + r], o, dot);
+    }
+    for (int t = tid; t < epb * 8; t += nt) {
+      const int el = t >> 3, r = t & 7;
+      const int off = hdr[el * kHdrInts + 20 + r];
+      if (off < 0) continue;
+      const T* E = elems + el * L.size;
+      const T o = E[L.Vo + r];
+      atomicAdd(v + off, o);
+      dot = fma(E[L.Vt + r], o, dot);
+    }
+  }
+
+  if (st != nullptr) {
+    double vals[1] = {(double)dot}, tot[1];
+    if (reduce_grid<1>(vals, partials, &st->counter[0], tot) && threadIdx.x == 0) {
+      const double pq = tot[0];
+      st->pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) st->done = 2;
+      else st->alpha = st->rho / pq;
+    }
+  }
+}
+
+int num_sms_cached() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+template <typename T, int NC>
+void launch_nc(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, double* partials, PcgState* st,
+               const ApplyConfig& c, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {   // once per instantiation; the first launch happens in sem_setup, outside any capture
+    cudaFuncSetAttribute(k_tpt_apply<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  int o = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tpt_apply<T, NC>, c.threads, c.smem);
+  if (o < 1) o = 1;
+  const long long ntiles = (g.nelem + c.epb - 1) / c.epb;
+  long long grid = (long long)num_sms_cached() * o;
+  if (grid > ntiles) grid = ntiles;
+  k_tpt_apply<T, NC><<<(int)grid, c.threads, c.smem, s>>>(g, t, x, y, c.epb, c.ks, partials, st);
+  sem_count_launch();
+}
+
+}  // namespace
+
+ApplyConfig sem_apply_config(int n, size_t elem_bytes) {
+  ApplyConfig c;
+  c.threads = kThreads;
+  const size_t big = 200 * 1024, small = 96 * 1024;
+  int ks = n;
+  int epb = 1;
+  const int n3 = n * n * n;
+  const int want = n3 >= 512 ? 1 : (512 + n3 - 1) / n3;
+  epb = want > 64 ? 64 : want;
+  auto bytes = [&](int e, int k) { return hdr_bytes(e) + (size_t)e * elem_sm(n, k).size * elem_bytes; };
+  while (epb > 1 && bytes(epb, ks) > small) --epb;
+  while (ks > 1 && bytes(epb, ks) > (epb == 1 ? big : small)) ks = (ks + 1) / 2;
+  c.epb = epb;
+  c.ks = ks;
+  c.smem = bytes(epb, ks);
+  return c;
+}
+
+template <typename T>
+void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
+                      double* partials, PcgState* st, cudaStream_t s) {
+  (void)b;
+  const ApplyConfig c = sem_apply_config(g.n, sizeof(T));
+  switch (g.n) {
+    case 1: launch_nc<T, 1>(g, t, x, y, partials, st, c, s); break;
+    case 3: launch_nc<T, 3>(g, t, x, y, partials, st, c, s); break;
+    case 7: launch_nc<T, 7>(g, t, x, y, partials, st, c, s); break;
+    case 15: launch_nc<T, 15>(g, t, x, y, partials, st, c, s); break;
+    case 31: launch_nc<T, 31>(g, t, x, y, partials, st, c, s); break;
+    default: launch_nc<T, 0>(g, t, x, y, partials, st, c, s); break;
+  }
+}
+
+template <typename T>
+void launch_class_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoef, const double* dinv, T* coef,
+                         cudaStream_t s) {
+  const long long work = (long long)g.ux * g.uy * g.uz * coef_offsets(g.n).stride;
+  long long blocks = (work + 255) / 256;
+  if (blocks > (long long)num_sms_cached() * 16) blocks = (long long)num_sms_cached() * 16;
+  if (blocks < 1) blocks = 1;
+  k_class_coeffs<T><<<(int)blocks, 256, 0, s>>>(g, b, dcoef, dinv, coef);
+  sem_count_launch();
+}
+
+template void launch_tpt_apply<double>(const SemGeom&, const SemBasis&, const SemClassTables<double>&,
+                                       const double*, double*, double*, PcgState*, cudaStream_t);
+template void launch_tpt_apply<float>(const SemGeom&, const SemBasis&, const SemClassTables<float>&,
+                                      const float*, float*, double*, PcgState*, cudaStream_t);
+template void launch_class_coeffs<double>(const SemGeom&, const SemBasis&, const double*, const double*, double*,
+                                          cudaStream_t);
+template void launch_class_coeffs<float>(const SemGeom&, const SemBasis&, const double*, const double*, float*,
+                                         cudaStream_t);

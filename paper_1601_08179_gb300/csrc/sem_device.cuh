@@ -1,0 +1,172 @@
+// Device helpers shared by the kernels of the condensed spectral-element library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sem_internal.h"
+
+namespace semdev {
+
+// ---------------------------------------------------------------------------
+// Mesh helpers
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ void elem_coords(const SemGeom& g, long long e, int* ex, int* ey, int* ez) {
+  *ex = (int)(e % g.mx);
+  long long r = e / g.mx;
+  *ey = (int)(r % g.my);
+  *ez = (int)(r / g.my);
+}
+
+// Face slot 0..5 = (dir, side): 0 w, 1 e, 2 s, 3 n, 4 b, 5 t.
+static __device__ __forceinline__ long long face_base(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
+  const int d = slot >> 1, s = slot & 1;
+  const long long n2 = (long long)g.n * g.n;
+  if (d == 0) {
+    const int f = ex + s;
+    *dir = (f == 0 || f == g.mx);
+    return g.off[0] + (f + (long long)(g.mx + 1) * (ey + (long long)g.my * ez)) * n2;
+  }
+  if (d == 1) {
+    const int f = ey + s;
+    *dir = (f == 0 || f == g.my);
+    return g.off[1] + (ex + (long long)g.mx * (f + (long long)(g.my + 1) * ez)) * n2;
+  }
+  const int f = ez + s;
+  *dir = (f == 0 || f == g.mz);
+  return g.off[2] + (ex + (long long)g.mx * (ey + (long long)g.my * f)) * n2;
+}
+
+// Edge slot 0..11: group = slot >> 2 (0 x-edges Ex[sb][sc], 1 y-edges Ey[sa][sc],
+// 2 z-edges Ez[sa][sb]); the two side bits are slot & 1 and (slot >> 1) & 1.
+static __device__ __forceinline__ long long edge_base(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
+  const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+  if (grp == 0) {
+    const int vy = ey + s1, vz = ez + s2;
+    *dir = (vy == 0 || vy == g.my || vz == 0 || vz == g.mz);
+    return g.off[3] + (ex + (long long)g.mx * (vy + (long long)(g.my + 1) * vz)) * g.n;
+  }
+  if (grp == 1) {
+    const int vx = ex + s1, vz = ez + s2;
+    *dir = (vx == 0 || vx == g.mx || vz == 0 || vz == g.mz);
+    return g.off[4] + (vx + (long long)(g.mx + 1) * (ey + (long long)g.my * vz)) * g.n;
+  }
+  const int vx = ex + s1, vy = ey + s2;
+  *dir = (vx == 0 || vx == g.mx || vy == 0 || vy == g.my);
+  return g.off[5] + (vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * ez)) * g.n;
+}
+
+// Vertex slot 0..7 = sa + 2 sb + 4 sc.
+static __device__ __forceinline__ long long vert_index(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
+  const int vx = ex + (slot & 1), vy = ey + ((slot >> 1) & 1), vz = ez + (slot >> 2);
+  *dir = (vx == 0 || vx == g.mx || vy == 0 || vy == g.my || vz == 0 || vz == g.mz);
+  return g.off[6] + vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * vz);
+}
+
+template <typename T>
+static __device__ __forceinline__ int elem_class(const SemGeom& g, const SemClassTables<T>& t, int ex, int ey, int ez) {
+  return t.cls_x[ex] + g.ux * (t.cls_y[ey] + g.uy * t.cls_z[ez]);
+}
+
+// Global node (gx, gy, gz) of packed skeleton entry idx.
+static __device__ __forceinline__ void skel_node(const SemGeom& g, long long idx, long long* gx, long long* gy,
+                                          long long* gz) {
+  const int p = g.p, n = g.n;
+  const long long n2 = (long long)n * n;
+  int b = 0;
+  while (b < 6 && idx >= g.off[b + 1]) ++b;
+  const long long loc = idx - g.off[b];
+  if (b < 3) {
+    const long long ent = loc / n2, r = loc - ent * n2;
+    const int fast = (int)(r % n) + 1, slow = (int)(r / n) + 1;
+    if (b == 0) {
+      const long long f = ent % (g.mx + 1), t = ent / (g.mx + 1);
+      *gx = f * p; *gy = (t % g.my) * p + fast; *gz = (t / g.my) * p + slow;
+    } else if (b == 1) {
+      const long long ex = ent % g.mx, t = ent / g.mx;
+      *gx = ex * p + fast; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p + slow;
+    } else {
+      const long long ex = ent % g.mx, t = ent / g.mx;
+      *gx = ex * p + fast; *gy = (t % g.my) * p + slow; *gz = (t / g.my) * p;
+    }
+  } else if (b < 6) {
+    const long long ent = loc / n;
+    const int l = (int)(loc - ent * n) + 1;
+    if (b == 3) {
+      const long long ex = ent % g.mx, t = ent / g.mx;
+      *gx = ex * p + l; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p;
+    } else if (b == 4) {
+      const long long vx = ent % (g.mx + 1), t = ent / (g.mx + 1);
+      *gx = vx * p; *gy = (t % g.my) * p + l; *gz = (t / g.my) * p;
+    } else {
+      const long long vx = ent % (g.mx + 1), t = ent / (g.mx + 1);
+      *gx = vx * p; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p + l;
+    }
+  } else {
+    const long long vx = loc % (g.mx + 1), t = loc / (g.mx + 1);
+    *gx = vx * p; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p;
+  }
+}
+
+static __device__ __forceinline__ bool node_on_boundary(const SemGeom& g, long long gx, long long gy, long long gz) {
+  return gx == 0 || gx == g.Nx - 1 || gy == 0 || gy == g.Ny - 1 || gz == 0 || gz == g.Nz - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic block reduction + last-block finalisation
+// ---------------------------------------------------------------------------
+template <int NV>
+static __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k * 32 + wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < nw ? sh[k * 32 + lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;   // valid in thread 0
+    }
+  }
+  __syncthreads();
+}
+
+// Writes this block's NV sums to partials[k * G + block]; the last block to
+// arrive sums all partials in a fixed order and returns true with the totals
+// in tot (valid in thread 0).
+template <int NV>
+static __device__ bool reduce_grid(double (&v)[NV], double* partials, unsigned int* counter, double (&tot)[NV]) {
+  __shared__ double sh[NV * 32];
+  __shared__ bool last;
+  block_sum<NV>(v, sh);
+  const unsigned G = gridDim.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[k * G + blockIdx.x] = v[k];
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    last = (t == G - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    s[k] = 0.0;
+    for (unsigned i = threadIdx.x; i < G; i += blockDim.x) s[k] += __ldcg(partials + k * G + i);
+  }
+  block_sum<NV>(s, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = s[k];
+    *counter = 0u;
+  }
+  return true;
+}
+
+}  // namespace semdev

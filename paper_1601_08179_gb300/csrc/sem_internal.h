@@ -14,6 +14,7 @@
 struct SemGeom {
   int p, n, mx, my, mz;
   int ux, uy, uz;        // distinct element widths per axis (width classes)
+  int slow;              // axis visited slowest by the operator kernel (most classes)
   long long nelem;
   long long off[8];      // block offsets: xf, yf, zf, xe, ye, ze, v, end(=N_B)
   long long nb;
@@ -51,7 +52,34 @@ struct SemClassTables {
   const int* cls_z;   // [mz]
   const T* dcoef;     // [ncls][4] metric coefficients d0..d3
   const T* dinv;      // [ncls][n^3] D^-1, index (k n + j) n + i
+  const T* coef;      // [ncls][coef_stride] operator coefficients (sem_apply.cu)
+  long long coef_stride;
 };
+
+// Offsets inside one class's operator coefficient block (units of T):
+//   [0, 18n + 24): scaled line vectors and couplings, copied to shared memory
+//       skd [3][2][n] = d_{dir+1} k_side        (condensed part)
+//       skw [3][2][n] = d_{dir+1} w0 k_side     (lines inside a face)
+//       skww[3][2][n] = d_{dir+1} w0^2 k_side   (lines along an edge)
+//       cO[6], eO[6], vO[6] = d_{dir+1} {1, w0, w0^2} K~_{s,1-s}
+//   fdiag [6][n^2]   diagonal of the primary part on the faces
+//   ediag [12][n]    diagonal of the primary part on the edges
+//   vdiag [8]        diagonal of the primary part at the vertices
+//   ndinv [n^3]      -D^-1
+struct CoefOffsets {
+  int sm, fdiag, ediag, vdiag, ndinv;
+  long long stride;
+};
+inline __host__ __device__ CoefOffsets coef_offsets(int n) {
+  CoefOffsets o;
+  o.sm = 18 * n + 24;
+  o.fdiag = o.sm;
+  o.ediag = o.fdiag + 6 * n * n;
+  o.vdiag = o.ediag + 12 * n;
+  o.ndinv = (o.vdiag + 8 + 3) & ~3;
+  o.stride = ((long long)o.ndinv + (long long)n * n * n + 3) & ~3LL;
+  return o;
+}
 
 // Device-resident CG scalars (one per solve in flight).
 struct PcgState {

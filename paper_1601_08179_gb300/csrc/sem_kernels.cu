@@ -1,6 +1,8 @@
-// sm_103a kernels of the statically condensed spectral-element Helmholtz solver.
+// sm_103a kernels of the statically condensed spectral-element Helmholtz solver:
+// per-class tables, preconditioner, skeleton transforms, loads, recovery and
+// the CG vector kernels.  The operator kernel itself is in sem_apply.cu:
 //
-// The hot kernel is k_tpt_apply: the assembled transformed condensed operator
+// k_tpt_apply: the assembled transformed condensed operator
 //   v~ = sum_e Rhat_e (H~_BB - H~_BI D^-1 H~_IB) Rhat_e^T u~
 // evaluated element by element (Sec. 6):
 //   * condensed part, Table 2: expand the six faces into the interior
@@ -22,7 +24,10 @@
 #include <atomic>
 #include <cstdio>
 
+#include "sem_device.cuh"
 #include "sem_kernels.cuh"
+
+using namespace semdev;
 
 static std::atomic<long long> g_launches{0};
 void sem_count_launch(long long k) { g_launches += k; }
@@ -31,169 +36,6 @@ long long sem_launch_total() { return g_launches.load(); }
 namespace {
 
 constexpr int kVecThreads = 256;
-constexpr int kApplyThreads = 256;
-
-// ---------------------------------------------------------------------------
-// Mesh helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void elem_coords(const SemGeom& g, long long e, int* ex, int* ey, int* ez) {
-  *ex = (int)(e % g.mx);
-  long long r = e / g.mx;
-  *ey = (int)(r % g.my);
-  *ez = (int)(r / g.my);
-}
-
-// Face slot 0..5 = (dir, side): 0 w, 1 e, 2 s, 3 n, 4 b, 5 t.
-__device__ __forceinline__ long long face_base(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
-  const int d = slot >> 1, s = slot & 1;
-  const long long n2 = (long long)g.n * g.n;
-  if (d == 0) {
-    const int f = ex + s;
-    *dir = (f == 0 || f == g.mx);
-    return g.off[0] + (f + (long long)(g.mx + 1) * (ey + (long long)g.my * ez)) * n2;
-  }
-  if (d == 1) {
-    const int f = ey + s;
-    *dir = (f == 0 || f == g.my);
-    return g.off[1] + (ex + (long long)g.mx * (f + (long long)(g.my + 1) * ez)) * n2;
-  }
-  const int f = ez + s;
-  *dir = (f == 0 || f == g.mz);
-  return g.off[2] + (ex + (long long)g.mx * (ey + (long long)g.my * f)) * n2;
-}
-
-// Edge slot 0..11: group = slot >> 2 (0 x-edges Ex[sb][sc], 1 y-edges Ey[sa][sc],
-// 2 z-edges Ez[sa][sb]); the two side bits are slot & 1 and (slot >> 1) & 1.
-__device__ __forceinline__ long long edge_base(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
-  const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
-  if (grp == 0) {
-    const int vy = ey + s1, vz = ez + s2;
-    *dir = (vy == 0 || vy == g.my || vz == 0 || vz == g.mz);
-    return g.off[3] + (ex + (long long)g.mx * (vy + (long long)(g.my + 1) * vz)) * g.n;
-  }
-  if (grp == 1) {
-    const int vx = ex + s1, vz = ez + s2;
-    *dir = (vx == 0 || vx == g.mx || vz == 0 || vz == g.mz);
-    return g.off[4] + (vx + (long long)(g.mx + 1) * (ey + (long long)g.my * vz)) * g.n;
-  }
-  const int vx = ex + s1, vy = ey + s2;
-  *dir = (vx == 0 || vx == g.mx || vy == 0 || vy == g.my);
-  return g.off[5] + (vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * ez)) * g.n;
-}
-
-// Vertex slot 0..7 = sa + 2 sb + 4 sc.
-__device__ __forceinline__ long long vert_index(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
-  const int vx = ex + (slot & 1), vy = ey + ((slot >> 1) & 1), vz = ez + (slot >> 2);
-  *dir = (vx == 0 || vx == g.mx || vy == 0 || vy == g.my || vz == 0 || vz == g.mz);
-  return g.off[6] + vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * vz);
-}
-
-template <typename T>
-__device__ __forceinline__ int elem_class(const SemGeom& g, const SemClassTables<T>& t, int ex, int ey, int ez) {
-  return t.cls_x[ex] + g.ux * (t.cls_y[ey] + g.uy * t.cls_z[ez]);
-}
-
-// Global node (gx, gy, gz) of packed skeleton entry idx.
-__device__ __forceinline__ void skel_node(const SemGeom& g, long long idx, long long* gx, long long* gy,
-                                          long long* gz) {
-  const int p = g.p, n = g.n;
-  const long long n2 = (long long)n * n;
-  int b = 0;
-  while (b < 6 && idx >= g.off[b + 1]) ++b;
-  const long long loc = idx - g.off[b];
-  if (b < 3) {
-    const long long ent = loc / n2, r = loc - ent * n2;
-    const int fast = (int)(r % n) + 1, slow = (int)(r / n) + 1;
-    if (b == 0) {
-      const long long f = ent % (g.mx + 1), t = ent / (g.mx + 1);
-      *gx = f * p; *gy = (t % g.my) * p + fast; *gz = (t / g.my) * p + slow;
-    } else if (b == 1) {
-      const long long ex = ent % g.mx, t = ent / g.mx;
-      *gx = ex * p + fast; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p + slow;
-    } else {
-      const long long ex = ent % g.mx, t = ent / g.mx;
-      *gx = ex * p + fast; *gy = (t % g.my) * p + slow; *gz = (t / g.my) * p;
-    }
-  } else if (b < 6) {
-    const long long ent = loc / n;
-    const int l = (int)(loc - ent * n) + 1;
-    if (b == 3) {
-      const long long ex = ent % g.mx, t = ent / g.mx;
-      *gx = ex * p + l; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p;
-    } else if (b == 4) {
-      const long long vx = ent % (g.mx + 1), t = ent / (g.mx + 1);
-      *gx = vx * p; *gy = (t % g.my) * p + l; *gz = (t / g.my) * p;
-    } else {
-      const long long vx = ent % (g.mx + 1), t = ent / (g.mx + 1);
-      *gx = vx * p; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p + l;
-    }
-  } else {
-    const long long vx = loc % (g.mx + 1), t = loc / (g.mx + 1);
-    *gx = vx * p; *gy = (t % (g.my + 1)) * p; *gz = (t / (g.my + 1)) * p;
-  }
-}
-
-__device__ __forceinline__ bool node_on_boundary(const SemGeom& g, long long gx, long long gy, long long gz) {
-  return gx == 0 || gx == g.Nx - 1 || gy == 0 || gy == g.Ny - 1 || gz == 0 || gz == g.Nz - 1;
-}
-
-// ---------------------------------------------------------------------------
-// Deterministic block reduction + last-block finalisation
-// ---------------------------------------------------------------------------
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* [NV][32] */) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double x = v[k];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[k * 32 + wid] = x;
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double x = lane < nw ? sh[k * 32 + lane] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      v[k] = x;   // valid in thread 0
-    }
-  }
-  __syncthreads();
-}
-
-// Writes this block's NV sums to partials[k * G + block]; the last block to
-// arrive sums all partials in a fixed order and returns true with the totals
-// in tot (valid in thread 0).
-template <int NV>
-__device__ bool reduce_grid(double (&v)[NV], double* partials, unsigned int* counter, double (&tot)[NV]) {
-  __shared__ double sh[NV * 32];
-  __shared__ bool last;
-  block_sum<NV>(v, sh);
-  const unsigned G = gridDim.x;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) partials[k * G + blockIdx.x] = v[k];
-    __threadfence();
-    const unsigned t = atomicAdd(counter, 1u);
-    last = (t == G - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  double s[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    s[k] = 0.0;
-    for (unsigned i = threadIdx.x; i < G; i += blockDim.x) s[k] += __ldcg(partials + k * G + i);
-  }
-  block_sum<NV>(s, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = s[k];
-    *counter = 0u;
-  }
-  return true;
-}
 
 // ---------------------------------------------------------------------------
 // Per-width-class tables: d (Eq. metriccoeffelement) and D^-1 (Eq. hii_diagonal)
@@ -217,322 +59,6 @@ __global__ void k_class_tables(SemGeom g, SemBasis b, const double* __restrict__
       const long long q = r - 4;
       const int i = (int)(q % n), j = (int)((q / n) % n), k = (int)(q / ((long long)n * n));
       dinv[c * n3 + q] = 1.0 / (d0 + d1 * b.lam[i] + d2 * b.lam[j] + d3 * b.lam[k]);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Fused transformed condensed operator
-// ---------------------------------------------------------------------------
-// Per-element coefficient arrays (offsets inside the sk / co regions):
-//   skd [dir][side][i] = d_{dir+1} k_side[i]          condensed expansion/contraction
-//   skw [dir][side][i] = d_{dir+1} w0 k_side[i]       lines inside a face
-//   skww[dir][side][i] = d_{dir+1} w0^2 k_side[i]     lines along an edge
-//   lw  [dir][i]       = d_{dir+1} w0 Lambda_i        face diagonal
-//   lww [dir][i]       = d_{dir+1} w0^2 Lambda_i      edge diagonal
-//   co: cF[6] = d0 w0 + d K_ss, cO[6] = d K_so, eS[6] = d w0 K_ss, eO[6] = d w0 K_so,
-//       vS[6] = d w0^2 K_ss, vO[6] = d w0^2 K_so (index dir*2+side), d0 w0^2, d0 w0^3
-template <typename T>
-__device__ __forceinline__ void elem_coeffs(const SemBasis& b, const T* dd, T* sk, T* co, int n, int t) {
-  const double w0 = b.w0;
-  const double d[4] = {(double)dd[0], (double)dd[1], (double)dd[2], (double)dd[3]};
-  if (t < 18 * n) {
-    const int which = t / (6 * n), r = t - which * 6 * n, ds = r / n, i = r - ds * n;
-    const int dir = ds >> 1, side = ds & 1;
-    const double sc = which == 0 ? 1.0 : (which == 1 ? w0 : w0 * w0);
-    sk[t] = (T)(d[dir + 1] * sc * b.k[side][i]);
-  } else if (t < 24 * n) {
-    const int r = t - 18 * n, which = r / (3 * n), q = r - which * 3 * n, dir = q / n, i = q - dir * n;
-    sk[t] = (T)(d[dir + 1] * (which == 0 ? w0 : w0 * w0) * b.lam[i]);
-  } else if (t < 24 * n + 40) {
-    const int c = t - 24 * n;
-    double v = 0.0;
-    if (c < 36) {
-      const int grp = c / 6, ds = c - grp * 6, dir = ds >> 1, side = ds & 1;
-      const double dv = d[dir + 1], Kss = b.K[side][side], Kso = b.K[side][1 - side];
-      switch (grp) {
-        case 0: v = d[0] * w0 + dv * Kss; break;
-        case 1: v = dv * Kso; break;
-        case 2: v = dv * w0 * Kss; break;
-        case 3: v = dv * w0 * Kso; break;
-        case 4: v = dv * w0 * w0 * Kss; break;
-        default: v = dv * w0 * w0 * Kso; break;
-      }
-    } else if (c == 36) {
-      v = d[0] * w0 * w0;
-    } else if (c == 37) {
-      v = d[0] * w0 * w0 * w0;
-    }
-    co[c] = (T)v;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kApplyThreads)
-k_tpt_apply(SemGeom g, SemBasis b, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
-            int epb, int ks, double* __restrict__ partials, PcgState* st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (st != nullptr && st->done) return;
-
-  const int n = g.n, n2 = n * n;
-  const ElemLayout L = elem_layout(n, ks);
-  int* s_cls = reinterpret_cast<int*>(smem_raw);                          // [epb]
-  T* s_dd = reinterpret_cast<T*>(smem_raw + apply_hdr_cls_bytes(epb));     // [epb][4]
-  T* base = reinterpret_cast<T*>(smem_raw + apply_hdr_bytes(epb, sizeof(T)));
-  const int per_load = 6 * n2 + 12 * n + 8;
-  const long long ntiles = (g.nelem + epb - 1) / epb;
-  double dot = 0.0;
-
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long e0 = tile * epb;
-    // --- element classes and metric coefficients
-    for (int t = threadIdx.x; t < epb; t += blockDim.x) {
-      const long long e = e0 + t;
-      int c = 0;
-      if (e < g.nelem) {
-        int ex, ey, ez;
-        elem_coords(g, e, &ex, &ey, &ez);
-        c = elem_class(g, tab, ex, ey, ez);
-      }
-      s_cls[t] = c;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) s_dd[t * 4 + k] = tab.dcoef[c * 4 + k];
-    }
-    __syncthreads();
-    // --- gather R^T: faces, edges, vertices (Dirichlet entities read as 0)
-    for (int t = threadIdx.x; t < epb * per_load; t += blockDim.x) {
-      const int el = t / per_load, r = t - el * per_load;
-      const long long e = e0 + el;
-      T val = T(0);
-      if (e < g.nelem) {
-        int ex, ey, ez;
-        elem_coords(g, e, &ex, &ey, &ez);
-        bool dir;
-        long long gi;
-        if (r < 6 * n2) {
-          const int slot = r / n2;
-          gi = face_base(g, ex, ey, ez, slot, &dir) + (r - slot * n2);
-        } else if (r < 6 * n2 + 12 * n) {
-          const int q = r - 6 * n2, slot = q / n;
-          gi = edge_base(g, ex, ey, ez, slot, &dir) + (q - slot * n);
-        } else {
-          gi = vert_index(g, ex, ey, ez, r - 6 * n2 - 12 * n, &dir);
-        }
-        if (!dir) val = u[gi];
-      }
-      T* E = base + el * L.size;
-      if (r < 6 * n2) E[L.F + r] = val;
-      else if (r < 6 * n2 + 12 * n) E[L.E + (r - 6 * n2)] = val;
-      else E[L.Vt + (r - 6 * n2 - 12 * n)] = val;
-    }
-    // --- per-element scaled coefficient vectors
-    const int per_co = 24 * n + 40;
-    for (int t = threadIdx.x; t < epb * per_co; t += blockDim.x) {
-      const int el = t / per_co, r = t - el * per_co;
-      T* E = base + el * L.size;
-      elem_coeffs<T>(b, s_dd + 4 * el, E + L.sk, E + L.co, n, r);
-    }
-    __syncthreads();
-
-    // --- condensed part, slab by slab of the eigenspace cube (Table 2)
-    for (int k0 = 0; k0 < n; k0 += ks) {
-      const int kn = min(ks, n - k0);
-      const int per_cube = kn * n2;
-      for (int t = threadIdx.x; t < epb * per_cube; t += blockDim.x) {
-        const int el = t / per_cube, r = t - el * per_cube;
-        const int kk = r / n2, ji = r - kk * n2, j = ji / n, i = ji - j * n, k = k0 + kk;
-        T* E = base + el * L.size;
-        const T* F = E + L.F;
-        const T* skd = E + L.sk;
-        T x = skd[0 * n + i] * F[0 * n2 + k * n + j];
-        x = fma(skd[1 * n + i], F[1 * n2 + k * n + j], x);
-        x = fma(skd[2 * n + j], F[2 * n2 + k * n + i], x);
-        x = fma(skd[3 * n + j], F[3 * n2 + k * n + i], x);
-        x = fma(skd[4 * n + k], F[4 * n2 + j * n + i], x);
-        x = fma(skd[5 * n + k], F[5 * n2 + j * n + i], x);
-        const T di = __ldg(tab.dinv + (long long)s_cls[el] * n2 * n + (long long)k * n2 + ji);
-        E[L.cube + r] = di * x;
-      }
-      __syncthreads();
-      const int per_con = 4 * kn * n + 2 * n2;
-      for (int t = threadIdx.x; t < epb * per_con; t += blockDim.x) {
-        const int el = t / per_con, r = t - el * per_con;
-        T* E = base + el * L.size;
-        const T* C = E + L.cube;
-        const T* skd = E + L.sk;
-        T* Acc = E + L.Acc;
-        if (r < 2 * kn * n) {          // w / e: sum over i
-          const int side = r / (kn * n), q = r - side * kn * n, kk = q / n, j = q - kk * n;
-          const T* kv = skd + side * n;
-          const T* row = C + kk * n2 + j * n;
-          T s = T(0);
-          for (int i = 0; i < n; ++i) s = fma(kv[i], row[i], s);
-          Acc[side * n2 + (k0 + kk) * n + j] = s;
-        } else if (r < 4 * kn * n) {   // s / n: sum over j
-          const int q0 = r - 2 * kn * n, side = q0 / (kn * n), q = q0 - side * kn * n;
-          const int kk = q / n, i = q - kk * n;
-          const T* kv = skd + (2 + side) * n;
-          const T* col = C + kk * n2 + i;
-          T s = T(0);
-          for (int j = 0; j < n; ++j) s = fma(kv[j], col[j * n], s);
-          Acc[(2 + side) * n2 + (k0 + kk) * n + i] = s;
-        } else {                       // b / t: sum over k, accumulated over slabs
-          const int q0 = r - 4 * kn * n, side = q0 / n2, ji = q0 - side * n2;
-          const T* kv = skd + (4 + side) * n + k0;
-          const T* col = C + ji;
-          T s = k0 == 0 ? T(0) : Acc[(4 + side) * n2 + ji];
-          for (int kk = 0; kk < kn; ++kk) s = fma(kv[kk], col[kk * n2], s);
-          Acc[(4 + side) * n2 + ji] = s;
-        }
-      }
-      __syncthreads();
-    }
-
-    // --- primary part minus condensed part, scatter-add R
-    for (int t = threadIdx.x; t < epb * per_load; t += blockDim.x) {
-      const int el = t / per_load, r = t - el * per_load;
-      const long long e = e0 + el;
-      if (e >= g.nelem) continue;
-      int ex, ey, ez;
-      elem_coords(g, e, &ex, &ey, &ez);
-      const T* E = base + el * L.size;
-      const T* F = E + L.F;
-      const T* Ed = E + L.E;
-      const T* Vt = E + L.Vt;
-      const T* skw = E + L.sk + 6 * n;
-      const T* skww = E + L.sk + 12 * n;
-      const T* lw = E + L.sk + 18 * n;
-      const T* lww = E + L.sk + 21 * n;
-      const T* co = E + L.co;
-      const T* cF = co, *cO = co + 6, *eS = co + 12, *eO = co + 18, *vS = co + 24, *vO = co + 30;
-      T out, uval;
-      bool dir;
-      long long gi;
-      if (r < 6 * n2) {
-        const int slot = r / n2, idx = r - slot * n2, dd = slot >> 1, s = slot & 1;
-        const int slow = idx / n, fast = idx - slow * n;
-        gi = face_base(g, ex, ey, ez, slot, &dir) + idx;
-        uval = F[r];
-        const T uo = F[(slot ^ 1) * n2 + idx];
-        // edges bounding this face that carry its in-face lines; see the
-        // per-direction formulas in the header comment of this function
-        if (dd == 0) {          // x-face (j = fast, k = slow)
-          const int j = fast, k = slow;
-          const T* Ez0 = Ed + (8 + s + 0) * n;   // Ez[sa=s][sb=0]
-          const T* Ez1 = Ed + (8 + s + 2) * n;   // Ez[s][1]
-          const T* Ey0 = Ed + (4 + s + 0) * n;   // Ey[sa=s][sc=0]
-          const T* Ey1 = Ed + (4 + s + 2) * n;   // Ey[s][1]
-          out = (cF[slot] + lw[n + j] + lw[2 * n + k]) * uval + cO[slot] * uo;
-          out = fma(skw[2 * n + j], Ez0[k], out);
-          out = fma(skw[3 * n + j], Ez1[k], out);
-          out = fma(skw[4 * n + k], Ey0[j], out);
-          out = fma(skw[5 * n + k], Ey1[j], out);
-        } else if (dd == 1) {   // y-face (i = fast, k = slow)
-          const int i = fast, k = slow;
-          const T* Ez0 = Ed + (8 + 0 + 2 * s) * n;   // Ez[sa=0][sb=s]
-          const T* Ez1 = Ed + (8 + 1 + 2 * s) * n;   // Ez[1][s]
-          const T* Ex0 = Ed + (0 + s + 0) * n;       // Ex[sb=s][sc=0]
-          const T* Ex1 = Ed + (0 + s + 2) * n;       // Ex[s][1]
-          out = (cF[slot] + lw[i] + lw[2 * n + k]) * uval + cO[slot] * uo;
-          out = fma(skw[0 * n + i], Ez0[k], out);
-          out = fma(skw[1 * n + i], Ez1[k], out);
-          out = fma(skw[4 * n + k], Ex0[i], out);
-          out = fma(skw[5 * n + k], Ex1[i], out);
-        } else {                // z-face (i = fast, j = slow)
-          const int i = fast, j = slow;
-          const T* Ey0 = Ed + (4 + 0 + 2 * s) * n;   // Ey[sa=0][sc=s]
-          const T* Ey1 = Ed + (4 + 1 + 2 * s) * n;   // Ey[1][s]
-          const T* Ex0 = Ed + (0 + 0 + 2 * s) * n;   // Ex[sb=0][sc=s]
-          const T* Ex1 = Ed + (0 + 1 + 2 * s) * n;   // Ex[1][s]
-          out = (cF[slot] + lw[i] + lw[n + j]) * uval + cO[slot] * uo;
-          out = fma(skw[0 * n + i], Ey0[j], out);
-          out = fma(skw[1 * n + i], Ey1[j], out);
-          out = fma(skw[2 * n + j], Ex0[i], out);
-          out = fma(skw[3 * n + j], Ex1[i], out);
-        }
-        out -= E[L.Acc + r];
-      } else if (r < 6 * n2 + 12 * n) {
-        const int q = r - 6 * n2, slot = q / n, l = q - slot * n;
-        const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
-        gi = edge_base(g, ex, ey, ez, slot, &dir) + l;
-        uval = Ed[q];
-        if (grp == 0) {         // x-edge Ex[sb=s1][sc=s2], index i = l
-          const int sb = s1, sc = s2, i = l;
-          const T* Fz = F + (4 + sc) * n2;   // z-face sc, [j][i]
-          const T* Fy = F + (2 + sb) * n2;   // y-face sb, [k][i]
-          out = (co[36] + lww[i] + eS[2 + sb] + eS[4 + sc]) * uval;
-          out = fma(skww[0 * n + i], Vt[0 + 2 * sb + 4 * sc], out);
-          out = fma(skww[1 * n + i], Vt[1 + 2 * sb + 4 * sc], out);
-          const T* kb = skw + (2 + sb) * n;
-          const T* kc = skw + (4 + sc) * n;
-          for (int m = 0; m < n; ++m) out = fma(kb[m], Fz[m * n + i], out);
-          for (int m = 0; m < n; ++m) out = fma(kc[m], Fy[m * n + i], out);
-          out = fma(eO[2 + sb], Ed[(0 + (1 - sb) + 2 * sc) * n + i], out);
-          out = fma(eO[4 + sc], Ed[(0 + sb + 2 * (1 - sc)) * n + i], out);
-        } else if (grp == 1) {  // y-edge Ey[sa=s1][sc=s2], index j = l
-          const int sa = s1, sc = s2, j = l;
-          const T* Fz = F + (4 + sc) * n2;   // [j][i]
-          const T* Fx = F + (0 + sa) * n2;   // [k][j]
-          out = (co[36] + lww[n + j] + eS[0 + sa] + eS[4 + sc]) * uval;
-          out = fma(skww[2 * n + j], Vt[sa + 0 + 4 * sc], out);
-          out = fma(skww[3 * n + j], Vt[sa + 2 + 4 * sc], out);
-          const T* ka = skw + (0 + sa) * n;
-          const T* kc = skw + (4 + sc) * n;
-          for (int m = 0; m < n; ++m) out = fma(ka[m], Fz[j * n + m], out);
-          for (int m = 0; m < n; ++m) out = fma(kc[m], Fx[m * n + j], out);
-          out = fma(eO[0 + sa], Ed[(4 + (1 - sa) + 2 * sc) * n + j], out);
-          out = fma(eO[4 + sc], Ed[(4 + sa + 2 * (1 - sc)) * n + j], out);
-        } else {                // z-edge Ez[sa=s1][sb=s2], index k = l
-          const int sa = s1, sb = s2, k = l;
-          const T* Fy = F + (2 + sb) * n2;   // [k][i]
-          const T* Fx = F + (0 + sa) * n2;   // [k][j]
-          out = (co[36] + lww[2 * n + k] + eS[0 + sa] + eS[2 + sb]) * uval;
-          out = fma(skww[4 * n + k], Vt[sa + 2 * sb + 0], out);
-          out = fma(skww[5 * n + k], Vt[sa + 2 * sb + 4], out);
-          const T* ka = skw + (0 + sa) * n;
-          const T* kb = skw + (2 + sb) * n;
-          for (int m = 0; m < n; ++m) out = fma(ka[m], Fy[k * n + m], out);
-          for (int m = 0; m < n; ++m) out = fma(kb[m], Fx[k * n + m], out);
-          out = fma(eO[0 + sa], Ed[(8 + (1 - sa) + 2 * sb) * n + k], out);
-          out = fma(eO[2 + sb], Ed[(8 + sa + 2 * (1 - sb)) * n + k], out);
-        }
-      } else {
-        const int slot = r - 6 * n2 - 12 * n;
-        const int sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
-        gi = vert_index(g, ex, ey, ez, slot, &dir);
-        uval = Vt[slot];
-        out = (co[37] + vS[0 + sa] + vS[2 + sb] + vS[4 + sc]) * uval;
-        const T* ka = skww + (0 + sa) * n;
-        const T* kb = skww + (2 + sb) * n;
-        const T* kc = skww + (4 + sc) * n;
-        const T* ex_ = Ed + (0 + sb + 2 * sc) * n;    // Ex[sb][sc]
-        const T* ey_ = Ed + (4 + sa + 2 * sc) * n;    // Ey[sa][sc]
-        const T* ez_ = Ed + (8 + sa + 2 * sb) * n;    // Ez[sa][sb]
-        for (int m = 0; m < n; ++m) out = fma(ka[m], ex_[m], out);
-        for (int m = 0; m < n; ++m) out = fma(kb[m], ey_[m], out);
-        for (int m = 0; m < n; ++m) out = fma(kc[m], ez_[m], out);
-        out = fma(vO[0 + sa], Vt[slot ^ 1], out);
-        out = fma(vO[2 + sb], Vt[slot ^ 2], out);
-        out = fma(vO[4 + sc], Vt[slot ^ 4], out);
-      }
-      if (!dir) {
-        atomicAdd(v + gi, out);
-        dot += (double)uval * (double)out;
-      }
-    }
-    __syncthreads();
-  }
-
-  if (st != nullptr) {
-    double vals[1] = {dot}, tot[1];
-    if (reduce_grid<1>(vals, partials, &st->counter[0], tot) && threadIdx.x == 0) {
-      const double pq = tot[0];
-      st->pq = pq;
-      if (!(pq > 0.0) || !isfinite(pq)) {
-        st->done = 2;
-      } else {
-        st->alpha = st->rho / pq;
-      }
     }
   }
 }
@@ -939,54 +465,6 @@ int sem_vec_blocks() { return num_sms() * 4; }
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-ApplyConfig sem_apply_config(int n, size_t elem_bytes) {
-  ApplyConfig c;
-  c.threads = kApplyThreads;
-  const int n2 = n * n;
-  // slab depth: whole cube when it fits in ~64 KB of shared memory
-  const size_t budget = 64 * 1024;
-  int ks = n;
-  while (ks > 1 && (size_t)elem_layout(n, ks).size * elem_bytes > budget + (size_t)(12 * n2) * elem_bytes) ks = (ks + 1) / 2;
-  c.ks = ks;
-  // elements per block: enough cube work for the block
-  int per = n2 * n > 6 * n2 + 12 * n + 8 ? n2 * n : 6 * n2 + 12 * n + 8;
-  int epb = (kApplyThreads + per - 1) / per;
-  if (epb < 1) epb = 1;
-  if (epb > 32) epb = 32;
-  c.epb = epb;
-  const ElemLayout L = elem_layout(n, ks);
-  c.smem = apply_hdr_bytes(epb, elem_bytes) + (size_t)epb * L.size * elem_bytes;
-  return c;
-}
-
-template <typename T>
-void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
-                      double* partials, PcgState* st, cudaStream_t s) {
-  const ApplyConfig c = sem_apply_config(g.n, sizeof(T));
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tpt_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
-  int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply<T>, c.threads, c.smem);
-  if (occ < 1) occ = 1;
-  const long long ntiles = (g.nelem + c.epb - 1) / c.epb;
-  long long grid = (long long)num_sms() * occ;
-  if (grid > ntiles) grid = ntiles;
-  k_tpt_apply<T><<<(int)grid, c.threads, c.smem, s>>>(g, b, t, x, y, c.epb, c.ks, partials, st);
-  sem_count_launch();
-}
-template void launch_tpt_apply<double>(const SemGeom&, const SemBasis&, const SemClassTables<double>&,
-                                       const double*, double*, double*, PcgState*, cudaStream_t);
-template void launch_tpt_apply<float>(const SemGeom&, const SemBasis&, const SemClassTables<float>&,
-                                      const float*, float*, double*, PcgState*, cudaStream_t);
-
-void launch_tpt_apply_f64(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t, const double* x,
-                          double* y, double* partials, PcgState* st, cudaStream_t s) {
-  launch_tpt_apply<double>(g, b, t, x, y, partials, st, s);
-}
-
 void launch_cast_f32(long long n, const double* in, float* out, cudaStream_t s) {
   k_scale_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, in, 1.0, out);
   sem_count_launch();

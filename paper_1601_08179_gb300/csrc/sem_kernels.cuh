@@ -3,47 +3,26 @@
 
 #include "sem_internal.h"
 
-// Layout of one element's working set in shared memory (units of T).
-struct ElemLayout {
-  int F, Acc, E, Vt, sk, co, cube, size;
-};
-
-inline __host__ __device__ ElemLayout elem_layout(int n, int ks) {
-  const int n2 = n * n;
-  ElemLayout L;
-  L.F = 0;                  // 6 faces, n^2 each
-  L.Acc = 6 * n2;           // 6 condensed face contractions
-  L.E = 12 * n2;            // 12 edges, n each
-  L.Vt = L.E + 12 * n;      // 8 vertices
-  L.sk = L.Vt + 8;          // skd, skw, skww [3][2][n]; lw, lww [3][n]
-  L.co = L.sk + 24 * n;     // 40 scalars
-  L.cube = L.co + 40;       // ks * n^2 slab of the eigenspace cube
-  L.size = L.cube + ks * n2;
-  L.size = (L.size + 1) & ~1;
-  return L;
-}
-
-// Shared-memory header of the operator kernel: element classes, then metric
-// coefficients, each padded to 16 bytes.
-inline __host__ __device__ size_t apply_hdr_cls_bytes(int epb) { return ((size_t)epb * 4 + 15) & ~size_t(15); }
-inline __host__ __device__ size_t apply_hdr_bytes(int epb, size_t elem_bytes) {
-  return apply_hdr_cls_bytes(epb) + (((size_t)epb * 4 * elem_bytes + 15) & ~size_t(15));
-}
-
-// Launch configuration of the fused operator kernel for degree p.
+// Operator launch configuration for degree p (sem_apply.cu).
 struct ApplyConfig {
-  int epb;      // elements per block
+  int epb;      // elements per CTA tile
   int ks;       // eigenspace slab depth (k planes held at once)
   int threads;
   size_t smem;  // dynamic shared memory bytes
 };
 ApplyConfig sem_apply_config(int n, size_t elem_bytes);
 
-// y = Hhat~ x on the skeleton (transformed space).  y must be zero on entry.
-// If st != nullptr: also x^T y -> st->pq, alpha = rho / pq (CG step).
-void launch_tpt_apply_f64(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
-                          const double* x, double* y, double* partials, PcgState* st,
-                          cudaStream_t s);
+// Per-class operator coefficient blocks (layout in sem_internal.h), computed in
+// FP64 and stored in T.
+template <typename T>
+void launch_class_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoef, const double* dinv, T* coef,
+                         cudaStream_t s);
+
+// y = Hhat~ x on the skeleton (transformed space); y must be zero on entry.
+// If st != nullptr: also x^T y -> st->pq and alpha = rho / pq (CG step).
+template <typename T>
+void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
+                      double* partials, PcgState* st, cudaStream_t s);
 
 void launch_class_tables(const SemGeom& g, const SemBasis& b, const double* ux_w, const double* uy_w,
                          const double* uz_w, double lambda, double* dcoef, double* dinv,
@@ -101,11 +80,6 @@ void launch_pcg_update(long long nb, T* x, T* r, const T* p, const T* q, const T
 // p = P r + beta p, q = 0.
 template <typename T>
 void launch_pcg_dir(long long nb, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s);
-
-// Generic operator launcher (T = double or float tables and vectors).
-template <typename T>
-void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
-                      double* partials, PcgState* st, cudaStream_t s);
 
 // Iterative refinement: r = b - Ax and st->rr = r.r (FP64); out = (float)(in * scale);
 // x += scale * c.
