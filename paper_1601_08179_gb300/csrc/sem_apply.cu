@@ -36,7 +36,7 @@ constexpr int kHdrInts = 28;   // per element: class, loaded class, 6 + 12 + 8 e
 
 // Shared-memory layout of one element (units of T).
 struct ElemSm {
-  int F, Acc, E, Eo, Vt, Vo, C, cube, size;
+  int F, Acc, E, Eo, Vt, Vo, C, Bt, cube, size;
 };
 
 __host__ __device__ inline ElemSm elem_sm(int n, int ks) {
@@ -49,7 +49,8 @@ __host__ __device__ inline ElemSm elem_sm(int n, int ks) {
   L.Vt = L.Eo + 12 * n;
   L.Vo = L.Vt + 8;
   L.C = L.Vo + 8;
-  L.cube = L.C + 18 * n + 24;
+  L.Bt = L.C + 18 * n + 24;     // b/t contractions (summed over all k-slabs)
+  L.cube = L.Bt + 2 * n2;
   L.size = (L.cube + ks * n2 + 3) & ~3;
   return L;
 }
@@ -324,58 +325,78 @@ k_tpt_apply(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __rest
       E[L.Vo + slot] = out;
     }
 
-    // ---- condensed part, one k-slab of the eigenspace cube at a time
+    // ---- condensed part, one k-slab of the eigenspace cube at a time.
+    // Expansion (Table 2) and -D^-1: one thread per (j, i) column of the cube,
+    // face values and scaled vectors of the column held in registers; the b/t
+    // contraction (sum over k) is done in the same registers.
     for (int k0 = 0; k0 < n; k0 += ks) {
       const int kn = min(ks, n - k0);
-      const int per = kn * n2;
-      for (int t = tid; t < epb * per; t += nt) {       // expansion and -D^-1 (Table 2)
-        const int el = t / per, r = t - el * per;
-        const int kk = r / n2, ji = r - kk * n2, j = ji / n, i = ji - j * n, k = k0 + kk;
+      for (int t = tid; t < epb * n2; t += nt) {
+        const int el = t / n2, ji = t - el * n2, j = ji / n, i = ji - j * n;
         T* E = elems + el * L.size;
         const int cls = hdr[el * kHdrInts];
         const T* F = E + L.F;
         const T* skd = E + L.C;
-        T x = skd[i] * F[k * n + j];
-        x = fma(skd[n + i], F[n2 + k * n + j], x);
-        x = fma(skd[2 * n + j], F[2 * n2 + k * n + i], x);
-        x = fma(skd[3 * n + j], F[3 * n2 + k * n + i], x);
-        x = fma(skd[4 * n + k], F[4 * n2 + ji], x);
-        x = fma(skd[5 * n + k], F[5 * n2 + ji], x);
-        const T nd = cls >= 0 ? __ldg(tab.coef + (long long)cls * co.stride + co.ndinv + k * n2 + ji) : T(0);
-        E[L.cube + r] = nd * x;
+        const T ai = skd[i], bi = skd[n + i], cj = skd[2 * n + j], dj = skd[3 * n + j];
+        const T fb = F[4 * n2 + ji], ft = F[5 * n2 + ji];
+        const T* nd = tab.coef + (cls >= 0 ? (long long)cls * co.stride : 0LL) + co.ndinv + ji;
+        T sb = k0 == 0 ? T(0) : E[L.Bt + ji];
+        T st_ = k0 == 0 ? T(0) : E[L.Bt + n2 + ji];
+        T* cube = E + L.cube + ji;
+#pragma unroll 4
+        for (int kk = 0; kk < kn; ++kk) {
+          const int k = k0 + kk;
+          const T ek = skd[4 * n + k], gk = skd[5 * n + k];
+          T x = ai * F[k * n + j];
+          x = fma(bi, F[n2 + k * n + j], x);
+          x = fma(cj, F[2 * n2 + k * n + i], x);
+          x = fma(dj, F[3 * n2 + k * n + i], x);
+          x = fma(ek, fb, x);
+          x = fma(gk, ft, x);
+          const T vv = (cls >= 0 ? __ldg(nd + k * n2) : T(0)) * x;
+          cube[kk * n2] = vv;
+          sb = fma(ek, vv, sb);
+          st_ = fma(gk, vv, st_);
+        }
+        E[L.Bt + ji] = sb;
+        E[L.Bt + n2 + ji] = st_;
       }
       __syncthreads();
-      // contractions back to the faces, accumulated onto the primary part
-      for (int t = tid; t < epb * 2 * kn * n; t += nt) {   // w / e: sum over i
-        const int el = t / (2 * kn * n), r = t - el * 2 * kn * n, s = r / (kn * n), q = r - s * kn * n;
-        const int kk = q / n, j = q - kk * n;
+      // w / e: rows over i, both faces from one pass over the row
+      for (int t = tid; t < epb * kn * n; t += nt) {
+        const int el = t / (kn * n), q = t - el * kn * n, kk = q / n, j = q - kk * n;
         T* E = elems + el * L.size;
-        const T* kv = E + L.C + s * n;
+        const T* ka = E + L.C;
+        const T* kb = E + L.C + n;
         const T* row = E + L.cube + kk * n2 + j * n;
-        T acc = E[L.Acc + s * n2 + (k0 + kk) * n + j];
+        const int o = (k0 + kk) * n + j;
+        T s0 = E[L.Acc + o], s1 = E[L.Acc + n2 + o];
 #pragma unroll 8
-        for (int i = 0; i < n; ++i) acc = fma(kv[i], row[i], acc);
-        E[L.Acc + s * n2 + (k0 + kk) * n + j] = acc;
+        for (int i = 0; i < n; ++i) {
+          const T c = row[i];
+          s0 = fma(ka[i], c, s0);
+          s1 = fma(kb[i], c, s1);
+        }
+        E[L.Acc + o] = s0;
+        E[L.Acc + n2 + o] = s1;
       }
-      for (int t = tid; t < epb * 2 * kn * n; t += nt) {   // s / n: sum over j
-        const int el = t / (2 * kn * n), r = t - el * 2 * kn * n, s = r / (kn * n), q = r - s * kn * n;
-        const int kk = q / n, i = q - kk * n;
+      // s / n: columns over j
+      for (int t = tid; t < epb * kn * n; t += nt) {
+        const int el = t / (kn * n), q = t - el * kn * n, kk = q / n, i = q - kk * n;
         T* E = elems + el * L.size;
-        const T* kv = E + L.C + (2 + s) * n;
+        const T* ka = E + L.C + 2 * n;
+        const T* kb = E + L.C + 3 * n;
         const T* col = E + L.cube + kk * n2 + i;
-        T acc = E[L.Acc + (2 + s) * n2 + (k0 + kk) * n + i];
+        const int o = (k0 + kk) * n + i;
+        T s0 = E[L.Acc + 2 * n2 + o], s1 = E[L.Acc + 3 * n2 + o];
 #pragma unroll 8
-        for (int j = 0; j < n; ++j) acc = fma(kv[j], col[j * n], acc);
-        E[L.Acc + (2 + s) * n2 + (k0 + kk) * n + i] = acc;
-      }
-      for (int t = tid; t < epb * 2 * n2; t += nt) {       // b / t: sum over the slab's k
-        const int el = t / (2 * n2), r = t - el * 2 * n2, s = r / n2, ji = r - s * n2;
-        T* E = elems + el * L.size;
-        const T* kv = E + L.C + (4 + s) * n + k0;
-        const T* col = E + L.cube + ji;
-        T acc = E[L.Acc + (4 + s) * n2 + ji];
-        for (int kk = 0; kk < kn; ++kk) acc = fma(kv[kk], col[kk * n2], acc);
-        E[L.Acc + (4 + s) * n2 + ji] = acc;
+        for (int j = 0; j < n; ++j) {
+          const T c = col[j * n];
+          s0 = fma(ka[j], c, s0);
+          s1 = fma(kb[j], c, s1);
+        }
+        E[L.Acc + 2 * n2 + o] = s0;
+        E[L.Acc + 3 * n2 + o] = s1;
       }
       __syncthreads();
     }
@@ -386,7 +407,7 @@ k_tpt_apply(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __rest
       const int off = hdr[el * kHdrInts + 2 + slot];
       if (off < 0) continue;
       const T* E = elems + el * L.size;
-      const T o = E[L.Acc + r];
+      const T o = slot >= 4 ? E[L.Acc + r] + E[L.Bt + r - 4 * n2] : E[L.Acc + r];
       atomicAdd(v + off + idx, o);
       dot = fma(E[L.F + r], o, dot);
     }
@@ -458,8 +479,9 @@ ApplyConfig sem_apply_config(int n, size_t elem_bytes) {
   const size_t big = 200 * 1024, small = 96 * 1024;
   int ks = n;
   int epb = 1;
-  const int n3 = n * n * n;
-  const int want = n3 >= 512 ? 1 : (512 + n3 - 1) / n3;
+  // one thread per (j, i) cube column: aim for epb * n^2 close to the block size
+  const int n2 = n * n;
+  const int want = n2 >= kThreads ? 1 : kThreads / n2;
   epb = want > 64 ? 64 : want;
   auto bytes = [&](int e, int k) { return hdr_bytes(e) + (size_t)e * elem_sm(n, k).size * elem_bytes; };
   while (epb > 1 && bytes(epb, ks) > small) --epb;

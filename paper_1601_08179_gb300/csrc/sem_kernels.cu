@@ -331,6 +331,12 @@ __global__ void k_recover_expand(SemGeom g, SemBasis b, SemClassTables<double> t
 // ---------------------------------------------------------------------------
 // Per-thread partial sums are kept in T (FP32 for the inner solver, whose
 // scalars need only FP32 accuracy) and combined across the grid in FP64.
+// Vectors are accessed as 16-byte packs (float4 / double2) with a scalar tail.
+template <typename T, int W>
+struct alignas(sizeof(T) * W) Pack {
+  T v[W];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restrict__ p,
@@ -371,9 +377,30 @@ k_pcg_update(long long nb, T* __restrict__ x, T* __restrict__ r, const T* __rest
              const T* __restrict__ q, const T* __restrict__ P, double* __restrict__ partials,
              PcgState* st) {
   if (st->done) return;
+  constexpr int W = 16 / sizeof(T);
+  using V = Pack<T, W>;
   const T alpha = (T)st->alpha;
   T rz = T(0), rr = T(0);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+  const long long nv = nb / W;
+  const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+  for (long long iv = g0; iv < nv; iv += gs) {
+    V xv = reinterpret_cast<const V*>(x)[iv];
+    V rv = reinterpret_cast<const V*>(r)[iv];
+    const V pv = reinterpret_cast<const V*>(p)[iv];
+    const V qv = reinterpret_cast<const V*>(q)[iv];
+    const V Pv = reinterpret_cast<const V*>(P)[iv];
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      xv.v[c] = fma(alpha, pv.v[c], xv.v[c]);
+      const T ri = fma(-alpha, qv.v[c], rv.v[c]);
+      rv.v[c] = ri;
+      rz = fma(ri, Pv.v[c] * ri, rz);
+      rr = fma(ri, ri, rr);
+    }
+    reinterpret_cast<V*>(x)[iv] = xv;
+    reinterpret_cast<V*>(r)[iv] = rv;
+  }
+  for (long long i = nv * W + g0; i < nb; i += gs) {
     x[i] = fma(alpha, p[i], x[i]);
     const T ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
@@ -404,8 +431,24 @@ __global__ void __launch_bounds__(kVecThreads)
 k_pcg_dir(long long nb, const T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
           const T* __restrict__ P, PcgState* st) {
   if (st->done) return;
+  constexpr int W = 16 / sizeof(T);
+  using V = Pack<T, W>;
   const T beta = (T)st->beta;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+  const long long nv = nb / W;
+  const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+  V zero;
+#pragma unroll
+  for (int c = 0; c < W; ++c) zero.v[c] = T(0);
+  for (long long iv = g0; iv < nv; iv += gs) {
+    const V rv = reinterpret_cast<const V*>(r)[iv];
+    const V Pv = reinterpret_cast<const V*>(P)[iv];
+    V pv = reinterpret_cast<const V*>(p)[iv];
+#pragma unroll
+    for (int c = 0; c < W; ++c) pv.v[c] = fma(beta, pv.v[c], Pv.v[c] * rv.v[c]);
+    reinterpret_cast<V*>(p)[iv] = pv;
+    reinterpret_cast<V*>(q)[iv] = zero;
+  }
+  for (long long i = nv * W + g0; i < nb; i += gs) {
     p[i] = fma(beta, p[i], P[i] * r[i]);
     q[i] = T(0);
   }

@@ -1,0 +1,80 @@
+"""Full benchmark size (graded p = 8 workload, 32^3 elements, N = 1.68e7)
+against the oracle's own Algorithm-4 solve of the same problem, recorded in
+tests/golden/oracle_<workload>.json by `python -m oracle.reference_solve 8`
+(oracle-only script; seeded samples of the solution, of the transformed
+diagonal and of the nodal condensed load, and the CG iteration count)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import sem_inputs as si
+from oracle.mesh import Mesh
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+W = si.scale_workload(8)
+GOLD = os.path.join(os.path.dirname(__file__), "golden", f"oracle_{W.name}.json")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    from paper_1601_08179_gb300 import build, sem
+    if not os.path.exists(GOLD):
+        pytest.fail(f"missing {GOLD}: run python -m oracle.reference_solve 8")
+    rec = json.load(open(GOLD))
+    build.build()
+    hx, hy, hz = W.widths()
+    ms = Mesh(W.p, hx, hy, hz)
+    X, Y, Z = ms.coords()
+    f = (si.manufactured_f(X, Y, Z, W.lam) + si.node_noise(X.size, W.seed).reshape(X.shape)).ravel()
+    ctx = sem.sem_setup(W.p, hx, hy, hz, W.lam)
+    return rec, ctx, dev(f)
+
+
+def _sampled_rel(got, want):
+    return np.linalg.norm(got - want) / np.linalg.norm(want)
+
+
+def test_precond_diag_and_condensed_load_samples(setup):
+    import torch
+    from paper_1601_08179_gb300 import sem
+    rec, ctx, f = setup
+    d = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+    sem.sem_precond_diag(ctx, d)
+    idx = np.array(rec["diag_samples"]["index"])
+    assert _sampled_rel(host(d)[idx], np.array(rec["diag_samples"]["value"])) <= 1e-12
+    fb = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+    sem.sem_condense_rhs(ctx, f, fb, sem.SPACE_NODAL)
+    got = host(fb)
+    idx = np.array(rec["fhat_nodal_samples"]["index"])
+    assert _sampled_rel(got[idx], np.array(rec["fhat_nodal_samples"]["value"])) <= 1e-12
+    assert np.linalg.norm(got) == pytest.approx(rec["fhat_nodal_norm2"], rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solution_samples_and_iterations(setup, precision):
+    import torch
+    from paper_1601_08179_gb300 import sem
+    rec, ctx, f = setup
+    prec = sem.PREC_FP64 if precision == "fp64" else sem.PREC_MIXED
+    u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+    idx = np.array(rec["u_samples"]["index"])
+    want = np.array(rec["u_samples"]["value"])
+    # to the oracle's tolerance: parity of the solver itself
+    sem.sem_set_opts(ctx, sem.default_opts(precision=prec, rtol=rec["rtol"]))
+    sem.sem_solve(ctx, f, u)
+    got = host(u)
+    assert _sampled_rel(got[idx], want) <= 1e-9
+    assert np.linalg.norm(got) == pytest.approx(rec["u_norm2"], rel=1e-9)
+    # at the benchmark tolerance 1e-10
+    sem.sem_set_opts(ctx, sem.default_opts(precision=prec))
+    info = sem.sem_solve(ctx, f, u)
+    err = _sampled_rel(host(u)[idx], want)
+    print(f"{precision}: sampled error at rtol 1e-10: {err:.2e}, iterations {info['iters']}")
+    assert err <= 1e-8
+    if precision == "fp64":
+        assert abs(info["iters"] - rec["iterations_to_1e-10"]) <= 2
