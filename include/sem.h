@@ -94,8 +94,16 @@ typedef struct {
   int precision;      /* sem_precision (default SEM_PREC_FP64) */
   int check_every;    /* CG iterations per device-side batch between host
                          convergence checks (default 16) */
-  double inner_rtol;  /* MIXED: residual reduction of each FP32 inner solve (default 1e-4) */
+  double inner_rtol;  /* MIXED scheme 0: residual reduction of each restarted FP32 inner
+                         solve (default 1e-4) */
   int max_refine;     /* MIXED: cap on FP64 refinement steps (default 40) */
+  int mixed_scheme;   /* MIXED: 1 = one FP32 CG kept across refinement steps, whose
+                         residual is replaced by the FP64 residual at each step
+                         ("reliable updates", default); 0 = the FP32 CG restarts from
+                         zero at every refinement step (classical refinement) */
+  double reliable_delta; /* MIXED scheme 1: a refinement step is taken when the FP32
+                         recursive residual has fallen by this factor since the
+                         previous step (default 0.1) */
 } sem_opts;
 
 /* Result of a solve. */
@@ -175,9 +183,10 @@ sem_status sem_recover_interior(sem_ctx* ctx, const double* f, const double* uB,
 /* Full solve (Algorithm 4): condense the load, CG with the BT preconditioner
  * to opts.rtol, recover the interior.  With opts.precision = SEM_PREC_MIXED the
  * CG runs in FP32 (FP32 operator, vectors and preconditioner) inside FP64
- * iterative refinement: each step solves A c = r_k/||r_k|| to opts.inner_rtol
- * and updates x += ||r_k|| c with the residual r = b - A x recomputed by the
- * FP64 operator; the stopping rule is the FP64 residual.  f, u: device full nodal fields; u0:
+ * iterative refinement: every refinement step adds the FP32 correction to the
+ * FP64 iterate x and recomputes the residual r = b - A x with the FP64
+ * operator and FP64 dot products (see opts.mixed_scheme); the stopping rule
+ * is that FP64 residual.  f, u: device full nodal fields; u0:
  * optional device skeleton start vector in NODAL space (NULL = 0); info may be
  * NULL.  Returns SEM_ENOCONV / SEM_EBREAKDOWN with u still written. */
 sem_status sem_solve(sem_ctx* ctx, const double* f, double* u, const double* u0,
@@ -225,6 +234,28 @@ sem_status sem_unpack_skeleton(sem_ctx* ctx, const double* uB, double* u_full, v
  * be cleared between calls.  Asynchronous on `stream`. */
 sem_status sem_condense_rhs_noalloc(sem_ctx* ctx, const double* f, double* fB,
                                     sem_space space, void* stream);
+
+/* Adjoint solve for gradients of a solve: w = A^-1 g, A the assembled
+ * (uncondensed) Helmholtz operator on the free nodes and g a nodal load vector
+ * (for J(u), g = dJ/du).  A is symmetric, so this is the same condensed solve
+ * as sem_solve with the load g in place of (lumped mass) o f.  g, w: device
+ * full nodal fields; boundary entries of g are ignored and w is 0 there.
+ * Uses the context's options (precision, rtol).  Allocates its buffers on
+ * first use. */
+sem_status sem_solve_adjoint(sem_ctx* ctx, const double* g, double* w, sem_info* info, void* stream);
+
+/* Gradients of J(u(f, lambda, h)) from the adjoint w of a solve u (u =
+ * sem_solve(f), w = sem_solve_adjoint(dJ/du)):
+ *   df        = M w                          (device full field; 0 on the boundary)
+ *   *dlambda  = -w^T M u                     (M: assembled lumped mass, dA/dlambda)
+ *   dh*[i]    = sum over the elements of slab i of
+ *               -sum_k (dd_k/dh) w_e^T K_k u_e + (dJ_e/dh) sum_abc w_a w_b w_c (w f)_e,
+ * with d = J (lambda, 4/h1^2, 4/h2^2, 4/h3^2), J = h1 h2 h3 / 8
+ * (Eq. metriccoeffelement) and K_k the Kronecker terms of Eq. helmholtz_operator.
+ * w, u, f, df: device full fields.  dlambda, dhx[mx], dhy[my], dhz[mz]: HOST
+ * outputs (may be NULL).  Synchronous. */
+sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const double* f, double* df,
+                         double* dlambda, double* dhx, double* dhy, double* dhz, void* stream);
 
 /* Residual history of the last MIXED solve: rel_res[k] = ||b - A x_k|| / ||b||
  * (FP64, transformed condensed space) before refinement step k and after the

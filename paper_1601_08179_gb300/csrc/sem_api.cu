@@ -68,6 +68,11 @@ struct sem_ctx {
   float* d_coef_f = nullptr;           // the same in FP32 (mixed precision)
   double* d_mats = nullptr;            // 4 n*n: S_II, V, V^T M_II, M_II V
   double* d_mass = nullptr;            // [Nx + Ny + Nz] assembled 1D lumped masses
+  double* d_h = nullptr;               // [mx + my + mz] element widths
+  double* d_K = nullptr;               // (p+1)^2 stiffness, [p+1] GLL weights
+  double* d_full = nullptr;            // full-field scratch (adjoint right-hand side)
+  double* d_E = nullptr;               // [n_e][5] element bilinear forms (gradients)
+  double* d_grad = nullptr;            // [1 + mx + my + mz] gradient outputs
   double* d_P = nullptr;               // BT preconditioner (inverse diagonal)
   double *d_x = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_b = nullptr;
   double *d_t1 = nullptr, *d_t2 = nullptr;
@@ -443,6 +448,114 @@ sem_status pcg_mixed(sem_ctx* c, bool warm, sem_info* info) {
   return SEM_OK;
 }
 
+// Mixed precision with reliable updates: one FP32 CG whose search direction
+// is kept across refinement steps.  A refinement step (when the FP32
+// recursive residual has fallen by reliable_delta since the previous step, or
+// the FP32 CG stops) adds the FP32 correction to the FP64 iterate, recomputes the
+// true residual b - A x with the FP64 operator and restarts the FP32
+// recursion from it (rho, |r|^2) without resetting the direction.
+sem_status pcg_mixed_reliable(sem_ctx* c, bool warm, sem_info* info) {
+  const SemGeom& g = c->g;
+  cudaStream_t s = c->stream;
+  sem_status st = ensure_mixed(c);
+  if (st != SEM_OK) return st;
+  st = build_graph32(c);
+  if (st != SEM_OK) return st;
+  c->refine_hist.clear();
+  if (warm) {
+    st = apply_t(c, c->d_x, c->d_q, s);
+    if (st != SEM_OK) return st;
+  } else {
+    SEM_CUDA(cudaMemsetAsync(c->d_x, 0, sizeof(double) * g.nb, s));
+    SEM_CUDA(cudaMemsetAsync(c->d_q, 0, sizeof(double) * g.nb, s));
+  }
+  SEM_CUDA(cudaMemsetAsync(c->d_t2, 0, sizeof(double) * g.nb, s));
+  launch_ir_residual(g.nb, c->d_b, c->d_t2, c->d_r, c->d_partials, c->d_st, s);
+  SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  const double bb = c->h_st->rr;
+  launch_ir_residual(g.nb, c->d_b, c->d_q, c->d_r, c->d_partials, c->d_st, s);
+  SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  double rr_hi = c->h_st->rr;
+  double rel = bb > 0.0 ? std::sqrt(rr_hi / bb) : 0.0;
+  c->refine_hist.push_back(rel);
+  if (!std::isfinite(rr_hi)) return fail(SEM_EBREAKDOWN, "non-finite residual");
+  int refinements = 0, total = 0;
+  sem_status result = SEM_ENOCONV;
+  if (rel <= c->opts.rtol) {
+    result = SEM_OK;
+  } else {
+    // FP32 CG on A c = r, unscaled; its own stopping target is the global one
+    launch_scale_to_f32(g.nb, c->d_r, 1.0, c->d_b32, s);
+    launch_pcg_init<float>(g.nb, c->d_b32, c->d_r32, c->d_p32, c->d_q32, c->d_x32, c->d_P32, c->d_partials,
+                           c->d_st32, bb > 0 ? c->opts.rtol * std::sqrt(bb / rr_hi) : 1.0, c->opts.maxit, 0, s);
+    SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    double rr_ref = c->h_st->rr;
+    const double trig = c->opts.reliable_delta * c->opts.reliable_delta;
+    int stalls = 0;
+    double best = rel;
+    const int max_batches = c->opts.maxit / c->opts.check_every + 2 + c->opts.max_refine;
+    for (int b = 0; b < max_batches; ++b) {
+      if (c->h_st->done == 0) {
+        const int it0 = c->h_st->iter;
+        SEM_CUDA(cudaGraphLaunch(c->graph32, s));
+        sem_count_launch(3LL * c->graph32_iters);
+        SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+        SEM_CUDA(cudaStreamSynchronize(s));
+        if (c->graph32_prof) {
+          int worked = c->h_st->iter - it0 + (c->h_st->done == 2 ? 1 : 0);
+          if (worked > c->graph32_iters) worked = c->graph32_iters;
+          for (int it = 0; it < worked; ++it) {
+            float ms = 0.f;
+            SEM_CUDA(cudaEventElapsedTime(&ms, c->pev32[2 * it], c->pev32[2 * it + 1]));
+            c->prof_ms += ms;
+            c->prof_count += 1;
+          }
+        }
+      }
+      total = c->h_st->iter;
+      const int done32 = c->h_st->done;
+      if (done32 == 0 && c->h_st->rr > trig * rr_ref) continue;
+      // refinement step: fold the FP32 correction into x, true residual in FP64
+      launch_ir_update(g.nb, c->d_x, c->d_x32, 1.0, s);
+      SEM_CUDA(cudaMemsetAsync(c->d_x32, 0, sizeof(float) * g.nb, s));
+      st = apply_t(c, c->d_x, c->d_q, s);
+      if (st != SEM_OK) return st;
+      launch_ir_residual(g.nb, c->d_b, c->d_q, c->d_r, c->d_partials, c->d_st, s);
+      SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+      SEM_CUDA(cudaStreamSynchronize(s));
+      rr_hi = c->h_st->rr;
+      ++refinements;
+      rel = bb > 0.0 ? std::sqrt(rr_hi / bb) : 0.0;
+      c->refine_hist.push_back(rel);
+      if (!std::isfinite(rr_hi)) { result = SEM_EBREAKDOWN; break; }
+      if (rel <= c->opts.rtol) { result = SEM_OK; break; }
+      if (done32 == 2) { result = SEM_EBREAKDOWN; break; }
+      if (done32 == 3 || refinements >= c->opts.max_refine) break;
+      stalls = rel < 0.9 * best ? 0 : stalls + 1;
+      if (rel < best) best = rel;
+      if (stalls >= 3) break;     // no progress at the FP32 accuracy limit
+      // restart the FP32 recursion from the true residual, keeping the direction
+      launch_scale_to_f32(g.nb, c->d_r, 1.0, c->d_r32, s);
+      launch_pcg_rebase_f32(g.nb, c->d_r32, c->d_P32, c->d_p32, c->d_q32, done32 != 0 ? 1 : 0, c->d_partials,
+                            c->d_st32, s);
+      SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+      SEM_CUDA(cudaStreamSynchronize(s));
+      rr_ref = c->h_st->rr;
+    }
+  }
+  if (info) {
+    info->iters += total;
+    info->refinements = refinements;
+    info->rel_res = rel;
+  }
+  if (result == SEM_EBREAKDOWN) return fail(result, "CG breakdown or non-finite residual in the refinement");
+  if (result != SEM_OK) return fail(result, "refinement did not reach rtol (maxit, max_refine or stagnation)");
+  return SEM_OK;
+}
+
 void free_ctx(sem_ctx* c) {
   if (c == nullptr) return;
   int prev = 0;
@@ -455,6 +568,9 @@ void free_ctx(sem_ctx* c) {
   for (void* p : ptrs32)
     if (p) cudaFree(p);
   for (cudaEvent_t ev : c->pev32) cudaEventDestroy(ev);
+  void* ptrs_adj[] = {c->d_h, c->d_K, c->d_full, c->d_E, c->d_grad};
+  for (void* p : ptrs_adj)
+    if (p) cudaFree(p);
   void* ptrs[] = {c->d_cls, c->d_uw, c->d_dcoef, c->d_dinv, c->d_mats, c->d_mass, c->d_P, c->d_x, c->d_r,
                   c->d_p, c->d_q, c->d_b, c->d_t1, c->d_t2, c->d_c0, c->d_c1, c->d_FtI, c->d_partials, c->d_st};
   for (void* p : ptrs)
@@ -485,6 +601,8 @@ void sem_default_opts(sem_opts* o) {
   o->check_every = 16;
   o->inner_rtol = 1e-4;
   o->max_refine = 40;
+  o->mixed_scheme = 1;
+  o->reliable_delta = 0.1;
 }
 
 static sem_status check_opts(const sem_opts* o) {
@@ -494,6 +612,8 @@ static sem_status check_opts(const sem_opts* o) {
   if (o->precision != SEM_PREC_FP64 && o->precision != SEM_PREC_MIXED) return fail(SEM_EINVAL, "unknown precision");
   if (!(o->inner_rtol > 0.0 && o->inner_rtol < 1.0)) return fail(SEM_EINVAL, "inner_rtol must be in (0, 1)");
   if (o->max_refine < 1) return fail(SEM_EINVAL, "max_refine must be >= 1");
+  if (o->mixed_scheme != 0 && o->mixed_scheme != 1) return fail(SEM_EINVAL, "mixed_scheme must be 0 or 1");
+  if (!(o->reliable_delta > 0.0 && o->reliable_delta < 1.0)) return fail(SEM_EINVAL, "reliable_delta must be in (0, 1)");
   return SEM_OK;
 }
 
@@ -764,8 +884,11 @@ sem_status sem_solve(sem_ctx* c, const double* f, double* u, const double* u0, s
   sem_status st = condense_rhs_t(c, f, c->d_b, s);
   if (st != SEM_OK) return st;
   if (u0) launch_skel_transform(c->g, c->mat(2), u0, c->d_x, s);
-  sem_status cg = c->opts.precision == SEM_PREC_MIXED ? pcg_mixed(c, u0 != nullptr, info)
-                                                     : pcg_fp64(c, u0 != nullptr, info);
+  sem_status cg;
+  if (c->opts.precision == SEM_PREC_MIXED)
+    cg = c->opts.mixed_scheme == 1 ? pcg_mixed_reliable(c, u0 != nullptr, info) : pcg_mixed(c, u0 != nullptr, info);
+  else
+    cg = pcg_fp64(c, u0 != nullptr, info);
   if (cg != SEM_OK && cg != SEM_ENOCONV && cg != SEM_EBREAKDOWN) return cg;
   std::string cg_err = t_err;
   st = recover_t(c, c->d_x, u, s);
@@ -853,6 +976,71 @@ sem_status sem_profile_read(sem_ctx* c, double* apply_ms, long long* apply_launc
     c->prof_ms = 0.0;
     c->prof_count = 0;
   }
+  return SEM_OK;
+}
+
+static sem_status ensure_adjoint(sem_ctx* c) {
+  if (c->d_grad != nullptr) return SEM_OK;
+  const SemGeom& g = c->g;
+  const int q = g.p + 1;
+  std::vector<double> h(c->hx);
+  h.insert(h.end(), c->hy.begin(), c->hy.end());
+  h.insert(h.end(), c->hz.begin(), c->hz.end());
+  std::vector<double> kw(c->h1.K);
+  kw.insert(kw.end(), c->h1.w.begin(), c->h1.w.end());
+  bool ok = dalloc(&c->d_h, h.size()) == cudaSuccess && dalloc(&c->d_K, kw.size()) == cudaSuccess &&
+            dalloc(&c->d_full, (size_t)(g.Nx * g.Ny * g.Nz)) == cudaSuccess &&
+            dalloc(&c->d_E, (size_t)g.nelem * 5) == cudaSuccess &&
+            dalloc(&c->d_grad, (size_t)(1 + g.mx + g.my + g.mz)) == cudaSuccess;
+  if (!ok) return fail(SEM_ENOMEM, "cannot allocate adjoint buffers");
+  SEM_CUDA(cudaMemcpy(c->d_h, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SEM_CUDA(cudaMemcpy(c->d_K, kw.data(), kw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  (void)q;
+  return SEM_OK;
+}
+
+sem_status sem_solve_adjoint(sem_ctx* c, const double* gload, double* w, sem_info* info, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (gload == nullptr || w == nullptr) return fail(SEM_EINVAL, "null vector");
+  sem_status st = ensure_adjoint(c);
+  if (st != SEM_OK) return st;
+  const SemGeom& g = c->g;
+  const double *mx = c->d_mass, *my = mx + g.Nx, *mz = my + g.Ny;
+  // sem_solve's load is (lumped mass) o f: pass f = g / m so that the load is g
+  launch_mass_divide(g, mx, my, mz, gload, c->d_full, 0, (cudaStream_t)stream);
+  SEM_CUDA(cudaGetLastError());
+  return sem_solve(c, c->d_full, w, nullptr, info, stream);
+}
+
+sem_status sem_gradients(sem_ctx* c, const double* w, const double* u, const double* f, double* df,
+                         double* dlambda, double* dhx, double* dhy, double* dhz, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (w == nullptr || u == nullptr || f == nullptr || df == nullptr) return fail(SEM_EINVAL, "null vector");
+  sem_status st = ensure_adjoint(c);
+  if (st != SEM_OK) return st;
+  const SemGeom& g = c->g;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double *mx = c->d_mass, *my = mx + g.Nx, *mz = my + g.Ny;
+  const int q = g.p + 1;
+  launch_mass_divide(g, mx, my, mz, w, df, 1, s);
+  launch_lambda_gradient(g, mx, my, mz, w, u, c->d_partials, c->d_grad, &c->d_st->counter[3], s);
+  launch_element_forms(g, c->d_K + q * q, c->d_K, w, u, f, c->d_E, s);
+  const double* hx = c->d_h;
+  const double* hy = hx + g.mx;
+  const double* hz = hy + g.my;
+  launch_width_gradient(g, 0, hx, hy, hz, c->lambda, c->d_E, c->d_grad + 1, s);
+  launch_width_gradient(g, 1, hx, hy, hz, c->lambda, c->d_E, c->d_grad + 1 + g.mx, s);
+  launch_width_gradient(g, 2, hx, hy, hz, c->lambda, c->d_E, c->d_grad + 1 + g.mx + g.my, s);
+  SEM_CUDA(cudaGetLastError());
+  std::vector<double> out(1 + g.mx + g.my + g.mz);
+  SEM_CUDA(cudaMemcpyAsync(out.data(), c->d_grad, out.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  if (dlambda) *dlambda = out[0];
+  if (dhx) std::memcpy(dhx, out.data() + 1, g.mx * sizeof(double));
+  if (dhy) std::memcpy(dhy, out.data() + 1 + g.mx, g.my * sizeof(double));
+  if (dhz) std::memcpy(dhz, out.data() + 1 + g.mx + g.my, g.mz * sizeof(double));
   return SEM_OK;
 }
 

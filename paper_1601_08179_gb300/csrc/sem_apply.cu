@@ -453,6 +453,286 @@ int num_sms_cached() {
   return sms;
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-element variant for small degrees (n <= 7)
+// ---------------------------------------------------------------------------
+// One warp owns one element at a time: its whole working set sits in the
+// warp's slice of shared memory and phases are separated by __syncwarp only,
+// so warps of a CTA progress independently.  Trip counts are compile-time.
+template <int N>
+struct WarpSm {
+  static constexpr int N2 = N * N, N3 = N2 * N;
+  static constexpr int F = 0, E = 6 * N2, Vt = E + 12 * N, Acc = Vt + 8, Eo = Acc + 6 * N2, Vo = Eo + 12 * N,
+                       C = Vo + 8, cube = C + 18 * N + 24, size = (cube + N3 + 3) & ~3;
+};
+constexpr int kWarpHdr = 32;   // ints per warp: 26 entity offsets, class, loaded class
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
+k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
+                 double* __restrict__ partials, PcgState* st) {
+  using S = WarpSm<N>;
+  constexpr int N2 = S::N2;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  if (st != nullptr && st->done) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  int* H = reinterpret_cast<int*>(smem_raw) + wib * kWarpHdr;
+  T* W = reinterpret_cast<T*>(smem_raw + ((size_t)wpb * kWarpHdr * 4 + 31) / 32 * 32) + (size_t)wib * S::size;
+  const CoefOffsets co = coef_offsets(N);
+  const long long nwarps = (long long)gridDim.x * wpb, gw = (long long)blockIdx.x * wpb + wib;
+  const long long e_begin = g.nelem * gw / nwarps, e_end = g.nelem * (gw + 1) / nwarps;
+  if (lane == 0) H[27] = -1;
+  T dot = T(0);
+  const int mx = g.mx, my = g.my, mz = g.mz;
+
+  for (long long e = e_begin; e < e_end; ++e) {
+    // element coordinates (visiting order: most-graded axis slowest)
+    int ex, ey, ez;
+    {
+      const int ei = (int)e;
+      if (g.slow == 0) { ex = ei / (my * mz); const int r = ei - ex * (my * mz); ey = r % my; ez = r / my; }
+      else if (g.slow == 1) { ey = ei / (mx * mz); const int r = ei - ey * (mx * mz); ex = r % mx; ez = r / mx; }
+      else { ex = ei % mx; const int r = ei / mx; ey = r % my; ez = r / my; }
+    }
+    __syncwarp();
+    if (lane < 26) {
+      bool dir;
+      long long off;
+      if (lane < 6) off = face_base(g, ex, ey, ez, lane, &dir);
+      else if (lane < 18) off = edge_base(g, ex, ey, ez, lane - 6, &dir);
+      else off = vert_index(g, ex, ey, ez, lane - 18, &dir);
+      H[lane] = dir ? -1 : (int)off;
+    } else if (lane == 26) {
+      H[26] = elem_class(g, tab, ex, ey, ez);
+    }
+    __syncwarp();
+    const int cls = H[26];
+    const T* cb = tab.coef + (long long)cls * co.stride;
+    // gather R^T
+#pragma unroll
+    for (int r = lane; r < 6 * N2; r += 32) {
+      const int slot = r / N2, off = H[slot];
+      W[S::F + r] = off >= 0 ? u[off + r - slot * N2] : T(0);
+    }
+#pragma unroll
+    for (int r = lane; r < 12 * N; r += 32) {
+      const int slot = r / N, off = H[6 + slot];
+      W[S::E + r] = off >= 0 ? u[off + r - slot * N] : T(0);
+    }
+    if (lane < 8) {
+      const int off = H[18 + lane];
+      W[S::Vt + lane] = off >= 0 ? u[off] : T(0);
+    }
+    if (cls != H[27]) {
+      for (int r = lane; r < 18 * N + 18; r += 32) W[S::C + r] = cb[r];
+    }
+    __syncwarp();
+    if (lane == 0) H[27] = cls;
+    const T* F = W + S::F;
+    const T* Ed = W + S::E;
+    const T* Vt = W + S::Vt;
+    const T* skd = W + S::C;
+    const T* skw = W + S::C + 6 * N;
+    const T* skww = W + S::C + 12 * N;
+    const T* cO = W + S::C + 18 * N;
+    const T* eO = cO + 6;
+    const T* vO = cO + 12;
+    // primary part: faces
+#pragma unroll
+    for (int r = lane; r < 6 * N2; r += 32) {
+      const int slot = r / N2, idx = r - slot * N2, dd = slot >> 1, s = slot & 1;
+      const int slow = idx / N, fast = idx - slow * N;
+      T out = __ldg(cb + co.fdiag + r) * F[r];
+      out = fma(cO[slot], F[(slot ^ 1) * N2 + idx], out);
+      if (dd == 0) {
+        out = fma(skw[2 * N + fast], Ed[(8 + s) * N + slow], out);
+        out = fma(skw[3 * N + fast], Ed[(10 + s) * N + slow], out);
+        out = fma(skw[4 * N + slow], Ed[(4 + s) * N + fast], out);
+        out = fma(skw[5 * N + slow], Ed[(6 + s) * N + fast], out);
+      } else if (dd == 1) {
+        out = fma(skw[fast], Ed[(8 + 2 * s) * N + slow], out);
+        out = fma(skw[N + fast], Ed[(9 + 2 * s) * N + slow], out);
+        out = fma(skw[4 * N + slow], Ed[s * N + fast], out);
+        out = fma(skw[5 * N + slow], Ed[(2 + s) * N + fast], out);
+      } else {
+        out = fma(skw[fast], Ed[(4 + 2 * s) * N + slow], out);
+        out = fma(skw[N + fast], Ed[(5 + 2 * s) * N + slow], out);
+        out = fma(skw[2 * N + slow], Ed[2 * s * N + fast], out);
+        out = fma(skw[3 * N + slow], Ed[(1 + 2 * s) * N + fast], out);
+      }
+      W[S::Acc + r] = out;
+    }
+    // primary part: edges
+#pragma unroll
+    for (int r = lane; r < 12 * N; r += 32) {
+      const int slot = r / N, l = r - slot * N, grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+      T out = __ldg(cb + co.ediag + r) * Ed[r];
+      const T *k1, *k2, *f1, *f2;
+      int st1, st2;
+      T va, vb;
+      if (grp == 0) {          // x-edge Ex[sb=s1][sc=s2], index i
+        va = Vt[2 * s1 + 4 * s2];
+        vb = Vt[1 + 2 * s1 + 4 * s2];
+        k1 = skw + (2 + s1) * N; f1 = F + (4 + s2) * N2 + l; st1 = N;
+        k2 = skw + (4 + s2) * N; f2 = F + (2 + s1) * N2 + l; st2 = N;
+        out = fma(eO[2 + s1], Ed[((1 - s1) + 2 * s2) * N + l], out);
+        out = fma(eO[4 + s2], Ed[(s1 + 2 * (1 - s2)) * N + l], out);
+      } else if (grp == 1) {   // y-edge Ey[sa=s1][sc=s2], index j
+        va = Vt[s1 + 4 * s2];
+        vb = Vt[s1 + 2 + 4 * s2];
+        k1 = skw + s1 * N; f1 = F + (4 + s2) * N2 + l * N; st1 = 1;
+        k2 = skw + (4 + s2) * N; f2 = F + s1 * N2 + l; st2 = N;
+        out = fma(eO[s1], Ed[(4 + (1 - s1) + 2 * s2) * N + l], out);
+        out = fma(eO[4 + s2], Ed[(4 + s1 + 2 * (1 - s2)) * N + l], out);
+      } else {                 // z-edge Ez[sa=s1][sb=s2], index k
+        va = Vt[s1 + 2 * s2];
+        vb = Vt[s1 + 2 * s2 + 4];
+        k1 = skw + s1 * N; f1 = F + (2 + s2) * N2 + l * N; st1 = 1;
+        k2 = skw + (2 + s2) * N; f2 = F + s1 * N2 + l * N; st2 = 1;
+        out = fma(eO[s1], Ed[(8 + (1 - s1) + 2 * s2) * N + l], out);
+        out = fma(eO[2 + s2], Ed[(8 + s1 + 2 * (1 - s2)) * N + l], out);
+      }
+      out = fma(skww[2 * grp * N + l], va, out);
+      out = fma(skww[(2 * grp + 1) * N + l], vb, out);
+#pragma unroll
+      for (int m = 0; m < N; ++m) out = fma(k1[m], f1[m * st1], out);
+#pragma unroll
+      for (int m = 0; m < N; ++m) out = fma(k2[m], f2[m * st2], out);
+      W[S::Eo + r] = out;
+    }
+    // primary part: vertices
+    if (lane < 8) {
+      const int slot = lane, sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
+      T out = __ldg(cb + co.vdiag + slot) * Vt[slot];
+      const T* ka = skww + sa * N;
+      const T* kb = skww + (2 + sb) * N;
+      const T* kc = skww + (4 + sc) * N;
+      const T* exl = Ed + (sb + 2 * sc) * N;
+      const T* eyl = Ed + (4 + sa + 2 * sc) * N;
+      const T* ezl = Ed + (8 + sa + 2 * sb) * N;
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        out = fma(ka[m], exl[m], out);
+        out = fma(kb[m], eyl[m], out);
+        out = fma(kc[m], ezl[m], out);
+      }
+      out = fma(vO[sa], Vt[slot ^ 1], out);
+      out = fma(vO[2 + sb], Vt[slot ^ 2], out);
+      out = fma(vO[4 + sc], Vt[slot ^ 4], out);
+      W[S::Vo + slot] = out;
+    }
+    __syncwarp();
+    // condensed part: expansion, -D^-1, b/t contraction in registers (Table 2)
+#pragma unroll
+    for (int ji = lane; ji < N2; ji += 32) {
+      const int j = ji / N, i = ji - j * N;
+      const T ai = skd[i], bi = skd[N + i], cj = skd[2 * N + j], dj = skd[3 * N + j];
+      const T fb = F[4 * N2 + ji], ft = F[5 * N2 + ji];
+      T sb = W[S::Acc + 4 * N2 + ji], stt = W[S::Acc + 5 * N2 + ji];
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const T ek = skd[4 * N + k], gk = skd[5 * N + k];
+        T x = ai * F[k * N + j];
+        x = fma(bi, F[N2 + k * N + j], x);
+        x = fma(cj, F[2 * N2 + k * N + i], x);
+        x = fma(dj, F[3 * N2 + k * N + i], x);
+        x = fma(ek, fb, x);
+        x = fma(gk, ft, x);
+        const T vv = __ldg(cb + co.ndinv + k * N2 + ji) * x;
+        W[S::cube + k * N2 + ji] = vv;
+        sb = fma(ek, vv, sb);
+        stt = fma(gk, vv, stt);
+      }
+      W[S::Acc + 4 * N2 + ji] = sb;
+      W[S::Acc + 5 * N2 + ji] = stt;
+    }
+    __syncwarp();
+    // w / e (rows over i) and s / n (columns over j)
+#pragma unroll
+    for (int q = lane; q < N2; q += 32) {
+      const int k = q / N, m = q - k * N;
+      const T* row = W + S::cube + k * N2 + m * N;    // (k, j = m), over i
+      const T* col = W + S::cube + k * N2 + m;        // (k, i = m), over j
+      T s0 = W[S::Acc + q], s1 = W[S::Acc + N2 + q];
+      T s2 = W[S::Acc + 2 * N2 + q], s3 = W[S::Acc + 3 * N2 + q];
+#pragma unroll
+      for (int t = 0; t < N; ++t) {
+        const T c = row[t], d = col[t * N];
+        s0 = fma(skd[t], c, s0);
+        s1 = fma(skd[N + t], c, s1);
+        s2 = fma(skd[2 * N + t], d, s2);
+        s3 = fma(skd[3 * N + t], d, s3);
+      }
+      W[S::Acc + q] = s0;
+      W[S::Acc + N2 + q] = s1;
+      W[S::Acc + 2 * N2 + q] = s2;
+      W[S::Acc + 3 * N2 + q] = s3;
+    }
+    __syncwarp();
+    // scatter R and the element share of x^T (A x)
+#pragma unroll
+    for (int r = lane; r < 6 * N2; r += 32) {
+      const int slot = r / N2, off = H[slot];
+      if (off >= 0) {
+        const T o = W[S::Acc + r];
+        atomicAdd(v + off + r - slot * N2, o);
+        dot = fma(F[r], o, dot);
+      }
+    }
+#pragma unroll
+    for (int r = lane; r < 12 * N; r += 32) {
+      const int slot = r / N, off = H[6 + slot];
+      if (off >= 0) {
+        const T o = W[S::Eo + r];
+        atomicAdd(v + off + r - slot * N, o);
+        dot = fma(Ed[r], o, dot);
+      }
+    }
+    if (lane < 8) {
+      const int off = H[18 + lane];
+      if (off >= 0) {
+        const T o = W[S::Vo + lane];
+        atomicAdd(v + off, o);
+        dot = fma(Vt[lane], o, dot);
+      }
+    }
+  }
+  if (st != nullptr) {
+    double vals[1] = {(double)dot}, tot[1];
+    if (reduce_grid<1>(vals, partials, &st->counter[0], tot) && threadIdx.x == 0) {
+      const double pq = tot[0];
+      st->pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) st->done = 2;
+      else st->alpha = st->rho / pq;
+    }
+  }
+}
+
+template <typename T, int N>
+size_t warp_smem(int wpb) {
+  return ((size_t)wpb * kWarpHdr * 4 + 31) / 32 * 32 + (size_t)wpb * WarpSm<N>::size * sizeof(T);
+}
+
+template <typename T, int N>
+void launch_warp(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, double* partials, PcgState* st,
+                 cudaStream_t s) {
+  const int wpb = kThreads / 32;
+  const size_t smem = warp_smem<T, N>(wpb);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tpt_apply_warp<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_warp<T, N>, kThreads, smem);
+  if (occ < 1) occ = 1;
+  long long grid = (long long)num_sms_cached() * occ;
+  const long long need = (g.nelem + wpb - 1) / wpb;
+  if (grid > need) grid = need;
+  k_tpt_apply_warp<T, N><<<(int)grid, kThreads, smem, s>>>(g, t, x, y, partials, st);
+  sem_count_launch();
+}
+
 template <typename T, int NC>
 void launch_nc(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, double* partials, PcgState* st,
                const ApplyConfig& c, cudaStream_t s) {
@@ -497,6 +777,20 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
                       double* partials, PcgState* st, cudaStream_t s) {
   (void)b;
   const ApplyConfig c = sem_apply_config(g.n, sizeof(T));
+  // Measured on GB300: the warp-per-element variant wins for FP32 at
+  // 3 <= n <= 7; FP64 (bound by the FP64 pipe) and n = 1, 2 run best with
+  // the CTA-tile kernel.
+  if constexpr (sizeof(T) == 4) {
+    if (g.n >= 3 && g.n <= 7) {
+      switch (g.n) {
+        case 3: launch_warp<T, 3>(g, t, x, y, partials, st, s); return;
+        case 4: launch_warp<T, 4>(g, t, x, y, partials, st, s); return;
+        case 5: launch_warp<T, 5>(g, t, x, y, partials, st, s); return;
+        case 6: launch_warp<T, 6>(g, t, x, y, partials, st, s); return;
+        default: launch_warp<T, 7>(g, t, x, y, partials, st, s); return;
+      }
+    }
+  }
   switch (g.n) {
     case 1: launch_nc<T, 1>(g, t, x, y, partials, st, c, s); break;
     case 3: launch_nc<T, 3>(g, t, x, y, partials, st, c, s); break;

@@ -454,6 +454,31 @@ k_pcg_dir(long long nb, const T* __restrict__ r, T* __restrict__ p, T* __restric
   }
 }
 
+// Replaces the CG residual by a freshly computed one: rho = r.P r, rr = r.r,
+// done = 0; the search direction and the iteration count are kept.
+// q is cleared for the next operator application; if the CG had stopped
+// (restart != 0) the direction is restarted as p = P r.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads)
+k_pcg_rebase(long long nb, const T* __restrict__ r, const T* __restrict__ P, T* __restrict__ p, T* __restrict__ q,
+             int restart, double* __restrict__ partials, PcgState* st) {
+  T rz = T(0), rr = T(0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    const T ri = r[i];
+    const T zi = P[i] * ri;
+    if (restart) p[i] = zi;
+    q[i] = T(0);
+    rz = fma(ri, zi, rz);
+    rr = fma(ri, ri, rr);
+  }
+  double v[2] = {(double)rz, (double)rr}, tot[2];
+  if (reduce_grid<2>(v, partials, &st->counter[1], tot) && threadIdx.x == 0) {
+    st->rho = tot[0];
+    st->rr = tot[1];
+    st->done = (isfinite(tot[0]) && isfinite(tot[1])) ? 0 : 2;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Iterative refinement (FP64 outer loop around the FP32 inner CG)
 // ---------------------------------------------------------------------------
@@ -626,6 +651,12 @@ void launch_pcg_dir(long long nb, const T* r, T* p, T* q, const T* P, PcgState* 
 SEM_INST_VEC(double)
 SEM_INST_VEC(float)
 
+void launch_pcg_rebase_f32(long long nb, const float* r, const float* P, float* p, float* q, int restart,
+                           double* partials, PcgState* st, cudaStream_t s) {
+  k_pcg_rebase<float><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, P, p, q, restart, partials, st);
+  sem_count_launch();
+}
+
 void launch_ir_residual(long long nb, const double* b, const double* Ax, double* r, double* partials,
                         PcgState* st, cudaStream_t s) {
   k_ir_residual<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, b, Ax, r, partials, st);
@@ -639,5 +670,176 @@ void launch_scale_to_f32(long long n, const double* in, double scale, float* out
 
 void launch_ir_update(long long nb, double* x, const float* c, double scale, cudaStream_t s) {
   k_ir_update<<<grid_for(nb, 256), 256, 0, s>>>(nb, x, c, scale);
+  sem_count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint (differentiable solve) support
+// ---------------------------------------------------------------------------
+namespace {
+
+// out = g / m at free nodes (m the assembled lumped mass), 0 on the boundary.
+__global__ void k_mass_divide(SemGeom g, const double* __restrict__ mxs, const double* __restrict__ mys,
+                              const double* __restrict__ mzs, const double* __restrict__ in, double* __restrict__ out,
+                              int multiply) {
+  const long long N = g.Nx * g.Ny * g.Nz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    const long long gx = t % g.Nx, r = t / g.Nx, gy = r % g.Ny, gz = r / g.Ny;
+    const bool bnd = gx == 0 || gx == g.Nx - 1 || gy == 0 || gy == g.Ny - 1 || gz == 0 || gz == g.Nz - 1;
+    const double m = mxs[gx] * mys[gy] * mzs[gz];
+    out[t] = bnd ? 0.0 : (multiply ? in[t] * m : in[t] / m);
+  }
+}
+
+// Per element: E[0] = w^T (M(x)M(x)M) u, E[1] = w^T (M(x)M(x)K) u, E[2] = w^T (M(x)K(x)M) u,
+// E[3] = w^T (K(x)M(x)M) u on the reference element (metric factors excluded),
+// E[4] = sum w_a w_b w_c w(node) f(node).  One CTA per element, local arrays
+// in shared memory, each 1D stiffness product done line by line.
+__global__ void k_element_forms(SemGeom g, const double* __restrict__ wgll, const double* __restrict__ Kmat,
+                                const double* __restrict__ wf, const double* __restrict__ uf,
+                                const double* __restrict__ ff, double* __restrict__ E) {
+  extern __shared__ double sh[];
+  const int p = g.p, q = p + 1, q3 = q * q * q;
+  double* sw = sh;
+  double* su = sh + q3;
+  double* sK = su + q3;
+  double* sg = sK + q * q;
+  double* red = sg + q;   // [5][32]
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) sK[t] = Kmat[t];
+  for (int t = threadIdx.x; t < q; t += blockDim.x) sg[t] = wgll[t];
+  for (long long e = blockIdx.x; e < g.nelem; e += gridDim.x) {
+    int ex, ey, ez;
+    semdev::elem_coords(g, e, &ex, &ey, &ez);
+    __syncthreads();
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < q3; t += blockDim.x) {
+      const int a = t % q, b = (t / q) % q, c = t / (q * q);
+      const long long gi = (long long)ex * p + a + g.Nx * ((long long)ey * p + b + g.Ny * ((long long)ez * p + c));
+      sw[t] = wf[gi];
+      su[t] = uf[gi];
+      acc[4] += sg[a] * sg[b] * sg[c] * wf[gi] * ff[gi];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < q3; t += blockDim.x) {
+      const int a = t % q, b = (t / q) % q, c = t / (q * q);
+      const double wv = sw[t];
+      double kx = 0.0, ky = 0.0, kz = 0.0;
+      for (int m = 0; m < q; ++m) {
+        kx = fma(sK[a * q + m], su[(c * q + b) * q + m], kx);
+        ky = fma(sK[b * q + m], su[(c * q + m) * q + a], ky);
+        kz = fma(sK[c * q + m], su[(m * q + b) * q + a], kz);
+      }
+      acc[0] += sg[a] * sg[b] * sg[c] * wv * su[t];
+      acc[1] += sg[b] * sg[c] * wv * kx;
+      acc[2] += sg[a] * sg[c] * wv * ky;
+      acc[3] += sg[a] * sg[b] * wv * kz;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      double x = acc[k];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) red[k * 32 + wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+      double s = 0.0;
+      for (int i = 0; i < nw; ++i) s += red[threadIdx.x * 32 + i];
+      E[e * 5 + threadIdx.x] = s;
+    }
+  }
+}
+
+// dJ/dh for one axis: for each width index i, sum over the elements in that
+// slab of -(dd/dh) . E[0..3] + (dJ_e/dh) E[4], with d = J (lambda, 4/h1^2,
+// 4/h2^2, 4/h3^2) and J = h1 h2 h3 / 8.  axis 0: h1 = hx[ex], etc.
+__global__ void k_width_gradient(SemGeom g, int axis, const double* __restrict__ hx, const double* __restrict__ hy,
+                                 const double* __restrict__ hz, double lambda, const double* __restrict__ E,
+                                 double* __restrict__ out) {
+  const int m = axis == 0 ? g.mx : (axis == 1 ? g.my : g.mz);
+  for (int i = blockIdx.x; i < m; i += gridDim.x) {
+    const long long cnt = g.nelem / m;
+    double s = 0.0;
+    for (long long t = threadIdx.x; t < cnt; t += blockDim.x) {
+      long long ex, ey, ez;
+      if (axis == 0) { ex = i; ey = t % g.my; ez = t / g.my; }
+      else if (axis == 1) { ey = i; ex = t % g.mx; ez = t / g.mx; }
+      else { ez = i; ex = t % g.mx; ey = t / g.mx; }
+      const long long e = ex + g.mx * (ey + (long long)g.my * ez);
+      const double h[3] = {hx[ex], hy[ey], hz[ez]};
+      const double ha = h[axis], hb = h[(axis + 1) % 3], hc = h[(axis + 2) % 3];
+      const double J = h[0] * h[1] * h[2] / 8.0, dJ = hb * hc / 8.0;   // dJ/dh_axis
+      // d_k = J * 4 / h_k^2 for k = 1..3 (k - 1 = axis of that width)
+      double dd[4];
+      dd[0] = lambda * dJ;
+      for (int k = 0; k < 3; ++k) {
+        const double hk = h[k];
+        dd[k + 1] = (k == axis) ? (4.0 * dJ / (hk * hk) - 8.0 * J / (hk * hk * hk)) : 4.0 * dJ / (hk * hk);
+      }
+      (void)ha;
+      const double* Ee = E + e * 5;
+      s += -(dd[0] * Ee[0] + dd[1] * Ee[1] + dd[2] * Ee[2] + dd[3] * Ee[3]) + dJ * Ee[4];
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int k = 0; k < (int)((blockDim.x + 31) >> 5); ++k) tot += red[k];
+      out[i] = tot;
+    }
+    __syncthreads();
+  }
+}
+
+// dJ/dlambda = -sum_free w m u and the same pass' partial sums (deterministic).
+__global__ void k_lambda_gradient(SemGeom g, const double* __restrict__ mxs, const double* __restrict__ mys,
+                                  const double* __restrict__ mzs, const double* __restrict__ w,
+                                  const double* __restrict__ u, double* __restrict__ partials, double* __restrict__ out,
+                                  unsigned int* counter) {
+  const long long N = g.Nx * g.Ny * g.Nz;
+  double s = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    const long long gx = t % g.Nx, r = t / g.Nx, gy = r % g.Ny, gz = r / g.Ny;
+    const bool bnd = gx == 0 || gx == g.Nx - 1 || gy == 0 || gy == g.Ny - 1 || gz == 0 || gz == g.Nz - 1;
+    if (!bnd) s = fma(w[t] * mxs[gx] * mys[gy] * mzs[gz], u[t], s);
+  }
+  double v[1] = {s}, tot[1];
+  if (semdev::reduce_grid<1>(v, partials, counter, tot) && threadIdx.x == 0) *out = -tot[0];
+}
+
+}  // namespace
+
+void launch_mass_divide(const SemGeom& g, const double* mxs, const double* mys, const double* mzs, const double* in,
+                        double* out, int multiply, cudaStream_t s) {
+  k_mass_divide<<<grid_for(g.Nx * g.Ny * g.Nz, 256), 256, 0, s>>>(g, mxs, mys, mzs, in, out, multiply);
+  sem_count_launch();
+}
+
+void launch_element_forms(const SemGeom& g, const double* wgll, const double* K, const double* w, const double* u,
+                          const double* f, double* E, cudaStream_t s) {
+  const int q = g.p + 1;
+  const size_t smem = (size_t)(2 * q * q * q + q * q + q + 5 * 32) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_element_forms, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_element_forms<<<grid_for(g.nelem, 1, 8), 256, smem, s>>>(g, wgll, K, w, u, f, E);
+  sem_count_launch();
+}
+
+void launch_width_gradient(const SemGeom& g, int axis, const double* hx, const double* hy, const double* hz,
+                           double lambda, const double* E, double* out, cudaStream_t s) {
+  const int m = axis == 0 ? g.mx : (axis == 1 ? g.my : g.mz);
+  k_width_gradient<<<m < 4096 ? m : 4096, 256, 0, s>>>(g, axis, hx, hy, hz, lambda, E, out);
+  sem_count_launch();
+}
+
+void launch_lambda_gradient(const SemGeom& g, const double* mxs, const double* mys, const double* mzs,
+                            const double* w, const double* u, double* partials, double* out, unsigned int* counter,
+                            cudaStream_t s) {
+  k_lambda_gradient<<<sem_vec_blocks(), kVecThreads, 0, s>>>(g, mxs, mys, mzs, w, u, partials, out, counter);
   sem_count_launch();
 }

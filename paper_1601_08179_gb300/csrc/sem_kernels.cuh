@@ -88,5 +88,26 @@ void launch_ir_residual(long long nb, const double* b, const double* Ax, double*
 void launch_scale_to_f32(long long n, const double* in, double scale, float* out, cudaStream_t s);
 void launch_ir_update(long long nb, double* x, const float* c, double scale, cudaStream_t s);
 void launch_cast_f32(long long n, const double* in, float* out, cudaStream_t s);
+// Reliable update of the FP32 CG: rho = r.P r and rr = r.r from the new r, q = 0,
+// done = 0; with restart also p = P r.
+void launch_pcg_rebase_f32(long long nb, const float* r, const float* P, float* p, float* q, int restart,
+                           double* partials, PcgState* st, cudaStream_t s);
 
 int sem_vec_blocks();
+
+// ---- adjoint support ----
+// out = in / m (multiply = 0) or in * m (multiply = 1) at free nodes, 0 on the
+// boundary; m the assembled lumped mass of the full nodal grid.
+void launch_mass_divide(const SemGeom& g, const double* mxs, const double* mys, const double* mzs, const double* in,
+                        double* out, int multiply, cudaStream_t s);
+// E[e][0..3] = w_e^T K_k u_e on the reference element (K_0 = M(x)M(x)M, K_1 =
+// M(x)M(x)K, K_2 = M(x)K(x)M, K_3 = K(x)M(x)M), E[e][4] = sum w w w w_e f_e.
+void launch_element_forms(const SemGeom& g, const double* wgll, const double* K, const double* w, const double* u,
+                          const double* f, double* E, cudaStream_t s);
+// out[i] = dJ/dh_axis[i] from the element forms (device widths hx, hy, hz).
+void launch_width_gradient(const SemGeom& g, int axis, const double* hx, const double* hy, const double* hz,
+                           double lambda, const double* E, double* out, cudaStream_t s);
+// *out = -sum_free w m u.
+void launch_lambda_gradient(const SemGeom& g, const double* mxs, const double* mys, const double* mzs,
+                            const double* w, const double* u, double* partials, double* out, unsigned int* counter,
+                            cudaStream_t s);

@@ -34,7 +34,8 @@ class SemError(RuntimeError):
 
 class sem_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double)]
 
 
 class sem_info(ctypes.Structure):
@@ -76,6 +77,8 @@ def lib():
         "sem_pack_skeleton": (ctypes.c_int, [_P, _P, _P, _P]),
         "sem_unpack_skeleton": (ctypes.c_int, [_P, _P, _P, _P]),
         "sem_refine_history": (ctypes.c_int, [_P, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "sem_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(sem_info), _P]),
+        "sem_gradients": (ctypes.c_int, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _P]),
         "sem_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
         "sem_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                             ctypes.c_int]),
@@ -99,6 +102,7 @@ def exported_symbols():
             "sem_condense_rhs_noalloc",
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
+            "sem_solve_adjoint", "sem_gradients",
             "sem_profile_enable",
             "sem_profile_read", "sem_launch_count",
             "sem_destroy", "sem_status_string", "sem_last_error"]
@@ -264,6 +268,29 @@ def sem_pack_skeleton(ctx: SemContext, u_full, uB, stream=None):
 def sem_unpack_skeleton(ctx: SemContext, uB, u_full, stream=None):
     _check(lib().sem_unpack_skeleton(ctx.handle, _dptr(uB, ctx.nb, "uB"), _dptr(u_full, ctx.n_nodes, "u_full"),
                                      _stream(stream, uB)))
+
+
+def sem_solve_adjoint(ctx: SemContext, g, w, stream=None, check=True) -> dict:
+    """w = A^-1 g (g a nodal load, e.g. dJ/du)."""
+    info = sem_info()
+    st = lib().sem_solve_adjoint(ctx.handle, _dptr(g, ctx.n_nodes, "g"), _dptr(w, ctx.n_nodes, "w"),
+                                 ctypes.byref(info), _stream(stream, g))
+    if check:
+        _check(st)
+    return dict(status=st, iters=info.iters, refinements=info.refinements, rel_res=info.rel_res,
+                t_solve_s=info.t_solve_s)
+
+
+def sem_gradients(ctx: SemContext, w, u, f, df, stream=None):
+    """Returns (dlambda, dhx, dhy, dhz); writes df (device) in place."""
+    mx, my, mz = ctx.m
+    dl = ctypes.c_double()
+    dhx, dhy, dhz = np.empty(mx), np.empty(my), np.empty(mz)
+    _check(lib().sem_gradients(ctx.handle, _dptr(w, ctx.n_nodes, "w"), _dptr(u, ctx.n_nodes, "u"),
+                               _dptr(f, ctx.n_nodes, "f"), _dptr(df, ctx.n_nodes, "df"), ctypes.byref(dl),
+                               dhx.ctypes.data_as(_D), dhy.ctypes.data_as(_D), dhz.ctypes.data_as(_D),
+                               _stream(stream, w)))
+    return dl.value, dhx, dhy, dhz
 
 
 def sem_refine_history(ctx: SemContext):

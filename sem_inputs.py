@@ -165,3 +165,21 @@ def batched_problems(count: int = 64, seed: int = SEED_BASE + 3):
         out.append(Workload(f"batch{b}_p{p}_m{m}", p=p, m=(m, m, m), lam=lam, ar=ar,
                             noise=True, seed=SEED_BASE * 100 + b))
     return out
+
+
+def smooth_target(x, y, z, seed: int, terms: int = 8):
+    """Seeded smooth field: a sum of `terms` products of low-wavenumber sines
+    with random amplitudes and phases (the target of the differentiable solve)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = np.zeros(np.broadcast(x, y, z).shape)
+    for _ in range(terms):
+        a = g.uniform(-1.0, 1.0)
+        k = g.integers(1, 4, size=3)
+        ph = g.uniform(0.0, 2.0 * np.pi, size=3)
+        out += a * np.sin(k[0] * np.pi * x + ph[0]) * np.sin(k[1] * np.pi * y + ph[1]) * np.sin(k[2] * np.pi * z + ph[2])
+    return out
+
+
+# Differentiable-solve workload: p = 8 on 16^3 elements, lambda = 1, FP64,
+# J = 1/2 ||u - u_target||^2 with a smooth seeded target.
+ADJOINT = Workload("uniform_p8_m16_lam1_adjoint", p=8, m=(16, 16, 16), lam=1.0, seed=SEED_BASE + 4)

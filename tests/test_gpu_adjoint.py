@@ -1,0 +1,84 @@
+"""Differentiable solve (torch.autograd.Function around the C ABI) against the
+oracle's dense adjoint gradient and against central finite differences of the
+GPU solve itself, for J = 1/2 ||u - u_t||^2."""
+import numpy as np
+import pytest
+
+import sem_inputs as si
+from oracle.adjoint import solve_and_gradient
+from oracle.mesh import Mesh
+
+pytestmark = pytest.mark.gpu
+
+
+def _grad_gpu(p, hx, hy, hz, lam, f, ut, opts):
+    import torch
+    from paper_1601_08179_gb300.autograd import helmholtz_solve
+    fd = torch.tensor(f, dtype=torch.float64, device="cuda", requires_grad=True)
+    lt = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+    hxt = torch.tensor(hx, dtype=torch.float64, requires_grad=True)
+    hyt = torch.tensor(hy, dtype=torch.float64, requires_grad=True)
+    hzt = torch.tensor(hz, dtype=torch.float64, requires_grad=True)
+    u = helmholtz_solve(fd, lt, hxt, hyt, hzt, p, opts)
+    J = 0.5 * ((u - torch.tensor(ut, device="cuda")) ** 2).sum()
+    J.backward()
+    return (float(J), fd.grad.cpu().numpy(), float(lt.grad), hxt.grad.numpy(), hyt.grad.numpy(),
+            hzt.grad.numpy())
+
+
+@pytest.mark.parametrize("p,m,lam,ar", [(4, (3, 2, 2), 1.0, 3.0), (3, (2, 3, 2), 0.0, 1.0)])
+def test_gradient_vs_oracle(p, m, lam, ar):
+    from paper_1601_08179_gb300 import sem
+    hx, hy, hz, _ = si.graded_widths(*m, ar=ar)
+    ms = Mesh(p, hx, hy, hz)
+    X, Y, Z = ms.coords()
+    f = (si.manufactured_f(X, Y, Z, lam) + si.node_noise(X.size, 51).reshape(X.shape)).ravel()
+    ut = si.smooth_target(X, Y, Z, 52).ravel()
+    J0, u0, df0, dl0, dh0 = solve_and_gradient(ms, lam, f, ut)
+    J, df, dl, dhx, dhy, dhz = _grad_gpu(p, hx, hy, hz, lam, f, ut, sem.default_opts(rtol=1e-13))
+    assert J == pytest.approx(J0, rel=1e-9)
+    assert np.linalg.norm(df - df0) <= 1e-6 * np.linalg.norm(df0)
+    assert dl == pytest.approx(dl0, rel=1e-6, abs=1e-12)
+    for got, want in zip((dhx, dhy, dhz), dh0):
+        np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-9 * np.abs(want).max())
+
+
+def test_gradient_vs_finite_differences_full_size():
+    """p = 8 on 16^3 elements, lambda = 1: directional derivatives in f, lambda
+    and one width of each axis against central differences (step 1e-6) of the
+    GPU objective."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    from paper_1601_08179_gb300.autograd import context_for
+    w = si.ADJOINT
+    hx, hy, hz = w.widths()
+    opts = sem.default_opts(rtol=1e-13)
+    ctx = context_for(w.p, hx, hy, hz, w.lam, opts)
+    x, y, z = sem.sem_node_coords(ctx)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    f = si.manufactured_f(X, Y, Z, w.lam).ravel()
+    ut = si.smooth_target(X, Y, Z, w.seed).ravel()
+    J, df, dl, dhx, dhy, dhz = _grad_gpu(w.p, hx, hy, hz, w.lam, f, ut, opts)
+    utd = torch.tensor(ut, device="cuda")
+
+    def obj(ff, lam, hx_, hy_, hz_):
+        c = context_for(w.p, hx_, hy_, hz_, lam, opts)
+        fd = torch.tensor(ff, device="cuda")
+        u = torch.empty_like(fd)
+        sem.sem_solve(c, fd, u)
+        return 0.5 * float(((u - utd) ** 2).sum())
+
+    eps = 1e-6
+    d = si.random_vector(f.size, 53)
+    fdv = (obj(f + eps * d, w.lam, hx, hy, hz) - obj(f - eps * d, w.lam, hx, hy, hz)) / (2 * eps)
+    assert float(df @ d) == pytest.approx(fdv, rel=1e-5)
+    fdv = (obj(f, w.lam + eps, hx, hy, hz) - obj(f, w.lam - eps, hx, hy, hz)) / (2 * eps)
+    assert dl == pytest.approx(fdv, rel=1e-5)
+    for axis, (arr, g) in enumerate(((hx, dhx), (hy, dhy), (hz, dhz))):
+        i = 5
+        hp = [hx.copy(), hy.copy(), hz.copy()]
+        hm = [hx.copy(), hy.copy(), hz.copy()]
+        hp[axis][i] += eps
+        hm[axis][i] -= eps
+        fdv = (obj(f, w.lam, *hp) - obj(f, w.lam, *hm)) / (2 * eps)
+        assert g[i] == pytest.approx(fdv, rel=1e-5, abs=1e-9 * abs(J)), axis

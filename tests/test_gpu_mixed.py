@@ -18,12 +18,13 @@ def _mixed(**kw):
     return sem.default_opts(precision=sem.PREC_MIXED, **kw)
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("p,m,lam,ar", [(4, (4, 4, 4), 1.0, 1.0), (6, (3, 3, 3), 0.0, 8.0),
                                         (8, (3, 2, 2), 10.0, 16.0), (2, (5, 4, 3), 0.5, 4.0)])
-def test_mixed_solve_vs_direct(p, m, lam, ar):
+def test_mixed_solve_vs_direct(p, m, lam, ar, scheme):
     import torch
     from paper_1601_08179_gb300 import sem
-    ctx, ms = make_pair(p, m, lam, ar, opts=_mixed())
+    ctx, ms = make_pair(p, m, lam, ar, opts=_mixed(mixed_scheme=scheme))
     X, Y, Z = ms.coords()
     f = (si.manufactured_f(X, Y, Z, lam) + si.node_noise(X.size, 21).reshape(X.shape)).ravel()
     u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
@@ -36,7 +37,8 @@ def test_mixed_solve_vs_direct(p, m, lam, ar):
     assert info["rel_res"] == hist[-1]
 
 
-def test_mixed_error_per_refinement_step():
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_mixed_error_per_refinement_step(scheme):
     """Error against the FP64 oracle after k refinement steps (max_refine = k):
     it falls by orders of magnitude per step down to the 1e-9 bar."""
     import torch
@@ -49,12 +51,12 @@ def test_mixed_error_per_refinement_step():
     u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
     errs = []
     for k in range(1, 6):
-        sem.sem_set_opts(ctx, _mixed(max_refine=k))
+        sem.sem_set_opts(ctx, _mixed(max_refine=k, mixed_scheme=scheme))
         info = sem.sem_solve(ctx, dev(f), u, check=False)
         errs.append(relerr(host(u), ref))
         if info["status"] == sem.SEM_OK:
             break
-    print("error vs oracle per refinement step:", ["%.2e" % e for e in errs])
+    print(f"scheme {scheme}: error vs oracle per refinement step:", ["%.2e" % e for e in errs])
     assert errs[-1] <= SOLVE_TOL
     assert all(b < 0.1 * a for a, b in zip(errs, errs[1:]))
 
