@@ -257,6 +257,37 @@ sem_status sem_solve_adjoint(sem_ctx* ctx, const double* g, double* w, sem_info*
 sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const double* f, double* df,
                          double* dlambda, double* dhx, double* dhy, double* dhz, void* stream);
 
+/* Autotuner: times the operator kernel over a set of CTA-tile shapes
+ * (elements per CTA, eigenspace slab depth) for this context's degree, mesh
+ * and precision (FP32 when opts.precision is MIXED, else FP64), keeps the
+ * fastest (the built-in choice included) for all later applications and
+ * solves, and caches the choice per (p, mx, my, mz, precision) for the
+ * process.  *ms_default / *ms_best (may be NULL): milliseconds per application
+ * of the built-in and the chosen configuration.  Synchronous. */
+sem_status sem_autotune(sem_ctx* ctx, double* ms_default, double* ms_best);
+
+/* Batched solves (independent problems of any degree and mesh size).
+ * sem_batch_create captures, for `count` distinct FP64 contexts with device
+ * fields f[i] (input) and u[i] (output), ONE CUDA graph: a prologue that
+ * condenses every load and initialises every CG (one graph branch per
+ * problem), a device-side `while` loop whose body runs opts.check_every CG
+ * iterations of every problem in parallel branches followed by a one-thread
+ * kernel that ends the loop once no problem is still iterating (bounded by the
+ * largest maxit), and an epilogue that recovers every interior.  Converged
+ * problems' kernels exit at once.  The graph bakes in the context and field
+ * pointers; create a new batch when they change.  sem_batch_solve launches the
+ * graph once on `stream` and fills infos[count] (may be NULL); it returns
+ * SEM_ENOCONV or SEM_EBREAKDOWN if any problem failed (all u[i] are written).
+ * The contexts must not be used concurrently while the batch runs.
+ * sem_solve_batch = create + solve + destroy. */
+typedef struct sem_batch sem_batch;
+sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const double* const* f, double* const* u,
+                            sem_batch** out);
+sem_status sem_batch_solve(sem_batch* batch, sem_info* infos, void* stream);
+void sem_batch_destroy(sem_batch* batch);
+sem_status sem_solve_batch(sem_ctx* const* ctxs, int count, const double* const* f, double* const* u,
+                           sem_info* infos, void* stream);
+
 /* Residual history of the last MIXED solve: rel_res[k] = ||b - A x_k|| / ||b||
  * (FP64, transformed condensed space) before refinement step k and after the
  * last one; *count = number of entries (up to max_refine + 1).  HOST array of

@@ -15,7 +15,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -101,6 +103,8 @@ struct sem_ctx {
   bool graph32_prof = false;
   std::vector<cudaEvent_t> pev32;
   std::vector<double> refine_hist;     // ||b - A x_k|| / ||b|| after each refinement step
+  bool tuned64_set = false, tuned32_set = false;
+  ApplyConfig tuned64{}, tuned32{};     // autotuned CTA-tile operator configurations
 
   const double* mat(int k) const { return d_mats + (size_t)k * g.n * g.n; }
 };
@@ -247,7 +251,8 @@ sem_status recover_t(sem_ctx* c, const double* ut, double* u, cudaStream_t s) {
 
 sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
   SEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * c->g.nb, s));
-  launch_tpt_apply<double>(c->g, c->h1.basis, c->tab, x, y, nullptr, nullptr, s);
+  launch_tpt_apply<double>(c->g, c->h1.basis, c->tab, x, y, nullptr, nullptr, s,
+                           c->tuned64_set ? &c->tuned64 : nullptr);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -272,7 +277,8 @@ sem_status build_graph(sem_ctx* c) {
   for (int it = 0; it < c->opts.check_every; ++it) {
     // external event-record nodes: recorded at every replay, usable for timing
     if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it], c->stream, cudaEventRecordExternal);
-    launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, c->stream);
+    launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, c->stream,
+                             c->tuned64_set ? &c->tuned64 : nullptr);
     if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it + 1], c->stream, cudaEventRecordExternal);
     launch_pcg_update(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, c->stream);
     launch_pcg_dir(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, c->stream);
@@ -349,7 +355,8 @@ sem_status build_graph32(sem_ctx* c) {
   const long long before = sem_launch_total();
   for (int it = 0; it < c->opts.check_every; ++it) {
     if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it], c->stream, cudaEventRecordExternal);
-    launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, c->stream);
+    launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, c->stream,
+                            c->tuned32_set ? &c->tuned32 : nullptr);
     if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it + 1], c->stream, cudaEventRecordExternal);
     launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32,
                              c->stream);
@@ -1141,4 +1148,368 @@ extern "C" sem_status sem_condense_rhs_noalloc(sem_ctx* c, const double* f, doub
   if (space == SEM_SPACE_NODAL) launch_skel_transform(g, c->mat(3), fB, fB, s);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: CTA-tile shape of the operator kernel per (p, mesh, precision)
+// ---------------------------------------------------------------------------
+namespace {
+
+using TuneKey = std::tuple<int, int, int, int, int>;   // p, mx, my, mz, element bytes
+struct TuneResult {
+  bool use_default;
+  ApplyConfig cfg;
+  double ms_default, ms_best;
+};
+std::map<TuneKey, TuneResult> g_tune_cache;
+std::mutex g_tune_mu;
+
+template <typename T>
+sem_status time_apply(sem_ctx* c, const SemClassTables<T>& tab, const T* x, T* y, const ApplyConfig* cfg,
+                      double* ms_out) {
+  const SemGeom& g = c->g;
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  SEM_CUDA(cudaEventCreate(&e0));
+  SEM_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    SEM_CUDA(cudaMemsetAsync(y, 0, sizeof(T) * g.nb, s));
+    SEM_CUDA(cudaEventRecord(e0, s));
+    launch_tpt_apply<T>(g, c->h1.basis, tab, x, y, nullptr, nullptr, s, cfg);
+    SEM_CUDA(cudaEventRecord(e1, s));
+    SEM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    SEM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0 && ms < best) best = ms;   // first launch is a warm-up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SEM_CUDA(cudaGetLastError());
+  *ms_out = best;
+  return SEM_OK;
+}
+
+template <typename T>
+sem_status tune_one(sem_ctx* c, const SemClassTables<T>& tab, const T* x, T* y, TuneResult* out) {
+  const int n = c->g.n;
+  double ms_def = 0.0;
+  sem_status st = time_apply<T>(c, tab, x, y, nullptr, &ms_def);
+  if (st != SEM_OK) return st;
+  TuneResult r{true, ApplyConfig{}, ms_def, ms_def};
+  const int epbs[] = {1, 2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 48, 64};
+  const int kss[] = {n, (n + 1) / 2, (n + 3) / 4, 8, 4, 2};
+  int tried = 0;
+  for (int epb : epbs) {
+    if (epb * n * n > 4096) continue;
+    int last_ks = -1;
+    for (int ks : kss) {
+      if (ks < 1 || ks > n || ks == last_ks) continue;
+      last_ks = ks;
+      const ApplyConfig cfg = sem_apply_config_make(n, sizeof(T), epb, ks);
+      if (!sem_apply_config_valid(n, sizeof(T), cfg)) continue;
+      double ms = 0.0;
+      st = time_apply<T>(c, tab, x, y, &cfg, &ms);
+      if (st != SEM_OK) return st;
+      ++tried;
+      if (ms < r.ms_best) {
+        r.ms_best = ms;
+        r.use_default = false;
+        r.cfg = cfg;
+      }
+      if (tried >= 40) break;
+    }
+  }
+  *out = r;
+  return SEM_OK;
+}
+
+}  // namespace
+
+extern "C" sem_status sem_autotune(sem_ctx* c, double* ms_default, double* ms_best) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  const SemGeom& g = c->g;
+  const bool mixed = c->opts.precision == SEM_PREC_MIXED;
+  const TuneKey key{g.p, g.mx, g.my, g.mz, mixed ? 4 : 8};
+  TuneResult r;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      r = it->second;
+      have = true;
+    }
+  }
+  if (!have) {
+    sem_status st;
+    if (mixed) {
+      st = ensure_mixed(c);
+      if (st != SEM_OK) return st;
+      launch_cast_f32(g.nb, c->d_P, c->d_p32, c->stream);
+      st = tune_one<float>(c, c->tab_f, c->d_p32, c->d_q32, &r);
+    } else {
+      st = tune_one<double>(c, c->tab, c->d_P, c->d_t2, &r);
+    }
+    if (st != SEM_OK) return st;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = r;
+  }
+  if (mixed) {
+    c->tuned32_set = !r.use_default;
+    c->tuned32 = r.cfg;
+    if (c->graph32) { cudaGraphExecDestroy(c->graph32); c->graph32 = nullptr; }
+  } else {
+    c->tuned64_set = !r.use_default;
+    c->tuned64 = r.cfg;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  }
+  if (ms_default) *ms_default = r.ms_default;
+  if (ms_best) *ms_best = r.ms_best;
+  return SEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solves: one instantiated CUDA graph for many independent problems
+// ---------------------------------------------------------------------------
+namespace {
+
+// One thread: keep looping while any problem is still iterating (and the
+// safety cap on loop trips is not reached).
+__global__ void k_batch_decide(PcgState* const* states, int count, int* trips, int cap,
+                               cudaGraphConditionalHandle handle) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int active = 0;
+  for (int i = 0; i < count; ++i) active |= (states[i]->done == 0);
+  const int t = ++(*trips);
+  cudaGraphSetConditional(handle, (active && t < cap) ? 1u : 0u);
+}
+
+}  // namespace
+
+struct sem_batch {
+  std::vector<sem_ctx*> ctxs;
+  std::vector<const double*> f;
+  std::vector<double*> u;
+  std::vector<cudaStream_t> streams;   // [0] orchestrates, [1..count] one per problem
+  std::vector<cudaEvent_t> events;
+  PcgState** d_states = nullptr;
+  int* d_trips = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches_fixed = 0, launches_per_trip = 0;
+  int device = 0;
+};
+
+namespace {
+
+void batch_free(sem_batch* b) {
+  if (b == nullptr) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  if (b->d_states) cudaFree(b->d_states);
+  if (b->d_trips) cudaFree(b->d_trips);
+  delete b;
+}
+
+// Fork the problems onto their streams, run body(i, stream_i), join back.
+template <typename F>
+sem_status batch_fork_join(sem_batch* b, F body) {
+  cudaStream_t s0 = b->streams[0];
+  const int count = (int)b->ctxs.size();
+  SEM_CUDA(cudaEventRecord(b->events[0], s0));
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t si = b->streams[1 + i];
+    SEM_CUDA(cudaStreamWaitEvent(si, b->events[0], 0));
+    sem_status st = body(i, si);
+    if (st != SEM_OK) return st;
+    SEM_CUDA(cudaEventRecord(b->events[1 + i], si));
+    SEM_CUDA(cudaStreamWaitEvent(s0, b->events[1 + i], 0));
+  }
+  return SEM_OK;
+}
+
+}  // namespace
+
+extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const double* const* f, double* const* u,
+                                       sem_batch** out) {
+  t_err.clear();
+  if (out == nullptr || ctxs == nullptr || f == nullptr || u == nullptr || count < 1)
+    return fail(SEM_EINVAL, "null argument or empty batch");
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (ctxs[i] == nullptr || f[i] == nullptr || u[i] == nullptr) return fail(SEM_EINVAL, "null context or field");
+    if (ctxs[i]->opts.precision != SEM_PREC_FP64) return fail(SEM_ENOTSUP, "batched solves run in FP64");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(SEM_EINVAL, "a context appears twice in the batch");
+  }
+  sem_batch* b = new sem_batch();
+  cudaGetDevice(&b->device);
+  b->ctxs.assign(ctxs, ctxs + count);
+  b->f.assign(f, f + count);
+  b->u.assign(u, u + count);
+  auto bail = [&](sem_status st) {
+    std::string keep = t_err;
+    batch_free(b);
+    t_err = keep;
+    return st;
+  };
+  for (int i = 0; i <= count; ++i) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(SEM_ECUDA, "cannot create batch streams"));
+    b->streams.push_back(st);
+    b->events.push_back(ev);
+  }
+  std::vector<PcgState*> states(count);
+  int check = 1 << 30, cap = 0;
+  for (int i = 0; i < count; ++i) {
+    sem_status st = ensure_cubes(ctxs[i]);
+    if (st != SEM_OK) return bail(st);
+    states[i] = ctxs[i]->d_st;
+    check = std::min(check, ctxs[i]->opts.check_every);
+    cap = std::max(cap, ctxs[i]->opts.maxit);
+  }
+  cap = cap / check + 2;
+  if (dalloc(&b->d_states, count) != cudaSuccess || dalloc(&b->d_trips, 1) != cudaSuccess)
+    return bail(fail(SEM_ENOMEM, "cannot allocate batch state"));
+  if (cudaMemcpy(b->d_states, states.data(), count * sizeof(PcgState*), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(SEM_ECUDA, "cannot upload batch state"));
+  cudaStream_t s0 = b->streams[0];
+  cudaGraph_t pro = nullptr, epi = nullptr, main_g = nullptr;
+  cudaError_t e;
+  // prologue: condensed loads and CG initialisation, one branch per problem
+  long long l0 = sem_launch_total();
+  e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bail(fail(SEM_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e)));
+  sem_status cst = cudaMemsetAsync(b->d_trips, 0, sizeof(int), s0) == cudaSuccess ? SEM_OK : SEM_ECUDA;
+  if (cst == SEM_OK)
+    cst = batch_fork_join(b, [&](int i, cudaStream_t si) -> sem_status {
+      sem_ctx* c = b->ctxs[i];
+      sem_status st = condense_rhs_t(c, b->f[i], c->d_b, si);
+      if (st != SEM_OK) return st;
+      launch_pcg_init<double>(c->g.nb, c->d_b, c->d_r, c->d_p, c->d_q, c->d_x, c->d_P, c->d_partials, c->d_st,
+                              c->opts.rtol, c->opts.maxit, 0, si);
+      return SEM_OK;
+    });
+  e = cudaStreamEndCapture(s0, &pro);
+  if (cst != SEM_OK || e != cudaSuccess) {
+    if (pro) cudaGraphDestroy(pro);
+    return bail(cst != SEM_OK ? cst : fail(SEM_ECUDA, std::string("batch prologue: ") + cudaGetErrorString(e)));
+  }
+  // epilogue: interior recovery
+  e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+  cst = e == cudaSuccess ? batch_fork_join(b, [&](int i, cudaStream_t si) -> sem_status {
+    sem_ctx* c = b->ctxs[i];
+    return recover_t(c, c->d_x, b->u[i], si);
+  }) : SEM_ECUDA;
+  e = cudaStreamEndCapture(s0, &epi);
+  const long long l1 = sem_launch_total();
+  if (cst != SEM_OK || e != cudaSuccess) {
+    cudaGraphDestroy(pro);
+    if (epi) cudaGraphDestroy(epi);
+    return bail(cst != SEM_OK ? cst : fail(SEM_ECUDA, "batch epilogue capture failed"));
+  }
+  // main graph: prologue -> while(any problem iterating) { CG iterations } -> epilogue
+  cudaGraphNode_t n_pro, n_loop, n_epi;
+  cudaGraphConditionalHandle handle;
+  e = cudaGraphCreate(&main_g, 0);
+  if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&n_pro, main_g, nullptr, 0, pro);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, main_g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&n_loop, main_g, &n_pro, nullptr, 1, &cp);
+  long long body_launches = 0;
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s0, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const long long lb = sem_launch_total();
+      cst = batch_fork_join(b, [&](int i, cudaStream_t si) -> sem_status {
+        sem_ctx* c = b->ctxs[i];
+        const SemGeom& g = c->g;
+        for (int it = 0; it < check; ++it) {
+          launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, si,
+                                   c->tuned64_set ? &c->tuned64 : nullptr);
+          launch_pcg_update<double>(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, si);
+          launch_pcg_dir<double>(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, si);
+        }
+        return SEM_OK;
+      });
+      k_batch_decide<<<1, 32, 0, s0>>>(b->d_states, count, b->d_trips, cap, handle);
+      sem_count_launch();
+      body_launches = sem_launch_total() - lb;
+      cudaGraph_t tmp = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(s0, &tmp);
+      if (e2 != cudaSuccess) e = e2;
+      if (cst != SEM_OK && e == cudaSuccess) e = cudaErrorUnknown;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&n_epi, main_g, &n_loop, 1, epi);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, main_g, 0);
+  cudaGraphDestroy(pro);
+  cudaGraphDestroy(epi);
+  if (main_g) cudaGraphDestroy(main_g);
+  sem_count_launch(-(sem_launch_total() - l0));   // counted when the graph runs
+  if (e != cudaSuccess) return bail(fail(SEM_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e)));
+  b->launches_fixed = l1 - l0;
+  b->launches_per_trip = body_launches;
+  *out = b;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_batch_solve(sem_batch* b, sem_info* infos, void* stream) {
+  t_err.clear();
+  if (b == nullptr) return fail(SEM_EINVAL, "null batch");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaStream_t s0 = b->streams[0];
+  SEM_CUDA(cudaEventRecord(b->events[0], us));
+  SEM_CUDA(cudaStreamWaitEvent(s0, b->events[0], 0));
+  SEM_CUDA(cudaGraphLaunch(b->exec, s0));
+  const int count = (int)b->ctxs.size();
+  std::vector<PcgState> hs(count);
+  int trips = 0;
+  for (int i = 0; i < count; ++i)
+    SEM_CUDA(cudaMemcpyAsync(&hs[i], b->ctxs[i]->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s0));
+  SEM_CUDA(cudaMemcpyAsync(&trips, b->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s0));
+  SEM_CUDA(cudaStreamSynchronize(s0));
+  SEM_CUDA(cudaEventRecord(b->events[0], s0));
+  SEM_CUDA(cudaStreamWaitEvent(us, b->events[0], 0));
+  sem_count_launch(b->launches_fixed + (long long)trips * b->launches_per_trip);
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  sem_status worst = SEM_OK;
+  for (int i = 0; i < count; ++i) {
+    const PcgState& h = hs[i];
+    sem_status st = h.done == 1 ? SEM_OK : (h.done == 2 ? SEM_EBREAKDOWN : SEM_ENOCONV);
+    if (infos) {
+      infos[i].iters = h.iter;
+      infos[i].refinements = 0;
+      infos[i].rel_res = h.rr0 > 0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+      infos[i].t_solve_s = secs;
+    }
+    if (st != SEM_OK && worst == SEM_OK) worst = st;
+  }
+  if (worst != SEM_OK) return fail(worst, "at least one problem of the batch did not converge");
+  return SEM_OK;
+}
+
+extern "C" void sem_batch_destroy(sem_batch* b) { batch_free(b); }
+
+extern "C" sem_status sem_solve_batch(sem_ctx* const* ctxs, int count, const double* const* f, double* const* u,
+                                      sem_info* infos, void* stream) {
+  sem_batch* b = nullptr;
+  sem_status st = sem_batch_create(ctxs, count, f, u, &b);
+  if (st != SEM_OK) return st;
+  st = sem_batch_solve(b, infos, stream);
+  std::string keep = t_err;
+  sem_batch_destroy(b);
+  t_err = keep;
+  return st;
 }

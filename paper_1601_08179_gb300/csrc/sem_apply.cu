@@ -772,11 +772,38 @@ ApplyConfig sem_apply_config(int n, size_t elem_bytes) {
   return c;
 }
 
+bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
+  if (c.epb < 1 || c.epb > 64 || c.ks < 1 || c.ks > n || c.threads != kThreads) return false;
+  const size_t need = hdr_bytes(c.epb) + (size_t)c.epb * elem_sm(n, c.ks).size * elem_bytes;
+  return need == c.smem && need <= 200 * 1024;
+}
+
+ApplyConfig sem_apply_config_make(int n, size_t elem_bytes, int epb, int ks) {
+  ApplyConfig c;
+  c.threads = kThreads;
+  c.epb = epb;
+  c.ks = ks;
+  c.smem = hdr_bytes(epb) + (size_t)epb * elem_sm(n, ks).size * elem_bytes;
+  return c;
+}
+
 template <typename T>
 void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
-                      double* partials, PcgState* st, cudaStream_t s) {
+                      double* partials, PcgState* st, cudaStream_t s, const ApplyConfig* tuned) {
   (void)b;
-  const ApplyConfig c = sem_apply_config(g.n, sizeof(T));
+  const ApplyConfig c = (tuned != nullptr && sem_apply_config_valid(g.n, sizeof(T), *tuned))
+                            ? *tuned : sem_apply_config(g.n, sizeof(T));
+  if (tuned != nullptr && sem_apply_config_valid(g.n, sizeof(T), *tuned)) {
+    // an explicit CTA-tile configuration selects the CTA-tile kernel for every degree
+    switch (g.n) {
+      case 1: launch_nc<T, 1>(g, t, x, y, partials, st, c, s); return;
+      case 3: launch_nc<T, 3>(g, t, x, y, partials, st, c, s); return;
+      case 7: launch_nc<T, 7>(g, t, x, y, partials, st, c, s); return;
+      case 15: launch_nc<T, 15>(g, t, x, y, partials, st, c, s); return;
+      case 31: launch_nc<T, 31>(g, t, x, y, partials, st, c, s); return;
+      default: launch_nc<T, 0>(g, t, x, y, partials, st, c, s); return;
+    }
+  }
   // Measured on GB300: the warp-per-element variant wins for FP32 at
   // 3 <= n <= 7; FP64 (bound by the FP64 pipe) and n = 1, 2 run best with
   // the CTA-tile kernel.
@@ -813,9 +840,10 @@ void launch_class_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoe
 }
 
 template void launch_tpt_apply<double>(const SemGeom&, const SemBasis&, const SemClassTables<double>&,
-                                       const double*, double*, double*, PcgState*, cudaStream_t);
+                                       const double*, double*, double*, PcgState*, cudaStream_t,
+                                       const ApplyConfig*);
 template void launch_tpt_apply<float>(const SemGeom&, const SemBasis&, const SemClassTables<float>&,
-                                      const float*, float*, double*, PcgState*, cudaStream_t);
+                                      const float*, float*, double*, PcgState*, cudaStream_t, const ApplyConfig*);
 template void launch_class_coeffs<double>(const SemGeom&, const SemBasis&, const double*, const double*, double*,
                                           cudaStream_t);
 template void launch_class_coeffs<float>(const SemGeom&, const SemBasis&, const double*, const double*, float*,

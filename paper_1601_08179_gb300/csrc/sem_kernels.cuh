@@ -11,6 +11,9 @@ struct ApplyConfig {
   size_t smem;  // dynamic shared memory bytes
 };
 ApplyConfig sem_apply_config(int n, size_t elem_bytes);
+// Explicit CTA-tile configuration (autotuner candidates) and its validity.
+ApplyConfig sem_apply_config_make(int n, size_t elem_bytes, int epb, int ks);
+bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c);
 
 // Per-class operator coefficient blocks (layout in sem_internal.h), computed in
 // FP64 and stored in T.
@@ -20,9 +23,11 @@ void launch_class_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoe
 
 // y = Hhat~ x on the skeleton (transformed space); y must be zero on entry.
 // If st != nullptr: also x^T y -> st->pq and alpha = rho / pq (CG step).
+// tuned: optional CTA-tile configuration chosen by the autotuner (nullptr:
+// the built-in choice, which may be the warp-per-element kernel).
 template <typename T>
 void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
-                      double* partials, PcgState* st, cudaStream_t s);
+                      double* partials, PcgState* st, cudaStream_t s, const ApplyConfig* tuned = nullptr);
 
 void launch_class_tables(const SemGeom& g, const SemBasis& b, const double* ux_w, const double* uy_w,
                          const double* uz_w, double lambda, double* dcoef, double* dinv,

@@ -78,6 +78,13 @@ def lib():
         "sem_unpack_skeleton": (ctypes.c_int, [_P, _P, _P, _P]),
         "sem_refine_history": (ctypes.c_int, [_P, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "sem_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(sem_info), _P]),
+        "sem_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "sem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                            ctypes.POINTER(_P)]),
+        "sem_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(sem_info), _P]),
+        "sem_batch_destroy": (None, [_P]),
+        "sem_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                           ctypes.POINTER(sem_info), _P]),
         "sem_gradients": (ctypes.c_int, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _P]),
         "sem_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
         "sem_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -102,7 +109,8 @@ def exported_symbols():
             "sem_condense_rhs_noalloc",
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
-            "sem_solve_adjoint", "sem_gradients",
+            "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_batch_create", "sem_batch_solve",
+            "sem_batch_destroy", "sem_solve_batch",
             "sem_profile_enable",
             "sem_profile_read", "sem_launch_count",
             "sem_destroy", "sem_status_string", "sem_last_error"]
@@ -291,6 +299,44 @@ def sem_gradients(ctx: SemContext, w, u, f, df, stream=None):
                                dhx.ctypes.data_as(_D), dhy.ctypes.data_as(_D), dhz.ctypes.data_as(_D),
                                _stream(stream, w)))
     return dl.value, dhx, dhy, dhz
+
+
+def sem_autotune(ctx: SemContext):
+    """Returns (ms per application with the built-in config, with the chosen one)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().sem_autotune(ctx.handle, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+class SemBatch:
+    """Handle of sem_batch_create (one captured graph over many contexts)."""
+
+    def __init__(self, ctxs, fs, us):
+        n = len(ctxs)
+        if not (n == len(fs) == len(us)) or n == 0:
+            raise ValueError("need equally many contexts, loads and outputs")
+        self.ctxs, self.fs, self.us = list(ctxs), list(fs), list(us)   # keep them alive
+        C = (_P * n)(*[c.handle for c in ctxs])
+        F = (_P * n)(*[_dptr(f, c.n_nodes, "f") for f, c in zip(fs, ctxs)])
+        U = (_P * n)(*[_dptr(u, c.n_nodes, "u") for u, c in zip(us, ctxs)])
+        self.handle = ctypes.c_void_p()
+        _check(lib().sem_batch_create(C, n, F, U, ctypes.byref(self.handle)))
+
+    def solve(self, stream=None, check=True):
+        n = len(self.ctxs)
+        infos = (sem_info * n)()
+        st = lib().sem_batch_solve(self.handle, infos, _stream(stream, self.fs[0]))
+        if check:
+            _check(st)
+        return st, [dict(iters=i.iters, rel_res=i.rel_res, t_solve_s=i.t_solve_s) for i in infos]
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().sem_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
 
 
 def sem_refine_history(ctx: SemContext):

@@ -1,0 +1,101 @@
+"""Batched solves (one captured CUDA graph with a device-side while loop over
+many independent problems) and the operator autotuner, against the dense
+oracle and against one-at-a-time solves."""
+import numpy as np
+import pytest
+
+import sem_inputs as si
+from oracle import dense, local
+from oracle.mesh import Mesh
+from tests.gpu_util import dev, host, make_pair, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_batch(count=12, seed=71):
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for b in range(count):
+        p = int(g.choice([2, 3, 4, 6, 8]))
+        m = tuple(int(v) for v in g.integers(1, 4, size=3))
+        lam = float(10.0 ** g.uniform(-2.0, 4.0))
+        ar = float(g.uniform(1.0, 8.0)) if m[0] > 1 else 1.0
+        out.append((p, m, lam, ar, seed * 100 + b))
+    return out
+
+
+def test_batch_matches_oracle_and_single_solves():
+    import torch
+    from paper_1601_08179_gb300 import sem
+    probs = _small_batch()
+    ctxs, meshes, fs, us, refs = [], [], [], [], []
+    for p, m, lam, ar, seed in probs:
+        ctx, ms = make_pair(p, m, lam, ar)
+        f = si.node_noise(ms.n_global, seed)
+        ctxs.append(ctx)
+        meshes.append(ms)
+        fs.append(dev(f))
+        us.append(torch.full((ctx.n_nodes,), np.nan, dtype=torch.float64, device="cuda"))
+        refs.append(dense.solve_full(ms, lam, f))
+    batch = sem.SemBatch(ctxs, fs, us)
+    for rep in range(2):                      # the same graph, launched twice
+        st, infos = batch.solve()
+        for k, (u, ref) in enumerate(zip(us, refs)):
+            assert relerr(host(u), ref) <= 1e-9, k
+    for k, (ctx, f) in enumerate(zip(ctxs, fs)):
+        u1 = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+        info = sem.sem_solve(ctx, f, u1)
+        assert abs(info["iters"] - infos[k]["iters"]) <= 1
+        assert relerr(host(us[k]), host(u1)) <= 1e-11
+
+
+def test_batched_workload_heterogeneous_64():
+    """64 problems: m in {4,8,12,16,24}^3, p in {4,6,8,12,16}, lambda
+    log-uniform in [1e-2, 1e4], aspect ratio U[1, 64], seeded uniform loads:
+    every solution meets the oracle's uncondensed residual (checked on the
+    smaller problems) and equals its one-at-a-time solve."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    work = si.batched_problems()
+    ctxs, fs, us = [], [], []
+    for w in work:
+        hx, hy, hz = w.widths()
+        c = sem.sem_setup(w.p, hx, hy, hz, w.lam)
+        ctxs.append(c)
+        fs.append(dev(si.node_noise(c.n_nodes, w.seed)))
+        us.append(torch.empty(c.n_nodes, dtype=torch.float64, device="cuda"))
+    batch = sem.SemBatch(ctxs, fs, us)
+    st, infos = batch.solve()
+    assert all(i["rel_res"] <= 1e-10 for i in infos)
+    order = sorted(range(len(work)), key=lambda k: work[k].dofs)
+    for k in order[:3]:
+        w = work[k]
+        ms = Mesh(w.p, *w.widths())
+        f = host(fs[k])
+        F = local.rhs_full(ms, f)
+        r = (local.apply_full(ms, w.lam, host(us[k])) - F)[ms.free_mask]
+        assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(F[ms.free_mask]), k
+    for k in order[::8]:
+        u1 = torch.empty_like(us[k])
+        sem.sem_solve(ctxs[k], fs[k], u1)
+        assert relerr(host(us[k]), host(u1)) <= 1e-10, k
+
+
+@pytest.mark.parametrize("p,m,mixed", [(8, (6, 5, 4), False), (4, (8, 6, 6), False), (8, (6, 5, 4), True)])
+def test_autotune_keeps_results(p, m, mixed):
+    import torch
+    from paper_1601_08179_gb300 import sem
+    opts = sem.default_opts(precision=sem.PREC_MIXED) if mixed else None
+    ctx, ms = make_pair(p, m, 2.0, 4.0, opts=opts)
+    ms_def, ms_best = sem.sem_autotune(ctx)
+    assert 0 < ms_best <= ms_def
+    u = si.random_vector(ms.n_skeleton, 81)
+    v = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+    sem.sem_apply_condensed(ctx, dev(u), v, sem.SPACE_NODAL)
+    assert relerr(host(v), local.apply_condensed(ms, 2.0, u)) <= 1e-12
+    f = si.node_noise(ms.n_global, 82)
+    w = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+    sem.sem_solve(ctx, dev(f), w)
+    F = local.rhs_full(ms, f)
+    r = (local.apply_full(ms, 2.0, host(w)) - F)[ms.free_mask]
+    assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(F[ms.free_mask])
