@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--workload", default="scale", choices=["scale", "mixed16", "batched", "adjoint"],
+                    help="scale: graded N~1.68e7 workload of degree --p (default); mixed16: p = 16 on 16^3, "
+                         "lambda = 10, AR 16; batched: 64 heterogeneous problems in one graph launch; "
+                         "adjoint: forward + backward of the differentiable solve (p = 8 on 16^3)")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
                     help="'both': time the plain FP64 solve and the mixed-precision solve (the headline)")
     return ap.parse_args()
@@ -86,6 +90,17 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def replica_seed(w: si.Workload, rank: int) -> int:
+    """Seed of rank `rank`'s replica: every rank solves its own right-hand side."""
+    return w.seed + 1000 * rank
+
+
+def whole_job_value(step_s_max: float, dofs_per_rank: int, world: int) -> float:
+    """s/DOF of the whole job: the slowest rank's step time over all unknowns
+    the ranks solved together."""
+    return step_s_max / (dofs_per_rank * world)
 
 
 def max_over_ranks(x: float, world: int) -> float:
@@ -249,8 +264,8 @@ def our_arm(args, rank, world, local_rank):
 
     build.build()
     torch.cuda.set_device(local_rank)
-    w = si.scale_workload(args.p, ar=args.ar, lam=args.lam)
-    seed = w.seed + 1000 * rank
+    w = si.MIXED if args.workload == "mixed16" else si.scale_workload(args.p, ar=args.ar, lam=args.lam)
+    seed = replica_seed(w, rank)
     hx, hy, hz = w.widths()
     t0 = time.perf_counter()
     ctx = sem.sem_setup(w.p, hx, hy, hz, w.lam)
@@ -312,7 +327,7 @@ def our_arm(args, rank, world, local_rank):
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)", "bytes_per_launch": 8.0 * nb}
     out = {
         "metric": METRIC,
-        "value": r["step_s"] / (w.dofs * world),
+        "value": whole_job_value(r["step_s"], w.dofs, world),
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
@@ -332,7 +347,7 @@ def our_arm(args, rank, world, local_rank):
         "operator": {"gdof_s": w.dofs / r["apply_s"] / 1e9, "apply_ms": r["apply_s"] * 1e3,
                      "timed_launches": r["apply_n"], "dtype": "f64" if head == "fp64" else "f32"},
         "roofline": roof,
-        "e2e": {"value": e2e_s / (w.dofs * world) if e2e_s else None, "unit": UNIT,
+        "e2e": {"value": whole_job_value(e2e_s, w.dofs, world) if e2e_s else None, "unit": UNIT,
                 "h2d_bytes_per_step": f_host.nbytes, "d2h_bytes_per_step": f_host.nbytes},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
@@ -341,7 +356,7 @@ def our_arm(args, rank, world, local_rank):
         out["solve"]["refine_hist"] = res["mixed"]["refine_hist"]
     if "fp64" in res and head != "fp64":
         p64 = res["fp64"]
-        out["fp64"] = {"value": p64["step_s"] / (w.dofs * world), "ms_per_step": p64["step_s"] * 1e3,
+        out["fp64"] = {"value": whole_job_value(p64["step_s"], w.dofs, world), "ms_per_step": p64["step_s"] * 1e3,
                        "iters": p64["info"]["iters"], "operator_gdof_s": w.dofs / p64["apply_s"] / 1e9,
                        "operator_ms": p64["apply_s"] * 1e3,
                        "operator_frac_fp64_peak": flops / p64["apply_s"] / 1e12 / FP64_PEAK_TFLOPS,
@@ -355,6 +370,98 @@ def our_arm(args, rank, world, local_rank):
             out["cpu_baseline"]["sample"] += " (iteration count of this GPU FP64 solve; no oracle solve recorded)"
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def batched_arm(args, rank, world, local_rank):
+    """64 heterogeneous FP64 problems solved by one graph launch per step."""
+    import torch
+
+    from paper_1601_08179_gb300 import build, sem
+    build.build()
+    torch.cuda.set_device(local_rank)
+    work = si.batched_problems()
+    ctxs, fs, us = [], [], []
+    for w in work:
+        hx, hy, hz = w.widths()
+        c = sem.sem_setup(w.p, hx, hy, hz, w.lam)
+        sem.sem_autotune(c)
+        ctxs.append(c)
+        fs.append(torch.from_numpy(si.node_noise(c.n_nodes, replica_seed(w, rank))).cuda())
+        us.append(torch.empty(c.n_nodes, dtype=torch.float64, device="cuda"))
+    batch = sem.SemBatch(ctxs, fs, us)
+    for _ in range(args.warmup):
+        batch.solve()
+    torch.cuda.synchronize()
+    barrier(world)
+    l0 = sem.sem_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            st, infos = batch.solve()
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    step_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / args.steps, world)
+    dofs = sum(w.dofs for w in work)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC + " (batched problems)", "value": whole_job_value(step_s, dofs, world), "unit": UNIT,
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic",
+                          "config": {"workload": "batched64", "problems": len(work), "dofs_total": dofs,
+                                     "degrees": sorted(set(w.p for w in work)), "rtol": 1e-10,
+                                     "parallelism": f"replicas{world}"},
+                          "iters_max": max(i["iters"] for i in infos), "iters_sum": sum(i["iters"] for i in infos),
+                          "gpu_launches": sem.sem_launch_count() - l0, "clocks": clk.summary()}), flush=True)
+
+
+def adjoint_arm(args, rank, world, local_rank):
+    """Forward solve + backward (adjoint solve and gradient kernels) of the
+    differentiable solve, J = 1/2 ||u - u_target||^2."""
+    import torch
+
+    from paper_1601_08179_gb300 import build, sem
+    from paper_1601_08179_gb300.autograd import context_for, helmholtz_solve
+    build.build()
+    torch.cuda.set_device(local_rank)
+    w = si.ADJOINT
+    hx, hy, hz = w.widths()
+    ctx = context_for(w.p, hx, hy, hz, w.lam)
+    x, y, z = sem.sem_node_coords(ctx)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    f0 = torch.tensor(si.manufactured_f(X, Y, Z, w.lam).ravel(), device="cuda")
+    ut = torch.tensor(si.smooth_target(X, Y, Z, w.seed).ravel(), device="cuda")
+    lam = torch.tensor(w.lam, dtype=torch.float64, requires_grad=True)
+    hs = [torch.tensor(h, dtype=torch.float64, requires_grad=True) for h in (hx, hy, hz)]
+
+    def step():
+        f = f0.clone().requires_grad_(True)
+        u = helmholtz_solve(f, lam, *hs, w.p)
+        J = 0.5 * ((u - ut) ** 2).sum()
+        J.backward()
+        return float(J)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(world)
+    step_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / args.steps, world)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC + " (forward + adjoint gradient)", "value": whole_job_value(step_s, w.dofs, world),
+                          "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "lambda": w.lam},
+                          "clocks": clk.summary()}), flush=True)
 
 
 def reference_iterations(w: si.Workload):
@@ -405,6 +512,10 @@ def main():
     try:
         if args.impl == "reference":
             reference_arm(args, rank, world)
+        elif args.workload == "batched":
+            batched_arm(args, rank, world, local_rank)
+        elif args.workload == "adjoint":
+            adjoint_arm(args, rank, world, local_rank)
         else:
             our_arm(args, rank, world, local_rank)
     finally:

@@ -103,7 +103,7 @@ typedef struct {
                          zero at every refinement step (classical refinement) */
   double reliable_delta; /* MIXED scheme 1: a refinement step is taken when the FP32
                          recursive residual has fallen by this factor since the
-                         previous step (default 0.1) */
+                         previous step (default 0.03) */
 } sem_opts;
 
 /* Result of a solve. */
@@ -160,6 +160,12 @@ sem_status sem_get_basis(const sem_ctx* ctx, double* gll_x, double* gll_w,
  * uB, vB: device, length N_B, must not overlap.  Asynchronous on stream. */
 sem_status sem_apply_condensed(sem_ctx* ctx, const double* uB, double* vB,
                                sem_space space, void* stream);
+
+/* The transformed condensed operator in FP32 (the operator of the mixed-
+ * precision inner solver): v~ = T Hhat T^T u~ with FP32 tables and
+ * arithmetic.  uB, vB: device float arrays of length N_B, not overlapping.
+ * Prepares the FP32 tables on first use.  Asynchronous on stream. */
+sem_status sem_apply_condensed_f32(sem_ctx* ctx, const float* uB, float* vB, void* stream);
 
 /* Condensed load fhat = sum_e Rhat_e (F_B - H_BI H_II^-1 F_I) (Algorithm 1,
  * first loop; Algorithm 4 in the TRANSFORMED space), with F_e the GLL-quadrature

@@ -609,7 +609,7 @@ void sem_default_opts(sem_opts* o) {
   o->inner_rtol = 1e-4;
   o->max_refine = 40;
   o->mixed_scheme = 1;
-  o->reliable_delta = 0.1;
+  o->reliable_delta = 0.03;
 }
 
 static sem_status check_opts(const sem_opts* o) {
@@ -830,6 +830,22 @@ sem_status sem_apply_condensed(sem_ctx* c, const double* uB, double* vB, sem_spa
   sem_status st = apply_t(c, c->d_t1, c->d_t2, s);
   if (st != SEM_OK) return st;
   launch_skel_transform(c->g, c->mat(3), c->d_t2, vB, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status sem_apply_condensed_f32(sem_ctx* c, const float* uB, float* vB, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (uB == nullptr || vB == nullptr) return fail(SEM_EINVAL, "null vector");
+  if ((const void*)uB == (const void*)vB) return fail(SEM_EINVAL, "uB and vB must not alias");
+  sem_status st = ensure_mixed(c);
+  if (st != SEM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  SEM_CUDA(cudaStreamSynchronize(c->stream));   // FP32 tables are prepared on the context stream
+  SEM_CUDA(cudaMemsetAsync(vB, 0, sizeof(float) * c->g.nb, s));
+  launch_tpt_apply<float>(c->g, c->h1.basis, c->tab_f, uB, vB, nullptr, nullptr, s,
+                          c->tuned32_set ? &c->tuned32 : nullptr);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }

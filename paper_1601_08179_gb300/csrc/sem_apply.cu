@@ -461,18 +461,27 @@ int num_sms_cached() {
 // so warps of a CTA progress independently.  Trip counts are compile-time.
 template <int N>
 struct WarpSm {
-  static constexpr int N2 = N * N, N3 = N2 * N;
-  static constexpr int F = 0, E = 6 * N2, Vt = E + 12 * N, Acc = Vt + 8, Eo = Acc + 6 * N2, Vo = Eo + 12 * N,
-                       C = Vo + 8, cube = C + 18 * N + 24, size = (cube + N3 + 3) & ~3;
+  static constexpr int N2 = N * N, N3 = N2 * N, RS = (N + 3) & ~3;   // cube rows padded to 4
+  static constexpr int F = 0, E = 6 * N2, Vt = E + 12 * N, C = Vt + 8, P2 = C + 18 * N + 24,
+                       cube = (P2 + 6 * N + 3) & ~3, size = (cube + N2 * RS + 3) & ~3;
 };
 constexpr int kWarpHdr = 32;   // ints per warp: 26 entity offsets, class, loaded class
 
+template <typename T>
+struct Two {
+  T x, y;
+};
+
+// The face primary part is evaluated where its inputs already sit in
+// registers: z-faces in the cube-column loop, x- and y-faces in the
+// contraction loop; every face output goes to the skeleton straight from
+// registers.  skw = w0 * skd is used for the in-face line couplings.
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
 k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
-                 double* __restrict__ partials, PcgState* st) {
+                 double* __restrict__ partials, PcgState* st, T w0) {
   using S = WarpSm<N>;
-  constexpr int N2 = S::N2;
+  constexpr int N2 = S::N2, RS = S::RS;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   if (st != nullptr && st->done) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -484,9 +493,9 @@ k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* _
   if (lane == 0) H[27] = -1;
   T dot = T(0);
   const int mx = g.mx, my = g.my, mz = g.mz;
+  const Two<T>* P2 = reinterpret_cast<const Two<T>*>(W + S::P2);   // [dir][t]: (skd[2dir N + t], skd[(2dir+1) N + t])
 
   for (long long e = e_begin; e < e_end; ++e) {
-    // element coordinates (visiting order: most-graded axis slowest)
     int ex, ey, ez;
     {
       const int ei = (int)e;
@@ -525,6 +534,10 @@ k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* _
     }
     if (cls != H[27]) {
       for (int r = lane; r < 18 * N + 18; r += 32) W[S::C + r] = cb[r];
+      for (int r = lane; r < 6 * N; r += 32) {
+        const int dir = r / (2 * N), rem = r - dir * 2 * N, t = rem >> 1, side = rem & 1;
+        W[S::P2 + r] = cb[(2 * dir + side) * N + t];
+      }
     }
     __syncwarp();
     if (lane == 0) H[27] = cls;
@@ -537,32 +550,7 @@ k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* _
     const T* cO = W + S::C + 18 * N;
     const T* eO = cO + 6;
     const T* vO = cO + 12;
-    // primary part: faces
-#pragma unroll
-    for (int r = lane; r < 6 * N2; r += 32) {
-      const int slot = r / N2, idx = r - slot * N2, dd = slot >> 1, s = slot & 1;
-      const int slow = idx / N, fast = idx - slow * N;
-      T out = __ldg(cb + co.fdiag + r) * F[r];
-      out = fma(cO[slot], F[(slot ^ 1) * N2 + idx], out);
-      if (dd == 0) {
-        out = fma(skw[2 * N + fast], Ed[(8 + s) * N + slow], out);
-        out = fma(skw[3 * N + fast], Ed[(10 + s) * N + slow], out);
-        out = fma(skw[4 * N + slow], Ed[(4 + s) * N + fast], out);
-        out = fma(skw[5 * N + slow], Ed[(6 + s) * N + fast], out);
-      } else if (dd == 1) {
-        out = fma(skw[fast], Ed[(8 + 2 * s) * N + slow], out);
-        out = fma(skw[N + fast], Ed[(9 + 2 * s) * N + slow], out);
-        out = fma(skw[4 * N + slow], Ed[s * N + fast], out);
-        out = fma(skw[5 * N + slow], Ed[(2 + s) * N + fast], out);
-      } else {
-        out = fma(skw[fast], Ed[(4 + 2 * s) * N + slow], out);
-        out = fma(skw[N + fast], Ed[(5 + 2 * s) * N + slow], out);
-        out = fma(skw[2 * N + slow], Ed[2 * s * N + fast], out);
-        out = fma(skw[3 * N + slow], Ed[(1 + 2 * s) * N + fast], out);
-      }
-      W[S::Acc + r] = out;
-    }
-    // primary part: edges
+    // ---- edges: primary part, straight to the skeleton
 #pragma unroll
     for (int r = lane; r < 12 * N; r += 32) {
       const int slot = r / N, l = r - slot * N, grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
@@ -570,21 +558,21 @@ k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* _
       const T *k1, *k2, *f1, *f2;
       int st1, st2;
       T va, vb;
-      if (grp == 0) {          // x-edge Ex[sb=s1][sc=s2], index i
+      if (grp == 0) {
         va = Vt[2 * s1 + 4 * s2];
         vb = Vt[1 + 2 * s1 + 4 * s2];
         k1 = skw + (2 + s1) * N; f1 = F + (4 + s2) * N2 + l; st1 = N;
         k2 = skw + (4 + s2) * N; f2 = F + (2 + s1) * N2 + l; st2 = N;
         out = fma(eO[2 + s1], Ed[((1 - s1) + 2 * s2) * N + l], out);
         out = fma(eO[4 + s2], Ed[(s1 + 2 * (1 - s2)) * N + l], out);
-      } else if (grp == 1) {   // y-edge Ey[sa=s1][sc=s2], index j
+      } else if (grp == 1) {
         va = Vt[s1 + 4 * s2];
         vb = Vt[s1 + 2 + 4 * s2];
         k1 = skw + s1 * N; f1 = F + (4 + s2) * N2 + l * N; st1 = 1;
         k2 = skw + (4 + s2) * N; f2 = F + s1 * N2 + l; st2 = N;
         out = fma(eO[s1], Ed[(4 + (1 - s1) + 2 * s2) * N + l], out);
         out = fma(eO[4 + s2], Ed[(4 + s1 + 2 * (1 - s2)) * N + l], out);
-      } else {                 // z-edge Ez[sa=s1][sb=s2], index k
+      } else {
         va = Vt[s1 + 2 * s2];
         vb = Vt[s1 + 2 * s2 + 4];
         k1 = skw + s1 * N; f1 = F + (2 + s2) * N2 + l * N; st1 = 1;
@@ -598,9 +586,13 @@ k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* _
       for (int m = 0; m < N; ++m) out = fma(k1[m], f1[m * st1], out);
 #pragma unroll
       for (int m = 0; m < N; ++m) out = fma(k2[m], f2[m * st2], out);
-      W[S::Eo + r] = out;
+      const int off = H[6 + slot];
+      if (off >= 0) {
+        atomicAdd(v + off + l, out);
+        dot = fma(Ed[r], out, dot);
+      }
     }
-    // primary part: vertices
+    // ---- vertices
     if (lane < 8) {
       const int slot = lane, sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
       T out = __ldg(cb + co.vdiag + slot) * Vt[slot];
@@ -619,81 +611,101 @@ k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* _
       out = fma(vO[sa], Vt[slot ^ 1], out);
       out = fma(vO[2 + sb], Vt[slot ^ 2], out);
       out = fma(vO[4 + sc], Vt[slot ^ 4], out);
-      W[S::Vo + slot] = out;
+      const int off = H[18 + slot];
+      if (off >= 0) {
+        atomicAdd(v + off, out);
+        dot = fma(Vt[slot], out, dot);
+      }
     }
-    __syncwarp();
-    // condensed part: expansion, -D^-1, b/t contraction in registers (Table 2)
+    // ---- cube columns: expansion, -D^-1, b/t contraction and the z-face
+    //      primary part (Table 2; Eq. east_east_primary_part_transformed)
 #pragma unroll
     for (int ji = lane; ji < N2; ji += 32) {
       const int j = ji / N, i = ji - j * N;
       const T ai = skd[i], bi = skd[N + i], cj = skd[2 * N + j], dj = skd[3 * N + j];
       const T fb = F[4 * N2 + ji], ft = F[5 * N2 + ji];
-      T sb = W[S::Acc + 4 * N2 + ji], stt = W[S::Acc + 5 * N2 + ji];
+      T sb = T(0), stt = T(0);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        const T ek = skd[4 * N + k], gk = skd[5 * N + k];
+        const Two<T> ez = P2[2 * N + k];
         T x = ai * F[k * N + j];
         x = fma(bi, F[N2 + k * N + j], x);
         x = fma(cj, F[2 * N2 + k * N + i], x);
         x = fma(dj, F[3 * N2 + k * N + i], x);
-        x = fma(ek, fb, x);
-        x = fma(gk, ft, x);
+        x = fma(ez.x, fb, x);
+        x = fma(ez.y, ft, x);
         const T vv = __ldg(cb + co.ndinv + k * N2 + ji) * x;
-        W[S::cube + k * N2 + ji] = vv;
-        sb = fma(ek, vv, sb);
-        stt = fma(gk, vv, stt);
+        W[S::cube + (k * N + j) * RS + i] = vv;
+        sb = fma(ez.x, vv, sb);
+        stt = fma(ez.y, vv, stt);
       }
-      W[S::Acc + 4 * N2 + ji] = sb;
-      W[S::Acc + 5 * N2 + ji] = stt;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const T own = s ? ft : fb, opp = s ? fb : ft;
+        T pr = ai * Ed[(4 + 2 * s) * N + j];
+        pr = fma(bi, Ed[(5 + 2 * s) * N + j], pr);
+        pr = fma(cj, Ed[2 * s * N + i], pr);
+        pr = fma(dj, Ed[(1 + 2 * s) * N + i], pr);
+        T out = fma(__ldg(cb + co.fdiag + (4 + s) * N2 + ji), own, (s ? stt : sb));
+        out = fma(cO[4 + s], opp, out);
+        out = fma(w0, pr, out);
+        const int off = H[4 + s];
+        if (off >= 0) {
+          atomicAdd(v + off + ji, out);
+          dot = fma(own, out, dot);
+        }
+      }
     }
     __syncwarp();
-    // w / e (rows over i) and s / n (columns over j)
+    // ---- x-faces (k, j = m) and y-faces (k, i = m): primary part and the
+    //      w/e and s/n contractions
 #pragma unroll
     for (int q = lane; q < N2; q += 32) {
       const int k = q / N, m = q - k * N;
-      const T* row = W + S::cube + k * N2 + m * N;    // (k, j = m), over i
-      const T* col = W + S::cube + k * N2 + m;        // (k, i = m), over j
-      T s0 = W[S::Acc + q], s1 = W[S::Acc + N2 + q];
-      T s2 = W[S::Acc + 2 * N2 + q], s3 = W[S::Acc + 3 * N2 + q];
+      const Two<T> pa = P2[m], pb = P2[N + m], pc = P2[2 * N + k];   // (skd[m], skd[N+m]), ...
+      const T* row = W + S::cube + (k * N + m) * RS;                   // over i
+      const T* col = W + S::cube + k * N * RS + m;                     // over j (stride RS)
+      T sx0 = T(0), sx1 = T(0), sy0 = T(0), sy1 = T(0);
 #pragma unroll
       for (int t = 0; t < N; ++t) {
-        const T c = row[t], d = col[t * N];
-        s0 = fma(skd[t], c, s0);
-        s1 = fma(skd[N + t], c, s1);
-        s2 = fma(skd[2 * N + t], d, s2);
-        s3 = fma(skd[3 * N + t], d, s3);
+        const T c = row[t], d = col[t * RS];
+        const Two<T> ka = P2[t], kb = P2[N + t];
+        sx0 = fma(ka.x, c, sx0);
+        sx1 = fma(ka.y, c, sx1);
+        sy0 = fma(kb.x, d, sy0);
+        sy1 = fma(kb.y, d, sy1);
       }
-      W[S::Acc + q] = s0;
-      W[S::Acc + N2 + q] = s1;
-      W[S::Acc + 2 * N2 + q] = s2;
-      W[S::Acc + 3 * N2 + q] = s3;
-    }
-    __syncwarp();
-    // scatter R and the element share of x^T (A x)
+      const T fx0 = F[q], fx1 = F[N2 + q], fy0 = F[2 * N2 + q], fy1 = F[3 * N2 + q];
 #pragma unroll
-    for (int r = lane; r < 6 * N2; r += 32) {
-      const int slot = r / N2, off = H[slot];
-      if (off >= 0) {
-        const T o = W[S::Acc + r];
-        atomicAdd(v + off + r - slot * N2, o);
-        dot = fma(F[r], o, dot);
-      }
-    }
-#pragma unroll
-    for (int r = lane; r < 12 * N; r += 32) {
-      const int slot = r / N, off = H[6 + slot];
-      if (off >= 0) {
-        const T o = W[S::Eo + r];
-        atomicAdd(v + off + r - slot * N, o);
-        dot = fma(Ed[r], o, dot);
-      }
-    }
-    if (lane < 8) {
-      const int off = H[18 + lane];
-      if (off >= 0) {
-        const T o = W[S::Vo + lane];
-        atomicAdd(v + off, o);
-        dot = fma(Vt[lane], o, dot);
+      for (int s = 0; s < 2; ++s) {
+        // x-face side s at (k, j = m)
+        T pr = pb.x * Ed[(8 + s) * N + k];
+        pr = fma(pb.y, Ed[(10 + s) * N + k], pr);
+        pr = fma(pc.x, Ed[(4 + s) * N + m], pr);
+        pr = fma(pc.y, Ed[(6 + s) * N + m], pr);
+        const T own = s ? fx1 : fx0, opp = s ? fx0 : fx1;
+        T out = fma(__ldg(cb + co.fdiag + s * N2 + q), own, s ? sx1 : sx0);
+        out = fma(cO[s], opp, out);
+        out = fma(w0, pr, out);
+        int off = H[s];
+        if (off >= 0) {
+          atomicAdd(v + off + q, out);
+          dot = fma(own, out, dot);
+        }
+        // y-face side s at (k, i = m)
+        pr = pa.x * Ed[(8 + 2 * s) * N + k];
+        pr = fma(pa.y, Ed[(9 + 2 * s) * N + k], pr);
+        pr = fma(pc.x, Ed[s * N + m], pr);
+        pr = fma(pc.y, Ed[(2 + s) * N + m], pr);
+        const T owny = s ? fy1 : fy0, oppy = s ? fy0 : fy1;
+        out = fma(__ldg(cb + co.fdiag + (2 + s) * N2 + q), owny, s ? sy1 : sy0);
+        out = fma(cO[2 + s], oppy, out);
+        out = fma(w0, pr, out);
+        off = H[2 + s];
+        if (off >= 0) {
+          atomicAdd(v + off + q, out);
+          dot = fma(owny, out, dot);
+        }
       }
     }
   }
@@ -708,6 +720,159 @@ k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Thread-per-element variant for p = 2 (n = 1)
+// ---------------------------------------------------------------------------
+// With one interior node per element every entity carries one value: a
+// thread holds its element's 26 boundary values, the class coefficients and
+// the 26 outputs in registers (the formulas are those of the CTA-tile kernel
+// with n = 1).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_tpt_apply_p2(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
+               double* __restrict__ partials, PcgState* st) {
+  if (st != nullptr && st->done) return;
+  const CoefOffsets co = coef_offsets(1);
+  T dot = T(0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.nelem;
+       e += (long long)gridDim.x * blockDim.x) {
+    int ex, ey, ez;
+    elem_of(g, e, &ex, &ey, &ez);
+    int off[26];
+    T F[6], Ed[12], Vt[8];
+#pragma unroll
+    for (int r = 0; r < 26; ++r) {
+      bool dir;
+      long long o;
+      if (r < 6) o = face_base(g, ex, ey, ez, r, &dir);
+      else if (r < 18) o = edge_base(g, ex, ey, ez, r - 6, &dir);
+      else o = vert_index(g, ex, ey, ez, r - 18, &dir);
+      off[r] = dir ? -1 : (int)o;
+    }
+#pragma unroll
+    for (int r = 0; r < 6; ++r) F[r] = off[r] >= 0 ? u[off[r]] : T(0);
+#pragma unroll
+    for (int r = 0; r < 12; ++r) Ed[r] = off[6 + r] >= 0 ? u[off[6 + r]] : T(0);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) Vt[r] = off[18 + r] >= 0 ? u[off[18 + r]] : T(0);
+    const T* cb = tab.coef + (long long)elem_class(g, tab, ex, ey, ez) * co.stride;
+    T skd[6], skw[6], skww[6], cO[6], eO[6], vO[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      skd[k] = __ldg(cb + k);
+      skw[k] = __ldg(cb + 6 + k);
+      skww[k] = __ldg(cb + 12 + k);
+      cO[k] = __ldg(cb + 18 + k);
+      eO[k] = __ldg(cb + 24 + k);
+      vO[k] = __ldg(cb + 30 + k);
+    }
+    // condensed part: one eigenspace value
+    T x = skd[0] * F[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k) x = fma(skd[k], F[k], x);
+    const T vv = __ldg(cb + co.ndinv) * x;
+    T Fo[6], Eo[12], Vo[8];
+    // faces: primary part + condensed contraction
+#pragma unroll
+    for (int slot = 0; slot < 6; ++slot) {
+      const int dd = slot >> 1, s = slot & 1;
+      T out = fma(__ldg(cb + co.fdiag + slot), F[slot], skd[slot] * vv);
+      out = fma(cO[slot], F[slot ^ 1], out);
+      if (dd == 0) {
+        out = fma(skw[2], Ed[8 + s], out);
+        out = fma(skw[3], Ed[10 + s], out);
+        out = fma(skw[4], Ed[4 + s], out);
+        out = fma(skw[5], Ed[6 + s], out);
+      } else if (dd == 1) {
+        out = fma(skw[0], Ed[8 + 2 * s], out);
+        out = fma(skw[1], Ed[9 + 2 * s], out);
+        out = fma(skw[4], Ed[s], out);
+        out = fma(skw[5], Ed[2 + s], out);
+      } else {
+        out = fma(skw[0], Ed[4 + 2 * s], out);
+        out = fma(skw[1], Ed[5 + 2 * s], out);
+        out = fma(skw[2], Ed[2 * s], out);
+        out = fma(skw[3], Ed[1 + 2 * s], out);
+      }
+      Fo[slot] = out;
+    }
+    // edges
+#pragma unroll
+    for (int slot = 0; slot < 12; ++slot) {
+      const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+      T out = __ldg(cb + co.ediag + slot) * Ed[slot];
+      if (grp == 0) {
+        out = fma(skww[0], Vt[2 * s1 + 4 * s2], out);
+        out = fma(skww[1], Vt[1 + 2 * s1 + 4 * s2], out);
+        out = fma(skw[2 + s1], F[4 + s2], out);
+        out = fma(skw[4 + s2], F[2 + s1], out);
+        out = fma(eO[2 + s1], Ed[(1 - s1) + 2 * s2], out);
+        out = fma(eO[4 + s2], Ed[s1 + 2 * (1 - s2)], out);
+      } else if (grp == 1) {
+        out = fma(skww[2], Vt[s1 + 4 * s2], out);
+        out = fma(skww[3], Vt[s1 + 2 + 4 * s2], out);
+        out = fma(skw[s1], F[4 + s2], out);
+        out = fma(skw[4 + s2], F[s1], out);
+        out = fma(eO[s1], Ed[4 + (1 - s1) + 2 * s2], out);
+        out = fma(eO[4 + s2], Ed[4 + s1 + 2 * (1 - s2)], out);
+      } else {
+        out = fma(skww[4], Vt[s1 + 2 * s2], out);
+        out = fma(skww[5], Vt[s1 + 2 * s2 + 4], out);
+        out = fma(skw[s1], F[2 + s2], out);
+        out = fma(skw[2 + s2], F[s1], out);
+        out = fma(eO[s1], Ed[8 + (1 - s1) + 2 * s2], out);
+        out = fma(eO[2 + s2], Ed[8 + s1 + 2 * (1 - s2)], out);
+      }
+      Eo[slot] = out;
+    }
+    // vertices
+#pragma unroll
+    for (int slot = 0; slot < 8; ++slot) {
+      const int sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
+      T out = __ldg(cb + co.vdiag + slot) * Vt[slot];
+      out = fma(skww[sa], Ed[sb + 2 * sc], out);
+      out = fma(skww[2 + sb], Ed[4 + sa + 2 * sc], out);
+      out = fma(skww[4 + sc], Ed[8 + sa + 2 * sb], out);
+      out = fma(vO[sa], Vt[slot ^ 1], out);
+      out = fma(vO[2 + sb], Vt[slot ^ 2], out);
+      out = fma(vO[4 + sc], Vt[slot ^ 4], out);
+      Vo[slot] = out;
+    }
+    // scatter R and the element share of x^T (A x)
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+      if (off[r] >= 0) { atomicAdd(v + off[r], Fo[r]); dot = fma(F[r], Fo[r], dot); }
+#pragma unroll
+    for (int r = 0; r < 12; ++r)
+      if (off[6 + r] >= 0) { atomicAdd(v + off[6 + r], Eo[r]); dot = fma(Ed[r], Eo[r], dot); }
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      if (off[18 + r] >= 0) { atomicAdd(v + off[18 + r], Vo[r]); dot = fma(Vt[r], Vo[r], dot); }
+  }
+  if (st != nullptr) {
+    double vals[1] = {(double)dot}, tot[1];
+    if (reduce_grid<1>(vals, partials, &st->counter[0], tot) && threadIdx.x == 0) {
+      const double pq = tot[0];
+      st->pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) st->done = 2;
+      else st->alpha = st->rho / pq;
+    }
+  }
+}
+
+template <typename T>
+void launch_p2(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, double* partials, PcgState* st,
+               cudaStream_t s) {
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_p2<T>, kThreads, 0);
+  if (occ < 1) occ = 1;
+  long long grid = (long long)num_sms_cached() * occ;
+  const long long need = (g.nelem + kThreads - 1) / kThreads;
+  if (grid > need) grid = need;
+  k_tpt_apply_p2<T><<<(int)grid, kThreads, 0, s>>>(g, t, x, y, partials, st);
+  sem_count_launch();
+}
+
 template <typename T, int N>
 size_t warp_smem(int wpb) {
   return ((size_t)wpb * kWarpHdr * 4 + 31) / 32 * 32 + (size_t)wpb * WarpSm<N>::size * sizeof(T);
@@ -715,7 +880,7 @@ size_t warp_smem(int wpb) {
 
 template <typename T, int N>
 void launch_warp(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, double* partials, PcgState* st,
-                 cudaStream_t s) {
+                 double w0, cudaStream_t s) {
   const int wpb = kThreads / 32;
   const size_t smem = warp_smem<T, N>(wpb);
   static bool attr = false;
@@ -729,7 +894,7 @@ void launch_warp(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y,
   long long grid = (long long)num_sms_cached() * occ;
   const long long need = (g.nelem + wpb - 1) / wpb;
   if (grid > need) grid = need;
-  k_tpt_apply_warp<T, N><<<(int)grid, kThreads, smem, s>>>(g, t, x, y, partials, st);
+  k_tpt_apply_warp<T, N><<<(int)grid, kThreads, smem, s>>>(g, t, x, y, partials, st, (T)w0);
   sem_count_launch();
 }
 
@@ -790,7 +955,6 @@ ApplyConfig sem_apply_config_make(int n, size_t elem_bytes, int epb, int ks) {
 template <typename T>
 void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
                       double* partials, PcgState* st, cudaStream_t s, const ApplyConfig* tuned) {
-  (void)b;
   const ApplyConfig c = (tuned != nullptr && sem_apply_config_valid(g.n, sizeof(T), *tuned))
                             ? *tuned : sem_apply_config(g.n, sizeof(T));
   if (tuned != nullptr && sem_apply_config_valid(g.n, sizeof(T), *tuned)) {
@@ -810,16 +974,19 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
   if constexpr (sizeof(T) == 4) {
     if (g.n >= 3 && g.n <= 7) {
       switch (g.n) {
-        case 3: launch_warp<T, 3>(g, t, x, y, partials, st, s); return;
-        case 4: launch_warp<T, 4>(g, t, x, y, partials, st, s); return;
-        case 5: launch_warp<T, 5>(g, t, x, y, partials, st, s); return;
-        case 6: launch_warp<T, 6>(g, t, x, y, partials, st, s); return;
-        default: launch_warp<T, 7>(g, t, x, y, partials, st, s); return;
+        case 3: launch_warp<T, 3>(g, t, x, y, partials, st, b.w0, s); return;
+        case 4: launch_warp<T, 4>(g, t, x, y, partials, st, b.w0, s); return;
+        case 5: launch_warp<T, 5>(g, t, x, y, partials, st, b.w0, s); return;
+        case 6: launch_warp<T, 6>(g, t, x, y, partials, st, b.w0, s); return;
+        default: launch_warp<T, 7>(g, t, x, y, partials, st, b.w0, s); return;
       }
     }
   }
+  if (g.n == 1) {
+    launch_p2<T>(g, t, x, y, partials, st, s);
+    return;
+  }
   switch (g.n) {
-    case 1: launch_nc<T, 1>(g, t, x, y, partials, st, c, s); break;
     case 3: launch_nc<T, 3>(g, t, x, y, partials, st, c, s); break;
     case 7: launch_nc<T, 7>(g, t, x, y, partials, st, c, s); break;
     case 15: launch_nc<T, 15>(g, t, x, y, partials, st, c, s); break;

@@ -68,6 +68,7 @@ def lib():
         "sem_get_basis": (ctypes.c_int, [_P, _D, _D, _D, _D]),
         "sem_apply_condensed": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
         "sem_condense_rhs": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+        "sem_apply_condensed_f32": (ctypes.c_int, [_P, _P, _P, _P]),
         "sem_condense_rhs_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
         "sem_precond_diag": (ctypes.c_int, [_P, _P, _P]),
         "sem_recover_interior": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
@@ -106,7 +107,7 @@ def exported_symbols():
     """Names of the entry points the binding expects the library to export."""
     return ["sem_default_opts", "sem_setup", "sem_set_lambda", "sem_set_opts", "sem_skeleton_size",
             "sem_grid_size", "sem_node_coords", "sem_get_basis", "sem_apply_condensed", "sem_condense_rhs",
-            "sem_condense_rhs_noalloc",
+            "sem_condense_rhs_noalloc", "sem_apply_condensed_f32",
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
             "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_batch_create", "sem_batch_solve",
@@ -215,6 +216,21 @@ def sem_get_basis(ctx: SemContext):
 def sem_apply_condensed(ctx: SemContext, uB, vB, space=SPACE_TRANSFORMED, stream=None):
     _check(lib().sem_apply_condensed(ctx.handle, _dptr(uB, ctx.nb, "uB"), _dptr(vB, ctx.nb, "vB"), int(space),
                                      _stream(stream, uB)))
+
+
+def _fptr(t, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA float32 tensor")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sem_apply_condensed_f32(ctx: SemContext, uB, vB, stream=None):
+    """FP32 transformed-space operator (float32 tensors of length N_B)."""
+    _check(lib().sem_apply_condensed_f32(ctx.handle, _fptr(uB, ctx.nb, "uB"), _fptr(vB, ctx.nb, "vB"),
+                                         _stream(stream, uB)))
 
 
 def sem_condense_rhs(ctx: SemContext, f, fB, space=SPACE_TRANSFORMED, stream=None):

@@ -20,7 +20,7 @@ def L():
 def _declared():
     src = open(os.path.join(ROOT, "include", "sem.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sem_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sem_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_expected_entry_points():

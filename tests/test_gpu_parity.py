@@ -262,3 +262,23 @@ def test_solve_full_size_residual():
     r = (local.apply_full(ms, w.lam, got) - F)[ms.free_mask]
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(F[ms.free_mask])
     assert info["rel_res"] <= 1e-10
+
+
+@pytest.mark.parametrize("p,m,lam,ar", [(2, (3, 2, 4), 0.5, 3.0), (3, (2, 3, 2), 2.5, 2.0), (4, (3, 2, 3), 1.0, 4.0),
+                                        (6, (2, 3, 2), 0.0, 2.0), (7, (2, 2, 2), 3.0, 1.0), (8, (3, 2, 2), 1.0, 2.0),
+                                        (12, (2, 2, 1), 1.0, 1.0), (16, (2, 1, 1), 2.0, 1.0)])
+def test_apply_f32_vs_oracle(p, m, lam, ar):
+    """The FP32 operator of the mixed-precision solver against the FP64
+    oracle: FP32 rounding only (relative error well below 1e-5)."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, lam, ar)
+    ut = si.random_vector(ms.n_skeleton, 91)
+    free = ms.skeleton_free
+    v = torch.empty(ctx.nb, dtype=torch.float32, device="cuda")
+    sem.sem_apply_condensed_f32(ctx, torch.tensor(ut, dtype=torch.float32, device="cuda"), v)
+    u_nodal = transform.solution_from_transformed(ms, np.where(free, ut.astype(np.float32).astype(np.float64), 0.0))
+    ref = transform.load_to_transformed(ms, np.where(free, local.apply_condensed(ms, lam, u_nodal), 0.0))
+    got = host(v)
+    assert np.all(got[~free] == 0.0)
+    assert relerr(got, ref) <= 1e-5
