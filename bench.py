@@ -173,6 +173,20 @@ def node_field(x, y, z, w: si.Workload, seed: int):
     return np.ascontiguousarray(f.ravel())
 
 
+def kernel_name(sem, ctx, precision: int, p: int) -> str:
+    """Name of the operator kernel in use for one precision."""
+    kind, epb, ks = sem.sem_get_operator_kernel(ctx, precision)
+    n = p - 1
+    t = "float" if precision == sem.PREC_MIXED else "double"
+    if kind == sem.KERNEL_PLANE:
+        return f"k_tpt_apply_plane<{n}>"
+    if kind == sem.KERNEL_WARP:
+        return f"k_tpt_apply_warp<{t}, {n}>"
+    if kind == sem.KERNEL_ELEMENT:
+        return f"k_tpt_apply_p2<{t}>"
+    return f"k_tpt_apply<{t}, {n if n in (1, 3, 7, 15, 31) else 0}> (epb {epb}, ks {ks})"
+
+
 def apply_flops(w: si.Workload) -> float:
     """Algorithmic FP64 flops of one condensed-operator application: the
     multiplication counts of Table 3 (TPT: 13 n^3 + 68 n^2 per element), each
@@ -305,7 +319,7 @@ def our_arm(args, rank, world, local_rank):
     nb = ctx.nb
     if head == "fp64":
         achieved = flops / r["apply_s"] / 1e12
-        roof = {"kernel": "k_tpt_apply<double>", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+        roof = {"kernel": kernel_name(sem, ctx, sem.PREC_FP64, w.p), "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "FP64 FMA units x SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "flops_per_launch": flops}
@@ -316,13 +330,13 @@ def our_arm(args, rank, world, local_rank):
         t_hbm = 8.0 * nb / (HBM_GBS * 1e9)
         if t_alu >= t_hbm:
             achieved = flops / r["apply_s"] / 1e12
-            roof = {"kernel": "k_tpt_apply<float>", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+            roof = {"kernel": kernel_name(sem, ctx, sem.PREC_MIXED, w.p), "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                     "peak_source": "FP32 FMA units x SM clock (152 SMs x 128 FMA/clk x 2.07 GHz)",
                     "flops_per_launch": flops}
         else:
             achieved = 8.0 * nb / r["apply_s"] / 1e9
-            roof = {"kernel": "k_tpt_apply<float>", "bound": "hbm", "achieved": achieved, "peak": HBM_GBS,
+            roof = {"kernel": kernel_name(sem, ctx, sem.PREC_MIXED, w.p), "bound": "hbm", "achieved": achieved, "peak": HBM_GBS,
                     "unit": "GB/s", "frac": achieved / HBM_GBS, "traffic": None,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)", "bytes_per_launch": 8.0 * nb}
     out = {

@@ -263,13 +263,47 @@ sem_status sem_solve_adjoint(sem_ctx* ctx, const double* g, double* w, sem_info*
 sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const double* f, double* df,
                          double* dlambda, double* dhx, double* dhy, double* dhz, void* stream);
 
-/* Autotuner: times the operator kernel over a set of CTA-tile shapes
- * (elements per CTA, eigenspace slab depth) for this context's degree, mesh
- * and precision (FP32 when opts.precision is MIXED, else FP64), keeps the
- * fastest (the built-in choice included) for all later applications and
- * solves, and caches the choice per (p, mx, my, mz, precision) for the
- * process.  *ms_default / *ms_best (may be NULL): milliseconds per application
- * of the built-in and the chosen configuration.  Synchronous. */
+/* Operator kernel variants.  All compute the same transformed condensed
+ * operator (Sec. 6, Table 2); they differ only in how the elements' work is
+ * mapped onto the GPU.  The paper has no counterpart: this is a performance
+ * choice of this library.
+ *   SEM_KERNEL_AUTO      the built-in choice for the degree and precision
+ *   SEM_KERNEL_CTA_TILE  a CTA works on a tile of epb elements, the n^3
+ *                        eigenspace cube in slabs of ks planes (any degree)
+ *   SEM_KERNEL_WARP      one warp per element (FP32, 3 <= n <= 7)
+ *   SEM_KERNEL_PLANE     a group of 4 or 8 lanes per element, one lane per
+ *                        plane of the cube (FP32, 2 <= n <= 8)
+ *   SEM_KERNEL_ELEMENT   one thread per element (p = 2)
+ * where n = p - 1. */
+enum {
+  SEM_KERNEL_AUTO = 0,
+  SEM_KERNEL_CTA_TILE = 1,
+  SEM_KERNEL_WARP = 2,
+  SEM_KERNEL_PLANE = 3,
+  SEM_KERNEL_ELEMENT = 4
+};
+
+/* Selects the operator kernel of one precision: SEM_PREC_FP64 (the FP64
+ * operator of FP64 solves, of the refinement residuals and of
+ * sem_apply_condensed) or SEM_PREC_MIXED (the FP32 operator of the inner CG
+ * and of sem_apply_condensed_f32).  epb (1..64) and ks (1..n) are used by
+ * SEM_KERNEL_CTA_TILE only.  Applies to every later call on this context;
+ * batches created earlier keep the kernel they captured.  Returns SEM_EINVAL
+ * if the variant does not exist for this degree and precision, or the tile
+ * does not fit in shared memory. */
+sem_status sem_set_operator_kernel(sem_ctx* ctx, int precision, int kind, int epb, int ks);
+/* The kernel in use for one precision, SEM_KERNEL_AUTO resolved: *kind, and
+ * for a CTA tile *epb, *ks (else 0; epb, ks may be NULL). */
+sem_status sem_get_operator_kernel(const sem_ctx* ctx, int precision, int* kind, int* epb, int* ks);
+
+/* Autotuner: times the operator kernel for this context's degree, mesh and
+ * precision (FP32 when opts.precision is MIXED, else FP64) over the variants
+ * that exist for it and a set of CTA-tile shapes (elements per CTA,
+ * eigenspace slab depth), keeps the fastest (the built-in choice included)
+ * for all later applications and solves, and caches the choice per
+ * (p, mx, my, mz, precision) for the process.  *ms_default / *ms_best (may be
+ * NULL): milliseconds per application of the built-in and the chosen
+ * configuration.  Synchronous. */
 sem_status sem_autotune(sem_ctx* ctx, double* ms_default, double* ms_best);
 
 /* Batched solves (independent problems of any degree and mesh size).

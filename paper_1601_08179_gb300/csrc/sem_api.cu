@@ -68,6 +68,7 @@ struct sem_ctx {
   double* d_dinv = nullptr;
   double* d_coef = nullptr;            // per-class operator coefficient blocks (FP64)
   float* d_coef_f = nullptr;           // the same in FP32 (mixed precision)
+  float* d_plane = nullptr;            // class blocks of the plane-per-lane FP32 kernel
   double* d_mats = nullptr;            // 4 n*n: S_II, V, V^T M_II, M_II V
   double* d_mass = nullptr;            // [Nx + Ny + Nz] assembled 1D lumped masses
   double* d_h = nullptr;               // [mx + my + mz] element widths
@@ -103,8 +104,7 @@ struct sem_ctx {
   bool graph32_prof = false;
   std::vector<cudaEvent_t> pev32;
   std::vector<double> refine_hist;     // ||b - A x_k|| / ||b|| after each refinement step
-  bool tuned64_set = false, tuned32_set = false;
-  ApplyConfig tuned64{}, tuned32{};     // autotuned CTA-tile operator configurations
+  ApplyConfig op64{}, op32{};           // operator kernel per precision (kind kApplyAuto: built-in)
 
   const double* mat(int k) const { return d_mats + (size_t)k * g.n * g.n; }
 };
@@ -176,6 +176,7 @@ sem_status cast_tables_f32(sem_ctx* c, cudaStream_t s) {
   launch_cast_f32(ncls * 4, c->d_dcoef, c->d_dcoef_f, s);
   launch_cast_f32(ncls * (long long)g.n * g.n * g.n, c->d_dinv, c->d_dinv_f, s);
   launch_class_coeffs<float>(g, c->h1.basis, c->d_dcoef, c->d_dinv, c->d_coef_f, s);
+  if (c->d_plane != nullptr) launch_plane_coeffs(g, c->h1.basis, c->d_dcoef, c->d_plane, s);
   launch_cast_f32(g.nb, c->d_P, c->d_P32, s);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
@@ -191,7 +192,8 @@ sem_status ensure_mixed(sem_ctx* c) {
             dalloc(&c->d_x32, g.nb) == cudaSuccess && dalloc(&c->d_r32, g.nb) == cudaSuccess &&
             dalloc(&c->d_p32, g.nb) == cudaSuccess && dalloc(&c->d_q32, g.nb) == cudaSuccess &&
             dalloc(&c->d_st32, 1) == cudaSuccess &&
-            dalloc(&c->d_coef_f, ncls * coef_offsets(g.n).stride) == cudaSuccess;
+            dalloc(&c->d_coef_f, ncls * coef_offsets(g.n).stride) == cudaSuccess &&
+            (!plane_supported(g.n) || dalloc(&c->d_plane, ncls * plane_layout(g.n).stride) == cudaSuccess);
   if (!ok) return fail(SEM_ENOMEM, "cannot allocate mixed-precision buffers");
   SEM_CUDA(cudaMemsetAsync(c->d_st32, 0, sizeof(PcgState), c->stream));
   c->tab_f.cls_x = c->tab.cls_x;
@@ -201,6 +203,8 @@ sem_status ensure_mixed(sem_ctx* c) {
   c->tab_f.dinv = c->d_dinv_f;
   c->tab_f.coef = c->d_coef_f;
   c->tab_f.coef_stride = coef_offsets(g.n).stride;
+  c->tab_f.plane = c->d_plane;
+  c->tab_f.plane_stride = plane_supported(g.n) ? plane_layout(g.n).stride : 0;
   sem_status st = cast_tables_f32(c, c->stream);
   if (st != SEM_OK) return st;
   // operator kernel attributes outside any capture
@@ -252,7 +256,7 @@ sem_status recover_t(sem_ctx* c, const double* ut, double* u, cudaStream_t s) {
 sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
   SEM_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * c->g.nb, s));
   launch_tpt_apply<double>(c->g, c->h1.basis, c->tab, x, y, nullptr, nullptr, s,
-                           c->tuned64_set ? &c->tuned64 : nullptr);
+                           &c->op64);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -278,7 +282,7 @@ sem_status build_graph(sem_ctx* c) {
     // external event-record nodes: recorded at every replay, usable for timing
     if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it], c->stream, cudaEventRecordExternal);
     launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, c->stream,
-                             c->tuned64_set ? &c->tuned64 : nullptr);
+                             &c->op64);
     if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it + 1], c->stream, cudaEventRecordExternal);
     launch_pcg_update(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, c->stream);
     launch_pcg_dir(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, c->stream);
@@ -356,7 +360,7 @@ sem_status build_graph32(sem_ctx* c) {
   for (int it = 0; it < c->opts.check_every; ++it) {
     if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it], c->stream, cudaEventRecordExternal);
     launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, c->stream,
-                            c->tuned32_set ? &c->tuned32 : nullptr);
+                            &c->op32);
     if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it + 1], c->stream, cudaEventRecordExternal);
     launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32,
                              c->stream);
@@ -571,7 +575,7 @@ void free_ctx(sem_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->graph32) cudaGraphExecDestroy(c->graph32);
   void* ptrs32[] = {c->d_dcoef_f, c->d_dinv_f, c->d_P32, c->d_b32, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_st32,
-                    c->d_coef_f, c->d_coef};
+                    c->d_coef_f, c->d_coef, c->d_plane};
   for (void* p : ptrs32)
     if (p) cudaFree(p);
   for (cudaEvent_t ev : c->pev32) cudaEventDestroy(ev);
@@ -845,7 +849,7 @@ sem_status sem_apply_condensed_f32(sem_ctx* c, const float* uB, float* vB, void*
   SEM_CUDA(cudaStreamSynchronize(c->stream));   // FP32 tables are prepared on the context stream
   SEM_CUDA(cudaMemsetAsync(vB, 0, sizeof(float) * c->g.nb, s));
   launch_tpt_apply<float>(c->g, c->h1.basis, c->tab_f, uB, vB, nullptr, nullptr, s,
-                          c->tuned32_set ? &c->tuned32 : nullptr);
+                          &c->op32);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -1213,6 +1217,26 @@ sem_status tune_one(sem_ctx* c, const SemClassTables<T>& tab, const T* x, T* y, 
   sem_status st = time_apply<T>(c, tab, x, y, nullptr, &ms_def);
   if (st != SEM_OK) return st;
   TuneResult r{true, ApplyConfig{}, ms_def, ms_def};
+  auto consider = [&](const ApplyConfig& cfg) -> sem_status {
+    if (!sem_apply_config_valid(n, sizeof(T), cfg)) return SEM_OK;
+    double ms = 0.0;
+    const sem_status s2 = time_apply<T>(c, tab, x, y, &cfg, &ms);
+    if (s2 != SEM_OK) return s2;
+    if (ms < r.ms_best) {
+      r.ms_best = ms;
+      r.use_default = false;
+      r.cfg = cfg;
+    }
+    return SEM_OK;
+  };
+  // the other work mappings that exist for this degree and precision
+  const int def = sem_apply_default_kind(n, sizeof(T));
+  for (int kind : {kApplyWarp, kApplyPlane, kApplyElement}) {
+    if (kind == def) continue;
+    st = consider(sem_apply_config_kind(kind));
+    if (st != SEM_OK) return st;
+  }
+  // CTA-tile shapes
   const int epbs[] = {1, 2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 48, 64};
   const int kss[] = {n, (n + 1) / 2, (n + 3) / 4, 8, 4, 2};
   int tried = 0;
@@ -1222,22 +1246,22 @@ sem_status tune_one(sem_ctx* c, const SemClassTables<T>& tab, const T* x, T* y, 
     for (int ks : kss) {
       if (ks < 1 || ks > n || ks == last_ks) continue;
       last_ks = ks;
-      const ApplyConfig cfg = sem_apply_config_make(n, sizeof(T), epb, ks);
-      if (!sem_apply_config_valid(n, sizeof(T), cfg)) continue;
-      double ms = 0.0;
-      st = time_apply<T>(c, tab, x, y, &cfg, &ms);
+      st = consider(sem_apply_config_make(n, sizeof(T), epb, ks));
       if (st != SEM_OK) return st;
-      ++tried;
-      if (ms < r.ms_best) {
-        r.ms_best = ms;
-        r.use_default = false;
-        r.cfg = cfg;
-      }
-      if (tried >= 40) break;
+      if (++tried >= 40) break;
     }
   }
   *out = r;
   return SEM_OK;
+}
+
+// Drops the instantiated CG graph of one precision (it holds the operator launch).
+void drop_graph(sem_ctx* c, bool mixed) {
+  cudaGraphExec_t& gr = mixed ? c->graph32 : c->graph;
+  if (gr) {
+    cudaGraphExecDestroy(gr);
+    gr = nullptr;
+  }
 }
 
 }  // namespace
@@ -1272,17 +1296,46 @@ extern "C" sem_status sem_autotune(sem_ctx* c, double* ms_default, double* ms_be
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = r;
   }
-  if (mixed) {
-    c->tuned32_set = !r.use_default;
-    c->tuned32 = r.cfg;
-    if (c->graph32) { cudaGraphExecDestroy(c->graph32); c->graph32 = nullptr; }
-  } else {
-    c->tuned64_set = !r.use_default;
-    c->tuned64 = r.cfg;
-    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-  }
+  (mixed ? c->op32 : c->op64) = r.use_default ? ApplyConfig{} : r.cfg;
+  drop_graph(c, mixed);
   if (ms_default) *ms_default = r.ms_default;
   if (ms_best) *ms_best = r.ms_best;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_set_operator_kernel(sem_ctx* c, int precision, int kind, int epb, int ks) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_MIXED)
+    return fail(SEM_EINVAL, "precision must be SEM_PREC_FP64 or SEM_PREC_MIXED");
+  const bool mixed = precision == SEM_PREC_MIXED;
+  const size_t bytes = mixed ? 4 : 8;
+  ApplyConfig cfg = kind == SEM_KERNEL_CTA_TILE ? sem_apply_config_make(c->g.n, bytes, epb, ks)
+                                                : sem_apply_config_kind(kind);
+  if (!sem_apply_config_valid(c->g.n, bytes, cfg))
+    return fail(SEM_EINVAL, "operator kernel variant not available for this degree and precision");
+  if (mixed) {
+    const sem_status st = ensure_mixed(c);
+    if (st != SEM_OK) return st;
+  }
+  (mixed ? c->op32 : c->op64) = cfg;
+  drop_graph(c, mixed);
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_get_operator_kernel(const sem_ctx* c, int precision, int* kind, int* epb, int* ks) {
+  t_err.clear();
+  if (c == nullptr || kind == nullptr) return fail(SEM_EINVAL, "null argument");
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_MIXED)
+    return fail(SEM_EINVAL, "precision must be SEM_PREC_FP64 or SEM_PREC_MIXED");
+  const bool mixed = precision == SEM_PREC_MIXED;
+  const size_t bytes = mixed ? 4 : 8;
+  const ApplyConfig& op = mixed ? c->op32 : c->op64;
+  ApplyConfig eff = op.kind == kApplyAuto ? sem_apply_config_kind(sem_apply_default_kind(c->g.n, bytes)) : op;
+  if (eff.kind == kApplyCta && op.kind == kApplyAuto) eff = sem_apply_config(c->g.n, bytes);
+  *kind = eff.kind;
+  if (epb) *epb = eff.kind == kApplyCta ? eff.epb : 0;
+  if (ks) *ks = eff.kind == kApplyCta ? eff.ks : 0;
   return SEM_OK;
 }
 
@@ -1452,7 +1505,7 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
         const SemGeom& g = c->g;
         for (int it = 0; it < check; ++it) {
           launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, si,
-                                   c->tuned64_set ? &c->tuned64 : nullptr);
+                                   &c->op64);
           launch_pcg_update<double>(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, si);
           launch_pcg_dir<double>(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, si);
         }

@@ -57,24 +57,6 @@ __host__ __device__ inline ElemSm elem_sm(int n, int ks) {
 
 __host__ __device__ inline size_t hdr_bytes(int epb) { return ((size_t)epb * kHdrInts * 4 + 31) & ~size_t(31); }
 
-// Element visiting order: the axis with the most width classes is slowest, so
-// consecutive elements of a CTA share their class tables.
-__device__ __forceinline__ void elem_of(const SemGeom& g, long long e, int* ex, int* ey, int* ez) {
-  if (g.slow == 0) {
-    const long long r = e % ((long long)g.my * g.mz);
-    *ex = (int)(e / ((long long)g.my * g.mz));
-    *ey = (int)(r % g.my);
-    *ez = (int)(r / g.my);
-  } else if (g.slow == 1) {
-    const long long r = e % ((long long)g.mx * g.mz);
-    *ey = (int)(e / ((long long)g.mx * g.mz));
-    *ex = (int)(r % g.mx);
-    *ez = (int)(r / g.mx);
-  } else {
-    elem_coords(g, e, ex, ey, ez);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Per-class coefficient blocks
 // ---------------------------------------------------------------------------
@@ -161,7 +143,7 @@ k_tpt_apply(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __rest
         continue;
       }
       int ex, ey, ez;
-      elem_of(g, e, &ex, &ey, &ez);
+      elem_visit(g, e, &ex, &ey, &ez);
       bool dir;
       long long off;
       if (r < 6) off = face_base(g, ex, ey, ez, r, &dir);
@@ -442,16 +424,7 @@ k_tpt_apply(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __rest
   }
 }
 
-int num_sms_cached() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  return sms;
-}
+int num_sms_cached() { return sem_num_sms(); }
 
 // ---------------------------------------------------------------------------
 // Warp-per-element variant for small degrees (n <= 7)
@@ -737,7 +710,7 @@ k_tpt_apply_p2(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __r
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.nelem;
        e += (long long)gridDim.x * blockDim.x) {
     int ex, ey, ez;
-    elem_of(g, e, &ex, &ey, &ez);
+    elem_visit(g, e, &ex, &ey, &ez);
     int off[26];
     T F[6], Ed[12], Vt[8];
 #pragma unroll
@@ -920,6 +893,7 @@ void launch_nc(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, d
 
 ApplyConfig sem_apply_config(int n, size_t elem_bytes) {
   ApplyConfig c;
+  c.kind = kApplyCta;
   c.threads = kThreads;
   const size_t big = 200 * 1024, small = 96 * 1024;
   int ks = n;
@@ -937,42 +911,63 @@ ApplyConfig sem_apply_config(int n, size_t elem_bytes) {
   return c;
 }
 
-bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
-  if (c.epb < 1 || c.epb > 64 || c.ks < 1 || c.ks > n || c.threads != kThreads) return false;
-  const size_t need = hdr_bytes(c.epb) + (size_t)c.epb * elem_sm(n, c.ks).size * elem_bytes;
-  return need == c.smem && need <= 200 * 1024;
-}
-
 ApplyConfig sem_apply_config_make(int n, size_t elem_bytes, int epb, int ks) {
   ApplyConfig c;
+  c.kind = kApplyCta;
   c.threads = kThreads;
   c.epb = epb;
   c.ks = ks;
-  c.smem = hdr_bytes(epb) + (size_t)epb * elem_sm(n, ks).size * elem_bytes;
+  c.smem = (epb >= 1 && ks >= 1) ? hdr_bytes(epb) + (size_t)epb * elem_sm(n, ks).size * elem_bytes : 0;
   return c;
+}
+
+ApplyConfig sem_apply_config_kind(int kind) {
+  ApplyConfig c;
+  c.kind = kind;
+  return c;
+}
+
+bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
+  switch (c.kind) {
+    case kApplyAuto:
+      return true;
+    case kApplyCta: {
+      if (c.epb < 1 || c.epb > 64 || c.ks < 1 || c.ks > n || c.threads != kThreads) return false;
+      const size_t need = hdr_bytes(c.epb) + (size_t)c.epb * elem_sm(n, c.ks).size * elem_bytes;
+      return need == c.smem && need <= 200 * 1024;
+    }
+    case kApplyWarp:
+      return elem_bytes == 4 && n >= 3 && n <= 7;
+    case kApplyPlane:
+      return elem_bytes == 4 && plane_supported(n);
+    case kApplyElement:
+      return n == 1;
+    default:
+      return false;
+  }
+}
+
+// Measured on GB300: FP64 is bound by the FP64 pipe and runs best with the
+// CTA tile; FP32 at 2 <= n <= 8 with the plane-per-lane kernel; n = 1 with one
+// thread per element.
+int sem_apply_default_kind(int n, size_t elem_bytes) {
+  if (n == 1) return kApplyElement;
+  if (elem_bytes == 4 && plane_supported(n)) return kApplyPlane;
+  return kApplyCta;
 }
 
 template <typename T>
 void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
-                      double* partials, PcgState* st, cudaStream_t s, const ApplyConfig* tuned) {
-  const ApplyConfig c = (tuned != nullptr && sem_apply_config_valid(g.n, sizeof(T), *tuned))
-                            ? *tuned : sem_apply_config(g.n, sizeof(T));
-  if (tuned != nullptr && sem_apply_config_valid(g.n, sizeof(T), *tuned)) {
-    // an explicit CTA-tile configuration selects the CTA-tile kernel for every degree
-    switch (g.n) {
-      case 1: launch_nc<T, 1>(g, t, x, y, partials, st, c, s); return;
-      case 3: launch_nc<T, 3>(g, t, x, y, partials, st, c, s); return;
-      case 7: launch_nc<T, 7>(g, t, x, y, partials, st, c, s); return;
-      case 15: launch_nc<T, 15>(g, t, x, y, partials, st, c, s); return;
-      case 31: launch_nc<T, 31>(g, t, x, y, partials, st, c, s); return;
-      default: launch_nc<T, 0>(g, t, x, y, partials, st, c, s); return;
-    }
-  }
-  // Measured on GB300: the warp-per-element variant wins for FP32 at
-  // 3 <= n <= 7; FP64 (bound by the FP64 pipe) and n = 1, 2 run best with
-  // the CTA-tile kernel.
+                      double* partials, PcgState* st, cudaStream_t s, const ApplyConfig* cfg) {
+  const bool explicit_cfg = cfg != nullptr && cfg->kind != kApplyAuto && sem_apply_config_valid(g.n, sizeof(T), *cfg);
+  int kind = explicit_cfg ? cfg->kind : sem_apply_default_kind(g.n, sizeof(T));
   if constexpr (sizeof(T) == 4) {
-    if (g.n >= 3 && g.n <= 7) {
+    if (kind == kApplyPlane && t.plane == nullptr) kind = kApplyCta;   // tables not built (cannot happen via the API)
+    if (kind == kApplyPlane) {
+      launch_plane_apply(g, t, x, y, partials, st, s);
+      return;
+    }
+    if (kind == kApplyWarp) {
       switch (g.n) {
         case 3: launch_warp<T, 3>(g, t, x, y, partials, st, b.w0, s); return;
         case 4: launch_warp<T, 4>(g, t, x, y, partials, st, b.w0, s); return;
@@ -982,11 +977,13 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
       }
     }
   }
-  if (g.n == 1) {
+  if (kind == kApplyElement) {
     launch_p2<T>(g, t, x, y, partials, st, s);
     return;
   }
+  const ApplyConfig c = (explicit_cfg && cfg->kind == kApplyCta) ? *cfg : sem_apply_config(g.n, sizeof(T));
   switch (g.n) {
+    case 1: launch_nc<T, 1>(g, t, x, y, partials, st, c, s); break;
     case 3: launch_nc<T, 3>(g, t, x, y, partials, st, c, s); break;
     case 7: launch_nc<T, 7>(g, t, x, y, partials, st, c, s); break;
     case 15: launch_nc<T, 15>(g, t, x, y, partials, st, c, s); break;

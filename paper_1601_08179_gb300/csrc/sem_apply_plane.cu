@@ -1,0 +1,616 @@
+// Plane-per-lane variant of the transformed condensed operator (Sec. 6 of the
+// paper), for FP32 and 2 <= n <= 8: the inner operator of the mixed-precision
+// solve.
+//
+// The element operator is the one of the CTA-tile kernel (sem_apply.cu):
+// expansion of the six faces into the interior eigenspace (Table 2), -D^-1,
+// contraction back onto the faces, plus the primary part H~_BB restricted to
+// the skeleton; only the mapping of the work onto the GPU differs.
+//
+// * A group of G = 4 (n <= 4) or 8 lanes owns one element; a warp holds
+//   32 / G elements.  Lane j of a group owns the y-plane j of the n^3 cube
+//   and walks it in k, i.e. it holds a row of n points at a time.
+// * The x-contraction (sum over i) and the z-contraction (sum over k) are
+//   done in the lane's registers; the y-contraction (sum over j) is a
+//   butterfly reduce-scatter over the group (shuffles), after which lane i
+//   holds the y-face outputs at (k, i).
+// * D^-1 = 1 / (d0 + d1 lambda_i + d2 lambda_j + d3 lambda_k) (the diagonal
+//   of H~_II in the eigenbasis) is formed with one reciprocal per point, and
+//   the face, edge and vertex diagonals of H~_BB are formed from the same
+//   lambda vectors, so a class's coefficient block is 9n + O(1) numbers.
+// * The line sums of the primary part that run along k are accumulated in
+//   the same k walk; the others are one row or column of shared memory per
+//   lane, the edge position being the lane index.
+// * Face rows are padded to four floats (16-byte vector loads), and the
+//   element slots of a warp are offset by 32 / (elements per warp) banks, so
+//   a broadcast row load of the whole warp is one shared-memory wavefront.
+
+#include <cuda_runtime.h>
+
+#include "sem_device.cuh"
+#include "sem_kernels.cuh"
+
+using namespace semdev;
+
+namespace {
+
+constexpr int kPlaneThreads = 96;
+constexpr int kHdr = 32;   // ints per element slot: 26 entity offsets, class, loaded class
+
+template <int N>
+struct PlaneSm {
+  static constexpr int G = N <= 4 ? 4 : 8;     // lanes per element
+  static constexpr int EPW = 32 / G;           // elements per warp
+  static constexpr int RS = (N + 3) & ~3;      // padded row
+  static constexpr int FS = N * RS;            // padded face
+  static constexpr int F = 0;                  // faces [6][N][RS]
+  static constexpr int EX = 6 * FS;            // x-edges [4][RS] (slot sb + 2 sc), y-edges [4][RS] (4 + sa + 2 sc)
+  static constexpr int EZ = EX + 8 * RS;       // z-edges [N][4], component sa + 2 sb
+  static constexpr int VT = EZ + 4 * N;        // vertices [8]
+  static constexpr int C = VT + 8;             // class coefficient block (plane_layout)
+  static constexpr int PCS = 5 * RS + 4 * N + 36;
+  static constexpr int raw = C + PCS;
+  static constexpr int step = 32 / EPW;        // bank offset between the element slots of a warp
+  static constexpr int size = raw + ((step - raw % 32) % 32 + 32) % 32;
+  static_assert(size % 32 == step, "slot stride");
+  static_assert(EX % 4 == 0 && EZ % 4 == 0 && VT % 4 == 0 && C % 4 == 0, "16-byte alignment");
+};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// M floats from a 16-byte aligned row (M a multiple of 4).
+template <int M>
+__device__ __forceinline__ void load_row(const float* p, float (&r)[M]) {
+#pragma unroll
+  for (int t = 0; t < M; t += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p + t);
+    r[t] = v.x;
+    r[t + 1] = v.y;
+    r[t + 2] = v.z;
+    r[t + 3] = v.w;
+  }
+}
+
+// Sums P0[i], P1[i] over the G lanes of a group; lane jl of the group ends
+// with the sums for i = jl.  Each halving step keeps the half of the index
+// range named by one bit of jl and adds the partner's copy of it.
+template <int H, int G>
+__device__ __forceinline__ void halve(float (&P0)[G], float (&P1)[G], int jl) {
+  const bool up = (jl & H) != 0;
+#pragma unroll
+  for (int t = 0; t < H; ++t) {
+    const float s0 = up ? P0[t] : P0[t + H], k0 = up ? P0[t + H] : P0[t];
+    const float s1 = up ? P1[t] : P1[t + H], k1 = up ? P1[t + H] : P1[t];
+    P0[t] = k0 + __shfl_xor_sync(0xffffffffu, s0, H);
+    P1[t] = k1 + __shfl_xor_sync(0xffffffffu, s1, H);
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void reduce_scatter(float (&P0)[G], float (&P1)[G], int jl, float* y0, float* y1) {
+  if constexpr (G == 8) halve<4, G>(P0, P1, jl);
+  halve<2, G>(P0, P1, jl);
+  halve<1, G>(P0, P1, jl);
+  *y0 = P0[0];
+  *y1 = P1[0];
+}
+
+// cp.async of 4 bytes global -> shared; zero-fills the destination when
+// !valid (src-size 0: nothing is read).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+// cp.async of 16 bytes (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
+
+// Offsets of the element's 26 entities (-1: Dirichlet entity or no element)
+// and its class (fallback for a missing element) into H[0..26].
+template <int G>
+__device__ __forceinline__ void plane_header(const SemGeom& g, const SemClassTables<float>& tab, long long e,
+                                             bool live, int fallback, int jl, int* H) {
+  int ex = 0, ey = 0, ez = 0;
+  if (live) elem_visit(g, e, &ex, &ey, &ez);
+  for (int r = jl; r < 27; r += G) {
+    int val;
+    if (r == 26) {
+      val = live ? elem_class(g, tab, ex, ey, ez) : fallback;
+    } else if (!live) {
+      val = -1;
+    } else {
+      bool dir;
+      long long off;
+      if (r < 6) off = face_base(g, ex, ey, ez, r, &dir);
+      else if (r < 18) off = edge_base(g, ex, ey, ez, r - 6, &dir);
+      else off = vert_index(g, ex, ey, ez, r - 18, &dir);
+      val = dir ? -1 : (int)off;
+    }
+    H[r] = val;
+  }
+}
+
+// Issues the asynchronous gather R^T of one element (entity offsets in H)
+// into the slot buffer W: faces row by row with the lane as the column,
+// edges one value per lane, vertices; and the class block when load_cls.
+template <int N>
+__device__ __forceinline__ void plane_gather(const float* __restrict__ u, const float* cls_src, bool load_cls,
+                                             const int* H, float* W, int jl) {
+  using S = PlaneSm<N>;
+  if (jl < N) {
+#pragma unroll
+    for (int slot = 0; slot < 6; ++slot) {
+      const int off = H[slot];
+      const float* src = u + (off >= 0 ? off : 0) + jl;
+      float* dst = W + S::F + slot * S::FS + jl;
+#pragma unroll
+      for (int row = 0; row < N; ++row) cp_async4(dst + row * S::RS, src + row * N, off >= 0);
+    }
+#pragma unroll
+    for (int slot = 0; slot < 12; ++slot) {
+      const int off = H[6 + slot];
+      float* dst = slot < 8 ? W + S::EX + slot * S::RS + jl : W + S::EZ + 4 * jl + (slot - 8);
+      cp_async4(dst, u + (off >= 0 ? off : 0) + jl, off >= 0);
+    }
+  }
+  for (int r = jl; r < 8; r += S::G) {
+    const int off = H[18 + r];
+    cp_async4(W + S::VT + r, u + (off >= 0 ? off : 0), off >= 0);
+  }
+  if (load_cls)
+    for (int r = 4 * jl; r < S::PCS; r += 4 * S::G) cp_async16(W + S::C + r, cls_src + r);
+}
+
+// The element operator of one element whose gathered values sit in W
+// (offsets in H); scatter-adds into v and accumulates x^T (A x) into dot.
+template <int N>
+__device__ __forceinline__ void plane_element(const float* W, const int* H, float* __restrict__ v, int jl,
+                                              float& dot) {
+  using S = PlaneSm<N>;
+  constexpr int G = S::G, RS = S::RS, FS = S::FS;
+  constexpr int PA = 0, PB = RS, PL1 = 2 * RS, PL2 = 3 * RS, PL3 = 4 * RS, PQ = 5 * RS, PS = 5 * RS + 4 * N;
+  const float* Fp = W + S::F;
+  const float* Cf = W + S::C;
+  const bool act = jl < N;                 // lanes past n mirror plane n-1 and contribute zeros
+  const int j = act ? jl : N - 1;
+    // ---- per-element constants of this lane
+    const float w0 = Cf[PS + 32], w02 = Cf[PS + 33], d0 = Cf[PS + 34];
+    float a[RS], b[RS], l1[RS], e4[RS], e5[RS];
+    load_row<RS>(Cf + PA, a);
+    load_row<RS>(Cf + PB, b);
+    load_row<RS>(Cf + PL1, l1);
+    load_row<RS>(Fp + 4 * FS + j * RS, e4);   // z-face rows j
+    load_row<RS>(Fp + 5 * FS + j * RS, e5);
+    const float4 qj = *reinterpret_cast<const float4*>(Cf + PQ + 4 * j);
+    const float cj = act ? qj.x : 0.f, dj = act ? qj.y : 0.f;
+    const float l2j = Cf[PL2 + j], sj = d0 + l2j;
+    const float al = Cf[PA + j], bl = Cf[PB + j], l1l = Cf[PL1 + j];
+    float ey[4], ex[4];   // Ey[sa][sc][j] (slot 4 + sa + 2 sc), Ex[sb][sc][j] (slot sb + 2 sc)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ey[q] = W[S::EX + (4 + q) * RS + j];
+      ex[q] = W[S::EX + q * RS + j];
+    }
+    float fc[6], cO[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      cO[q] = Cf[PS + q];
+      fc[q] = Cf[PS + 6 + q];
+    }
+    float z4[RS], z5[RS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i) z4[i] = z5[i] = 0.f;
+    // line sums along k for the edges: sx[2 sa + sc] = sum_k (e|g)_k F_sa[k][j],
+    // sy[2 sb + sc] = sum_k (e|g)_k F_{2+sb}[k][i = jl]
+    float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f};
+    const int ox0 = H[0], ox1 = H[1], oy0 = H[2], oy1 = H[3];
+
+    // ---- walk the y-plane j in k: expansion, D^-1, contractions; x- and
+    //      y-face outputs at k
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      const float4 qk = *reinterpret_cast<const float4*>(Cf + PQ + 4 * k);
+      const float ek = qk.z, gk = qk.w, l3k = Cf[PL3 + k];
+      const float4 ezk = *reinterpret_cast<const float4*>(W + S::EZ + 4 * k);   // Ez[sa + 2 sb][k]
+      const float A = Fp[k * RS + j], B = Fp[FS + k * RS + j];
+      const float Cl = Fp[2 * FS + k * RS + j], Dl = Fp[3 * FS + k * RS + j];
+      float Cr[RS], Dr[RS];
+      load_row<RS>(Fp + 2 * FS + k * RS, Cr);
+      load_row<RS>(Fp + 3 * FS + k * RS, Dr);
+      const float sjk = sj + l3k;
+      float X0 = 0.f, X1 = 0.f;
+      float P0[G], P1[G];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float x = a[i] * A;
+        x = fmaf(b[i], B, x);
+        x = fmaf(cj, Cr[i], x);
+        x = fmaf(dj, Dr[i], x);
+        x = fmaf(ek, e4[i], x);
+        x = fmaf(gk, e5[i], x);
+        const float w = x * rcp_approx(sjk + l1[i]);   // D^-1 x (the sign is applied at the outputs)
+        X0 = fmaf(a[i], w, X0);
+        X1 = fmaf(b[i], w, X1);
+        z4[i] = fmaf(ek, w, z4[i]);
+        z5[i] = fmaf(gk, w, z5[i]);
+        P0[i] = cj * w;
+        P1[i] = dj * w;
+      }
+#pragma unroll
+      for (int i = N; i < G; ++i) P0[i] = P1[i] = 0.f;
+      float Y0, Y1;
+      reduce_scatter<G>(P0, P1, jl, &Y0, &Y1);
+      sx[0] = fmaf(ek, A, sx[0]);
+      sx[1] = fmaf(gk, A, sx[1]);
+      sx[2] = fmaf(ek, B, sx[2]);
+      sx[3] = fmaf(gk, B, sx[3]);
+      sy[0] = fmaf(ek, Cl, sy[0]);
+      sy[1] = fmaf(gk, Cl, sy[1]);
+      sy[2] = fmaf(ek, Dl, sy[2]);
+      sy[3] = fmaf(gk, Dl, sy[3]);
+      if (act) {
+        const int kj = k * N + j;
+        // x-faces at (k, j): diagonal, opposite face, the four edge lines, -condensed
+        const float bx = w0 * (l2j + l3k);
+        float o = (fc[0] + bx) * A;
+        o = fmaf(cO[0], B, o);
+        o = fmaf(w0, fmaf(cj, ezk.x, fmaf(dj, ezk.z, fmaf(ek, ey[0], gk * ey[2]))), o);
+        o -= X0;
+        if (ox0 >= 0) {
+          atomicAdd(v + ox0 + kj, o);
+          dot = fmaf(A, o, dot);
+        }
+        o = (fc[1] + bx) * B;
+        o = fmaf(cO[1], A, o);
+        o = fmaf(w0, fmaf(cj, ezk.y, fmaf(dj, ezk.w, fmaf(ek, ey[1], gk * ey[3]))), o);
+        o -= X1;
+        if (ox1 >= 0) {
+          atomicAdd(v + ox1 + kj, o);
+          dot = fmaf(B, o, dot);
+        }
+        // y-faces at (k, i = jl)
+        const float by = w0 * (l1l + l3k);
+        o = (fc[2] + by) * Cl;
+        o = fmaf(cO[2], Dl, o);
+        o = fmaf(w0, fmaf(al, ezk.x, fmaf(bl, ezk.y, fmaf(ek, ex[0], gk * ex[2]))), o);
+        o -= Y0;
+        if (oy0 >= 0) {
+          atomicAdd(v + oy0 + kj, o);
+          dot = fmaf(Cl, o, dot);
+        }
+        o = (fc[3] + by) * Dl;
+        o = fmaf(cO[3], Cl, o);
+        o = fmaf(w0, fmaf(al, ezk.z, fmaf(bl, ezk.w, fmaf(ek, ex[1], gk * ex[3]))), o);
+        o -= Y1;
+        if (oy1 >= 0) {
+          atomicAdd(v + oy1 + kj, o);
+          dot = fmaf(Dl, o, dot);
+        }
+      }
+    }
+
+    if (act) {
+      // ---- z-faces at (j, i)
+      const int oz0 = H[4], oz1 = H[5];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        float xa[RS], xb[RS];     // Ex[0][s][.], Ex[1][s][.] (slots 2 s, 2 s + 1)
+        load_row<RS>(W + S::EX + (2 * s) * RS, xa);
+        load_row<RS>(W + S::EX + (2 * s + 1) * RS, xb);
+        const float ya = ey[2 * s], yb = ey[2 * s + 1];   // Ey[0][s][j], Ey[1][s][j]
+        const int oz = s ? oz1 : oz0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const float own = s ? e5[i] : e4[i], opp = s ? e4[i] : e5[i];
+          float o = (fc[4 + s] + w0 * (l1[i] + l2j)) * own;
+          o = fmaf(cO[4 + s], opp, o);
+          o = fmaf(w0, fmaf(a[i], ya, fmaf(b[i], yb, fmaf(cj, xa[i], dj * xb[i]))), o);
+          o -= s ? z5[i] : z4[i];
+          if (oz >= 0) {
+            atomicAdd(v + oz + j * N + i, o);
+            dot = fmaf(own, o, dot);
+          }
+        }
+      }
+      // ---- edges at position l = jl
+      float szr[4] = {0.f, 0.f, 0.f, 0.f};   // z-face row j: szr[2 sc + sa] = sum_m (a|b)_m F_{4+sc}[j][m]
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        szr[0] = fmaf(a[m], e4[m], szr[0]);
+        szr[1] = fmaf(b[m], e4[m], szr[1]);
+        szr[2] = fmaf(a[m], e5[m], szr[2]);
+        szr[3] = fmaf(b[m], e5[m], szr[3]);
+      }
+      float cm[RS], dm[RS];
+      float szc[4] = {0.f, 0.f, 0.f, 0.f};   // z-face column l: szc[2 sc + sb] = sum_m (c|d)_m F_{4+sc}[m][l]
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        const float2 cd = *reinterpret_cast<const float2*>(Cf + PQ + 4 * m);
+        cm[m] = cd.x;
+        dm[m] = cd.y;
+        const float f0 = Fp[4 * FS + m * RS + j], f1 = Fp[5 * FS + m * RS + j];
+        szc[0] = fmaf(cd.x, f0, szc[0]);
+        szc[1] = fmaf(cd.y, f0, szc[1]);
+        szc[2] = fmaf(cd.x, f1, szc[2]);
+        szc[3] = fmaf(cd.y, f1, szc[3]);
+      }
+      float syr[4] = {0.f, 0.f, 0.f, 0.f};   // y-face row l: syr[2 sb + sa] = sum_m (a|b)_m F_{2+sb}[l][m]
+      float sxr[4] = {0.f, 0.f, 0.f, 0.f};   // x-face row l: sxr[2 sa + sb] = sum_m (c|d)_m F_sa[l][m]
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        float yr[RS], xr[RS];
+        load_row<RS>(Fp + (2 + f) * FS + j * RS, yr);
+        load_row<RS>(Fp + f * FS + j * RS, xr);
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          syr[2 * f] = fmaf(a[m], yr[m], syr[2 * f]);
+          syr[2 * f + 1] = fmaf(b[m], yr[m], syr[2 * f + 1]);
+          sxr[2 * f] = fmaf(cm[m], xr[m], sxr[2 * f]);
+          sxr[2 * f + 1] = fmaf(dm[m], xr[m], sxr[2 * f + 1]);
+        }
+      }
+      float Vt[8];
+      {
+        const float4 v0 = *reinterpret_cast<const float4*>(W + S::VT);
+        const float4 v1 = *reinterpret_cast<const float4*>(W + S::VT + 4);
+        Vt[0] = v0.x; Vt[1] = v0.y; Vt[2] = v0.z; Vt[3] = v0.w;
+        Vt[4] = v1.x; Vt[5] = v1.y; Vt[6] = v1.z; Vt[7] = v1.w;
+      }
+      const float4 ezl = *reinterpret_cast<const float4*>(W + S::EZ + 4 * j);
+      const float ez[4] = {ezl.x, ezl.y, ezl.z, ezl.w};
+      const float el = qj.z, gl = qj.w, l3l = Cf[PL3 + j];
+      // x-edges Ex[sb][sc] at i = l
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int sb = q & 1, sc = q >> 1;
+        float o = (w02 * (d0 + l1l) + Cf[PS + 12 + q]) * ex[q];
+        o = fmaf(w02, fmaf(al, Vt[2 * sb + 4 * sc], bl * Vt[1 + 2 * sb + 4 * sc]), o);
+        o = fmaf(w0, szc[2 * sc + sb] + sy[2 * sb + sc], o);
+        o = fmaf(w0 * cO[2 + sb], ex[(1 - sb) + 2 * sc], o);
+        o = fmaf(w0 * cO[4 + sc], ex[sb + 2 * (1 - sc)], o);
+        const int off = H[6 + q];
+        if (off >= 0) {
+          atomicAdd(v + off + j, o);
+          dot = fmaf(ex[q], o, dot);
+        }
+      }
+      // y-edges Ey[sa][sc] at j = l
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int sa = q & 1, sc = q >> 1;
+        float o = (w02 * (d0 + l2j) + Cf[PS + 16 + q]) * ey[q];
+        o = fmaf(w02, fmaf(cj, Vt[sa + 4 * sc], dj * Vt[sa + 2 + 4 * sc]), o);
+        o = fmaf(w0, szr[2 * sc + sa] + sx[2 * sa + sc], o);
+        o = fmaf(w0 * cO[sa], ey[(1 - sa) + 2 * sc], o);
+        o = fmaf(w0 * cO[4 + sc], ey[sa + 2 * (1 - sc)], o);
+        const int off = H[10 + q];
+        if (off >= 0) {
+          atomicAdd(v + off + j, o);
+          dot = fmaf(ey[q], o, dot);
+        }
+      }
+      // z-edges Ez[sa][sb] at k = l
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int sa = q & 1, sb = q >> 1;
+        float o = (w02 * (d0 + l3l) + Cf[PS + 20 + q]) * ez[q];
+        o = fmaf(w02, fmaf(el, Vt[sa + 2 * sb], gl * Vt[sa + 2 * sb + 4]), o);
+        o = fmaf(w0, syr[2 * sb + sa] + sxr[2 * sa + sb], o);
+        o = fmaf(w0 * cO[sa], ez[(1 - sa) + 2 * sb], o);
+        o = fmaf(w0 * cO[2 + sb], ez[sa + 2 * (1 - sb)], o);
+        const int off = H[14 + q];
+        if (off >= 0) {
+          atomicAdd(v + off + j, o);
+          dot = fmaf(ez[q], o, dot);
+        }
+      }
+    }
+    // ---- vertices (lanes 0..7 of the group, two per lane when G = 4)
+    for (int r = jl; r < 8; r += G) {
+      const int sa = r & 1, sb = (r >> 1) & 1, sc = r >> 2;
+      const float* exr = W + S::EX + (sb + 2 * sc) * RS;
+      const float* eyr = W + S::EX + (4 + sa + 2 * sc) * RS;
+      float sv = 0.f;
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        sv = fmaf(sa ? b[m] : a[m], exr[m], sv);
+        sv = fmaf(Cf[PQ + 4 * m + sb], eyr[m], sv);
+        sv = fmaf(Cf[PQ + 4 * m + 2 + sc], W[S::EZ + 4 * m + sa + 2 * sb], sv);
+      }
+      const float vr = W[S::VT + r];
+      float o = Cf[PS + 24 + r] * vr;
+      o = fmaf(w02, sv, o);
+      o = fmaf(w02 * Cf[PS + sa], W[S::VT + (r ^ 1)], o);       // cO from shared memory: the
+      o = fmaf(w02 * Cf[PS + 2 + sb], W[S::VT + (r ^ 2)], o);   // index depends on the lane
+      o = fmaf(w02 * Cf[PS + 4 + sc], W[S::VT + (r ^ 4)], o);
+      const int off = H[18 + r];
+      if (off >= 0) {
+        atomicAdd(v + off, o);
+        dot = fmaf(vr, o, dot);
+      }
+    }
+}
+
+// Two-stage pipeline per warp: while the element groups of quad q are
+// computed from one buffer, the entity offsets of quad q + 1 are formed and
+// its gather is in flight (cp.async) into the other buffer.
+template <int N>
+__global__ void __launch_bounds__(kPlaneThreads, 4)
+k_tpt_apply_plane(SemGeom g, SemClassTables<float> tab, const float* __restrict__ u, float* __restrict__ v,
+                  double* __restrict__ partials, PcgState* st, int qpw) {
+  using S = PlaneSm<N>;
+  constexpr int G = S::G, EPW = S::EPW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (st != nullptr && st->done) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int grp = lane / G, jl = lane - grp * G;
+  const int slot_id = wib * EPW + grp, nslots = wpb * EPW;
+  // buffer-major: buffer b of slot s at (b nslots + s); consecutive slots keep
+  // their bank offset
+  int* H0 = reinterpret_cast<int*>(smem_raw) + slot_id * kHdr;                 // buffer b: H0 + b hstep
+  float* W0 = reinterpret_cast<float*>(smem_raw + (size_t)2 * nslots * kHdr * sizeof(int)) +
+              (size_t)slot_id * S::size;                                      // buffer b: W0 + b wstep
+  const int hstep = nslots * kHdr, wstep = nslots * S::size;
+  const long long q_begin = ((long long)blockIdx.x * wpb + wib) * qpw;
+  const long long e_first = q_begin * EPW;
+  int nq = 0;
+  if (e_first < g.nelem) {
+    const long long left = (g.nelem - e_first + EPW - 1) / EPW;
+    nq = left < qpw ? (int)left : qpw;
+  }
+  int held0 = -1, held1 = -1;   // class in each buffer's coefficient block (equal over the group)
+  float dot = 0.f;
+
+  auto stage = [&](int qi, int b) {
+    int* H = H0 + b * hstep;
+    float* W = W0 + b * wstep;
+    const int held = b ? held1 : held0;
+    const long long e = (q_begin + qi) * EPW + grp;
+    plane_header<G>(g, tab, e, e < g.nelem, held >= 0 ? held : 0, jl, H);
+    __syncwarp();
+    const int cls = H[26];
+    plane_gather<N>(u, tab.plane + (long long)cls * tab.plane_stride, cls != held, H, W, jl);
+    cp_async_commit();
+    if (b) held1 = cls;
+    else held0 = cls;
+  };
+
+  if (nq > 0) stage(0, 0);
+  for (int qi = 0; qi < nq; ++qi) {
+    const int b = qi & 1;
+    if (qi + 1 < nq) {
+      stage(qi + 1, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    plane_element<N>(W0 + b * wstep, H0 + b * hstep, v, jl, dot);
+    __syncwarp();
+  }
+
+  if (st != nullptr) {
+    double vals[1] = {(double)dot}, tot[1];
+    if (reduce_grid<1>(vals, partials, &st->counter[0], tot) && threadIdx.x == 0) {
+      const double pq = tot[0];
+      st->pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) st->done = 2;
+      else st->alpha = st->rho / pq;
+    }
+  }
+}
+
+template <int N>
+size_t plane_smem() {
+  using S = PlaneSm<N>;
+  const int wpb = kPlaneThreads / 32;
+  return (size_t)wpb * S::EPW * 2 * kHdr * sizeof(int) + (size_t)wpb * S::EPW * 2 * S::size * sizeof(float);
+}
+
+template <int N>
+void launch_plane_n(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y, double* partials,
+                    PcgState* st, cudaStream_t s) {
+  using S = PlaneSm<N>;
+  const int wpb = kPlaneThreads / 32;
+  const size_t smem = plane_smem<N>();
+  static bool attr = false;
+  if (!attr) {   // once per instantiation; the first launch happens outside any capture
+    cudaFuncSetAttribute(k_tpt_apply_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_plane<N>, kPlaneThreads, smem);
+  if (occ < 1) occ = 1;
+  // element groups ("quads") split evenly over the resident warps
+  const long long cap = (long long)sem_num_sms() * occ * wpb;
+  const long long nq = (g.nelem + S::EPW - 1) / S::EPW;
+  const long long qpw = (nq + cap - 1) / cap;
+  const long long nwarps = (nq + qpw - 1) / qpw;
+  const long long grid = (nwarps + wpb - 1) / wpb;
+  k_tpt_apply_plane<N><<<(int)grid, kPlaneThreads, smem, s>>>(g, t, x, y, partials, st, (int)qpw);
+  sem_count_launch();
+}
+
+// Class blocks in the layout of plane_layout(n), from the metric
+// coefficients d0..d3 of each class and the 1D basis (FP64, stored in FP32).
+__global__ void k_plane_coeffs(SemGeom g, SemBasis b, const double* __restrict__ dcoef, float* __restrict__ out) {
+  const int n = g.n;
+  const PlaneLayout L = plane_layout(n);
+  const long long ncls = (long long)g.ux * g.uy * g.uz;
+  const double w0 = b.w0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ncls * L.stride;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long c = t / L.stride;
+    const int r = (int)(t - c * L.stride);
+    const double* d = dcoef + c * 4;
+    double val = 0.0;
+    if (r < L.pq) {
+      const int row = r / L.rs, i = r - row * L.rs;
+      if (i < n) {
+        if (row == 0) val = d[1] * b.k[0][i];
+        else if (row == 1) val = d[1] * b.k[1][i];
+        else val = d[row - 1] * b.lam[i];        // rows 2, 3, 4: d1, d2, d3 times lambda
+      }
+    } else if (r < L.ps) {
+      const int m = (r - L.pq) >> 2, comp = (r - L.pq) & 3;
+      val = d[comp < 2 ? 2 : 3] * b.k[comp & 1][m];
+    } else {
+      const int q = r - L.ps;
+      if (q < 6) {                                // cO
+        const int dir = q >> 1, s = q & 1;
+        val = d[dir + 1] * b.K[s][1 - s];
+      } else if (q < 12) {                        // face-diagonal constants
+        const int slot = q - 6, dir = slot >> 1, s = slot & 1;
+        val = d[0] * w0 + d[dir + 1] * b.K[s][s];
+      } else if (q < 24) {                        // edge-diagonal constants
+        const int slot = q - 12, grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+        const int t1 = grp == 0 ? 1 : 0, t2 = grp == 2 ? 1 : 2;
+        val = w0 * (d[t1 + 1] * b.K[s1][s1] + d[t2 + 1] * b.K[s2][s2]);
+      } else if (q < 32) {                        // vertex diagonals
+        const int slot = q - 24, sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
+        val = d[0] * w0 * w0 * w0 + w0 * w0 * (d[1] * b.K[sa][sa] + d[2] * b.K[sb][sb] + d[3] * b.K[sc][sc]);
+      } else if (q == 32) {
+        val = w0;
+      } else if (q == 33) {
+        val = w0 * w0;
+      } else if (q == 34) {
+        val = d[0];
+      }
+    }
+    out[t] = (float)val;
+  }
+}
+
+}  // namespace
+
+void launch_plane_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoef, float* plane, cudaStream_t s) {
+  const long long work = (long long)g.ux * g.uy * g.uz * plane_layout(g.n).stride;
+  long long blocks = (work + 255) / 256;
+  if (blocks > (long long)sem_num_sms() * 16) blocks = (long long)sem_num_sms() * 16;
+  if (blocks < 1) blocks = 1;
+  k_plane_coeffs<<<(int)blocks, 256, 0, s>>>(g, b, dcoef, plane);
+  sem_count_launch();
+}
+
+void launch_plane_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
+                        double* partials, PcgState* st, cudaStream_t s) {
+  switch (g.n) {
+    case 2: launch_plane_n<2>(g, t, x, y, partials, st, s); break;
+    case 3: launch_plane_n<3>(g, t, x, y, partials, st, s); break;
+    case 4: launch_plane_n<4>(g, t, x, y, partials, st, s); break;
+    case 5: launch_plane_n<5>(g, t, x, y, partials, st, s); break;
+    case 6: launch_plane_n<6>(g, t, x, y, partials, st, s); break;
+    case 7: launch_plane_n<7>(g, t, x, y, partials, st, s); break;
+    default: launch_plane_n<8>(g, t, x, y, partials, st, s); break;
+  }
+}

@@ -17,6 +17,24 @@ static __device__ __forceinline__ void elem_coords(const SemGeom& g, long long e
   *ez = (int)(r / g.my);
 }
 
+// Element visiting order of the operator kernels: the axis with the most width
+// classes is slowest, so consecutive elements share their class tables.
+static __device__ __forceinline__ void elem_visit(const SemGeom& g, long long e, int* ex, int* ey, int* ez) {
+  if (g.slow == 0) {
+    const long long r = e % ((long long)g.my * g.mz);
+    *ex = (int)(e / ((long long)g.my * g.mz));
+    *ey = (int)(r % g.my);
+    *ez = (int)(r / g.my);
+  } else if (g.slow == 1) {
+    const long long r = e % ((long long)g.mx * g.mz);
+    *ey = (int)(e / ((long long)g.mx * g.mz));
+    *ex = (int)(r % g.mx);
+    *ez = (int)(r / g.mx);
+  } else {
+    elem_coords(g, e, ex, ey, ez);
+  }
+}
+
 // Face slot 0..5 = (dir, side): 0 w, 1 e, 2 s, 3 n, 4 b, 5 t.
 static __device__ __forceinline__ long long face_base(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
   const int d = slot >> 1, s = slot & 1;

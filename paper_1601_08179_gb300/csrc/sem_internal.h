@@ -54,7 +54,36 @@ struct SemClassTables {
   const T* dinv;      // [ncls][n^3] D^-1, index (k n + j) n + i
   const T* coef;      // [ncls][coef_stride] operator coefficients (sem_apply.cu)
   long long coef_stride;
+  const float* plane = nullptr;   // [ncls][plane_stride] blocks of the plane-per-lane FP32 kernel
+  long long plane_stride = 0;     // (sem_apply_plane.cu); null where that kernel does not apply
 };
+
+// One class's coefficient block of the plane-per-lane FP32 operator (units of
+// float; rows padded to rs = 4 ceil(n / 4) for 16-byte vector loads):
+//   [pa, pa + rs)  a_i = d1 k_0[i]      [pb, pb + rs)  b_i = d1 k_1[i]
+//   [pl1 .. pl3]   d1 lambda, d2 lambda, d3 lambda (one row each)
+//   [pq, pq + 4n)  (c_m, d_m, e_m, g_m) = (d2 k_0, d2 k_1, d3 k_0, d3 k_1)[m]
+//   [ps, ps + 36)  cO[6] = d_{dir+1} K~_{s,1-s}; face-diagonal constants[6]
+//                  d0 w0 + d_{dir+1} K~_ss; edge-diagonal constants[12]
+//                  w0 (d K~_ss + d' K~_s's'); vertex diagonals[8]; w0, w0^2, d0, 0
+struct PlaneLayout {
+  int rs, pa, pb, pl1, pl2, pl3, pq, ps, stride;
+};
+inline __host__ __device__ PlaneLayout plane_layout(int n) {
+  PlaneLayout o;
+  o.rs = (n + 3) & ~3;
+  o.pa = 0;
+  o.pb = o.rs;
+  o.pl1 = 2 * o.rs;
+  o.pl2 = 3 * o.rs;
+  o.pl3 = 4 * o.rs;
+  o.pq = 5 * o.rs;
+  o.ps = o.pq + 4 * n;
+  o.stride = o.ps + 36;
+  return o;
+}
+// Degrees served by the plane-per-lane kernel: n = p - 1 in [2, 8].
+inline __host__ __device__ bool plane_supported(int n) { return n >= 2 && n <= 8; }
 
 // Offsets inside one class's operator coefficient block (units of T):
 //   [0, 18n + 24): scaled line vectors and couplings, copied to shared memory

@@ -528,6 +528,8 @@ int grid_for(long long work, int threads, int per_sm = 8) {
 
 }  // namespace
 
+int sem_num_sms() { return num_sms(); }
+
 int sem_vec_blocks() { return num_sms() * 4; }
 
 // ---------------------------------------------------------------------------

@@ -3,17 +3,46 @@
 
 #include "sem_internal.h"
 
-// Operator launch configuration for degree p (sem_apply.cu).
-struct ApplyConfig {
-  int epb;      // elements per CTA tile
-  int ks;       // eigenspace slab depth (k planes held at once)
-  int threads;
-  size_t smem;  // dynamic shared memory bytes
+// Operator kernel variants: one operator, four work mappings (sem_apply.cu,
+// sem_apply_plane.cu).  The numbering is the one of SEM_KERNEL_* in sem.h.
+enum ApplyKind {
+  kApplyAuto = 0,      // the built-in choice for (n, precision)
+  kApplyCta = 1,       // CTA tile of epb elements, k-slabs of depth ks
+  kApplyWarp = 2,      // one warp per element (FP32, 3 <= n <= 7)
+  kApplyPlane = 3,     // one lane per y-plane, 32/G elements per warp (FP32, 2 <= n <= 8)
+  kApplyElement = 4    // one thread per element (n = 1)
 };
+
+// Operator launch configuration.
+struct ApplyConfig {
+  int kind = kApplyAuto;
+  int epb = 0;      // CTA tile: elements per tile
+  int ks = 0;       // CTA tile: eigenspace slab depth (k planes held at once)
+  int threads = 0;
+  size_t smem = 0;  // CTA tile: dynamic shared memory bytes
+};
+// Built-in CTA-tile shape for n.
 ApplyConfig sem_apply_config(int n, size_t elem_bytes);
-// Explicit CTA-tile configuration (autotuner candidates) and its validity.
+// Explicit CTA-tile configuration (autotuner candidates).
 ApplyConfig sem_apply_config_make(int n, size_t elem_bytes, int epb, int ks);
+// A configuration of the given kind (no tile parameters).
+ApplyConfig sem_apply_config_kind(int kind);
+// Whether c names a variant that exists for (n, element bytes) and, for a
+// CTA tile, one that fits in shared memory.
 bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c);
+// The kind kApplyAuto resolves to.
+int sem_apply_default_kind(int n, size_t elem_bytes);
+
+// Number of SMs of the current device.
+int sem_num_sms();
+
+// Per-class coefficient blocks of the plane-per-lane kernel (layout
+// plane_layout(n) in sem_internal.h), computed in FP64, stored in FP32.
+void launch_plane_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoef, float* plane, cudaStream_t s);
+// y += Hhat~ x with the plane-per-lane kernel (FP32, plane_supported(n));
+// same contract as launch_tpt_apply.
+void launch_plane_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
+                        double* partials, PcgState* st, cudaStream_t s);
 
 // Per-class operator coefficient blocks (layout in sem_internal.h), computed in
 // FP64 and stored in T.
@@ -23,11 +52,11 @@ void launch_class_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoe
 
 // y = Hhat~ x on the skeleton (transformed space); y must be zero on entry.
 // If st != nullptr: also x^T y -> st->pq and alpha = rho / pq (CG step).
-// tuned: optional CTA-tile configuration chosen by the autotuner (nullptr:
-// the built-in choice, which may be the warp-per-element kernel).
+// cfg: optional kernel choice (nullptr or kind kApplyAuto: the built-in
+// choice sem_apply_default_kind).
 template <typename T>
 void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y,
-                      double* partials, PcgState* st, cudaStream_t s, const ApplyConfig* tuned = nullptr);
+                      double* partials, PcgState* st, cudaStream_t s, const ApplyConfig* cfg = nullptr);
 
 void launch_class_tables(const SemGeom& g, const SemBasis& b, const double* ux_w, const double* uy_w,
                          const double* uz_w, double lambda, double* dcoef, double* dinv,

@@ -80,6 +80,9 @@ def lib():
         "sem_refine_history": (ctypes.c_int, [_P, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "sem_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(sem_info), _P]),
         "sem_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "sem_set_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "sem_get_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "sem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                             ctypes.POINTER(_P)]),
         "sem_batch_solve": (ctypes.c_int, [_P, ctypes.POINTER(sem_info), _P]),
@@ -110,7 +113,8 @@ def exported_symbols():
             "sem_condense_rhs_noalloc", "sem_apply_condensed_f32",
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
-            "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_batch_create", "sem_batch_solve",
+            "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_set_operator_kernel",
+            "sem_get_operator_kernel", "sem_batch_create", "sem_batch_solve",
             "sem_batch_destroy", "sem_solve_batch",
             "sem_profile_enable",
             "sem_profile_read", "sem_launch_count",
@@ -315,6 +319,23 @@ def sem_gradients(ctx: SemContext, w, u, f, df, stream=None):
                                dhx.ctypes.data_as(_D), dhy.ctypes.data_as(_D), dhz.ctypes.data_as(_D),
                                _stream(stream, w)))
     return dl.value, dhx, dhy, dhz
+
+
+KERNEL_AUTO, KERNEL_CTA_TILE, KERNEL_WARP, KERNEL_PLANE, KERNEL_ELEMENT = 0, 1, 2, 3, 4
+KERNEL_NAMES = {KERNEL_CTA_TILE: "cta_tile", KERNEL_WARP: "warp", KERNEL_PLANE: "plane", KERNEL_ELEMENT: "element"}
+
+
+def sem_set_operator_kernel(ctx: SemContext, precision: int, kind: int, epb: int = 0, ks: int = 0):
+    """Selects the operator kernel variant of one precision (PREC_FP64 or PREC_MIXED)."""
+    _check(lib().sem_set_operator_kernel(ctx.handle, int(precision), int(kind), int(epb), int(ks)))
+
+
+def sem_get_operator_kernel(ctx: SemContext, precision: int):
+    """(kind, epb, ks) of the operator kernel in use for one precision."""
+    k, e, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().sem_get_operator_kernel(ctx.handle, int(precision), ctypes.byref(k), ctypes.byref(e),
+                                         ctypes.byref(s)))
+    return k.value, e.value, s.value
 
 
 def sem_autotune(ctx: SemContext):

@@ -1,0 +1,149 @@
+"""Every operator kernel variant against the FP64 oracle, through the C ABI.
+
+The variants (SEM_KERNEL_CTA_TILE, _WARP, _PLANE, _ELEMENT) compute the same
+transformed condensed operator (Sec. 6, Table 2) with different work
+mappings; each is selected explicitly with sem_set_operator_kernel and
+compared with the oracle's element-local tier on every skeleton entry.
+Meshes have element counts that are not multiples of the elements per warp
+or CTA tile (ragged tails) and graded widths (several width classes).
+"""
+import numpy as np
+import pytest
+
+import sem_inputs as si
+from oracle import local, transform
+from tests.gpu_util import dev, host, make_pair, relerr
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5      # FP32 rounding of one application (relative, 2-norm)
+F64_TOL = 1e-12
+
+
+def _oracle_apply(ms, lam, ut):
+    free = ms.skeleton_free
+    u_nodal = transform.solution_from_transformed(ms, np.where(free, ut, 0.0))
+    return transform.load_to_transformed(ms, np.where(free, local.apply_condensed(ms, lam, u_nodal), 0.0))
+
+
+def _check_f32(ctx, ms, lam, seed):
+    import torch
+    from paper_1601_08179_gb300 import sem
+    ut = si.random_vector(ms.n_skeleton, seed).astype(np.float32).astype(np.float64)
+    v = torch.empty(ctx.nb, dtype=torch.float32, device="cuda")
+    sem.sem_apply_condensed_f32(ctx, torch.tensor(ut, dtype=torch.float32, device="cuda"), v)
+    got = host(v)
+    ref = _oracle_apply(ms, lam, ut)
+    assert np.all(got[~ms.skeleton_free] == 0.0)
+    return relerr(got, ref)
+
+
+PLANE_CASES = [  # p (n = p - 1 in 2..8), elements, lambda, aspect ratio
+    (3, (3, 2, 3), 1.0, 3.0),
+    (4, (3, 3, 2), 0.0, 4.0),     # G = 4 lanes, 8 elements per warp, 18 elements
+    (5, (2, 3, 3), 2.5, 2.0),
+    (6, (3, 2, 2), 10.0, 1.0),    # G = 8 lanes, n = 5: three idle lanes per group
+    (7, (2, 2, 3), 0.5, 2.0),
+    (8, (3, 3, 3), 0.0, 8.0),     # the benchmark degree
+    (9, (2, 3, 2), 1.0, 1.5),     # n = 8 fills the group
+]
+
+
+@pytest.mark.parametrize("p,m,lam,ar", PLANE_CASES)
+def test_plane_kernel_vs_oracle(p, m, lam, ar):
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, lam, ar)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_PLANE)
+    assert sem.sem_get_operator_kernel(ctx, sem.PREC_MIXED)[0] == sem.KERNEL_PLANE
+    err = _check_f32(ctx, ms, lam, 300 + p)
+    print(f"plane p={p}: {err:.2e}")
+    assert err <= F32_TOL
+
+
+def test_plane_kernel_many_warps_ragged():
+    """p = 8 on 9 x 7 x 5 = 315 elements (79 element groups over many warps,
+    the last group one element short), x-graded to aspect ratio 32."""
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(8, (9, 7, 5), 1.0, 32.0)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_PLANE)
+    assert _check_f32(ctx, ms, 1.0, 17) <= F32_TOL
+
+
+@pytest.mark.parametrize("p,m,lam,ar", [(4, (3, 2, 3), 1.0, 3.0), (6, (2, 3, 2), 0.0, 2.0),
+                                        (8, (3, 2, 2), 2.0, 4.0)])
+def test_warp_kernel_vs_oracle(p, m, lam, ar):
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, lam, ar)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_WARP)
+    assert _check_f32(ctx, ms, lam, 400 + p) <= F32_TOL
+
+
+@pytest.mark.parametrize("p,m,epb,ks", [(3, (3, 2, 3), 5, 1), (8, (3, 2, 2), 3, 4), (8, (3, 2, 2), 1, 7),
+                                        (12, (2, 2, 1), 2, 6), (2, (3, 2, 4), 7, 1)])
+def test_cta_tile_fp32_vs_oracle(p, m, epb, ks):
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, 1.0, 2.0)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_CTA_TILE, epb, ks)
+    assert sem.sem_get_operator_kernel(ctx, sem.PREC_MIXED) == (sem.KERNEL_CTA_TILE, epb, ks)
+    assert _check_f32(ctx, ms, 1.0, 500 + p) <= F32_TOL
+
+
+@pytest.mark.parametrize("kind,epb,ks", [("cta", 1, 1), ("cta", 4, 1), ("element", 0, 0)])
+def test_p2_variants_fp64_vs_oracle(kind, epb, ks):
+    import torch
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(2, (5, 3, 4), 0.5, 4.0)
+    k = sem.KERNEL_CTA_TILE if kind == "cta" else sem.KERNEL_ELEMENT
+    sem.sem_set_operator_kernel(ctx, sem.PREC_FP64, k, epb, ks)
+    ut = si.random_vector(ms.n_skeleton, 61)
+    v = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+    sem.sem_apply_condensed(ctx, dev(ut), v, sem.SPACE_TRANSFORMED)
+    assert relerr(host(v), _oracle_apply(ms, 0.5, ut)) <= F64_TOL
+
+
+def test_defaults_and_rejected_variants():
+    from paper_1601_08179_gb300 import sem
+    ctx8, _ = make_pair(8, (2, 2, 2), 1.0)
+    assert sem.sem_get_operator_kernel(ctx8, sem.PREC_FP64)[0] == sem.KERNEL_CTA_TILE
+    assert sem.sem_get_operator_kernel(ctx8, sem.PREC_MIXED)[0] == sem.KERNEL_PLANE
+    ctx2, _ = make_pair(2, (2, 2, 2), 1.0)
+    assert sem.sem_get_operator_kernel(ctx2, sem.PREC_FP64)[0] == sem.KERNEL_ELEMENT
+    ctx16, _ = make_pair(16, (1, 1, 1), 1.0)
+    assert sem.sem_get_operator_kernel(ctx16, sem.PREC_MIXED)[0] == sem.KERNEL_CTA_TILE
+    bad = [(ctx8, sem.PREC_FP64, sem.KERNEL_PLANE, 0, 0),     # FP32-only variants
+           (ctx8, sem.PREC_FP64, sem.KERNEL_WARP, 0, 0),
+           (ctx8, sem.PREC_MIXED, sem.KERNEL_ELEMENT, 0, 0),  # p = 2 only
+           (ctx16, sem.PREC_MIXED, sem.KERNEL_PLANE, 0, 0),   # n = 15 > 8
+           (ctx2, sem.PREC_MIXED, sem.KERNEL_WARP, 0, 0),     # n = 1 < 3
+           (ctx8, sem.PREC_FP64, sem.KERNEL_CTA_TILE, 0, 7),  # epb out of range
+           (ctx8, sem.PREC_FP64, sem.KERNEL_CTA_TILE, 4, 8),  # ks > n
+           (ctx8, sem.PREC_FP64, 9, 0, 0),                    # no such kind
+           (ctx8, 5, sem.KERNEL_AUTO, 0, 0)]                  # no such precision
+    for c, prec, kind, epb, ks in bad:
+        with pytest.raises(sem.SemError) as ei:
+            sem.sem_set_operator_kernel(c, prec, kind, epb, ks)
+        assert ei.value.status == sem.SEM_EINVAL
+    # a rejected call leaves the choice unchanged; AUTO restores the default
+    sem.sem_set_operator_kernel(ctx8, sem.PREC_MIXED, sem.KERNEL_WARP)
+    assert sem.sem_get_operator_kernel(ctx8, sem.PREC_MIXED)[0] == sem.KERNEL_WARP
+    sem.sem_set_operator_kernel(ctx8, sem.PREC_MIXED, sem.KERNEL_AUTO)
+    assert sem.sem_get_operator_kernel(ctx8, sem.PREC_MIXED)[0] == sem.KERNEL_PLANE
+
+
+@pytest.mark.parametrize("kind", ["plane", "warp", "cta"])
+def test_mixed_solve_with_each_fp32_kernel(kind):
+    """The mixed-precision solve (FP32 inner CG, FP64 refinement) reaches the
+    FP64 oracle's solution to the solve bar with each FP32 operator kernel."""
+    import torch
+    from oracle import dense
+    from paper_1601_08179_gb300 import sem
+    p, m, lam, ar = 6, (3, 2, 3), 1.0, 8.0
+    ctx, ms = make_pair(p, m, lam, ar, opts=sem.default_opts(precision=sem.PREC_MIXED))
+    k = {"plane": sem.KERNEL_PLANE, "warp": sem.KERNEL_WARP, "cta": sem.KERNEL_CTA_TILE}[kind]
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, k, 4 if kind == "cta" else 0, 5 if kind == "cta" else 0)
+    X, Y, Z = ms.coords()
+    f = (si.manufactured_f(X, Y, Z, lam) + si.node_noise(X.size, 23).reshape(X.shape)).ravel()
+    u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+    info = sem.sem_solve(ctx, dev(f), u)
+    assert info["refinements"] >= 1
+    assert relerr(host(u), dense.solve_full(ms, lam, f)) <= 1e-9
