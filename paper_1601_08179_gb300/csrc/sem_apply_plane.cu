@@ -174,7 +174,7 @@ __device__ __forceinline__ void plane_gather(const float* __restrict__ u, const 
 // The element operator of one element whose gathered values sit in W
 // (offsets in H); scatter-adds into v and accumulates x^T (A x) into dot.
 template <int N>
-__device__ __forceinline__ void plane_element(const float* W, const int* H, float* __restrict__ v, int jl,
+__device__ __forceinline__ void plane_element(float* W, const int* H, float* __restrict__ v, int jl,
                                               float& dot) {
   using S = PlaneSm<N>;
   constexpr int G = S::G, RS = S::RS, FS = S::FS;
@@ -217,7 +217,7 @@ __device__ __forceinline__ void plane_element(const float* W, const int* H, floa
 
     // ---- walk the y-plane j in k: expansion, D^-1, contractions; x- and
     //      y-face outputs at k
-#pragma unroll 1
+#pragma unroll
     for (int k = 0; k < N; ++k) {
       const float4 qk = *reinterpret_cast<const float4*>(Cf + PQ + 4 * k);
       const float ek = qk.z, gk = qk.w, l3k = Cf[PL3 + k];
@@ -299,16 +299,31 @@ __device__ __forceinline__ void plane_element(const float* W, const int* H, floa
       }
     }
 
+    // ---- z-faces at (j, i).  The outputs of row j are formed in lane j and
+    //      staged in the (no longer needed) z-face rows of shared memory, then
+    //      scattered one row per instruction so each atomic row is contiguous.
+    float szc[4] = {0.f, 0.f, 0.f, 0.f};   // z-face column l: szc[2 sc + sb] = sum_m (c|d)_m F_{4+sc}[m][l]
     if (act) {
-      // ---- z-faces at (j, i)
-      const int oz0 = H[4], oz1 = H[5];
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        const float2 cd = *reinterpret_cast<const float2*>(Cf + PQ + 4 * m);
+        const float f0 = Fp[4 * FS + m * RS + j], f1 = Fp[5 * FS + m * RS + j];
+        szc[0] = fmaf(cd.x, f0, szc[0]);
+        szc[1] = fmaf(cd.y, f0, szc[1]);
+        szc[2] = fmaf(cd.x, f1, szc[2]);
+        szc[3] = fmaf(cd.y, f1, szc[3]);
+      }
+    }
+    __syncwarp();
+    const int oz0 = H[4], oz1 = H[5];
+    if (act) {
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         float xa[RS], xb[RS];     // Ex[0][s][.], Ex[1][s][.] (slots 2 s, 2 s + 1)
         load_row<RS>(W + S::EX + (2 * s) * RS, xa);
         load_row<RS>(W + S::EX + (2 * s + 1) * RS, xb);
         const float ya = ey[2 * s], yb = ey[2 * s + 1];   // Ey[0][s][j], Ey[1][s][j]
-        const int oz = s ? oz1 : oz0;
+        float* orow = W + S::F + (4 + s) * FS + j * RS;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const float own = s ? e5[i] : e4[i], opp = s ? e4[i] : e5[i];
@@ -316,12 +331,23 @@ __device__ __forceinline__ void plane_element(const float* W, const int* H, floa
           o = fmaf(cO[4 + s], opp, o);
           o = fmaf(w0, fmaf(a[i], ya, fmaf(b[i], yb, fmaf(cj, xa[i], dj * xb[i]))), o);
           o -= s ? z5[i] : z4[i];
-          if (oz >= 0) {
-            atomicAdd(v + oz + j * N + i, o);
-            dot = fmaf(own, o, dot);
-          }
+          orow[i] = o;
+          dot = fmaf(own, o, dot);   // a Dirichlet face was gathered as zeros: adds 0
         }
       }
+    }
+    __syncwarp();
+    if (jl < N) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int oz = s ? oz1 : oz0;
+        if (oz >= 0) {
+#pragma unroll
+          for (int t = 0; t < N; ++t) atomicAdd(v + oz + t * N + jl, W[S::F + (4 + s) * FS + t * RS + jl]);
+        }
+      }
+    }
+    if (act) {
       // ---- edges at position l = jl
       float szr[4] = {0.f, 0.f, 0.f, 0.f};   // z-face row j: szr[2 sc + sa] = sum_m (a|b)_m F_{4+sc}[j][m]
 #pragma unroll
@@ -330,19 +356,6 @@ __device__ __forceinline__ void plane_element(const float* W, const int* H, floa
         szr[1] = fmaf(b[m], e4[m], szr[1]);
         szr[2] = fmaf(a[m], e5[m], szr[2]);
         szr[3] = fmaf(b[m], e5[m], szr[3]);
-      }
-      float cm[RS], dm[RS];
-      float szc[4] = {0.f, 0.f, 0.f, 0.f};   // z-face column l: szc[2 sc + sb] = sum_m (c|d)_m F_{4+sc}[m][l]
-#pragma unroll
-      for (int m = 0; m < N; ++m) {
-        const float2 cd = *reinterpret_cast<const float2*>(Cf + PQ + 4 * m);
-        cm[m] = cd.x;
-        dm[m] = cd.y;
-        const float f0 = Fp[4 * FS + m * RS + j], f1 = Fp[5 * FS + m * RS + j];
-        szc[0] = fmaf(cd.x, f0, szc[0]);
-        szc[1] = fmaf(cd.y, f0, szc[1]);
-        szc[2] = fmaf(cd.x, f1, szc[2]);
-        szc[3] = fmaf(cd.y, f1, szc[3]);
       }
       float syr[4] = {0.f, 0.f, 0.f, 0.f};   // y-face row l: syr[2 sb + sa] = sum_m (a|b)_m F_{2+sb}[l][m]
       float sxr[4] = {0.f, 0.f, 0.f, 0.f};   // x-face row l: sxr[2 sa + sb] = sum_m (c|d)_m F_sa[l][m]
@@ -355,8 +368,9 @@ __device__ __forceinline__ void plane_element(const float* W, const int* H, floa
         for (int m = 0; m < N; ++m) {
           syr[2 * f] = fmaf(a[m], yr[m], syr[2 * f]);
           syr[2 * f + 1] = fmaf(b[m], yr[m], syr[2 * f + 1]);
-          sxr[2 * f] = fmaf(cm[m], xr[m], sxr[2 * f]);
-          sxr[2 * f + 1] = fmaf(dm[m], xr[m], sxr[2 * f + 1]);
+          const float2 cd = *reinterpret_cast<const float2*>(Cf + PQ + 4 * m);
+          sxr[2 * f] = fmaf(cd.x, xr[m], sxr[2 * f]);
+          sxr[2 * f + 1] = fmaf(cd.y, xr[m], sxr[2 * f + 1]);
         }
       }
       float Vt[8];
