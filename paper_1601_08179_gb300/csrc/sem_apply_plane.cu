@@ -115,26 +115,70 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
+// Entity offsets are affine in the element coordinates: offset of entity
+// slot r = base + ex sx + ey sy + ez sz, and the entity is on the Dirichlet
+// boundary iff one of the element's boundary flags in `mask` is set (bit 2a:
+// coordinate a is 0, bit 2a + 1: coordinate a is m_a - 1).  Slots as in
+// face_base / edge_base / vert_index (sem_device.cuh).
+struct EntityAffine {
+  int base, sx, sy, sz, mask;
+};
+
+__device__ void entity_affine(const SemGeom& g, int r, EntityAffine* out) {
+  const int n = g.n, n2 = n * n, mx = g.mx, my = g.my;
+  EntityAffine a;
+  if (r < 6) {
+    const int d = r >> 1, s = r & 1;
+    a.sx = n2;
+    if (d == 0) { a.base = (int)g.off[0] + s * n2; a.sy = (mx + 1) * n2; a.sz = (mx + 1) * my * n2; }
+    else if (d == 1) { a.base = (int)g.off[1] + s * mx * n2; a.sy = mx * n2; a.sz = mx * (my + 1) * n2; }
+    else { a.base = (int)g.off[2] + s * mx * my * n2; a.sy = mx * n2; a.sz = mx * my * n2; }
+    a.mask = 1 << (2 * d + s);
+  } else if (r < 18) {
+    const int q = r - 6, grp = q >> 2, s1 = q & 1, s2 = (q >> 1) & 1;
+    a.sx = n;
+    if (grp == 0) {        // x-edge (sb, sc) = (s1, s2): y and z shifted
+      a.base = (int)g.off[3] + (mx * s1 + mx * (my + 1) * s2) * n; a.sy = mx * n; a.sz = mx * (my + 1) * n;
+      a.mask = (1 << (2 + s1)) | (1 << (4 + s2));
+    } else if (grp == 1) { // y-edge (sa, sc): x and z shifted
+      a.base = (int)g.off[4] + (s1 + (mx + 1) * my * s2) * n; a.sy = (mx + 1) * n; a.sz = (mx + 1) * my * n;
+      a.mask = (1 << s1) | (1 << (4 + s2));
+    } else {               // z-edge (sa, sb): x and y shifted
+      a.base = (int)g.off[5] + (s1 + (mx + 1) * s2) * n; a.sy = (mx + 1) * n; a.sz = (mx + 1) * (my + 1) * n;
+      a.mask = (1 << s1) | (1 << (2 + s2));
+    }
+  } else {
+    const int q = r - 18, sa = q & 1, sb = (q >> 1) & 1, sc = q >> 2;
+    a.base = (int)g.off[6] + sa + (mx + 1) * sb + (mx + 1) * (my + 1) * sc;
+    a.sx = 1;
+    a.sy = mx + 1;
+    a.sz = (mx + 1) * (my + 1);
+    a.mask = (1 << sa) | (1 << (2 + sb)) | (1 << (4 + sc));
+  }
+  *out = a;
+}
+
 // Offsets of the element's 26 entities (-1: Dirichlet entity or no element)
 // and its class (fallback for a missing element) into H[0..26].
 template <int G>
-__device__ __forceinline__ void plane_header(const SemGeom& g, const SemClassTables<float>& tab, long long e,
-                                             bool live, int fallback, int jl, int* H) {
+__device__ __forceinline__ void plane_header(const SemGeom& g, const SemClassTables<float>& tab,
+                                             const EntityAffine* ent, int e, bool live, int fallback, int jl,
+                                             int* H) {
   int ex = 0, ey = 0, ez = 0;
-  if (live) elem_visit(g, e, &ex, &ey, &ez);
+  if (live) {   // visiting order of elem_visit, in 32-bit arithmetic
+    if (g.slow == 0) { const int myz = g.my * g.mz; ex = e / myz; const int r = e - ex * myz; ez = r / g.my; ey = r - ez * g.my; }
+    else if (g.slow == 1) { const int mxz = g.mx * g.mz; ey = e / mxz; const int r = e - ey * mxz; ez = r / g.mx; ex = r - ez * g.mx; }
+    else { const int mxy = g.mx * g.my; ez = e / mxy; const int r = e - ez * mxy; ey = r / g.mx; ex = r - ey * g.mx; }
+  }
+  const int bits = (ex == 0) | ((ex == g.mx - 1) << 1) | ((ey == 0) << 2) | ((ey == g.my - 1) << 3) |
+                   ((ez == 0) << 4) | ((ez == g.mz - 1) << 5);
   for (int r = jl; r < 27; r += G) {
     int val;
     if (r == 26) {
       val = live ? elem_class(g, tab, ex, ey, ez) : fallback;
-    } else if (!live) {
-      val = -1;
     } else {
-      bool dir;
-      long long off;
-      if (r < 6) off = face_base(g, ex, ey, ez, r, &dir);
-      else if (r < 18) off = edge_base(g, ex, ey, ez, r - 6, &dir);
-      else off = vert_index(g, ex, ey, ez, r - 18, &dir);
-      val = dir ? -1 : (int)off;
+      const EntityAffine a = ent[r];
+      val = (!live || (bits & a.mask)) ? -1 : a.base + ex * a.sx + ey * a.sy + ez * a.sz;
     }
     H[r] = val;
   }
@@ -323,7 +367,7 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
         load_row<RS>(W + S::EX + (2 * s) * RS, xa);
         load_row<RS>(W + S::EX + (2 * s + 1) * RS, xb);
         const float ya = ey[2 * s], yb = ey[2 * s + 1];   // Ey[0][s][j], Ey[1][s][j]
-        float* orow = W + S::F + (4 + s) * FS + j * RS;
+        float orow[RS];
 #pragma unroll
         for (int i = 0; i < N; ++i) {
           const float own = s ? e5[i] : e4[i], opp = s ? e4[i] : e5[i];
@@ -334,6 +378,12 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
           orow[i] = o;
           dot = fmaf(own, o, dot);   // a Dirichlet face was gathered as zeros: adds 0
         }
+#pragma unroll
+        for (int i = N; i < RS; ++i) orow[i] = 0.f;
+        float* dst = W + S::F + (4 + s) * FS + j * RS;   // row j, 16-byte stores
+#pragma unroll
+        for (int t = 0; t < RS; t += 4)
+          *reinterpret_cast<float4*>(dst + t) = make_float4(orow[t], orow[t + 1], orow[t + 2], orow[t + 3]);
       }
     }
     __syncwarp();
@@ -461,11 +511,14 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
 template <int N>
 __global__ void __launch_bounds__(kPlaneThreads, 4)
 k_tpt_apply_plane(SemGeom g, SemClassTables<float> tab, const float* __restrict__ u, float* __restrict__ v,
-                  double* __restrict__ partials, PcgState* st, int qpw) {
+                  double* __restrict__ partials, PcgState* st) {
   using S = PlaneSm<N>;
   constexpr int G = S::G, EPW = S::EPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ EntityAffine ent[26];
   if (st != nullptr && st->done) return;
+  if (threadIdx.x < 26) entity_affine(g, threadIdx.x, &ent[threadIdx.x]);
+  __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int grp = lane / G, jl = lane - grp * G;
   const int slot_id = wib * EPW + grp, nslots = wpb * EPW;
@@ -475,13 +528,12 @@ k_tpt_apply_plane(SemGeom g, SemClassTables<float> tab, const float* __restrict_
   float* W0 = reinterpret_cast<float*>(smem_raw + (size_t)2 * nslots * kHdr * sizeof(int)) +
               (size_t)slot_id * S::size;                                      // buffer b: W0 + b wstep
   const int hstep = nslots * kHdr, wstep = nslots * S::size;
-  const long long q_begin = ((long long)blockIdx.x * wpb + wib) * qpw;
-  const long long e_first = q_begin * EPW;
-  int nq = 0;
-  if (e_first < g.nelem) {
-    const long long left = (g.nelem - e_first + EPW - 1) / EPW;
-    nq = left < qpw ? (int)left : qpw;
-  }
+  // element groups ("quads") of EPW consecutive elements, split into equal
+  // contiguous ranges over all warps of the grid
+  const long long nq_all = (g.nelem + EPW - 1) / EPW, nw = (long long)gridDim.x * wpb;
+  const long long w = (long long)blockIdx.x * wpb + wib;
+  const long long q_begin = nq_all * w / nw;
+  const int nq = (int)(nq_all * (w + 1) / nw - q_begin);
   int held0 = -1, held1 = -1;   // class in each buffer's coefficient block (equal over the group)
   float dot = 0.f;
 
@@ -490,7 +542,7 @@ k_tpt_apply_plane(SemGeom g, SemClassTables<float> tab, const float* __restrict_
     float* W = W0 + b * wstep;
     const int held = b ? held1 : held0;
     const long long e = (q_begin + qi) * EPW + grp;
-    plane_header<G>(g, tab, e, e < g.nelem, held >= 0 ? held : 0, jl, H);
+    plane_header<G>(g, tab, ent, (int)e, e < g.nelem, held >= 0 ? held : 0, jl, H);
     __syncwarp();
     const int cls = H[26];
     plane_gather<N>(u, tab.plane + (long long)cls * tab.plane_stride, cls != held, H, W, jl);
@@ -545,13 +597,12 @@ void launch_plane_n(const SemGeom& g, const SemClassTables<float>& t, const floa
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_plane<N>, kPlaneThreads, smem);
   if (occ < 1) occ = 1;
-  // element groups ("quads") split evenly over the resident warps
-  const long long cap = (long long)sem_num_sms() * occ * wpb;
+  // one full wave of resident blocks (fewer if there are fewer element groups than warps)
   const long long nq = (g.nelem + S::EPW - 1) / S::EPW;
-  const long long qpw = (nq + cap - 1) / cap;
-  const long long nwarps = (nq + qpw - 1) / qpw;
-  const long long grid = (nwarps + wpb - 1) / wpb;
-  k_tpt_apply_plane<N><<<(int)grid, kPlaneThreads, smem, s>>>(g, t, x, y, partials, st, (int)qpw);
+  long long grid = (long long)sem_num_sms() * occ;
+  const long long need = (nq + wpb - 1) / wpb;
+  if (grid > need) grid = need;
+  k_tpt_apply_plane<N><<<(int)grid, kPlaneThreads, smem, s>>>(g, t, x, y, partials, st);
   sem_count_launch();
 }
 
