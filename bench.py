@@ -173,6 +173,15 @@ def node_field(x, y, z, w: si.Workload, seed: int):
     return np.ascontiguousarray(f.ravel())
 
 
+# DRAM bytes (read + written) of one operator launch, from one ncu capture of
+# the kernel as committed (profiles/k_tpt_apply_*_graded_p8_m32.md); a kernel
+# or workload with no capture reports null.
+TRAFFIC_BYTES = {
+    ("k_tpt_apply_plane<7>", "graded_p8_m32_ar128_lam0"): 43261184 + 0,
+    ("k_tpt_apply<double, 7> (epb 5, ks 7)", "graded_p8_m32_ar128_lam0"): 86415872 + 4352000,
+}
+
+
 def kernel_name(sem, ctx, precision: int, p: int) -> str:
     """Name of the operator kernel in use for one precision."""
     kind, epb, ks = sem.sem_get_operator_kernel(ctx, precision)
@@ -320,7 +329,8 @@ def our_arm(args, rank, world, local_rank):
     if head == "fp64":
         achieved = flops / r["apply_s"] / 1e12
         roof = {"kernel": kernel_name(sem, ctx, sem.PREC_FP64, w.p), "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": TRAFFIC_BYTES.get((kernel_name(sem, ctx, sem.PREC_FP64, w.p), w.name)),
                 "peak_source": "FP64 FMA units x SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
                 "flops_per_launch": flops}
     else:
@@ -331,13 +341,15 @@ def our_arm(args, rank, world, local_rank):
         if t_alu >= t_hbm:
             achieved = flops / r["apply_s"] / 1e12
             roof = {"kernel": kernel_name(sem, ctx, sem.PREC_MIXED, w.p), "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                    "traffic": TRAFFIC_BYTES.get((kernel_name(sem, ctx, sem.PREC_MIXED, w.p), w.name)),
                     "peak_source": "FP32 FMA units x SM clock (152 SMs x 128 FMA/clk x 2.07 GHz)",
                     "flops_per_launch": flops}
         else:
             achieved = 8.0 * nb / r["apply_s"] / 1e9
             roof = {"kernel": kernel_name(sem, ctx, sem.PREC_MIXED, w.p), "bound": "hbm", "achieved": achieved, "peak": HBM_GBS,
-                    "unit": "GB/s", "frac": achieved / HBM_GBS, "traffic": None,
+                    "unit": "GB/s", "frac": achieved / HBM_GBS,
+                    "traffic": TRAFFIC_BYTES.get((kernel_name(sem, ctx, sem.PREC_MIXED, w.p), w.name)),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)", "bytes_per_launch": 8.0 * nb}
     out = {
         "metric": METRIC,
