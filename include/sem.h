@@ -307,14 +307,19 @@ sem_status sem_get_operator_kernel(const sem_ctx* ctx, int precision, int* kind,
 sem_status sem_autotune(sem_ctx* ctx, double* ms_default, double* ms_best);
 
 /* Batched solves (independent problems of any degree and mesh size).
- * sem_batch_create captures, for `count` distinct FP64 contexts with device
+ * sem_batch_create captures, for `count` distinct contexts with device
  * fields f[i] (input) and u[i] (output), ONE CUDA graph: a prologue that
  * condenses every load and initialises every CG (one graph branch per
  * problem), a device-side `while` loop whose body runs opts.check_every CG
  * iterations of every problem in parallel branches followed by a one-thread
- * kernel that ends the loop once no problem is still iterating (bounded by the
+ * kernel that ends the loop once no problem is still running (bounded by the
  * largest maxit), and an epilogue that recovers every interior.  Converged
- * problems' kernels exit at once.  The graph bakes in the context and field
+ * problems' kernels exit at once.  A context may be FP64 or mixed precision
+ * with reliable updates (opts.mixed_scheme 1; scheme 0 is SEM_ENOTSUP): a
+ * mixed problem's loop body first runs its FP64 refinement step when one is
+ * due (its FP32 CG stops itself once its residual has fallen by
+ * opts.reliable_delta), all decided on the device, then FP32 CG iterations;
+ * infos[i].refinements and sem_refine_history report its steps.  The graph bakes in the context and field
  * pointers; create a new batch when they change.  sem_batch_solve launches the
  * graph once on `stream` and fills infos[count] (may be NULL); it returns
  * SEM_ENOCONV or SEM_EBREAKDOWN if any problem failed (all u[i] are written).

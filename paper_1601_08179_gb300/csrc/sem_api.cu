@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <algorithm>
 #include <map>
@@ -98,6 +99,13 @@ struct sem_ctx {
   float *d_dcoef_f = nullptr, *d_dinv_f = nullptr, *d_P32 = nullptr;
   float *d_b32 = nullptr, *d_x32 = nullptr, *d_r32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr;
   PcgState* d_st32 = nullptr;
+  MixedCtl* d_ctl = nullptr;           // device-side refinement control (graph-replayed mixed solves)
+  MixedCtl h_ctl{};                    // host copy of it
+  cudaGraphExec_t graph32m = nullptr;  // one loop trip of the reliable-update mixed solve
+  int graph32m_iters = 0;
+  bool graph32m_prof = false;
+  long long graph32m_launches = 0;
+  PcgState* d_stg = nullptr;           // gate of the FP64 operator in those solves
   SemClassTables<float> tab_f{};
   cudaGraphExec_t graph32 = nullptr;
   int graph32_iters = 0;
@@ -211,6 +219,18 @@ sem_status ensure_mixed(sem_ctx* c) {
   SEM_CUDA(cudaMemsetAsync(c->d_q32, 0, sizeof(float) * g.nb, c->stream));
   launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_P32, c->d_q32, nullptr, nullptr, c->stream);
   SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status ensure_ctl(sem_ctx* c) {
+  if (c->d_ctl != nullptr) return SEM_OK;
+  sem_status st = ensure_mixed(c);
+  if (st != SEM_OK) return st;
+  if (dalloc(&c->d_ctl, 1) != cudaSuccess || dalloc(&c->d_stg, 1) != cudaSuccess)
+    return fail(SEM_ENOMEM, "cannot allocate refinement control");
+  SEM_CUDA(cudaMemsetAsync(c->d_ctl, 0, sizeof(MixedCtl), c->stream));
+  SEM_CUDA(cudaMemsetAsync(c->d_stg, 0, sizeof(PcgState), c->stream));
+  SEM_CUDA(cudaStreamSynchronize(c->stream));
   return SEM_OK;
 }
 
@@ -465,105 +485,124 @@ sem_status pcg_mixed(sem_ctx* c, bool warm, sem_info* info) {
 // the FP32 CG stops) adds the FP32 correction to the FP64 iterate, recomputes the
 // true residual b - A x with the FP64 operator and restarts the FP32
 // recursion from it (rho, |r|^2) without resetting the direction.
+// One loop trip of the reliable-update mixed solve: the refinement step
+// (when due; every kernel gated on the device) and check_every FP32 CG
+// iterations, with event nodes around the FP32 operator when profiling.
+sem_status build_graph32m(sem_ctx* c) {
+  if (c->graph32m != nullptr && c->graph32m_iters == c->opts.check_every && c->graph32m_prof == c->prof)
+    return SEM_OK;
+  while (c->prof && (int)c->pev32.size() < 2 * c->opts.check_every) {
+    cudaEvent_t ev;
+    SEM_CUDA(cudaEventCreate(&ev));
+    c->pev32.push_back(ev);
+  }
+  if (c->graph32m != nullptr) {
+    cudaGraphExecDestroy(c->graph32m);
+    c->graph32m = nullptr;
+  }
+  const SemGeom& g = c->g;
+  cudaGraph_t graph;
+  SEM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  const long long before = sem_launch_total();
+  launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32, c->d_p32,
+                    c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, c->stream);
+  for (int it = 0; it < c->opts.check_every; ++it) {
+    if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it], c->stream, cudaEventRecordExternal);
+    launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, c->stream,
+                            &c->op32);
+    if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it + 1], c->stream, cudaEventRecordExternal);
+    launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32,
+                             c->stream);
+    launch_pcg_dir<float>(g.nb, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, c->stream);
+  }
+  c->graph32m_launches = sem_launch_total() - before;
+  sem_count_launch(-c->graph32m_launches);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph32m, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  c->graph32m_iters = c->opts.check_every;
+  c->graph32m_prof = c->prof;
+  return SEM_OK;
+}
+
+// The first part of a reliable-update mixed solve, d_b -> d_x: ||b||^2 into
+// d_st, r_0 = b - A x_0 (x_0 = d_x when warm, else 0), the FP32 CG on r_0 and
+// the refinement control.  Shared by single and batched solves.
+sem_status mixed_prologue(sem_ctx* c, bool warm, cudaStream_t s) {
+  const long long nb = c->g.nb;
+  SEM_CUDA(cudaMemsetAsync(c->d_q, 0, sizeof(double) * nb, s));
+  launch_ir_residual(nb, c->d_b, c->d_q, c->d_r, c->d_partials, c->d_st, s);   // ||b||^2
+  if (warm) {
+    sem_status st = apply_t(c, c->d_x, c->d_q, s);
+    if (st != SEM_OK) return st;
+    launch_ir_residual(nb, c->d_b, c->d_q, c->d_r, c->d_partials, c->d_stg, s);
+  } else {
+    SEM_CUDA(cudaMemsetAsync(c->d_x, 0, sizeof(double) * nb, s));
+  }
+  launch_scale_to_f32(nb, c->d_r, 1.0, c->d_b32, s);
+  launch_pcg_init<float>(nb, c->d_b32, c->d_r32, c->d_p32, c->d_q32, c->d_x32, c->d_P32, c->d_partials, c->d_st32,
+                         c->opts.rtol, c->opts.maxit, 0, s);
+  launch_mixed_start(c->d_ctl, c->d_st, c->d_st32, c->opts.rtol, c->opts.reliable_delta, c->opts.max_refine, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+// Reliable updates: one FP32 CG kept across the FP64 refinement steps; the
+// step is triggered on the device when the FP32 residual has fallen by
+// reliable_delta and replaces the FP32 residual by the true one (residual
+// replacement, direction kept), all decided by the kernels of
+// launch_mixed_step; the host replays one loop trip per graph launch and
+// reads the control record.  d_b -> d_x.
 sem_status pcg_mixed_reliable(sem_ctx* c, bool warm, sem_info* info) {
   const SemGeom& g = c->g;
   cudaStream_t s = c->stream;
-  sem_status st = ensure_mixed(c);
+  sem_status st = ensure_ctl(c);
   if (st != SEM_OK) return st;
-  st = build_graph32(c);
+  st = build_graph32m(c);
   if (st != SEM_OK) return st;
-  c->refine_hist.clear();
-  if (warm) {
-    st = apply_t(c, c->d_x, c->d_q, s);
-    if (st != SEM_OK) return st;
-  } else {
-    SEM_CUDA(cudaMemsetAsync(c->d_x, 0, sizeof(double) * g.nb, s));
-    SEM_CUDA(cudaMemsetAsync(c->d_q, 0, sizeof(double) * g.nb, s));
-  }
-  SEM_CUDA(cudaMemsetAsync(c->d_t2, 0, sizeof(double) * g.nb, s));
-  launch_ir_residual(g.nb, c->d_b, c->d_t2, c->d_r, c->d_partials, c->d_st, s);
-  SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-  SEM_CUDA(cudaStreamSynchronize(s));
-  const double bb = c->h_st->rr;
-  launch_ir_residual(g.nb, c->d_b, c->d_q, c->d_r, c->d_partials, c->d_st, s);
-  SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-  SEM_CUDA(cudaStreamSynchronize(s));
-  double rr_hi = c->h_st->rr;
-  double rel = bb > 0.0 ? std::sqrt(rr_hi / bb) : 0.0;
-  c->refine_hist.push_back(rel);
-  if (!std::isfinite(rr_hi)) return fail(SEM_EBREAKDOWN, "non-finite residual");
-  int refinements = 0, total = 0;
-  sem_status result = SEM_ENOCONV;
-  if (rel <= c->opts.rtol) {
-    result = SEM_OK;
-  } else {
-    // FP32 CG on A c = r, unscaled; its own stopping target is the global one
-    launch_scale_to_f32(g.nb, c->d_r, 1.0, c->d_b32, s);
-    launch_pcg_init<float>(g.nb, c->d_b32, c->d_r32, c->d_p32, c->d_q32, c->d_x32, c->d_P32, c->d_partials,
-                           c->d_st32, bb > 0 ? c->opts.rtol * std::sqrt(bb / rr_hi) : 1.0, c->opts.maxit, 0, s);
+  st = mixed_prologue(c, warm, s);
+  if (st != SEM_OK) return st;
+  MixedCtl* hc = &c->h_ctl;
+  const int cap = c->opts.maxit / c->opts.check_every + 2 + c->opts.max_refine;
+  int it0 = 0;
+  for (int trip = 0; trip < cap; ++trip) {
+    SEM_CUDA(cudaMemcpyAsync(hc, c->d_ctl, sizeof(MixedCtl), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    if (hc->finished != 0) break;
+    SEM_CUDA(cudaGraphLaunch(c->graph32m, s));
+    sem_count_launch(c->graph32m_launches);
     SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
-    double rr_ref = c->h_st->rr;
-    const double trig = c->opts.reliable_delta * c->opts.reliable_delta;
-    int stalls = 0;
-    double best = rel;
-    const int max_batches = c->opts.maxit / c->opts.check_every + 2 + c->opts.max_refine;
-    for (int b = 0; b < max_batches; ++b) {
-      if (c->h_st->done == 0) {
-        const int it0 = c->h_st->iter;
-        SEM_CUDA(cudaGraphLaunch(c->graph32, s));
-        sem_count_launch(3LL * c->graph32_iters);
-        SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-        SEM_CUDA(cudaStreamSynchronize(s));
-        if (c->graph32_prof) {
-          int worked = c->h_st->iter - it0 + (c->h_st->done == 2 ? 1 : 0);
-          if (worked > c->graph32_iters) worked = c->graph32_iters;
-          for (int it = 0; it < worked; ++it) {
-            float ms = 0.f;
-            SEM_CUDA(cudaEventElapsedTime(&ms, c->pev32[2 * it], c->pev32[2 * it + 1]));
-            c->prof_ms += ms;
-            c->prof_count += 1;
-          }
-        }
+    if (c->graph32m_prof) {
+      int worked = c->h_st->iter - it0 + (c->h_st->done == 2 ? 1 : 0);
+      if (worked > c->graph32m_iters) worked = c->graph32m_iters;
+      if (worked < 0) worked = 0;
+      for (int it = 0; it < worked; ++it) {
+        float ms = 0.f;
+        SEM_CUDA(cudaEventElapsedTime(&ms, c->pev32[2 * it], c->pev32[2 * it + 1]));
+        c->prof_ms += ms;
+        c->prof_count += 1;
       }
-      total = c->h_st->iter;
-      const int done32 = c->h_st->done;
-      if (done32 == 0 && c->h_st->rr > trig * rr_ref) continue;
-      // refinement step: fold the FP32 correction into x, true residual in FP64
-      launch_ir_update(g.nb, c->d_x, c->d_x32, 1.0, s);
-      SEM_CUDA(cudaMemsetAsync(c->d_x32, 0, sizeof(float) * g.nb, s));
-      st = apply_t(c, c->d_x, c->d_q, s);
-      if (st != SEM_OK) return st;
-      launch_ir_residual(g.nb, c->d_b, c->d_q, c->d_r, c->d_partials, c->d_st, s);
-      SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-      SEM_CUDA(cudaStreamSynchronize(s));
-      rr_hi = c->h_st->rr;
-      ++refinements;
-      rel = bb > 0.0 ? std::sqrt(rr_hi / bb) : 0.0;
-      c->refine_hist.push_back(rel);
-      if (!std::isfinite(rr_hi)) { result = SEM_EBREAKDOWN; break; }
-      if (rel <= c->opts.rtol) { result = SEM_OK; break; }
-      if (done32 == 2) { result = SEM_EBREAKDOWN; break; }
-      if (done32 == 3 || refinements >= c->opts.max_refine) break;
-      stalls = rel < 0.9 * best ? 0 : stalls + 1;
-      if (rel < best) best = rel;
-      if (stalls >= 3) break;     // no progress at the FP32 accuracy limit
-      // restart the FP32 recursion from the true residual, keeping the direction
-      launch_scale_to_f32(g.nb, c->d_r, 1.0, c->d_r32, s);
-      launch_pcg_rebase_f32(g.nb, c->d_r32, c->d_P32, c->d_p32, c->d_q32, done32 != 0 ? 1 : 0, c->d_partials,
-                            c->d_st32, s);
-      SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-      SEM_CUDA(cudaStreamSynchronize(s));
-      rr_ref = c->h_st->rr;
     }
+    it0 = c->h_st->iter;
   }
+  // a correction not yet folded in (the loop stopped between refinement steps)
+  launch_ir_update(g.nb, c->d_x, c->d_x32, 1.0, s);
+  SEM_CUDA(cudaMemsetAsync(c->d_x32, 0, sizeof(float) * g.nb, s));
+  SEM_CUDA(cudaMemcpyAsync(hc, c->d_ctl, sizeof(MixedCtl), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  const int last = std::min(hc->refinements, kMixedHist - 1);
+  c->refine_hist.assign(hc->hist, hc->hist + last + 1);
   if (info) {
-    info->iters += total;
-    info->refinements = refinements;
-    info->rel_res = rel;
+    info->iters += c->h_st->iter;
+    info->refinements = hc->refinements;
+    info->rel_res = hc->hist[last];
   }
-  if (result == SEM_EBREAKDOWN) return fail(result, "CG breakdown or non-finite residual in the refinement");
-  if (result != SEM_OK) return fail(result, "refinement did not reach rtol (maxit, max_refine or stagnation)");
+  if (hc->finished == 2) return fail(SEM_EBREAKDOWN, "CG breakdown or non-finite residual in the refinement");
+  if (hc->finished != 1) return fail(SEM_ENOCONV, "refinement did not reach rtol (maxit, max_refine or stagnation)");
   return SEM_OK;
 }
 
@@ -574,8 +613,9 @@ void free_ctx(sem_ctx* c) {
   cudaSetDevice(c->device);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   if (c->graph32) cudaGraphExecDestroy(c->graph32);
+  if (c->graph32m) cudaGraphExecDestroy(c->graph32m);
   void* ptrs32[] = {c->d_dcoef_f, c->d_dinv_f, c->d_P32, c->d_b32, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_st32,
-                    c->d_coef_f, c->d_coef, c->d_plane};
+                    c->d_coef_f, c->d_coef, c->d_plane, c->d_ctl, c->d_stg};
   for (void* p : ptrs32)
     if (p) cudaFree(p);
   for (cudaEvent_t ev : c->pev32) cudaEventDestroy(ev);
@@ -1255,12 +1295,17 @@ sem_status tune_one(sem_ctx* c, const SemClassTables<T>& tab, const T* x, T* y, 
   return SEM_OK;
 }
 
-// Drops the instantiated CG graph of one precision (it holds the operator launch).
+// Drops the instantiated graphs that hold an operator launch of one
+// precision (the mixed loop trip holds both precisions' operators).
 void drop_graph(sem_ctx* c, bool mixed) {
   cudaGraphExec_t& gr = mixed ? c->graph32 : c->graph;
   if (gr) {
     cudaGraphExecDestroy(gr);
     gr = nullptr;
+  }
+  if (c->graph32m) {
+    cudaGraphExecDestroy(c->graph32m);
+    c->graph32m = nullptr;
   }
 }
 
@@ -1346,11 +1391,13 @@ namespace {
 
 // One thread: keep looping while any problem is still iterating (and the
 // safety cap on loop trips is not reached).
-__global__ void k_batch_decide(PcgState* const* states, int count, int* trips, int cap,
+// A problem is still running while its flag is 0 (FP64: the CG state's
+// `done`; mixed: the refinement control's `finished`).
+__global__ void k_batch_decide(const int* const* flags, int count, int* trips, int cap,
                                cudaGraphConditionalHandle handle) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int active = 0;
-  for (int i = 0; i < count; ++i) active |= (states[i]->done == 0);
+  for (int i = 0; i < count; ++i) active |= (*flags[i] == 0);
   const int t = ++(*trips);
   cudaGraphSetConditional(handle, (active && t < cap) ? 1u : 0u);
 }
@@ -1363,7 +1410,7 @@ struct sem_batch {
   std::vector<double*> u;
   std::vector<cudaStream_t> streams;   // [0] orchestrates, [1..count] one per problem
   std::vector<cudaEvent_t> events;
-  PcgState** d_states = nullptr;
+  int** d_flags = nullptr;
   int* d_trips = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long launches_fixed = 0, launches_per_trip = 0;
@@ -1377,7 +1424,7 @@ void batch_free(sem_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
-  if (b->d_states) cudaFree(b->d_states);
+  if (b->d_flags) cudaFree(b->d_flags);
   if (b->d_trips) cudaFree(b->d_trips);
   delete b;
 }
@@ -1409,7 +1456,8 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
     if (ctxs[i] == nullptr || f[i] == nullptr || u[i] == nullptr) return fail(SEM_EINVAL, "null context or field");
-    if (ctxs[i]->opts.precision != SEM_PREC_FP64) return fail(SEM_ENOTSUP, "batched solves run in FP64");
+    if (ctxs[i]->opts.precision == SEM_PREC_MIXED && ctxs[i]->opts.mixed_scheme != 1)
+      return fail(SEM_ENOTSUP, "batched mixed-precision solves use reliable updates (mixed_scheme 1)");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(SEM_EINVAL, "a context appears twice in the batch");
   }
@@ -1433,19 +1481,24 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
     b->streams.push_back(st);
     b->events.push_back(ev);
   }
-  std::vector<PcgState*> states(count);
-  int check = 1 << 30, cap = 0;
+  std::vector<int*> flags(count);
+  int check = 1 << 30, cap = 0, refine_cap = 0;
   for (int i = 0; i < count; ++i) {
-    sem_status st = ensure_cubes(ctxs[i]);
+    sem_ctx* c = ctxs[i];
+    sem_status st = ensure_cubes(c);
+    if (st == SEM_OK && c->opts.precision == SEM_PREC_MIXED) st = ensure_ctl(c);
     if (st != SEM_OK) return bail(st);
-    states[i] = ctxs[i]->d_st;
-    check = std::min(check, ctxs[i]->opts.check_every);
-    cap = std::max(cap, ctxs[i]->opts.maxit);
+    flags[i] = c->opts.precision == SEM_PREC_MIXED
+                   ? reinterpret_cast<int*>(reinterpret_cast<char*>(c->d_ctl) + offsetof(MixedCtl, finished))
+                   : reinterpret_cast<int*>(reinterpret_cast<char*>(c->d_st) + offsetof(PcgState, done));
+    check = std::min(check, c->opts.check_every);
+    cap = std::max(cap, c->opts.maxit);
+    if (c->opts.precision == SEM_PREC_MIXED) refine_cap = std::max(refine_cap, c->opts.max_refine);
   }
-  cap = cap / check + 2;
-  if (dalloc(&b->d_states, count) != cudaSuccess || dalloc(&b->d_trips, 1) != cudaSuccess)
+  cap = cap / check + 2 + refine_cap;
+  if (dalloc(&b->d_flags, count) != cudaSuccess || dalloc(&b->d_trips, 1) != cudaSuccess)
     return bail(fail(SEM_ENOMEM, "cannot allocate batch state"));
-  if (cudaMemcpy(b->d_states, states.data(), count * sizeof(PcgState*), cudaMemcpyHostToDevice) != cudaSuccess)
+  if (cudaMemcpy(b->d_flags, flags.data(), count * sizeof(int*), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(SEM_ECUDA, "cannot upload batch state"));
   cudaStream_t s0 = b->streams[0];
   cudaGraph_t pro = nullptr, epi = nullptr, main_g = nullptr;
@@ -1458,11 +1511,16 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
   if (cst == SEM_OK)
     cst = batch_fork_join(b, [&](int i, cudaStream_t si) -> sem_status {
       sem_ctx* c = b->ctxs[i];
+      const long long nb = c->g.nb;
       sem_status st = condense_rhs_t(c, b->f[i], c->d_b, si);
       if (st != SEM_OK) return st;
-      launch_pcg_init<double>(c->g.nb, c->d_b, c->d_r, c->d_p, c->d_q, c->d_x, c->d_P, c->d_partials, c->d_st,
-                              c->opts.rtol, c->opts.maxit, 0, si);
-      return SEM_OK;
+      if (c->opts.precision != SEM_PREC_MIXED) {
+        launch_pcg_init<double>(nb, c->d_b, c->d_r, c->d_p, c->d_q, c->d_x, c->d_P, c->d_partials, c->d_st,
+                                c->opts.rtol, c->opts.maxit, 0, si);
+        return SEM_OK;
+      }
+      // mixed: x = 0, r = b in FP64, the FP32 CG on b32 = r, the refinement control
+      return mixed_prologue(c, false, si);
     });
   e = cudaStreamEndCapture(s0, &pro);
   if (cst != SEM_OK || e != cudaSuccess) {
@@ -1473,6 +1531,7 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
   e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
   cst = e == cudaSuccess ? batch_fork_join(b, [&](int i, cudaStream_t si) -> sem_status {
     sem_ctx* c = b->ctxs[i];
+    if (c->opts.precision == SEM_PREC_MIXED) launch_ir_update(c->g.nb, c->d_x, c->d_x32, 1.0, si);  // 0 once folded
     return recover_t(c, c->d_x, b->u[i], si);
   }) : SEM_ECUDA;
   e = cudaStreamEndCapture(s0, &epi);
@@ -1503,15 +1562,28 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
       cst = batch_fork_join(b, [&](int i, cudaStream_t si) -> sem_status {
         sem_ctx* c = b->ctxs[i];
         const SemGeom& g = c->g;
+        if (c->opts.precision != SEM_PREC_MIXED) {
+          for (int it = 0; it < check; ++it) {
+            launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, si,
+                                     &c->op64);
+            launch_pcg_update<double>(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, si);
+            launch_pcg_dir<double>(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, si);
+          }
+          return SEM_OK;
+        }
+        // mixed: a refinement step when due, then FP32 CG iterations
+        launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32,
+                          c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, si);
         for (int it = 0; it < check; ++it) {
-          launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, si,
-                                   &c->op64);
-          launch_pcg_update<double>(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, si);
-          launch_pcg_dir<double>(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, si);
+          launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, si,
+                                  &c->op32);
+          launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32,
+                                   si);
+          launch_pcg_dir<float>(g.nb, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, si);
         }
         return SEM_OK;
       });
-      k_batch_decide<<<1, 32, 0, s0>>>(b->d_states, count, b->d_trips, cap, handle);
+      k_batch_decide<<<1, 32, 0, s0>>>(b->d_flags, count, b->d_trips, cap, handle);
       sem_count_launch();
       body_launches = sem_launch_total() - lb;
       cudaGraph_t tmp = nullptr;
@@ -1544,9 +1616,14 @@ extern "C" sem_status sem_batch_solve(sem_batch* b, sem_info* infos, void* strea
   SEM_CUDA(cudaGraphLaunch(b->exec, s0));
   const int count = (int)b->ctxs.size();
   std::vector<PcgState> hs(count);
+  std::vector<MixedCtl> hc(count);
   int trips = 0;
-  for (int i = 0; i < count; ++i)
-    SEM_CUDA(cudaMemcpyAsync(&hs[i], b->ctxs[i]->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s0));
+  for (int i = 0; i < count; ++i) {
+    sem_ctx* c = b->ctxs[i];
+    const bool mixed = c->opts.precision == SEM_PREC_MIXED;
+    SEM_CUDA(cudaMemcpyAsync(&hs[i], mixed ? c->d_st32 : c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s0));
+    if (mixed) SEM_CUDA(cudaMemcpyAsync(&hc[i], c->d_ctl, sizeof(MixedCtl), cudaMemcpyDeviceToHost, s0));
+  }
   SEM_CUDA(cudaMemcpyAsync(&trips, b->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s0));
   SEM_CUDA(cudaStreamSynchronize(s0));
   SEM_CUDA(cudaEventRecord(b->events[0], s0));
@@ -1556,11 +1633,25 @@ extern "C" sem_status sem_batch_solve(sem_batch* b, sem_info* infos, void* strea
   sem_status worst = SEM_OK;
   for (int i = 0; i < count; ++i) {
     const PcgState& h = hs[i];
-    sem_status st = h.done == 1 ? SEM_OK : (h.done == 2 ? SEM_EBREAKDOWN : SEM_ENOCONV);
+    sem_ctx* c = b->ctxs[i];
+    sem_status st;
+    double rel;
+    int refinements = 0;
+    if (c->opts.precision == SEM_PREC_MIXED) {
+      const MixedCtl& m = hc[i];
+      st = m.finished == 1 ? SEM_OK : (m.finished == 2 ? SEM_EBREAKDOWN : SEM_ENOCONV);
+      refinements = m.refinements;
+      const int last = std::min(refinements, kMixedHist - 1);
+      rel = m.hist[last];
+      c->refine_hist.assign(m.hist, m.hist + last + 1);
+    } else {
+      st = h.done == 1 ? SEM_OK : (h.done == 2 ? SEM_EBREAKDOWN : SEM_ENOCONV);
+      rel = h.rr0 > 0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+    }
     if (infos) {
       infos[i].iters = h.iter;
-      infos[i].refinements = 0;
-      infos[i].rel_res = h.rr0 > 0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+      infos[i].refinements = refinements;
+      infos[i].rel_res = rel;
       infos[i].t_solve_s = secs;
     }
     if (st != SEM_OK && worst == SEM_OK) worst = st;

@@ -119,11 +119,28 @@ struct PcgState {
   double rr0;        // b^T b, reference of the stopping rule
   double alpha, beta;
   double tol2;       // rtol^2 * rr0 (stop when rr <= tol2)
+  double trig2;      // > 0: stop with done = 4 when rr <= trig2 (refinement trigger)
   int iter;          // iterations done
-  int done;          // 1: converged, 2: breakdown, 3: maxit
+  int done;          // 1: converged, 2: breakdown, 3: maxit, 4: refinement triggered
   int maxit;
   int pad;
   unsigned int counter[4];  // last-block reduction tickets
+};
+
+// Device-side control of one mixed-precision solve (FP32 CG with reliable
+// updates inside FP64 refinement) replayed from a CUDA graph: the refinement
+// kernels read `phase`, the loop decision reads `finished`.
+constexpr int kMixedHist = 64;
+struct MixedCtl {
+  double bb;         // ||b||^2 of the FP64 condensed load
+  double tol2;       // rtol^2 bb
+  double delta2;     // reliable_delta^2
+  double best;       // smallest relative FP64 residual so far
+  double hist[kMixedHist];  // relative FP64 residual after each refinement step ([0]: start)
+  int phase;         // 0: CG iterating, 1: refinement step due, 2: rebase the FP32 CG
+  int finished;      // 0: running, 1: converged, 2: breakdown, 3: maxit, max_refine or stagnation
+  int refinements, max_refine, stalls, restart;
+  unsigned int counter[2];
 };
 
 // ---- host helpers (sem_host.cpp) ----

@@ -365,6 +365,7 @@ k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restri
     st->iter = 0;
     st->maxit = maxit;
     st->alpha = st->beta = 0.0;
+    st->trig2 = 0.0;
     if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) st->done = 2;
     else if (tot[1] <= st->tol2) st->done = 1;
     else st->done = 0;
@@ -419,6 +420,8 @@ k_pcg_update(long long nb, T* __restrict__ x, T* __restrict__ r, const T* __rest
       st->done = 1;
     } else if (it >= st->maxit) {
       st->done = 3;
+    } else if (st->trig2 > 0.0 && tot[1] <= st->trig2) {
+      st->done = 4;              // refinement due: rho (of the previous residual) is kept
     } else {
       st->beta = tot[0] / st->rho;
       st->rho = tot[0];
@@ -494,6 +497,141 @@ k_ir_residual(long long nb, const double* __restrict__ b, const double* __restri
   }
   double v[1] = {rr}, tot[1];
   if (reduce_grid<1>(v, partials, &st->counter[3], tot) && threadIdx.x == 0) st->rr = tot[0];
+}
+
+// ---------------------------------------------------------------------------
+// Device-side refinement control (mixed-precision solves replayed from a graph)
+// ---------------------------------------------------------------------------
+// One loop trip: gate -> fold -> FP64 operator -> residual + decision ->
+// rebase -> direction, then FP32 CG iterations.  Each refinement kernel runs
+// only in its phase; a finished problem runs none of them, and its FP32 CG
+// state stays stopped (done != 0) so the CG kernels exit at once too.
+
+// Start: after ||b||^2 (in st64->rr), the FP64 residual r_0 = b - A x_0 and
+// the FP32 CG initialisation on b32 = r_0.  The FP32 CG stops at the global
+// target rtol^2 ||b||^2.
+__global__ void k_mixed_start(MixedCtl* ctl, const PcgState* st64, PcgState* st32, double rtol, double delta,
+                              int max_refine) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double bb = st64->rr;
+  ctl->bb = bb;
+  ctl->tol2 = rtol * rtol * bb;
+  ctl->delta2 = delta * delta;
+  ctl->hist[0] = bb > 0.0 ? sqrt(st32->rr / bb) : 0.0;
+  ctl->best = ctl->hist[0];
+  st32->tol2 = ctl->tol2;
+  ctl->phase = 0;
+  ctl->refinements = 0;
+  ctl->max_refine = max_refine;
+  ctl->stalls = 0;
+  ctl->restart = 0;
+  ctl->counter[0] = ctl->counter[1] = 0u;
+  if (!isfinite(bb) || !isfinite(st32->rr)) {
+    ctl->finished = 2;
+  } else if (bb == 0.0 || st32->rr <= ctl->tol2) {
+    ctl->finished = 1;
+  } else {
+    ctl->finished = 0;
+    st32->trig2 = ctl->delta2 * st32->rr;
+  }
+  if (ctl->finished != 0 && st32->done == 0) st32->done = 1;
+}
+
+// Top of a loop trip: a refinement step is due once the FP32 CG has stopped
+// (triggered, converged in FP32, maxit or breakdown).  gate->done = 0 lets the
+// FP64 operator run.
+__global__ void k_mixed_gate(MixedCtl* ctl, const PcgState* st32, PcgState* gate) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int d = st32->done;
+  const bool refine = ctl->finished == 0 && d != 0;
+  ctl->phase = refine ? 1 : 0;
+  ctl->restart = d != 4;
+  gate->done = refine ? 0 : 1;
+}
+
+// Phase 1: x += x32 (the FP32 correction), x32 = 0, q = 0 (output of the FP64 operator).
+__global__ void __launch_bounds__(kVecThreads)
+k_mixed_fold(long long nb, double* __restrict__ x, float* __restrict__ x32, double* __restrict__ q,
+             const MixedCtl* ctl) {
+  if (ctl->phase != 1) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    x[i] += (double)x32[i];
+    x32[i] = 0.f;
+    q[i] = 0.0;
+  }
+}
+
+// Phase 1: r = b - A x in FP64 and the decision of the refinement step (the
+// rules of the host-driven loop): converged, broken down, out of iterations or
+// refinement steps, stalled (three steps without a 10 % gain), else rebase.
+__global__ void __launch_bounds__(kVecThreads)
+k_mixed_residual(long long nb, const double* __restrict__ b, const double* __restrict__ Ax, double* __restrict__ r,
+                 double* __restrict__ partials, MixedCtl* ctl, const PcgState* st32) {
+  if (ctl->phase != 1) return;
+  double rr = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = b[i] - Ax[i];
+    r[i] = ri;
+    rr = fma(ri, ri, rr);
+  }
+  double v[1] = {rr}, tot[1];
+  if (reduce_grid<1>(v, partials, &ctl->counter[0], tot) && threadIdx.x == 0) {
+    const double rr_hi = tot[0];
+    const int k = ++ctl->refinements;
+    const double rel = ctl->bb > 0.0 ? sqrt(rr_hi / ctl->bb) : 0.0;
+    ctl->hist[k < kMixedHist ? k : kMixedHist - 1] = rel;
+    const int d = st32->done;
+    if (!isfinite(rr_hi)) {
+      ctl->finished = 2;
+    } else if (rr_hi <= ctl->tol2) {
+      ctl->finished = 1;
+    } else if (d == 2) {
+      ctl->finished = 2;
+    } else if (d == 3 || k >= ctl->max_refine) {
+      ctl->finished = 3;
+    } else {
+      ctl->stalls = rel < 0.9 * ctl->best ? 0 : ctl->stalls + 1;
+      if (rel < ctl->best) ctl->best = rel;
+      if (ctl->stalls >= 3) ctl->finished = 3;
+      else ctl->phase = 2;
+    }
+  }
+}
+
+// Phase 2: the FP32 CG continues from the true residual (residual
+// replacement): r32 = r, rho' = r32 . P r32, beta = rho' / rho (0 when the
+// direction restarts), rr, the next trigger delta^2 rr, done = 0.
+__global__ void __launch_bounds__(kVecThreads)
+k_mixed_rebase(long long nb, const double* __restrict__ r, const float* __restrict__ P, float* __restrict__ r32,
+               double* __restrict__ partials, MixedCtl* ctl, PcgState* st32) {
+  if (ctl->phase != 2) return;
+  float rz = 0.f, rr = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    const float ri = (float)r[i];
+    r32[i] = ri;
+    rz = fmaf(ri, P[i] * ri, rz);
+    rr = fmaf(ri, ri, rr);
+  }
+  double v[2] = {(double)rz, (double)rr}, tot[2];
+  if (reduce_grid<2>(v, partials, &ctl->counter[1], tot) && threadIdx.x == 0) {
+    st32->beta = ctl->restart ? 0.0 : tot[0] / st32->rho;
+    st32->rho = tot[0];
+    st32->rr = tot[1];
+    st32->trig2 = ctl->delta2 * tot[1];
+    st32->done = (isfinite(tot[0]) && isfinite(tot[1])) ? 0 : 2;
+  }
+}
+
+// Phase 2: p = P r32 + beta p, q = 0 (the direction step of the replaced residual).
+__global__ void __launch_bounds__(kVecThreads)
+k_mixed_dir(long long nb, const float* __restrict__ r32, float* __restrict__ p, float* __restrict__ q,
+            const float* __restrict__ P, const MixedCtl* ctl, const PcgState* st32) {
+  if (ctl->phase != 2 || st32->done != 0) return;
+  const float beta = (float)st32->beta;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
+    p[i] = fmaf(beta, p[i], P[i] * r32[i]);
+    q[i] = 0.f;
+  }
 }
 
 __global__ void k_scale_to_f32(long long nb, const double* __restrict__ in, double scale, float* __restrict__ out) {
@@ -629,6 +767,26 @@ void launch_pcg_init(long long nb, const T* b, T* r, T* p, T* q, T* x, const T* 
   k_pcg_init<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, b, r, p, q, x, P, partials, st, rtol, maxit, keep_x,
                                                          keep_x);
   sem_count_launch();
+}
+
+void launch_mixed_start(MixedCtl* ctl, const PcgState* st64, PcgState* st32, double rtol, double delta,
+                        int max_refine, cudaStream_t s) {
+  k_mixed_start<<<1, 32, 0, s>>>(ctl, st64, st32, rtol, delta, max_refine);
+  sem_count_launch();
+}
+
+void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& tab, const ApplyConfig* op,
+                       const double* rhs, double* x, double* q, double* r, float* x32, float* r32, float* p32,
+                       float* q32, const float* P32, double* partials, MixedCtl* ctl, PcgState* st32,
+                       PcgState* gate, cudaStream_t s) {
+  const long long nb = g.nb;
+  k_mixed_gate<<<1, 32, 0, s>>>(ctl, st32, gate);
+  k_mixed_fold<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, x32, q, ctl);
+  launch_tpt_apply<double>(g, b, tab, x, q, partials, gate, s, op);
+  k_mixed_residual<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, rhs, q, r, partials, ctl, st32);
+  k_mixed_rebase<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, P32, r32, partials, ctl, st32);
+  k_mixed_dir<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r32, p32, q32, P32, ctl, st32);
+  sem_count_launch(5);
 }
 
 template <typename T>

@@ -124,6 +124,17 @@ void launch_ir_update(long long nb, double* x, const float* c, double scale, cud
 void launch_cast_f32(long long n, const double* in, float* out, cudaStream_t s);
 // Reliable update of the FP32 CG: rho = r.P r and rr = r.r from the new r, q = 0,
 // done = 0; with restart also p = P r.
+// Device-side refinement of a mixed-precision solve (one MixedCtl per
+// problem): start after the FP64 residual r = b (st64) and the FP32 CG
+// initialisation; one step per loop trip (gate, fold x32 into x, FP64
+// operator q = A x through `gate`, residual and decision, rebase and
+// direction of the FP32 CG), each kernel running only in its phase.
+void launch_mixed_start(MixedCtl* ctl, const PcgState* st64, PcgState* st32, double rtol, double delta,
+                        int max_refine, cudaStream_t s);
+void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& tab, const ApplyConfig* op,
+                       const double* rhs, double* x, double* q, double* r, float* x32, float* r32, float* p32,
+                       float* q32, const float* P32, double* partials, MixedCtl* ctl, PcgState* st32,
+                       PcgState* gate, cudaStream_t s);
 void launch_pcg_rebase_f32(long long nb, const float* r, const float* P, float* p, float* q, int restart,
                            double* partials, PcgState* st, cudaStream_t s);
 

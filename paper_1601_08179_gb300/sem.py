@@ -365,7 +365,8 @@ class SemBatch:
         st = lib().sem_batch_solve(self.handle, infos, _stream(stream, self.fs[0]))
         if check:
             _check(st)
-        return st, [dict(iters=i.iters, rel_res=i.rel_res, t_solve_s=i.t_solve_s) for i in infos]
+        return st, [dict(iters=i.iters, refinements=i.refinements, rel_res=i.rel_res, t_solve_s=i.t_solve_s)
+                    for i in infos]
 
     def __del__(self):
         try:

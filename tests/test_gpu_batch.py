@@ -99,3 +99,88 @@ def test_autotune_keeps_results(p, m, mixed):
     F = local.rhs_full(ms, f)
     r = (local.apply_full(ms, 2.0, host(w)) - F)[ms.free_mask]
     assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(F[ms.free_mask])
+
+
+def _mixed():
+    from paper_1601_08179_gb300 import sem
+    return sem.default_opts(precision=sem.PREC_MIXED)
+
+
+def test_mixed_batch_matches_oracle_and_single_solves():
+    """Mixed-precision problems (FP32 CG, reliable updates, FP64 refinement
+    decided on the device) and FP64 problems in one graph: every solution
+    within the solve bar of the dense oracle; the relative FP64 residual of
+    each refinement step (sem_refine_history) ends below rtol."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    probs = _small_batch(count=10, seed=73)
+    ctxs, fs, us, refs, mixed = [], [], [], [], []
+    for k, (p, m, lam, ar, seed) in enumerate(probs):
+        mx = k % 4 != 3                       # every fourth problem stays FP64
+        ctx, ms = make_pair(p, m, lam, ar, opts=_mixed() if mx else None)
+        f = si.node_noise(ms.n_global, seed)
+        ctxs.append(ctx)
+        fs.append(dev(f))
+        us.append(torch.full((ctx.n_nodes,), np.nan, dtype=torch.float64, device="cuda"))
+        refs.append(dense.solve_full(ms, lam, f))
+        mixed.append(mx)
+    batch = sem.SemBatch(ctxs, fs, us)
+    for rep in range(2):
+        st, infos = batch.solve()
+        for k, (u, ref) in enumerate(zip(us, refs)):
+            assert relerr(host(u), ref) <= 1e-9, k
+            assert infos[k]["rel_res"] <= 1e-10, k
+            assert (infos[k]["refinements"] >= 1) == mixed[k], k
+    for k, c in enumerate(ctxs):
+        if not mixed[k]:
+            continue
+        hist = sem.sem_refine_history(c)
+        assert len(hist) == infos[k]["refinements"] + 1 and abs(hist[0] - 1.0) < 1e-5
+        assert hist[-1] <= 1e-10 and all(b < a for a, b in zip(hist, hist[1:])), hist
+        u1 = torch.empty_like(us[k])
+        sem.sem_solve(c, fs[k], u1)           # the single (host-looped) mixed solve of the same problem
+        assert relerr(host(us[k]), host(u1)) <= 1e-9, k
+
+
+def test_mixed_batch_heterogeneous_64_beats_fp64():
+    """The 64-problem workload in mixed precision: every problem converges to
+    rtol in FP64 terms, agrees with the FP64 batch to the solve bar, and the
+    mixed batch takes less time than the FP64 batch."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    work = si.batched_problems()
+    batches, outs, times = {}, {}, {}
+    for form in ("fp64", "mixed"):
+        ctxs, fs, us = [], [], []
+        for w in work:
+            hx, hy, hz = w.widths()
+            c = sem.sem_setup(w.p, hx, hy, hz, w.lam, _mixed() if form == "mixed" else None)
+            ctxs.append(c)
+            fs.append(dev(si.node_noise(c.n_nodes, w.seed)))
+            us.append(torch.empty(c.n_nodes, dtype=torch.float64, device="cuda"))
+        b = sem.SemBatch(ctxs, fs, us)
+        b.solve()                             # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, infos = b.solve()
+        e1.record()
+        torch.cuda.synchronize()
+        times[form] = e0.elapsed_time(e1)
+        assert all(i["rel_res"] <= 1e-10 for i in infos), form
+        batches[form], outs[form] = (b, ctxs, fs), us
+    print("batch ms: fp64 %.1f, mixed %.1f" % (times["fp64"], times["mixed"]))
+    for k in range(len(work)):
+        assert relerr(host(outs["mixed"][k]), host(outs["fp64"][k])) <= 1e-8, k
+    assert times["mixed"] < times["fp64"]
+
+
+def test_mixed_batch_rejects_restarted_scheme():
+    import torch
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(4, (2, 2, 2), 1.0, opts=sem.default_opts(precision=sem.PREC_MIXED, mixed_scheme=0))
+    f = dev(si.node_noise(ms.n_global, 5))
+    u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+    with pytest.raises(sem.SemError) as ei:
+        sem.SemBatch([ctx], [f], [u])
+    assert ei.value.status == sem.SEM_ENOTSUP

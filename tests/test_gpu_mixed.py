@@ -50,7 +50,7 @@ def test_mixed_error_per_refinement_step(scheme):
     ref = dense.solve_full(ms, lam, f)
     u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
     errs = []
-    for k in range(1, 6):
+    for k in range(1, 13):
         sem.sem_set_opts(ctx, _mixed(max_refine=k, mixed_scheme=scheme))
         info = sem.sem_solve(ctx, dev(f), u, check=False)
         errs.append(relerr(host(u), ref))
