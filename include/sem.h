@@ -103,7 +103,7 @@ typedef struct {
                          zero at every refinement step (classical refinement) */
   double reliable_delta; /* MIXED scheme 1: a refinement step is taken when the FP32
                          recursive residual has fallen by this factor since the
-                         previous step (default 0.03) */
+                         previous step (default 0.01) */
 } sem_opts;
 
 /* Result of a solve. */

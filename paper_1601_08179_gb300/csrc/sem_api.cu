@@ -653,7 +653,7 @@ void sem_default_opts(sem_opts* o) {
   o->inner_rtol = 1e-4;
   o->max_refine = 40;
   o->mixed_scheme = 1;
-  o->reliable_delta = 0.03;
+  o->reliable_delta = 0.01;
 }
 
 static sem_status check_opts(const sem_opts* o) {
