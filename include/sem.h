@@ -104,6 +104,13 @@ typedef struct {
   double reliable_delta; /* MIXED scheme 1: a refinement step is taken when the FP32
                          recursive residual has fallen by this factor since the
                          previous step (default 0.01) */
+  int fused_cg;       /* MIXED: 1 = each FP32 CG iteration of a single solve is one
+                         cooperative kernel (operator, vector updates, dot products,
+                         stopping tests) when the FP32 operator kernel is
+                         SEM_KERNEL_PLANE and the device supports cooperative
+                         launches; 0 = three kernels (default: faster on GB300 at
+                         p = 4 and 8, where the operator's 12 warps per SM limit the
+                         fused kernel's streaming phases) */
 } sem_opts;
 
 /* Result of a solve. */
@@ -295,6 +302,9 @@ sem_status sem_set_operator_kernel(sem_ctx* ctx, int precision, int kind, int ep
 /* The kernel in use for one precision, SEM_KERNEL_AUTO resolved: *kind, and
  * for a CTA tile *epb, *ks (else 0; epb, ks may be NULL). */
 sem_status sem_get_operator_kernel(const sem_ctx* ctx, int precision, int* kind, int* epb, int* ks);
+/* *fused = 1 if the FP32 CG iterations of this context's mixed solves run as
+ * one fused kernel each (see sem_opts.fused_cg), else 0. */
+sem_status sem_cg_fused(const sem_ctx* ctx, int* fused);
 
 /* Autotuner: times the operator kernel for this context's degree, mesh and
  * precision (FP32 when opts.precision is MIXED, else FP64) over the variants

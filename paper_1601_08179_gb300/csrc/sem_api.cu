@@ -101,6 +101,7 @@ struct sem_ctx {
   PcgState* d_st32 = nullptr;
   MixedCtl* d_ctl = nullptr;           // device-side refinement control (graph-replayed mixed solves)
   MixedCtl h_ctl{};                    // host copy of it
+  bool coop = false;                   // the device supports cooperative launches
   cudaGraphExec_t graph32m = nullptr;  // one loop trip of the reliable-update mixed solve
   int graph32m_iters = 0;
   bool graph32m_prof = false;
@@ -109,6 +110,7 @@ struct sem_ctx {
   SemClassTables<float> tab_f{};
   cudaGraphExec_t graph32 = nullptr;
   int graph32_iters = 0;
+  long long graph32_launches = 0;
   bool graph32_prof = false;
   std::vector<cudaEvent_t> pev32;
   std::vector<double> refine_hist;     // ||b - A x_k|| / ||b|| after each refinement step
@@ -218,6 +220,7 @@ sem_status ensure_mixed(sem_ctx* c) {
   // operator kernel attributes outside any capture
   SEM_CUDA(cudaMemsetAsync(c->d_q32, 0, sizeof(float) * g.nb, c->stream));
   launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_P32, c->d_q32, nullptr, nullptr, c->stream);
+  if (c->d_plane != nullptr) prepare_cg_plane(g);   // kernel attributes outside any capture
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -278,6 +281,35 @@ sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
   launch_tpt_apply<double>(c->g, c->h1.basis, c->tab, x, y, nullptr, nullptr, s,
                            &c->op64);
   SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+// Whether the FP32 CG iterations run as one fused cooperative kernel (single
+// solves; a batch's parallel branches keep the three-kernel form, so that no
+// two cooperative grids compete for residency).
+bool fused_f32(const sem_ctx* c) {
+  if (!c->opts.fused_cg || !c->coop || !plane_supported(c->g.n)) return false;
+  const int kind = c->op32.kind == kApplyAuto ? sem_apply_default_kind(c->g.n, 4) : c->op32.kind;
+  return kind == kApplyPlane;
+}
+
+// One FP32 CG iteration on the context's FP32 vectors (st32), as one fused
+// kernel or as operator + update + direction; e0/e1 (may be null) become
+// event nodes around the operator (the fused kernel when fused).
+sem_status cg_iter_f32(sem_ctx* c, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, bool allow_fused = true) {
+  const SemGeom& g = c->g;
+  if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
+  if (allow_fused && fused_f32(c)) {
+    const cudaError_t e = launch_cg_plane(g, c->tab_f, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32,
+                                          c->d_partials, c->d_st32, s);
+    if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("fused CG iteration: ") + cudaGetErrorString(e));
+    if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+    return SEM_OK;
+  }
+  launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, s, &c->op32);
+  if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+  launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32, s);
+  launch_pcg_dir<float>(g.nb, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, s);
   return SEM_OK;
 }
 
@@ -377,17 +409,16 @@ sem_status build_graph32(sem_ctx* c) {
   cudaGraph_t graph;
   SEM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   const long long before = sem_launch_total();
-  for (int it = 0; it < c->opts.check_every; ++it) {
-    if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it], c->stream, cudaEventRecordExternal);
-    launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, c->stream,
-                            &c->op32);
-    if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it + 1], c->stream, cudaEventRecordExternal);
-    launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32,
-                             c->stream);
-    launch_pcg_dir<float>(g.nb, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, c->stream);
-  }
-  sem_count_launch(-(sem_launch_total() - before));
+  sem_status cst = SEM_OK;
+  for (int it = 0; it < c->opts.check_every && cst == SEM_OK; ++it)
+    cst = cg_iter_f32(c, c->stream, c->prof ? c->pev32[2 * it] : nullptr, c->prof ? c->pev32[2 * it + 1] : nullptr);
+  c->graph32_launches = sem_launch_total() - before;
+  sem_count_launch(-c->graph32_launches);
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (cst != SEM_OK) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    return cst;
+  }
   if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   e = cudaGraphInstantiate(&c->graph32, graph, 0);
   cudaGraphDestroy(graph);
@@ -445,7 +476,7 @@ sem_status pcg_mixed(sem_ctx* c, bool warm, sem_info* info) {
     for (int b = 0; b < c->opts.maxit / c->opts.check_every + 2 && c->h_st->done == 0; ++b) {
       const int it0 = c->h_st->iter;
       SEM_CUDA(cudaGraphLaunch(c->graph32, s));
-      sem_count_launch(3LL * c->graph32_iters);
+      sem_count_launch(c->graph32_launches);
       SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
       SEM_CUDA(cudaStreamSynchronize(s));
       if (c->graph32_prof) {
@@ -506,18 +537,16 @@ sem_status build_graph32m(sem_ctx* c) {
   const long long before = sem_launch_total();
   launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32, c->d_p32,
                     c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, c->stream);
-  for (int it = 0; it < c->opts.check_every; ++it) {
-    if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it], c->stream, cudaEventRecordExternal);
-    launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, c->stream,
-                            &c->op32);
-    if (c->prof) cudaEventRecordWithFlags(c->pev32[2 * it + 1], c->stream, cudaEventRecordExternal);
-    launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32,
-                             c->stream);
-    launch_pcg_dir<float>(g.nb, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, c->stream);
-  }
+  sem_status cst = SEM_OK;
+  for (int it = 0; it < c->opts.check_every && cst == SEM_OK; ++it)
+    cst = cg_iter_f32(c, c->stream, c->prof ? c->pev32[2 * it] : nullptr, c->prof ? c->pev32[2 * it + 1] : nullptr);
   c->graph32m_launches = sem_launch_total() - before;
   sem_count_launch(-c->graph32m_launches);
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  if (cst != SEM_OK) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    return cst;
+  }
   if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   e = cudaGraphInstantiate(&c->graph32m, graph, 0);
   cudaGraphDestroy(graph);
@@ -654,6 +683,7 @@ void sem_default_opts(sem_opts* o) {
   o->max_refine = 40;
   o->mixed_scheme = 1;
   o->reliable_delta = 0.01;
+  o->fused_cg = 0;
 }
 
 static sem_status check_opts(const sem_opts* o) {
@@ -665,6 +695,7 @@ static sem_status check_opts(const sem_opts* o) {
   if (o->max_refine < 1) return fail(SEM_EINVAL, "max_refine must be >= 1");
   if (o->mixed_scheme != 0 && o->mixed_scheme != 1) return fail(SEM_EINVAL, "mixed_scheme must be 0 or 1");
   if (!(o->reliable_delta > 0.0 && o->reliable_delta < 1.0)) return fail(SEM_EINVAL, "reliable_delta must be in (0, 1)");
+  if (o->fused_cg != 0 && o->fused_cg != 1) return fail(SEM_EINVAL, "fused_cg must be 0 or 1");
   return SEM_OK;
 }
 
@@ -686,6 +717,11 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
 
   sem_ctx* c = new sem_ctx();
   cudaGetDevice(&c->device);
+  {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    c->coop = coop != 0;
+  }
   c->opts = o;
   c->lambda = lambda;
   std::string err;
@@ -828,6 +864,12 @@ sem_status sem_set_opts(sem_ctx* c, const sem_opts* opts) {
   if (opts) o = *opts;
   sem_status vs = check_opts(&o);
   if (vs != SEM_OK) return vs;
+  if (o.fused_cg != c->opts.fused_cg) {   // the FP32 CG graphs hold the iteration's kernels
+    if (c->graph32) cudaGraphExecDestroy(c->graph32);
+    if (c->graph32m) cudaGraphExecDestroy(c->graph32m);
+    c->graph32 = nullptr;
+    c->graph32m = nullptr;
+  }
   c->opts = o;
   return SEM_OK;
 }
@@ -1368,6 +1410,13 @@ extern "C" sem_status sem_set_operator_kernel(sem_ctx* c, int precision, int kin
   return SEM_OK;
 }
 
+extern "C" sem_status sem_cg_fused(const sem_ctx* c, int* fused) {
+  t_err.clear();
+  if (c == nullptr || fused == nullptr) return fail(SEM_EINVAL, "null argument");
+  *fused = fused_f32(c) ? 1 : 0;
+  return SEM_OK;
+}
+
 extern "C" sem_status sem_get_operator_kernel(const sem_ctx* c, int precision, int* kind, int* epb, int* ks) {
   t_err.clear();
   if (c == nullptr || kind == nullptr) return fail(SEM_EINVAL, "null argument");
@@ -1575,11 +1624,8 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
         launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32,
                           c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, si);
         for (int it = 0; it < check; ++it) {
-          launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, si,
-                                  &c->op32);
-          launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32,
-                                   si);
-          launch_pcg_dir<float>(g.nb, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, si);
+          const sem_status st = cg_iter_f32(c, si, nullptr, nullptr, false);
+          if (st != SEM_OK) return st;
         }
         return SEM_OK;
       });

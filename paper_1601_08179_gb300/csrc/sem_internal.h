@@ -125,6 +125,10 @@ struct PcgState {
   int maxit;
   int pad;
   unsigned int counter[4];  // last-block reduction tickets
+  unsigned int bar_count;   // grid barrier of the fused CG iteration kernel
+  unsigned int bar_gen;
+  int bar_timeout;          // set when a barrier wait gave up (the solve reports a breakdown)
+  int pad2;
 };
 
 // Device-side control of one mixed-precision solve (FP32 CG with reliable

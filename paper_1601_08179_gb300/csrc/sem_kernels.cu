@@ -366,6 +366,8 @@ k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restri
     st->maxit = maxit;
     st->alpha = st->beta = 0.0;
     st->trig2 = 0.0;
+    st->bar_count = 0u;
+    st->bar_timeout = 0;
     if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) st->done = 2;
     else if (tot[1] <= st->tol2) st->done = 1;
     else st->done = 0;

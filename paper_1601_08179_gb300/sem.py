@@ -35,7 +35,8 @@ class SemError(RuntimeError):
 class sem_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double)]
+                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double),
+                ("fused_cg", ctypes.c_int)]
 
 
 class sem_info(ctypes.Structure):
@@ -81,6 +82,7 @@ def lib():
         "sem_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(sem_info), _P]),
         "sem_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "sem_set_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "sem_cg_fused": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
         "sem_get_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "sem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -114,7 +116,7 @@ def exported_symbols():
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
             "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_set_operator_kernel",
-            "sem_get_operator_kernel", "sem_batch_create", "sem_batch_solve",
+            "sem_get_operator_kernel", "sem_cg_fused", "sem_batch_create", "sem_batch_solve",
             "sem_batch_destroy", "sem_solve_batch",
             "sem_profile_enable",
             "sem_profile_read", "sem_launch_count",
@@ -336,6 +338,13 @@ def sem_get_operator_kernel(ctx: SemContext, precision: int):
     _check(lib().sem_get_operator_kernel(ctx.handle, int(precision), ctypes.byref(k), ctypes.byref(e),
                                          ctypes.byref(s)))
     return k.value, e.value, s.value
+
+
+def sem_cg_fused(ctx: SemContext) -> bool:
+    """Whether the FP32 CG iterations of mixed solves run as one fused kernel each."""
+    f = ctypes.c_int()
+    _check(lib().sem_cg_fused(ctx.handle, ctypes.byref(f)))
+    return bool(f.value)
 
 
 def sem_autotune(ctx: SemContext):
