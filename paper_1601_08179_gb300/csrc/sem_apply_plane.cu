@@ -115,49 +115,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int K>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
-// Entity offsets are affine in the element coordinates: offset of entity
-// slot r = base + ex sx + ey sy + ez sz, and the entity is on the Dirichlet
-// boundary iff one of the element's boundary flags in `mask` is set (bit 2a:
-// coordinate a is 0, bit 2a + 1: coordinate a is m_a - 1).  Slots as in
-// face_base / edge_base / vert_index (sem_device.cuh).
-struct EntityAffine {
-  int base, sx, sy, sz, mask;
-};
-
-__device__ void entity_affine(const SemGeom& g, int r, EntityAffine* out) {
-  const int n = g.n, n2 = n * n, mx = g.mx, my = g.my;
-  EntityAffine a;
-  if (r < 6) {
-    const int d = r >> 1, s = r & 1;
-    a.sx = n2;
-    if (d == 0) { a.base = (int)g.off[0] + s * n2; a.sy = (mx + 1) * n2; a.sz = (mx + 1) * my * n2; }
-    else if (d == 1) { a.base = (int)g.off[1] + s * mx * n2; a.sy = mx * n2; a.sz = mx * (my + 1) * n2; }
-    else { a.base = (int)g.off[2] + s * mx * my * n2; a.sy = mx * n2; a.sz = mx * my * n2; }
-    a.mask = 1 << (2 * d + s);
-  } else if (r < 18) {
-    const int q = r - 6, grp = q >> 2, s1 = q & 1, s2 = (q >> 1) & 1;
-    a.sx = n;
-    if (grp == 0) {        // x-edge (sb, sc) = (s1, s2): y and z shifted
-      a.base = (int)g.off[3] + (mx * s1 + mx * (my + 1) * s2) * n; a.sy = mx * n; a.sz = mx * (my + 1) * n;
-      a.mask = (1 << (2 + s1)) | (1 << (4 + s2));
-    } else if (grp == 1) { // y-edge (sa, sc): x and z shifted
-      a.base = (int)g.off[4] + (s1 + (mx + 1) * my * s2) * n; a.sy = (mx + 1) * n; a.sz = (mx + 1) * my * n;
-      a.mask = (1 << s1) | (1 << (4 + s2));
-    } else {               // z-edge (sa, sb): x and y shifted
-      a.base = (int)g.off[5] + (s1 + (mx + 1) * s2) * n; a.sy = (mx + 1) * n; a.sz = (mx + 1) * (my + 1) * n;
-      a.mask = (1 << s1) | (1 << (2 + s2));
-    }
-  } else {
-    const int q = r - 18, sa = q & 1, sb = (q >> 1) & 1, sc = q >> 2;
-    a.base = (int)g.off[6] + sa + (mx + 1) * sb + (mx + 1) * (my + 1) * sc;
-    a.sx = 1;
-    a.sy = mx + 1;
-    a.sz = (mx + 1) * (my + 1);
-    a.mask = (1 << sa) | (1 << (2 + sb)) | (1 << (4 + sc));
-  }
-  *out = a;
-}
-
 // Offsets of the element's 26 entities (-1: Dirichlet entity or no element)
 // and its class (fallback for a missing element) into H[0..26].
 template <int G>

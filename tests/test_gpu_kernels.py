@@ -186,3 +186,25 @@ def test_fused_cg_only_with_the_plane_kernel():
     assert not sem.sem_cg_fused(ctx16)          # the CTA-tile kernel at n = 15
     ctx0, _ = make_pair(8, (2, 2, 2), 1.0, opts=sem.default_opts(precision=sem.PREC_MIXED))
     assert not sem.sem_cg_fused(ctx0)           # three kernels by default
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 8, 12])
+def test_f32_apply_entrywise_high_aspect_ratio(p):
+    """FP32 operator on an x-graded mesh of aspect ratio 128 (metric factors
+    d_1 : d_2 up to ~1.6e4 within one element), entry by entry (floor 1e-3 of
+    the largest entry), so a coefficient formed with cancellation in FP32 shows
+    even where the 2-norm would hide it.  The bar grows with the degree: the
+    primary and condensed parts cancel more at high n and aspect ratio
+    (measured worst entries ~2e-5 at p <= 8, ~3e-4 at p = 12)."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    m = {2: (12, 3, 2), 3: (10, 3, 2), 5: (8, 2, 2), 8: (8, 2, 2), 12: (6, 1, 1)}[p]
+    ctx, ms = make_pair(p, m, 0.0, 128.0)
+    ut = si.random_vector(ms.n_skeleton, 600 + p).astype(np.float32).astype(np.float64)
+    v = torch.empty(ctx.nb, dtype=torch.float32, device="cuda")
+    sem.sem_apply_condensed_f32(ctx, torch.tensor(ut, dtype=torch.float32, device="cuda"), v)
+    got, ref = host(v), _oracle_apply(ms, 0.0, ut)
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    worst = float(np.max(np.abs(got - ref) / scale))
+    print(f"p={p}: worst entry-wise error {worst:.2e}")
+    assert worst <= (1e-4 if p <= 9 else 1e-3)
