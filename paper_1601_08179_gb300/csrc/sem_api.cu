@@ -308,8 +308,8 @@ sem_status cg_iter_f32(sem_ctx* c, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e
   }
   launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, s, &c->op32);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-  launch_pcg_update<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32, s);
-  launch_pcg_dir<float>(g.nb, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, s);
+  launch_pcg_update<float>(g.nb, c->d_r32, c->d_q32, c->d_P32, c->d_partials, c->d_st32, s);
+  launch_pcg_dir<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, s);
   return SEM_OK;
 }
 
@@ -336,8 +336,8 @@ sem_status build_graph(sem_ctx* c) {
     launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, c->stream,
                              &c->op64);
     if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it + 1], c->stream, cudaEventRecordExternal);
-    launch_pcg_update(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, c->stream);
-    launch_pcg_dir(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, c->stream);
+    launch_pcg_update(g.nb, c->d_r, c->d_q, c->d_P, c->d_partials, c->d_st, c->stream);
+    launch_pcg_dir(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, c->stream);
   }
   sem_count_launch(-(sem_launch_total() - before));   // counted at replay instead
   cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
@@ -384,6 +384,8 @@ sem_status pcg_fp64(sem_ctx* c, bool warm, sem_info* info) {
       }
     }
   }
+  launch_pcg_flush<double>(g.nb, c->d_x, c->d_p, c->d_st, s);   // the last x += alpha p
+  SEM_CUDA(cudaGetLastError());
   const PcgState& h = *c->h_st;
   if (info) {
     info->iters += h.iter;
@@ -494,6 +496,7 @@ sem_status pcg_mixed(sem_ctx* c, bool warm, sem_info* info) {
     total += inner;
     ++refinements;
     if (c->h_st->done == 2 && inner == 0) { result = SEM_EBREAKDOWN; break; }
+    launch_pcg_flush<float>(g.nb, c->d_x32, c->d_p32, c->d_st32, s);
     launch_ir_update(g.nb, c->d_x, c->d_x32, norm, s);
     st = apply_t(c, c->d_x, c->d_q, s);
     if (st != SEM_OK) return st;
@@ -618,6 +621,7 @@ sem_status pcg_mixed_reliable(sem_ctx* c, bool warm, sem_info* info) {
     it0 = c->h_st->iter;
   }
   // a correction not yet folded in (the loop stopped between refinement steps)
+  launch_pcg_flush<float>(g.nb, c->d_x32, c->d_p32, c->d_st32, s);
   launch_ir_update(g.nb, c->d_x, c->d_x32, 1.0, s);
   SEM_CUDA(cudaMemsetAsync(c->d_x32, 0, sizeof(float) * g.nb, s));
   SEM_CUDA(cudaMemcpyAsync(hc, c->d_ctl, sizeof(MixedCtl), cudaMemcpyDeviceToHost, s));
@@ -1580,7 +1584,12 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
   e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
   cst = e == cudaSuccess ? batch_fork_join(b, [&](int i, cudaStream_t si) -> sem_status {
     sem_ctx* c = b->ctxs[i];
-    if (c->opts.precision == SEM_PREC_MIXED) launch_ir_update(c->g.nb, c->d_x, c->d_x32, 1.0, si);  // 0 once folded
+    if (c->opts.precision == SEM_PREC_MIXED) {   // whatever is not folded in yet (0 once folded)
+      launch_pcg_flush<float>(c->g.nb, c->d_x32, c->d_p32, c->d_st32, si);
+      launch_ir_update(c->g.nb, c->d_x, c->d_x32, 1.0, si);
+    } else {
+      launch_pcg_flush<double>(c->g.nb, c->d_x, c->d_p, c->d_st, si);
+    }
     return recover_t(c, c->d_x, b->u[i], si);
   }) : SEM_ECUDA;
   e = cudaStreamEndCapture(s0, &epi);
@@ -1615,8 +1624,8 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
           for (int it = 0; it < check; ++it) {
             launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, si,
                                      &c->op64);
-            launch_pcg_update<double>(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_partials, c->d_st, si);
-            launch_pcg_dir<double>(g.nb, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, si);
+            launch_pcg_update<double>(g.nb, c->d_r, c->d_q, c->d_P, c->d_partials, c->d_st, si);
+            launch_pcg_dir<double>(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, si);
           }
           return SEM_OK;
         }

@@ -648,6 +648,7 @@ k_cg_plane(SemGeom g, SemClassTables<float> tab, float* __restrict__ x, float* _
       st->beta = t2[0] / rho;
       st->rho = t2[0];
     }
+    st->xpend = 0;                 // x was updated above
     st->done = done;
   }
   if (done != 0) return;

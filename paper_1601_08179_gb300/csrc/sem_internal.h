@@ -128,6 +128,8 @@ struct PcgState {
   unsigned int bar_count;   // grid barrier of the fused CG iteration kernel
   unsigned int bar_gen;
   int bar_timeout;          // set when a barrier wait gave up (the solve reports a breakdown)
+  int xpend;                // 1: the last x += alpha p is still owed (the update stopped the CG)
+  unsigned int flush_ticket;
   int pad2;
 };
 
@@ -144,6 +146,7 @@ struct MixedCtl {
   int phase;         // 0: CG iterating, 1: refinement step due, 2: rebase the FP32 CG
   int finished;      // 0: running, 1: converged, 2: breakdown, 3: maxit, max_refine or stagnation
   int refinements, max_refine, stalls, restart;
+  int xpend;         // the FP32 CG's owed x32 += alpha p32, taken over by the fold of this step
   unsigned int counter[2];
 };
 

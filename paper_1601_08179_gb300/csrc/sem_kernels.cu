@@ -368,17 +368,22 @@ k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restri
     st->trig2 = 0.0;
     st->bar_count = 0u;
     st->bar_timeout = 0;
+    st->xpend = 0;
+    st->flush_ticket = 0u;
     if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) st->done = 2;
     else if (tot[1] <= st->tol2) st->done = 1;
     else st->done = 0;
   }
 }
 
+// r -= alpha q, rho' = r . P r, rr = r . r and the stopping tests.  The
+// matching x += alpha p is done by k_pcg_dir (which reads p anyway); when
+// this kernel stops the CG it is owed (st->xpend) and applied by
+// k_pcg_flush or by the refinement fold.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-k_pcg_update(long long nb, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-             const T* __restrict__ q, const T* __restrict__ P, double* __restrict__ partials,
-             PcgState* st) {
+k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* __restrict__ P,
+             double* __restrict__ partials, PcgState* st) {
   if (st->done) return;
   constexpr int W = 16 / sizeof(T);
   using V = Pack<T, W>;
@@ -387,24 +392,19 @@ k_pcg_update(long long nb, T* __restrict__ x, T* __restrict__ r, const T* __rest
   const long long nv = nb / W;
   const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
   for (long long iv = g0; iv < nv; iv += gs) {
-    V xv = reinterpret_cast<const V*>(x)[iv];
     V rv = reinterpret_cast<const V*>(r)[iv];
-    const V pv = reinterpret_cast<const V*>(p)[iv];
     const V qv = reinterpret_cast<const V*>(q)[iv];
     const V Pv = reinterpret_cast<const V*>(P)[iv];
 #pragma unroll
     for (int c = 0; c < W; ++c) {
-      xv.v[c] = fma(alpha, pv.v[c], xv.v[c]);
       const T ri = fma(-alpha, qv.v[c], rv.v[c]);
       rv.v[c] = ri;
       rz = fma(ri, Pv.v[c] * ri, rz);
       rr = fma(ri, ri, rr);
     }
-    reinterpret_cast<V*>(x)[iv] = xv;
     reinterpret_cast<V*>(r)[iv] = rv;
   }
   for (long long i = nv * W + g0; i < nb; i += gs) {
-    x[i] = fma(alpha, p[i], x[i]);
     const T ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
     rz = fma(ri, P[i] * ri, rz);
@@ -416,46 +416,75 @@ k_pcg_update(long long nb, T* __restrict__ x, T* __restrict__ r, const T* __rest
     st->iter = it;
     st->rho_new = tot[0];
     st->rr = tot[1];
+    int done = 0;
     if (!isfinite(tot[0]) || !isfinite(tot[1])) {
-      st->done = 2;
+      done = 2;
     } else if (tot[1] <= st->tol2) {
-      st->done = 1;
+      done = 1;
     } else if (it >= st->maxit) {
-      st->done = 3;
+      done = 3;
     } else if (st->trig2 > 0.0 && tot[1] <= st->trig2) {
-      st->done = 4;              // refinement due: rho (of the previous residual) is kept
+      done = 4;              // refinement due: rho (of the previous residual) is kept
     } else {
       st->beta = tot[0] / st->rho;
       st->rho = tot[0];
     }
+    st->xpend = done != 0 ? 1 : 0;
+    st->done = done;
   }
 }
 
+// x += alpha p (the update of this iteration), then p = P r + beta p and q = 0.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-k_pcg_dir(long long nb, const T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
+k_pcg_dir(long long nb, T* __restrict__ x, const T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
           const T* __restrict__ P, PcgState* st) {
   if (st->done) return;
   constexpr int W = 16 / sizeof(T);
   using V = Pack<T, W>;
-  const T beta = (T)st->beta;
+  const T alpha = (T)st->alpha, beta = (T)st->beta;
   const long long nv = nb / W;
   const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
   V zero;
 #pragma unroll
   for (int c = 0; c < W; ++c) zero.v[c] = T(0);
   for (long long iv = g0; iv < nv; iv += gs) {
+    V xv = reinterpret_cast<const V*>(x)[iv];
     const V rv = reinterpret_cast<const V*>(r)[iv];
     const V Pv = reinterpret_cast<const V*>(P)[iv];
     V pv = reinterpret_cast<const V*>(p)[iv];
 #pragma unroll
-    for (int c = 0; c < W; ++c) pv.v[c] = fma(beta, pv.v[c], Pv.v[c] * rv.v[c]);
+    for (int c = 0; c < W; ++c) {
+      xv.v[c] = fma(alpha, pv.v[c], xv.v[c]);
+      pv.v[c] = fma(beta, pv.v[c], Pv.v[c] * rv.v[c]);
+    }
+    reinterpret_cast<V*>(x)[iv] = xv;
     reinterpret_cast<V*>(p)[iv] = pv;
     reinterpret_cast<V*>(q)[iv] = zero;
   }
   for (long long i = nv * W + g0; i < nb; i += gs) {
+    x[i] = fma(alpha, p[i], x[i]);
     p[i] = fma(beta, p[i], P[i] * r[i]);
     q[i] = T(0);
+  }
+}
+
+// The owed x += alpha p of a CG that stopped in k_pcg_update (no-op
+// otherwise); the last block clears the flag, so a second call adds nothing.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads)
+k_pcg_flush(long long nb, T* __restrict__ x, const T* __restrict__ p, PcgState* st) {
+  if (!st->xpend) return;
+  const T alpha = (T)st->alpha;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(alpha, p[i], x[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->flush_ticket, 1u) == gridDim.x - 1) {
+      st->xpend = 0;
+      st->flush_ticket = 0u;
+    }
   }
 }
 
@@ -542,22 +571,28 @@ __global__ void k_mixed_start(MixedCtl* ctl, const PcgState* st64, PcgState* st3
 // Top of a loop trip: a refinement step is due once the FP32 CG has stopped
 // (triggered, converged in FP32, maxit or breakdown).  gate->done = 0 lets the
 // FP64 operator run.
-__global__ void k_mixed_gate(MixedCtl* ctl, const PcgState* st32, PcgState* gate) {
+__global__ void k_mixed_gate(MixedCtl* ctl, PcgState* st32, PcgState* gate) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int d = st32->done;
   const bool refine = ctl->finished == 0 && d != 0;
   ctl->phase = refine ? 1 : 0;
   ctl->restart = d != 4;
   gate->done = refine ? 0 : 1;
+  if (refine) {   // the fold applies the CG's owed x32 += alpha p32
+    ctl->xpend = st32->xpend;
+    st32->xpend = 0;
+  }
 }
 
-// Phase 1: x += x32 (the FP32 correction), x32 = 0, q = 0 (output of the FP64 operator).
+// Phase 1: x += x32 (the FP32 correction, with the CG's owed alpha p32),
+// x32 = 0, q = 0 (output of the FP64 operator).
 __global__ void __launch_bounds__(kVecThreads)
-k_mixed_fold(long long nb, double* __restrict__ x, float* __restrict__ x32, double* __restrict__ q,
-             const MixedCtl* ctl) {
+k_mixed_fold(long long nb, double* __restrict__ x, float* __restrict__ x32, const float* __restrict__ p32,
+             double* __restrict__ q, const MixedCtl* ctl, const PcgState* st32) {
   if (ctl->phase != 1) return;
+  const float a = ctl->xpend ? (float)st32->alpha : 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
-    x[i] += (double)x32[i];
+    x[i] += (double)fmaf(a, p32[i], x32[i]);
     x32[i] = 0.f;
     q[i] = 0.0;
   }
@@ -783,7 +818,7 @@ void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables
                        PcgState* gate, cudaStream_t s) {
   const long long nb = g.nb;
   k_mixed_gate<<<1, 32, 0, s>>>(ctl, st32, gate);
-  k_mixed_fold<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, x32, q, ctl);
+  k_mixed_fold<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, x32, p32, q, ctl, st32);
   launch_tpt_apply<double>(g, b, tab, x, q, partials, gate, s, op);
   k_mixed_residual<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, rhs, q, r, partials, ctl, st32);
   k_mixed_rebase<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, P32, r32, partials, ctl, st32);
@@ -792,24 +827,29 @@ void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables
 }
 
 template <typename T>
-void launch_pcg_update(long long nb, T* x, T* r, const T* p, const T* q, const T* P, double* partials,
-                       PcgState* st, cudaStream_t s) {
-  k_pcg_update<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, r, p, q, P, partials, st);
+void launch_pcg_update(long long nb, T* r, const T* q, const T* P, double* partials, PcgState* st, cudaStream_t s) {
+  k_pcg_update<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, q, P, partials, st);
   sem_count_launch();
 }
 
 template <typename T>
-void launch_pcg_dir(long long nb, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s) {
-  k_pcg_dir<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, p, q, P, st);
+void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s) {
+  k_pcg_dir<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, r, p, q, P, st);
+  sem_count_launch();
+}
+
+template <typename T>
+void launch_pcg_flush(long long nb, T* x, const T* p, PcgState* st, cudaStream_t s) {
+  k_pcg_flush<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, p, st);
   sem_count_launch();
 }
 
 #define SEM_INST_VEC(T)                                                                                       \
   template void launch_pcg_init<T>(long long, const T*, T*, T*, T*, T*, const T*, double*, PcgState*, double, \
                                    int, int, cudaStream_t);                                                   \
-  template void launch_pcg_update<T>(long long, T*, T*, const T*, const T*, const T*, double*, PcgState*,     \
-                                     cudaStream_t);                                                           \
-  template void launch_pcg_dir<T>(long long, const T*, T*, T*, const T*, PcgState*, cudaStream_t);
+  template void launch_pcg_update<T>(long long, T*, const T*, const T*, double*, PcgState*, cudaStream_t);     \
+  template void launch_pcg_dir<T>(long long, T*, const T*, T*, T*, const T*, PcgState*, cudaStream_t);         \
+  template void launch_pcg_flush<T>(long long, T*, const T*, PcgState*, cudaStream_t);
 SEM_INST_VEC(double)
 SEM_INST_VEC(float)
 

@@ -116,13 +116,16 @@ void launch_unpack(const SemGeom& g, const double* uB, double* full, int zero_di
 template <typename T>
 void launch_pcg_init(long long nb, const T* b, T* r, T* p, T* q, T* x, const T* P, double* partials,
                      PcgState* st, double rtol, int maxit, int keep_x, cudaStream_t s);
-// alpha from st: x += alpha p, r -= alpha q; rho_new = r.P r, rr = r.r; convergence test.
+// alpha from st: r -= alpha q; rho_new = r.P r, rr = r.r; convergence test.
+// When it stops the CG, the iteration's x += alpha p is owed (st->xpend).
 template <typename T>
-void launch_pcg_update(long long nb, T* x, T* r, const T* p, const T* q, const T* P, double* partials,
-                       PcgState* st, cudaStream_t s);
-// p = P r + beta p, q = 0.
+void launch_pcg_update(long long nb, T* r, const T* q, const T* P, double* partials, PcgState* st, cudaStream_t s);
+// x += alpha p, then p = P r + beta p, q = 0.
 template <typename T>
-void launch_pcg_dir(long long nb, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s);
+void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s);
+// Applies an owed x += alpha p (no-op when none is owed; idempotent).
+template <typename T>
+void launch_pcg_flush(long long nb, T* x, const T* p, PcgState* st, cudaStream_t s);
 
 // Iterative refinement: r = b - Ax and st->rr = r.r (FP64); out = (float)(in * scale);
 // x += scale * c.
