@@ -288,7 +288,7 @@ sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
 // solves; a batch's parallel branches keep the three-kernel form, so that no
 // two cooperative grids compete for residency).
 bool fused_f32(const sem_ctx* c) {
-  if (!c->opts.fused_cg || !c->coop || !plane_supported(c->g.n)) return false;
+  if (!c->opts.fused_cg || !c->coop || c->g.n < 2 || c->g.n > 8) return false;   // one-row plane kernel only
   const int kind = c->op32.kind == kApplyAuto ? sem_apply_default_kind(c->g.n, 4) : c->op32.kind;
   return kind == kApplyPlane;
 }

@@ -678,6 +678,450 @@ k_cg_plane(SemGeom g, SemClassTables<float> tab, float* __restrict__ x, float* _
   for (long long i = nv * 4 + t0; i < nb; i += ts) p[i] = fmaf(bf, p[i], P[i] * r[i]);
 }
 
+// ---------------------------------------------------------------------------
+// Two-chunk variant for 9 <= n <= 15: one element per warp, lane (c, j) owns
+// the half-row i in [8c, 8c + 8) of y-plane j (16 lanes per half).  The
+// x-contraction adds the two halves (one shuffle); the y-contraction is a
+// reduce-scatter over the 16 planes of a half (halving on lane bits 2, 1, 0,
+// then the pair differing in bit 3), which leaves the sums for position
+// l = 8c + (j & 7) on lanes j = 0..7 of half c: those lanes own everything
+// indexed by a position (y-face outputs, edges, the line sums along k).
+// Face rows are padded to 16 floats and the padding is zero-filled by the
+// gather, so the lanes of the short second half compute exact zeros there.
+// ---------------------------------------------------------------------------
+template <int N>
+struct Plane2Sm {
+  static constexpr int RS = 16;
+  static constexpr int FS = N * RS;
+  static constexpr int F = 0;
+  static constexpr int EX = 6 * FS;            // x-edges [4][RS], y-edges [4][RS]
+  static constexpr int EZ = EX + 8 * RS;       // z-edges [N][4]
+  static constexpr int VT = EZ + 4 * N;        // vertices [8]
+  static constexpr int C = VT + 8;             // class coefficient block (plane_layout, rs = 16)
+  static constexpr int PCS = 5 * RS + 4 * N + 36;
+  static constexpr int size = (C + PCS + 3) & ~3;
+  static_assert(EZ % 4 == 0 && VT % 4 == 0 && C % 4 == 0, "16-byte alignment");
+};
+
+template <int N>
+__device__ __forceinline__ void plane2_gather(const float* __restrict__ u, const float* cls_src, bool load_cls,
+                                              const int* H, float* W, int lane) {
+  using S = Plane2Sm<N>;
+  const int half = lane >> 4, col = lane & 15;
+#pragma unroll
+  for (int slot = 0; slot < 6; ++slot) {
+    const int off = H[slot];
+#pragma unroll
+    for (int rp = 0; rp < N; rp += 2) {
+      const int row = rp + half;
+      if (row < N) {
+        const bool ok = off >= 0 && col < N;
+        cp_async4(W + S::F + slot * S::FS + row * S::RS + col, ok ? u + off + row * N + col : u, ok);
+      }
+    }
+  }
+#pragma unroll
+  for (int sp = 0; sp < 12; sp += 2) {
+    const int slot = sp + half, off = H[6 + slot];
+    const bool ok = off >= 0 && col < N;
+    if (slot < 8) cp_async4(W + S::EX + slot * S::RS + col, ok ? u + off + col : u, ok);
+    else if (col < N) cp_async4(W + S::EZ + 4 * col + (slot - 8), ok ? u + off + col : u, ok);
+  }
+  if (lane < 8) {
+    const int off = H[18 + lane];
+    cp_async4(W + S::VT + lane, off >= 0 ? u + off : u, off >= 0);
+  }
+  if (load_cls)
+    for (int r = 4 * lane; r < S::PCS; r += 4 * 32) cp_async16(W + S::C + r, cls_src + r);
+}
+
+template <int N>
+__device__ __forceinline__ void plane2_element(float* W, const int* H, float* __restrict__ v, int lane,
+                                               float& dot) {
+  using S = Plane2Sm<N>;
+  constexpr int RS = S::RS, FS = S::FS;
+  constexpr int PA = 0, PB = RS, PL1 = 2 * RS, PL2 = 3 * RS, PL3 = 4 * RS, PQ = 5 * RS, PS = 5 * RS + 4 * N;
+  const float* Fp = W + S::F;
+  const float* Cf = W + S::C;
+  const int c = lane >> 4, jj = lane & 15, i0 = 8 * c;
+  const bool actj = jj < N;                   // planes past n mirror plane n-1 and contribute zeros
+  const int j = actj ? jj : N - 1;
+  const int l = i0 + (jj & 7);                // position owned for y-faces and edges
+  const bool actl = jj < 8 && l < N;
+  const int lc = actl ? l : N - 1;
+
+  const float w0 = Cf[PS + 32], w02 = Cf[PS + 33], d0 = Cf[PS + 34];
+  float a[8], b[8], l1[8], e4[8], e5[8];
+  load_row<8>(Cf + PA + i0, a);
+  load_row<8>(Cf + PB + i0, b);
+  load_row<8>(Cf + PL1 + i0, l1);
+  load_row<8>(Fp + 4 * FS + j * RS + i0, e4);   // z-face rows j, this half
+  load_row<8>(Fp + 5 * FS + j * RS + i0, e5);
+  const float4 qj = *reinterpret_cast<const float4*>(Cf + PQ + 4 * j);
+  const float cj = actj ? qj.x : 0.f, dj = actj ? qj.y : 0.f;
+  const float l2j = Cf[PL2 + j], sj = d0 + l2j;
+  const float al = Cf[PA + lc], bl = Cf[PB + lc], l1l = Cf[PL1 + lc];
+  float ey[4], ex[4];   // Ey[sa][sc][j] (x-faces of plane j), Ex[sb][sc][l] (y-faces, x-edges at l)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ey[q] = W[S::EX + (4 + q) * RS + j];
+    ex[q] = W[S::EX + q * RS + lc];
+  }
+  float fc[6], cO[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    cO[q] = Cf[PS + q];
+    fc[q] = Cf[PS + 6 + q];
+  }
+  float z4[8], z5[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) z4[t] = z5[t] = 0.f;
+  // line sums along k for the edges at l: sx[2 sa + sc] = sum_k (e|g)_k F_sa[k][l],
+  // sy[2 sb + sc] = sum_k (e|g)_k F_{2+sb}[k][l]
+  float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f};
+  const int ox0 = H[0], ox1 = H[1], oy0 = H[2], oy1 = H[3];
+
+#pragma unroll 1
+  for (int k = 0; k < N; ++k) {
+    const float4 qk = *reinterpret_cast<const float4*>(Cf + PQ + 4 * k);
+    const float ek = qk.z, gk = qk.w, l3k = Cf[PL3 + k];
+    const float4 ezk = *reinterpret_cast<const float4*>(W + S::EZ + 4 * k);
+    const float A = Fp[k * RS + j], B = Fp[FS + k * RS + j];
+    const float Al = Fp[k * RS + lc], Bl = Fp[FS + k * RS + lc];
+    const float Cl = Fp[2 * FS + k * RS + lc], Dl = Fp[3 * FS + k * RS + lc];
+    float Cr[8], Dr[8];
+    load_row<8>(Fp + 2 * FS + k * RS + i0, Cr);
+    load_row<8>(Fp + 3 * FS + k * RS + i0, Dr);
+    const float sjk = sj + l3k;
+    float X0 = 0.f, X1 = 0.f;
+    float P0[8], P1[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      float x = a[t] * A;
+      x = fmaf(b[t], B, x);
+      x = fmaf(cj, Cr[t], x);
+      x = fmaf(dj, Dr[t], x);
+      x = fmaf(ek, e4[t], x);
+      x = fmaf(gk, e5[t], x);
+      const float w = x * rcp_approx(sjk + l1[t]);
+      X0 = fmaf(a[t], w, X0);
+      X1 = fmaf(b[t], w, X1);
+      z4[t] = fmaf(ek, w, z4[t]);
+      z5[t] = fmaf(gk, w, z5[t]);
+      P0[t] = cj * w;
+      P1[t] = dj * w;
+    }
+    X0 += __shfl_xor_sync(0xffffffffu, X0, 16);   // both halves of the row
+    X1 += __shfl_xor_sync(0xffffffffu, X1, 16);
+    halve<4, 8>(P0, P1, jj);
+    halve<2, 8>(P0, P1, jj);
+    halve<1, 8>(P0, P1, jj);
+    const float Y0 = P0[0] + __shfl_xor_sync(0xffffffffu, P0[0], 8);
+    const float Y1 = P1[0] + __shfl_xor_sync(0xffffffffu, P1[0], 8);
+    sx[0] = fmaf(ek, Al, sx[0]);
+    sx[1] = fmaf(gk, Al, sx[1]);
+    sx[2] = fmaf(ek, Bl, sx[2]);
+    sx[3] = fmaf(gk, Bl, sx[3]);
+    sy[0] = fmaf(ek, Cl, sy[0]);
+    sy[1] = fmaf(gk, Cl, sy[1]);
+    sy[2] = fmaf(ek, Dl, sy[2]);
+    sy[3] = fmaf(gk, Dl, sy[3]);
+    if (c == 0 && actj) {
+      const int kj = k * N + j;
+      const float bx = w0 * (l2j + l3k);
+      float o = (fc[0] + bx) * A;
+      o = fmaf(cO[0], B, o);
+      o = fmaf(w0, fmaf(cj, ezk.x, fmaf(dj, ezk.z, fmaf(ek, ey[0], gk * ey[2]))), o);
+      o -= X0;
+      if (ox0 >= 0) {
+        atomicAdd(v + ox0 + kj, o);
+        dot = fmaf(A, o, dot);
+      }
+      o = (fc[1] + bx) * B;
+      o = fmaf(cO[1], A, o);
+      o = fmaf(w0, fmaf(cj, ezk.y, fmaf(dj, ezk.w, fmaf(ek, ey[1], gk * ey[3]))), o);
+      o -= X1;
+      if (ox1 >= 0) {
+        atomicAdd(v + ox1 + kj, o);
+        dot = fmaf(B, o, dot);
+      }
+    }
+    if (actl) {
+      const int kl = k * N + l;
+      const float by = w0 * (l1l + l3k);
+      float o = (fc[2] + by) * Cl;
+      o = fmaf(cO[2], Dl, o);
+      o = fmaf(w0, fmaf(al, ezk.x, fmaf(bl, ezk.y, fmaf(ek, ex[0], gk * ex[2]))), o);
+      o -= Y0;
+      if (oy0 >= 0) {
+        atomicAdd(v + oy0 + kl, o);
+        dot = fmaf(Cl, o, dot);
+      }
+      o = (fc[3] + by) * Dl;
+      o = fmaf(cO[3], Cl, o);
+      o = fmaf(w0, fmaf(al, ezk.z, fmaf(bl, ezk.w, fmaf(ek, ex[1], gk * ex[3]))), o);
+      o -= Y1;
+      if (oy1 >= 0) {
+        atomicAdd(v + oy1 + kl, o);
+        dot = fmaf(Dl, o, dot);
+      }
+    }
+  }
+
+  // ---- the z-face line sums at l (rows and columns of the z-faces), before
+  //      the z-face rows are reused for staging the outputs
+  float szr[4] = {0.f, 0.f, 0.f, 0.f};   // z-face row l: szr[2 sc + sa] = sum_m (a|b)_m F_{4+sc}[l][m]
+  float szc[4] = {0.f, 0.f, 0.f, 0.f};   // z-face column l: szc[2 sc + sb] = sum_m (c|d)_m F_{4+sc}[m][l]
+  if (actl) {
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      const float am = Cf[PA + m], bm = Cf[PB + m];
+      const float2 cd = *reinterpret_cast<const float2*>(Cf + PQ + 4 * m);
+      const float r4 = Fp[4 * FS + l * RS + m], r5 = Fp[5 * FS + l * RS + m];
+      const float c4 = Fp[4 * FS + m * RS + l], c5 = Fp[5 * FS + m * RS + l];
+      szr[0] = fmaf(am, r4, szr[0]);
+      szr[1] = fmaf(bm, r4, szr[1]);
+      szr[2] = fmaf(am, r5, szr[2]);
+      szr[3] = fmaf(bm, r5, szr[3]);
+      szc[0] = fmaf(cd.x, c4, szc[0]);
+      szc[1] = fmaf(cd.y, c4, szc[1]);
+      szc[2] = fmaf(cd.x, c5, szc[2]);
+      szc[3] = fmaf(cd.y, c5, szc[3]);
+    }
+  }
+  __syncwarp();
+  // ---- z-faces at (j, i), this half: staged in the z-face rows, then
+  //      scattered two rows per instruction
+  const int oz0 = H[4], oz1 = H[5];
+  if (actj) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      float xa[8], xb[8];     // Ex[0][s][.], Ex[1][s][.] (slots 2 s, 2 s + 1), this half
+      load_row<8>(W + S::EX + (2 * s) * RS + i0, xa);
+      load_row<8>(W + S::EX + (2 * s + 1) * RS + i0, xb);
+      const float ya = ey[2 * s], yb = ey[2 * s + 1];   // Ey[0][s][j], Ey[1][s][j]
+      float orow[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const float own = s ? e5[t] : e4[t], opp = s ? e4[t] : e5[t];
+        float o = (fc[4 + s] + w0 * (l1[t] + l2j)) * own;
+        o = fmaf(cO[4 + s], opp, o);
+        o = fmaf(w0, fmaf(a[t], ya, fmaf(b[t], yb, fmaf(cj, xa[t], dj * xb[t]))), o);
+        o -= s ? z5[t] : z4[t];
+        orow[t] = o;
+        dot = fmaf(own, o, dot);   // padding and Dirichlet faces were gathered as zeros: add 0
+      }
+      float* dst = W + S::F + (4 + s) * FS + j * RS + i0;
+      *reinterpret_cast<float4*>(dst) = make_float4(orow[0], orow[1], orow[2], orow[3]);
+      *reinterpret_cast<float4*>(dst + 4) = make_float4(orow[4], orow[5], orow[6], orow[7]);
+    }
+  }
+  __syncwarp();
+  {
+    const int half = lane >> 4, col = lane & 15;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int oz = s ? oz1 : oz0;
+      if (oz >= 0 && col < N) {
+#pragma unroll
+        for (int rp = 0; rp < N; rp += 2) {
+          const int row = rp + half;
+          if (row < N) atomicAdd(v + oz + row * N + col, W[S::F + (4 + s) * FS + row * RS + col]);
+        }
+      }
+    }
+  }
+  // ---- edges at position l
+  if (actl) {
+    float syr[4] = {0.f, 0.f, 0.f, 0.f};   // y-face row l: syr[2 sb + sa] = sum_m (a|b)_m F_{2+sb}[l][m]
+    float sxr[4] = {0.f, 0.f, 0.f, 0.f};   // x-face row l: sxr[2 sa + sb] = sum_m (c|d)_m F_sa[l][m]
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      const float am = Cf[PA + m], bm = Cf[PB + m];
+      const float2 cd = *reinterpret_cast<const float2*>(Cf + PQ + 4 * m);
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        const float yr = Fp[(2 + f) * FS + l * RS + m], xr = Fp[f * FS + l * RS + m];
+        syr[2 * f] = fmaf(am, yr, syr[2 * f]);
+        syr[2 * f + 1] = fmaf(bm, yr, syr[2 * f + 1]);
+        sxr[2 * f] = fmaf(cd.x, xr, sxr[2 * f]);
+        sxr[2 * f + 1] = fmaf(cd.y, xr, sxr[2 * f + 1]);
+      }
+    }
+    float Vt[8];
+    {
+      const float4 v0 = *reinterpret_cast<const float4*>(W + S::VT);
+      const float4 v1 = *reinterpret_cast<const float4*>(W + S::VT + 4);
+      Vt[0] = v0.x; Vt[1] = v0.y; Vt[2] = v0.z; Vt[3] = v0.w;
+      Vt[4] = v1.x; Vt[5] = v1.y; Vt[6] = v1.z; Vt[7] = v1.w;
+    }
+    const float4 ezl = *reinterpret_cast<const float4*>(W + S::EZ + 4 * l);
+    const float ez[4] = {ezl.x, ezl.y, ezl.z, ezl.w};
+    const float4 ql = *reinterpret_cast<const float4*>(Cf + PQ + 4 * l);
+    const float l2l = Cf[PL2 + l], l3l = Cf[PL3 + l];
+    float eyl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) eyl[q] = W[S::EX + (4 + q) * RS + l];
+    // x-edges Ex[sb][sc] at i = l
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int sb = q & 1, sc = q >> 1;
+      float o = (w02 * (d0 + l1l) + Cf[PS + 12 + q]) * ex[q];
+      o = fmaf(w02, fmaf(al, Vt[2 * sb + 4 * sc], bl * Vt[1 + 2 * sb + 4 * sc]), o);
+      o = fmaf(w0, szc[2 * sc + sb] + sy[2 * sb + sc], o);
+      o = fmaf(w0 * cO[2 + sb], ex[(1 - sb) + 2 * sc], o);
+      o = fmaf(w0 * cO[4 + sc], ex[sb + 2 * (1 - sc)], o);
+      const int off = H[6 + q];
+      if (off >= 0) {
+        atomicAdd(v + off + l, o);
+        dot = fmaf(ex[q], o, dot);
+      }
+    }
+    // y-edges Ey[sa][sc] at j = l
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int sa = q & 1, sc = q >> 1;
+      float o = (w02 * (d0 + l2l) + Cf[PS + 16 + q]) * eyl[q];
+      o = fmaf(w02, fmaf(ql.x, Vt[sa + 4 * sc], ql.y * Vt[sa + 2 + 4 * sc]), o);
+      o = fmaf(w0, szr[2 * sc + sa] + sx[2 * sa + sc], o);
+      o = fmaf(w0 * cO[sa], eyl[(1 - sa) + 2 * sc], o);
+      o = fmaf(w0 * cO[4 + sc], eyl[sa + 2 * (1 - sc)], o);
+      const int off = H[10 + q];
+      if (off >= 0) {
+        atomicAdd(v + off + l, o);
+        dot = fmaf(eyl[q], o, dot);
+      }
+    }
+    // z-edges Ez[sa][sb] at k = l
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int sa = q & 1, sb = q >> 1;
+      float o = (w02 * (d0 + l3l) + Cf[PS + 20 + q]) * ez[q];
+      o = fmaf(w02, fmaf(ql.z, Vt[sa + 2 * sb], ql.w * Vt[sa + 2 * sb + 4]), o);
+      o = fmaf(w0, syr[2 * sb + sa] + sxr[2 * sa + sb], o);
+      o = fmaf(w0 * cO[sa], ez[(1 - sa) + 2 * sb], o);
+      o = fmaf(w0 * cO[2 + sb], ez[sa + 2 * (1 - sb)], o);
+      const int off = H[14 + q];
+      if (off >= 0) {
+        atomicAdd(v + off + l, o);
+        dot = fmaf(ez[q], o, dot);
+      }
+    }
+  }
+  // ---- vertices (lanes 0..7)
+  if (lane < 8) {
+    const int r = lane, sa = r & 1, sb = (r >> 1) & 1, sc = r >> 2;
+    const float* exr = W + S::EX + (sb + 2 * sc) * RS;
+    const float* eyr = W + S::EX + (4 + sa + 2 * sc) * RS;
+    float sv = 0.f;
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      sv = fmaf(Cf[(sa ? PB : PA) + m], exr[m], sv);
+      sv = fmaf(Cf[PQ + 4 * m + sb], eyr[m], sv);
+      sv = fmaf(Cf[PQ + 4 * m + 2 + sc], W[S::EZ + 4 * m + sa + 2 * sb], sv);
+    }
+    const float vr = W[S::VT + r];
+    float o = Cf[PS + 24 + r] * vr;
+    o = fmaf(w02, sv, o);
+    o = fmaf(w02 * Cf[PS + sa], W[S::VT + (r ^ 1)], o);
+    o = fmaf(w02 * Cf[PS + 2 + sb], W[S::VT + (r ^ 2)], o);
+    o = fmaf(w02 * Cf[PS + 4 + sc], W[S::VT + (r ^ 4)], o);
+    const int off = H[18 + r];
+    if (off >= 0) {
+      atomicAdd(v + off, o);
+      dot = fmaf(vr, o, dot);
+    }
+  }
+}
+
+// One element per warp; the same two-stage gather pipeline as the one-row
+// kernel.  v += Hhat~ u; returns the thread's share of u^T v.
+template <int N>
+__device__ __forceinline__ float plane2_apply_all(const SemGeom& g, const SemClassTables<float>& tab,
+                                                  const EntityAffine* ent, const float* __restrict__ u,
+                                                  float* __restrict__ v, unsigned char* smem_raw) {
+  using S = Plane2Sm<N>;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  int* H0 = reinterpret_cast<int*>(smem_raw) + wib * kHdr;
+  float* W0 = reinterpret_cast<float*>(smem_raw + (size_t)2 * wpb * kHdr * sizeof(int)) + (size_t)wib * S::size;
+  const int hstep = wpb * kHdr, wstep = wpb * S::size;
+  const long long ne = g.nelem, nw = (long long)gridDim.x * wpb;
+  const long long w = (long long)blockIdx.x * wpb + wib;
+  const long long e_begin = ne * w / nw;
+  const int ncount = (int)(ne * (w + 1) / nw - e_begin);
+  int held0 = -1, held1 = -1;
+  float dot = 0.f;
+  auto stage = [&](int qi, int b) {
+    int* H = H0 + b * hstep;
+    float* W = W0 + b * wstep;
+    const int held = b ? held1 : held0;
+    const long long e = e_begin + qi;
+    plane_header<32>(g, tab, ent, (int)e, e < ne, held >= 0 ? held : 0, lane, H);
+    __syncwarp();
+    const int cls = H[26];
+    plane2_gather<N>(u, tab.plane + (long long)cls * tab.plane_stride, cls != held, H, W, lane);
+    cp_async_commit();
+    if (b) held1 = cls;
+    else held0 = cls;
+  };
+  if (ncount > 0) stage(0, 0);
+  for (int qi = 0; qi < ncount; ++qi) {
+    const int b = qi & 1;
+    if (qi + 1 < ncount) {
+      stage(qi + 1, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    plane2_element<N>(W0 + b * wstep, H0 + b * hstep, v, lane, dot);
+    __syncwarp();
+  }
+  return dot;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kPlaneThreads, 4)
+k_tpt_apply_plane2(SemGeom g, SemClassTables<float> tab, const float* __restrict__ u, float* __restrict__ v,
+                   double* __restrict__ partials, PcgState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ EntityAffine ent[26];
+  if (st != nullptr && st->done) return;
+  if (threadIdx.x < 26) entity_affine(g, threadIdx.x, &ent[threadIdx.x]);
+  __syncthreads();
+  const float dot = plane2_apply_all<N>(g, tab, ent, u, v, smem_raw);
+  if (st != nullptr) {
+    double vals[1] = {(double)dot}, tot[1];
+    if (reduce_grid<1>(vals, partials, &st->counter[0], tot) && threadIdx.x == 0) {
+      const double pq = tot[0];
+      st->pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) st->done = 2;
+      else st->alpha = st->rho / pq;
+    }
+  }
+}
+
+template <int N>
+void launch_plane2_n(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y, double* partials,
+                     PcgState* st, cudaStream_t s) {
+  using S = Plane2Sm<N>;
+  const int wpb = kPlaneThreads / 32;
+  const size_t smem = (size_t)2 * wpb * kHdr * sizeof(int) + (size_t)2 * wpb * S::size * sizeof(float);
+  static bool attr = false;
+  if (!attr) {   // once per instantiation; the first launch happens outside any capture
+    cudaFuncSetAttribute(k_tpt_apply_plane2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_plane2<N>, kPlaneThreads, smem);
+  if (occ < 1) occ = 1;
+  long long grid = (long long)sem_num_sms() * occ;
+  const long long need = (g.nelem + wpb - 1) / wpb;
+  if (grid > need) grid = need;
+  k_tpt_apply_plane2<N><<<(int)grid, kPlaneThreads, smem, s>>>(g, t, x, y, partials, st);
+  sem_count_launch();
+}
+
 template <int N>
 size_t plane_smem() {
   using S = PlaneSm<N>;
@@ -825,6 +1269,16 @@ cudaError_t launch_cg_plane(const SemGeom& g, const SemClassTables<float>& t, fl
 
 void launch_plane_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
                         double* partials, PcgState* st, cudaStream_t s) {
+  switch (g.n) {
+    case 9: launch_plane2_n<9>(g, t, x, y, partials, st, s); return;
+    case 10: launch_plane2_n<10>(g, t, x, y, partials, st, s); return;
+    case 11: launch_plane2_n<11>(g, t, x, y, partials, st, s); return;
+    case 12: launch_plane2_n<12>(g, t, x, y, partials, st, s); return;
+    case 13: launch_plane2_n<13>(g, t, x, y, partials, st, s); return;
+    case 14: launch_plane2_n<14>(g, t, x, y, partials, st, s); return;
+    case 15: launch_plane2_n<15>(g, t, x, y, partials, st, s); return;
+    default: break;
+  }
   switch (g.n) {
     case 2: launch_plane_n<2>(g, t, x, y, partials, st, s); break;
     case 3: launch_plane_n<3>(g, t, x, y, partials, st, s); break;

@@ -59,7 +59,8 @@ struct SemClassTables {
 };
 
 // One class's coefficient block of the plane-per-lane FP32 operator (units of
-// float; rows padded to rs = 4 ceil(n / 4) for 16-byte vector loads):
+// float; rows padded to rs = 4 ceil(n / 4), or 16 when n > 8, for 16-byte
+// vector loads; padding entries are 0):
 //   [pa, pa + rs)  a_i = d1 k_0[i]      [pb, pb + rs)  b_i = d1 k_1[i]
 //   [pl1 .. pl3]   d1 lambda, d2 lambda, d3 lambda (one row each)
 //   [pq, pq + 4n)  (c_m, d_m, e_m, g_m) = (d2 k_0, d2 k_1, d3 k_0, d3 k_1)[m]
@@ -71,7 +72,7 @@ struct PlaneLayout {
 };
 inline __host__ __device__ PlaneLayout plane_layout(int n) {
   PlaneLayout o;
-  o.rs = (n + 3) & ~3;
+  o.rs = n <= 8 ? (n + 3) & ~3 : 16;   // rows of 16 for the two-chunk kernel (9 <= n <= 15)
   o.pa = 0;
   o.pb = o.rs;
   o.pl1 = 2 * o.rs;
@@ -82,8 +83,9 @@ inline __host__ __device__ PlaneLayout plane_layout(int n) {
   o.stride = o.ps + 36;
   return o;
 }
-// Degrees served by the plane-per-lane kernel: n = p - 1 in [2, 8].
-inline __host__ __device__ bool plane_supported(int n) { return n >= 2 && n <= 8; }
+// Degrees served by the plane-per-lane kernels: n = p - 1 in [2, 15]
+// (one row per lane for n <= 8, two half-rows per plane for 9 <= n <= 15).
+inline __host__ __device__ bool plane_supported(int n) { return n >= 2 && n <= 15; }
 
 // Offsets inside one class's operator coefficient block (units of T):
 //   [0, 18n + 24): scaled line vectors and couplings, copied to shared memory

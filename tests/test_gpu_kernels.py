@@ -46,6 +46,9 @@ PLANE_CASES = [  # p (n = p - 1 in 2..8), elements, lambda, aspect ratio
     (7, (2, 2, 3), 0.5, 2.0),
     (8, (3, 3, 3), 0.0, 8.0),     # the benchmark degree
     (9, (2, 3, 2), 1.0, 1.5),     # n = 8 fills the group
+    (10, (3, 2, 2), 2.0, 4.0),    # two half-rows per plane from here on (9 <= n <= 15)
+    (12, (2, 2, 3), 0.0, 2.0),
+    (16, (3, 2, 1), 1.0, 8.0),    # n = 15, the mixed-precision workload's degree
 ]
 
 
@@ -109,11 +112,14 @@ def test_defaults_and_rejected_variants():
     ctx2, _ = make_pair(2, (2, 2, 2), 1.0)
     assert sem.sem_get_operator_kernel(ctx2, sem.PREC_FP64)[0] == sem.KERNEL_ELEMENT
     ctx16, _ = make_pair(16, (1, 1, 1), 1.0)
-    assert sem.sem_get_operator_kernel(ctx16, sem.PREC_MIXED)[0] == sem.KERNEL_CTA_TILE
+    assert sem.sem_get_operator_kernel(ctx16, sem.PREC_MIXED)[0] == sem.KERNEL_PLANE
+    ctx17, _ = make_pair(17, (1, 1, 1), 1.0)
+    assert sem.sem_get_operator_kernel(ctx17, sem.PREC_MIXED)[0] == sem.KERNEL_CTA_TILE
     bad = [(ctx8, sem.PREC_FP64, sem.KERNEL_PLANE, 0, 0),     # FP32-only variants
            (ctx8, sem.PREC_FP64, sem.KERNEL_WARP, 0, 0),
            (ctx8, sem.PREC_MIXED, sem.KERNEL_ELEMENT, 0, 0),  # p = 2 only
-           (ctx16, sem.PREC_MIXED, sem.KERNEL_PLANE, 0, 0),   # n = 15 > 8
+           (ctx17, sem.PREC_MIXED, sem.KERNEL_PLANE, 0, 0),   # n = 16 > 15
+           (ctx16, sem.PREC_MIXED, sem.KERNEL_WARP, 0, 0),    # n = 15 > 7
            (ctx2, sem.PREC_MIXED, sem.KERNEL_WARP, 0, 0),     # n = 1 < 3
            (ctx8, sem.PREC_FP64, sem.KERNEL_CTA_TILE, 0, 7),  # epb out of range
            (ctx8, sem.PREC_FP64, sem.KERNEL_CTA_TILE, 4, 8),  # ks > n
@@ -183,12 +189,12 @@ def test_fused_cg_only_with_the_plane_kernel():
     sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_AUTO)
     assert sem.sem_cg_fused(ctx)
     ctx16, _ = make_pair(16, (1, 1, 1), 1.0, opts=sem.default_opts(precision=sem.PREC_MIXED, fused_cg=1))
-    assert not sem.sem_cg_fused(ctx16)          # the CTA-tile kernel at n = 15
+    assert not sem.sem_cg_fused(ctx16)          # the two-half-row plane kernel has no fused form
     ctx0, _ = make_pair(8, (2, 2, 2), 1.0, opts=sem.default_opts(precision=sem.PREC_MIXED))
     assert not sem.sem_cg_fused(ctx0)           # three kernels by default
 
 
-@pytest.mark.parametrize("p", [2, 3, 5, 8, 12])
+@pytest.mark.parametrize("p", [2, 3, 5, 8, 12, 16])
 def test_f32_apply_entrywise_high_aspect_ratio(p):
     """FP32 operator on an x-graded mesh of aspect ratio 128 (metric factors
     d_1 : d_2 up to ~1.6e4 within one element), entry by entry (floor 1e-3 of
@@ -198,7 +204,7 @@ def test_f32_apply_entrywise_high_aspect_ratio(p):
     (measured worst entries ~2e-5 at p <= 8, ~3e-4 at p = 12)."""
     import torch
     from paper_1601_08179_gb300 import sem
-    m = {2: (12, 3, 2), 3: (10, 3, 2), 5: (8, 2, 2), 8: (8, 2, 2), 12: (6, 1, 1)}[p]
+    m = {2: (12, 3, 2), 3: (10, 3, 2), 5: (8, 2, 2), 8: (8, 2, 2), 12: (6, 1, 1), 16: (5, 1, 1)}[p]
     ctx, ms = make_pair(p, m, 0.0, 128.0)
     ut = si.random_vector(ms.n_skeleton, 600 + p).astype(np.float32).astype(np.float64)
     v = torch.empty(ctx.nb, dtype=torch.float32, device="cuda")
