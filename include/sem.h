@@ -278,8 +278,10 @@ sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const d
  *   SEM_KERNEL_CTA_TILE  a CTA works on a tile of epb elements, the n^3
  *                        eigenspace cube in slabs of ks planes (any degree)
  *   SEM_KERNEL_WARP      one warp per element (FP32, 3 <= n <= 7)
- *   SEM_KERNEL_PLANE     a group of 4 or 8 lanes per element, one lane per
- *                        plane of the cube (FP32, 2 <= n <= 8)
+ *   SEM_KERNEL_PLANE     one lane per plane of the cube: a group of 4 or 8
+ *                        lanes per element for 2 <= n <= 8, one warp per
+ *                        element (two lanes per plane, each a half row) for
+ *                        9 <= n <= 15 (FP32)
  *   SEM_KERNEL_ELEMENT   one thread per element (p = 2)
  * where n = p - 1. */
 enum {

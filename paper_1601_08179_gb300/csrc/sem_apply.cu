@@ -1088,7 +1088,7 @@ bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
 }
 
 // Measured on GB300: FP64 is bound by the FP64 pipe and runs best with the
-// CTA tile; FP32 at 2 <= n <= 8 with the plane-per-lane kernel; n = 1 with one
+// CTA tile; FP32 at 2 <= n <= 15 with the plane kernels; n = 1 with one
 // thread per element.
 int sem_apply_default_kind(int n, size_t elem_bytes) {
   if (n == 1) return kApplyElement;

@@ -9,7 +9,8 @@ enum ApplyKind {
   kApplyAuto = 0,      // the built-in choice for (n, precision)
   kApplyCta = 1,       // CTA tile of epb elements, k-slabs of depth ks
   kApplyWarp = 2,      // one warp per element (FP32, 3 <= n <= 7)
-  kApplyPlane = 3,     // one lane per y-plane, 32/G elements per warp (FP32, 2 <= n <= 8)
+  kApplyPlane = 3,     // lanes per y-plane: 32/G elements per warp (FP32, 2 <= n <= 8) or
+                       // one element per warp, half rows (FP32, 9 <= n <= 15)
   kApplyElement = 4    // one thread per element (n = 1)
 };
 
