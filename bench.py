@@ -189,7 +189,9 @@ def kernel_name(sem, ctx, precision: int, p: int) -> str:
     n = p - 1
     t = "float" if precision == sem.PREC_MIXED else "double"
     if kind == sem.KERNEL_PLANE:
-        return f"k_tpt_apply_plane<{n}>"
+        return f"k_tpt_apply_plane<{n}>" if n <= 8 else f"k_tpt_apply_plane2<{n}>"
+    if kind == sem.KERNEL_SLAB:
+        return "k_tpt_apply_slab"
     if kind == sem.KERNEL_WARP:
         return f"k_tpt_apply_warp<{t}, {n}>"
     if kind == sem.KERNEL_ELEMENT:

@@ -283,13 +283,17 @@ sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const d
  *                        element (two lanes per plane, each a half row) for
  *                        9 <= n <= 15 (FP32)
  *   SEM_KERNEL_ELEMENT   one thread per element (p = 2)
+ *   SEM_KERNEL_SLAB      a CTA works on one element and a slab of 8 planes k
+ *                        of its eigenspace cube at a time (FP32,
+ *                        16 <= n <= 31)
  * where n = p - 1. */
 enum {
   SEM_KERNEL_AUTO = 0,
   SEM_KERNEL_CTA_TILE = 1,
   SEM_KERNEL_WARP = 2,
   SEM_KERNEL_PLANE = 3,
-  SEM_KERNEL_ELEMENT = 4
+  SEM_KERNEL_ELEMENT = 4,
+  SEM_KERNEL_SLAB = 5
 };
 
 /* Selects the operator kernel of one precision: SEM_PREC_FP64 (the FP64

@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsemgb.so")
-SOURCES = ["sem_host.cpp", "sem_kernels.cu", "sem_apply.cu", "sem_apply_plane.cu", "sem_api.cu"]
+SOURCES = ["sem_host.cpp", "sem_kernels.cu", "sem_apply.cu", "sem_apply_plane.cu", "sem_apply_slab.cu",
+           "sem_api.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

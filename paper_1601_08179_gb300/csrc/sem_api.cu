@@ -203,7 +203,7 @@ sem_status ensure_mixed(sem_ctx* c) {
             dalloc(&c->d_p32, g.nb) == cudaSuccess && dalloc(&c->d_q32, g.nb) == cudaSuccess &&
             dalloc(&c->d_st32, 1) == cudaSuccess &&
             dalloc(&c->d_coef_f, ncls * coef_offsets(g.n).stride) == cudaSuccess &&
-            (!plane_supported(g.n) || dalloc(&c->d_plane, ncls * plane_layout(g.n).stride) == cudaSuccess);
+            (!plane_table_used(g.n) || dalloc(&c->d_plane, ncls * plane_layout(g.n).stride) == cudaSuccess);
   if (!ok) return fail(SEM_ENOMEM, "cannot allocate mixed-precision buffers");
   SEM_CUDA(cudaMemsetAsync(c->d_st32, 0, sizeof(PcgState), c->stream));
   c->tab_f.cls_x = c->tab.cls_x;
@@ -214,13 +214,13 @@ sem_status ensure_mixed(sem_ctx* c) {
   c->tab_f.coef = c->d_coef_f;
   c->tab_f.coef_stride = coef_offsets(g.n).stride;
   c->tab_f.plane = c->d_plane;
-  c->tab_f.plane_stride = plane_supported(g.n) ? plane_layout(g.n).stride : 0;
+  c->tab_f.plane_stride = plane_table_used(g.n) ? plane_layout(g.n).stride : 0;
   sem_status st = cast_tables_f32(c, c->stream);
   if (st != SEM_OK) return st;
   // operator kernel attributes outside any capture
   SEM_CUDA(cudaMemsetAsync(c->d_q32, 0, sizeof(float) * g.nb, c->stream));
   launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_P32, c->d_q32, nullptr, nullptr, c->stream);
-  if (c->d_plane != nullptr) prepare_cg_plane(g);   // kernel attributes outside any capture
+  if (c->d_plane != nullptr && plane_supported(g.n)) prepare_cg_plane(g);   // kernel attributes outside any capture
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -1317,7 +1317,7 @@ sem_status tune_one(sem_ctx* c, const SemClassTables<T>& tab, const T* x, T* y, 
   };
   // the other work mappings that exist for this degree and precision
   const int def = sem_apply_default_kind(n, sizeof(T));
-  for (int kind : {kApplyWarp, kApplyPlane, kApplyElement}) {
+  for (int kind : {kApplyWarp, kApplyPlane, kApplySlab, kApplyElement}) {
     if (kind == def) continue;
     st = consider(sem_apply_config_kind(kind));
     if (st != SEM_OK) return st;

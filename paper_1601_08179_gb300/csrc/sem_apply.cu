@@ -1082,17 +1082,20 @@ bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
       return elem_bytes == 4 && plane_supported(n);
     case kApplyElement:
       return n == 1;
+    case kApplySlab:
+      return elem_bytes == 4 && slab_supported(n);
     default:
       return false;
   }
 }
 
 // Measured on GB300: FP64 is bound by the FP64 pipe and runs best with the
-// CTA tile; FP32 at 2 <= n <= 15 with the plane kernels; n = 1 with one
-// thread per element.
+// CTA tile; FP32 at 2 <= n <= 15 with the plane kernels and at 16 <= n <= 31
+// with the k-slab kernel; n = 1 with one thread per element.
 int sem_apply_default_kind(int n, size_t elem_bytes) {
   if (n == 1) return kApplyElement;
   if (elem_bytes == 4 && plane_supported(n)) return kApplyPlane;
+  if (elem_bytes == 4 && slab_supported(n)) return kApplySlab;
   return kApplyCta;
 }
 
@@ -1102,9 +1105,13 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
   const bool explicit_cfg = cfg != nullptr && cfg->kind != kApplyAuto && sem_apply_config_valid(g.n, sizeof(T), *cfg);
   int kind = explicit_cfg ? cfg->kind : sem_apply_default_kind(g.n, sizeof(T));
   if constexpr (sizeof(T) == 4) {
-    if (kind == kApplyPlane && t.plane == nullptr) kind = kApplyCta;   // tables not built (cannot happen via the API)
+    if ((kind == kApplyPlane || kind == kApplySlab) && t.plane == nullptr) kind = kApplyCta;   // tables not built (cannot happen via the API)
     if (kind == kApplyPlane) {
       launch_plane_apply(g, t, x, y, partials, st, s);
+      return;
+    }
+    if (kind == kApplySlab) {
+      launch_slab_apply(g, t, x, y, partials, st, s);
       return;
     }
     if (kind == kApplyWarp) {

@@ -56,12 +56,6 @@ struct PlaneSm {
   static_assert(EX % 4 == 0 && EZ % 4 == 0 && VT % 4 == 0 && C % 4 == 0, "16-byte alignment");
 };
 
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
 // M floats from a 16-byte aligned row (M a multiple of 4).
 template <int M>
 __device__ __forceinline__ void load_row(const float* p, float (&r)[M]) {
@@ -98,22 +92,6 @@ __device__ __forceinline__ void reduce_scatter(float (&P0)[G], float (&P1)[G], i
   *y0 = P0[0];
   *y1 = P1[0];
 }
-
-// cp.async of 4 bytes global -> shared; zero-fills the destination when
-// !valid (src-size 0: nothing is read).
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const int n = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-// cp.async of 16 bytes (both addresses 16-byte aligned).
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
 // Offsets of the element's 26 entities (-1: Dirichlet entity or no element)
 // and its class (fallback for a missing element) into H[0..26].

@@ -72,7 +72,8 @@ struct PlaneLayout {
 };
 inline __host__ __device__ PlaneLayout plane_layout(int n) {
   PlaneLayout o;
-  o.rs = n <= 8 ? (n + 3) & ~3 : 16;   // rows of 16 for the two-chunk kernel (9 <= n <= 15)
+  // rows of 16 for the two-chunk kernel (9 <= n <= 15), of 32 for the k-slab kernel (n >= 16)
+  o.rs = n <= 8 ? (n + 3) & ~3 : (n <= 15 ? 16 : 32);
   o.pa = 0;
   o.pb = o.rs;
   o.pl1 = 2 * o.rs;
@@ -86,6 +87,10 @@ inline __host__ __device__ PlaneLayout plane_layout(int n) {
 // Degrees served by the plane-per-lane kernels: n = p - 1 in [2, 15]
 // (one row per lane for n <= 8, two half-rows per plane for 9 <= n <= 15).
 inline __host__ __device__ bool plane_supported(int n) { return n >= 2 && n <= 15; }
+// Degrees served by the k-slab kernel (sem_apply_slab.cu): 16 <= n <= 31.
+inline __host__ __device__ bool slab_supported(int n) { return n >= 16 && n <= 31; }
+// Whether the FP32 tables include the class blocks of plane_layout(n).
+inline __host__ __device__ bool plane_table_used(int n) { return plane_supported(n) || slab_supported(n); }
 
 // Offsets inside one class's operator coefficient block (units of T):
 //   [0, 18n + 24): scaled line vectors and couplings, copied to shared memory

@@ -3,15 +3,16 @@
 
 #include "sem_internal.h"
 
-// Operator kernel variants: one operator, four work mappings (sem_apply.cu,
-// sem_apply_plane.cu).  The numbering is the one of SEM_KERNEL_* in sem.h.
+// Operator kernel variants: one operator, five work mappings (sem_apply.cu,
+// sem_apply_plane.cu, sem_apply_slab.cu).  The numbering is the one of SEM_KERNEL_* in sem.h.
 enum ApplyKind {
   kApplyAuto = 0,      // the built-in choice for (n, precision)
   kApplyCta = 1,       // CTA tile of epb elements, k-slabs of depth ks
   kApplyWarp = 2,      // one warp per element (FP32, 3 <= n <= 7)
   kApplyPlane = 3,     // lanes per y-plane: 32/G elements per warp (FP32, 2 <= n <= 8) or
                        // one element per warp, half rows (FP32, 9 <= n <= 15)
-  kApplyElement = 4    // one thread per element (n = 1)
+  kApplyElement = 4,   // one thread per element (n = 1)
+  kApplySlab = 5       // element x slab of 8 planes k per CTA (FP32, 16 <= n <= 31)
 };
 
 // Operator launch configuration.
@@ -53,6 +54,10 @@ void launch_plane_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoe
 // same contract as launch_tpt_apply.
 void launch_plane_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
                         double* partials, PcgState* st, cudaStream_t s);
+// y += Hhat~ x with the k-slab kernel (FP32, slab_supported(n), class blocks of
+// plane_layout(n)); same contract as launch_tpt_apply.
+void launch_slab_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
+                       double* partials, PcgState* st, cudaStream_t s);
 
 // Per-class operator coefficient blocks (layout in sem_internal.h), computed in
 // FP64 and stored in T.

@@ -1,6 +1,6 @@
 """Every operator kernel variant against the FP64 oracle, through the C ABI.
 
-The variants (SEM_KERNEL_CTA_TILE, _WARP, _PLANE, _ELEMENT) compute the same
+The variants (SEM_KERNEL_CTA_TILE, _WARP, _PLANE, _ELEMENT, _SLAB) compute the same
 transformed condensed operator (Sec. 6, Table 2) with different work
 mappings; each is selected explicitly with sem_set_operator_kernel and
 compared with the oracle's element-local tier on every skeleton entry.
@@ -72,6 +72,36 @@ def test_plane_kernel_many_warps_ragged():
     assert _check_f32(ctx, ms, 1.0, 17) <= F32_TOL
 
 
+SLAB_CASES = [  # p (n = p - 1 in 16..31), elements, lambda, aspect ratio
+    (17, (2, 2, 2), 1.0, 2.0),    # n = 16: two full slabs of 8 planes, half of each row idle
+    (18, (3, 2, 2), 0.0, 4.0),    # n = 17: the third slab holds one plane
+    (25, (2, 2, 3), 2.5, 8.0),    # n = 24: three full slabs
+    (26, (2, 3, 2), 0.5, 3.0),    # n = 25: four slabs, the last with one plane
+    (32, (2, 2, 2), 1.0, 8.0),    # n = 31, the highest degree: last slab 7 planes, one idle lane per row
+    (32, (3, 2, 1), 10.0, 32.0),
+]
+
+
+@pytest.mark.parametrize("p,m,lam,ar", SLAB_CASES)
+def test_slab_kernel_vs_oracle(p, m, lam, ar):
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, lam, ar)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_SLAB)
+    assert sem.sem_get_operator_kernel(ctx, sem.PREC_MIXED)[0] == sem.KERNEL_SLAB
+    err = _check_f32(ctx, ms, lam, 700 + p)
+    print(f"slab p={p}: {err:.2e}")
+    assert err <= F32_TOL
+
+
+def test_slab_kernel_many_units_ragged():
+    """p = 20 on 5 x 3 x 4 = 60 elements x 3 slabs = 180 work units, more than
+    one unit per CTA on most CTAs and unequal unit counts, x-graded to aspect
+    ratio 16."""
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(20, (5, 3, 4), 1.0, 16.0)
+    assert _check_f32(ctx, ms, 1.0, 19) <= F32_TOL
+
+
 @pytest.mark.parametrize("p,m,lam,ar", [(4, (3, 2, 3), 1.0, 3.0), (6, (2, 3, 2), 0.0, 2.0),
                                         (8, (3, 2, 2), 2.0, 4.0)])
 def test_warp_kernel_vs_oracle(p, m, lam, ar):
@@ -114,12 +144,15 @@ def test_defaults_and_rejected_variants():
     ctx16, _ = make_pair(16, (1, 1, 1), 1.0)
     assert sem.sem_get_operator_kernel(ctx16, sem.PREC_MIXED)[0] == sem.KERNEL_PLANE
     ctx17, _ = make_pair(17, (1, 1, 1), 1.0)
-    assert sem.sem_get_operator_kernel(ctx17, sem.PREC_MIXED)[0] == sem.KERNEL_CTA_TILE
+    assert sem.sem_get_operator_kernel(ctx17, sem.PREC_MIXED)[0] == sem.KERNEL_SLAB
+    assert sem.sem_get_operator_kernel(ctx17, sem.PREC_FP64)[0] == sem.KERNEL_CTA_TILE
     bad = [(ctx8, sem.PREC_FP64, sem.KERNEL_PLANE, 0, 0),     # FP32-only variants
            (ctx8, sem.PREC_FP64, sem.KERNEL_WARP, 0, 0),
            (ctx8, sem.PREC_MIXED, sem.KERNEL_ELEMENT, 0, 0),  # p = 2 only
            (ctx17, sem.PREC_MIXED, sem.KERNEL_PLANE, 0, 0),   # n = 16 > 15
            (ctx16, sem.PREC_MIXED, sem.KERNEL_WARP, 0, 0),    # n = 15 > 7
+           (ctx16, sem.PREC_MIXED, sem.KERNEL_SLAB, 0, 0),    # n = 15 < 16
+           (ctx17, sem.PREC_FP64, sem.KERNEL_SLAB, 0, 0),     # FP32 only
            (ctx2, sem.PREC_MIXED, sem.KERNEL_WARP, 0, 0),     # n = 1 < 3
            (ctx8, sem.PREC_FP64, sem.KERNEL_CTA_TILE, 0, 7),  # epb out of range
            (ctx8, sem.PREC_FP64, sem.KERNEL_CTA_TILE, 4, 8),  # ks > n
@@ -153,6 +186,24 @@ def test_mixed_solve_with_each_fp32_kernel(kind):
     info = sem.sem_solve(ctx, dev(f), u)
     assert info["refinements"] >= 1
     assert relerr(host(u), dense.solve_full(ms, lam, f)) <= 1e-9
+
+
+def test_mixed_solve_with_the_slab_kernel():
+    """Mixed-precision solve at p = 20 (n = 19, the k-slab FP32 kernel by
+    default) against the oracle's factorized PCG at rtol 1e-13."""
+    import torch
+    from oracle import solve as osolve
+    from paper_1601_08179_gb300 import sem
+    p, m, lam, ar = 20, (2, 2, 2), 1.0, 4.0
+    ctx, ms = make_pair(p, m, lam, ar, opts=sem.default_opts(precision=sem.PREC_MIXED))
+    assert sem.sem_get_operator_kernel(ctx, sem.PREC_MIXED)[0] == sem.KERNEL_SLAB
+    X, Y, Z = ms.coords()
+    f = (si.manufactured_f(X, Y, Z, lam) + si.node_noise(X.size, 29).reshape(X.shape)).ravel()
+    u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+    info = sem.sem_solve(ctx, dev(f), u)
+    assert info["refinements"] >= 1
+    ref = osolve.bt_solve(ms, lam, f, rtol=1e-13)[0]
+    assert relerr(host(u), ref) <= 1e-9
 
 
 @pytest.mark.parametrize("p,m,lam,ar", [(8, (3, 3, 2), 1.0, 4.0), (4, (5, 3, 3), 0.0, 8.0), (3, (3, 2, 3), 10.0, 2.0)])
@@ -194,7 +245,7 @@ def test_fused_cg_only_with_the_plane_kernel():
     assert not sem.sem_cg_fused(ctx0)           # three kernels by default
 
 
-@pytest.mark.parametrize("p", [2, 3, 5, 8, 12, 16])
+@pytest.mark.parametrize("p", [2, 3, 5, 8, 12, 16, 24, 32])
 def test_f32_apply_entrywise_high_aspect_ratio(p):
     """FP32 operator on an x-graded mesh of aspect ratio 128 (metric factors
     d_1 : d_2 up to ~1.6e4 within one element), entry by entry (floor 1e-3 of
@@ -204,7 +255,8 @@ def test_f32_apply_entrywise_high_aspect_ratio(p):
     (measured worst entries ~2e-5 at p <= 8, ~3e-4 at p = 12)."""
     import torch
     from paper_1601_08179_gb300 import sem
-    m = {2: (12, 3, 2), 3: (10, 3, 2), 5: (8, 2, 2), 8: (8, 2, 2), 12: (6, 1, 1), 16: (5, 1, 1)}[p]
+    m = {2: (12, 3, 2), 3: (10, 3, 2), 5: (8, 2, 2), 8: (8, 2, 2), 12: (6, 1, 1), 16: (5, 1, 1), 24: (4, 2, 1),
+         32: (4, 1, 2)}[p]
     ctx, ms = make_pair(p, m, 0.0, 128.0)
     ut = si.random_vector(ms.n_skeleton, 600 + p).astype(np.float32).astype(np.float64)
     v = torch.empty(ctx.nb, dtype=torch.float32, device="cuda")
