@@ -163,17 +163,21 @@ __device__ __forceinline__ void slab_gather(const SemGeom& g, const SemClassTabl
   }
 }
 
-// The condensed part of one unit: the walk over the slab (x- and
-// z-contractions, D^-1 x stored), then the y-contraction from shared memory.
-// Leaves the x- and y-face sums in OX / OY and the z-face partial sums in the
-// slab area.
-__device__ __forceinline__ void slab_condensed(int k0, float* sm) {
+// The faces of one unit: the walk over the slab (x- and z-contractions,
+// D^-1 x stored), the y-contraction from shared memory, and the primary part
+// of each face output, formed by the thread that holds its operands (the walk
+// thread for the x- and z-faces, the y-contraction thread for the y-faces).
+// Leaves the finished outputs (primary minus condensed) in OX / OY and, for
+// the z-faces (the slab's partial sums), in the slab area; adds their share
+// of x^T (A x) to dot (inputs past n or on Dirichlet faces were gathered as
+// zeros, so those terms add 0).
+__device__ __forceinline__ void slab_faces(const SemGeom& g, int s, int nslab, int k0, float* sm, float& dot) {
   using S = SlabSm;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int n = g.n, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int jl = lane & 7, c = lane >> 3, j = 8 * w + jl, i0 = 8 * c;
+  const float w0 = sm[S::CPS + 32], d0 = sm[S::CPS + 34];
   float zb[8], zt[8];
   {
-    const float d0 = sm[S::CPS + 34];
     float a[8], b[8], l1[8], zi0[8], zi1[8];
     load8(sm + S::CA + i0, a);
     load8(sm + S::CB + i0, b);
@@ -181,7 +185,7 @@ __device__ __forceinline__ void slab_condensed(int k0, float* sm) {
     load_chunk(sm + S::FZ, j, c, zi0);
     load_chunk(sm + S::FZ + kZ, j, c, zi1);
     const float2 cd = *reinterpret_cast<const float2*>(sm + S::CCD + 2 * j);
-    const float cj = cd.x, dj = cd.y, sj = d0 + sm[S::CL2 + j];
+    const float cj = cd.x, dj = cd.y, l2j = sm[S::CL2 + j], sj = d0 + l2j;
     float X[2 * kK];
 #pragma unroll
     for (int t = 0; t < 8; ++t) zb[t] = zt[t] = 0.f;
@@ -231,15 +235,63 @@ __device__ __forceinline__ void slab_condensed(int k0, float* sm) {
         X[t] = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
       }
     }
-    const int f = c >> 1, kb = 4 * (c & 1);
+    // x-face outputs at (k, j), face f: diagonal, opposite face, the four edge
+    // lines, minus the condensed sum
+    {
+      const int f = c >> 1, kb = 4 * (c & 1);
+      const float ey0 = sm[S::EXY + (4 + f) * kR + j], ey1 = sm[S::EXY + (6 + f) * kR + j];   // Ey[f][0|1] at j
+      const float fcx = sm[S::CPS + 6 + f], cOx = sm[S::CPS + f];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) sm[S::OX + (f * kK + kb + t) * kR + j] = X[t];
+      for (int t = 0; t < 4; ++t) {
+        const int kk = kb + t, k = k0 + kk;
+        const float A = sm[S::FX + (f * kK + kk) * kR + j], B = sm[S::FX + ((1 - f) * kK + kk) * kR + j];
+        const float4 eg = *reinterpret_cast<const float4*>(sm + S::CEG + 4 * k);
+        const float ez0 = sm[S::EZ + 4 * k + f], ez1 = sm[S::EZ + 4 * k + 2 + f];   // Ez[f][0|1] at k
+        float o = (fcx + w0 * (l2j + eg.z)) * A;
+        o = fmaf(cOx, B, o);
+        o = fmaf(w0, fmaf(cj, ez0, fmaf(dj, ez1, fmaf(eg.x, ey0, eg.y * ey1))), o);
+        o -= X[t];
+        sm[S::OX + (f * kK + kk) * kR + j] = o;
+        dot = fmaf(A, o, dot);
+      }
+    }
+    // z-face outputs at (j, i in the chunk): the primary part of rows
+    // [jlo, jhi) (a 1 / S share) minus the slab's condensed sums
+    const int jrows = (n + nslab - 1) / nslab, jlo = s * jrows;
+    if (j >= jlo && j < jlo + jrows) {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        const float ya = sm[S::EXY + (4 + 2 * f) * kR + j], yb = sm[S::EXY + (5 + 2 * f) * kR + j];   // Ey[0|1][f] at j
+        float xa[8], xb[8];                                                                           // Ex[0|1][f] at i
+        load8(sm + S::EXY + (2 * f) * kR + i0, xa);
+        load8(sm + S::EXY + (1 + 2 * f) * kR + i0, xb);
+        const float fcz = sm[S::CPS + 10 + f] + w0 * l2j, cOz = sm[S::CPS + 4 + f];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const float own = f ? zi1[t] : zi0[t], opp = f ? zi0[t] : zi1[t];
+          float o = fmaf(w0, l1[t], fcz) * own;
+          o = fmaf(cOz, opp, o);
+          o = fmaf(w0, fmaf(a[t], ya, fmaf(b[t], yb, fmaf(cj, xa[t], dj * xb[t]))), o);
+          if (f) zt[t] = o - zt[t];
+          else zb[t] = o - zb[t];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        zb[t] = -zb[t];
+        zt[t] = -zt[t];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) dot = fmaf(zi0[t], zb[t], fmaf(zi1[t], zt[t], dot));
   }
   __syncthreads();
   // y-contraction: thread (kk, iq, jh) sums (c_j, d_j) times the slab over
-  // j in [16 jh, 16 jh + 16) for i in [4 iq, 4 iq + 4)
+  // j in [16 jh, 16 jh + 16) for i in [4 iq, 4 iq + 4); then the y-face
+  // outputs of face jh at (k, i)
   {
-    const int iq = lane & 7, jh = (lane >> 3) & 1, kk = (lane >> 4) + 2 * w;
+    const int iq = lane & 7, jh = (lane >> 3) & 1, kk = (lane >> 4) + 2 * w, k = k0 + kk, i = 4 * iq;
     float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
     const float* slab = sm + S::V + kk * kZ;
 #pragma unroll
@@ -262,17 +314,41 @@ __device__ __forceinline__ void slab_condensed(int k0, float* sm) {
       const float snd = jh ? s0[q] : s1[q], kp = jh ? s1[q] : s0[q];
       y[q] = kp + __shfl_xor_sync(0xffffffffu, snd, 8);
     }
-    *reinterpret_cast<float4*>(sm + S::OY + (jh * kK + kk) * kR + 4 * iq) = make_float4(y[0], y[1], y[2], y[3]);
+    const float4 cl = *reinterpret_cast<const float4*>(sm + S::FY + (jh * kK + kk) * kR + i);
+    const float4 dl = *reinterpret_cast<const float4*>(sm + S::FY + ((1 - jh) * kK + kk) * kR + i);
+    const float4 ex0 = *reinterpret_cast<const float4*>(sm + S::EXY + jh * kR + i);         // Ex[jh][0] at i
+    const float4 ex1 = *reinterpret_cast<const float4*>(sm + S::EXY + (2 + jh) * kR + i);   // Ex[jh][1] at i
+    const float4 ca = *reinterpret_cast<const float4*>(sm + S::CA + i);
+    const float4 cb = *reinterpret_cast<const float4*>(sm + S::CB + i);
+    const float4 c1 = *reinterpret_cast<const float4*>(sm + S::CL1 + i);
+    const float4 eg = *reinterpret_cast<const float4*>(sm + S::CEG + 4 * k);
+    const float ez0 = sm[S::EZ + 4 * k + 2 * jh], ez1 = sm[S::EZ + 4 * k + 2 * jh + 1];   // Ez[0|1][jh] at k
+    const float fcy = sm[S::CPS + 8 + jh] + w0 * eg.z, cOy = sm[S::CPS + 2 + jh];
+    const float clv[4] = {cl.x, cl.y, cl.z, cl.w}, dlv[4] = {dl.x, dl.y, dl.z, dl.w};
+    const float e0v[4] = {ex0.x, ex0.y, ex0.z, ex0.w}, e1v[4] = {ex1.x, ex1.y, ex1.z, ex1.w};
+    const float cav[4] = {ca.x, ca.y, ca.z, ca.w}, cbv[4] = {cb.x, cb.y, cb.z, cb.w};
+    const float c1v[4] = {c1.x, c1.y, c1.z, c1.w};
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float r = fmaf(w0, c1v[q], fcy) * clv[q];
+      r = fmaf(cOy, dlv[q], r);
+      r = fmaf(w0, fmaf(cav[q], ez0, fmaf(cbv[q], ez1, fmaf(eg.x, e0v[q], eg.y * e1v[q]))), r);
+      o[q] = r - y[q];
+      dot = fmaf(clv[q], o[q], dot);
+    }
+    *reinterpret_cast<float4*>(sm + S::OY + (jh * kK + kk) * kR + i) = make_float4(o[0], o[1], o[2], o[3]);
   }
   __syncthreads();
-  // z-face partial sums into the (now free) slab area
+  // z-face outputs into the (now free) slab area
   store_chunk(sm + S::V, j, c, zb);
   store_chunk(sm + S::V + kZ, j, c, zt);
 }
 
-// Primary part and scatter-add of one unit; returns its share of x^T (A x).
-__device__ __forceinline__ float slab_scatter(const SemGeom& g, const int* H, int s, int nslab, int k0,
-                                              const float* sm, float* __restrict__ v) {
+// Scatter-add of one unit's face outputs and the edges and vertices (primary
+// part only); returns the edges' and vertices' share of x^T (A x).
+__device__ __forceinline__ float slab_scatter(const SemGeom& g, const int* H, int s, int k0, const float* sm,
+                                              float* __restrict__ v) {
   using S = SlabSm;
   const int n = g.n, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const float w0 = sm[S::CPS + 32], w02 = sm[S::CPS + 33], d0 = sm[S::CPS + 34];
@@ -280,70 +356,21 @@ __device__ __forceinline__ float slab_scatter(const SemGeom& g, const int* H, in
   float dot = 0.f;
   // item t = tid + 128 r of each face loop: the lane is the position in the
   // row, the warp and r name the row
-  // ---- x-faces at (k, j = lane), rows k of the slab
+  // ---- x- and y-face rows k of the slab: [slot 0..3][kk][lane] of OX, OY
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int f = r >> 1, kk = w + 4 * (r & 1), j = lane, k = k0 + kk;
-    const int off = H[f];
-    if (off >= 0 && lin && k < n) {
-      const float A = sm[S::FX + (f * kK + kk) * kR + j], B = sm[S::FX + ((1 - f) * kK + kk) * kR + j];
-      const float4 eg = *reinterpret_cast<const float4*>(sm + S::CEG + 4 * k);
-      const float2 cd = *reinterpret_cast<const float2*>(sm + S::CCD + 2 * j);
-      const float ez0 = sm[S::EZ + 4 * k + f], ez1 = sm[S::EZ + 4 * k + 2 + f];   // Ez[f][0], Ez[f][1] at k
-      const float ey0 = sm[S::EXY + (4 + f) * kR + j], ey1 = sm[S::EXY + (6 + f) * kR + j];   // Ey[f][0|1] at j
-      const float bx = w0 * (sm[S::CL2 + j] + eg.z);
-      float o = (sm[S::CPS + 6 + f] + bx) * A;
-      o = fmaf(sm[S::CPS + f], B, o);
-      o = fmaf(w0, fmaf(cd.x, ez0, fmaf(cd.y, ez1, fmaf(eg.x, ey0, eg.y * ey1))), o);
-      o -= sm[S::OX + (f * kK + kk) * kR + j];
-      atomicAdd(v + off + k * n + j, o);
-      dot = fmaf(A, o, dot);
-    }
+  for (int r = 0; r < 8; ++r) {
+    const int slot = r >> 1, kk = w + 4 * (r & 1), k = k0 + kk;
+    const int off = H[slot];
+    if (off >= 0 && lin && k < n) atomicAdd(v + off + k * n + lane, sm[S::OX + tid + 128 * r]);
   }
-  // ---- y-faces at (k, i = lane), rows k of the slab
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int f = r >> 1, kk = w + 4 * (r & 1), i = lane, k = k0 + kk;
-    const int off = H[2 + f];
-    if (off >= 0 && lin && k < n) {
-      const float Cl = sm[S::FY + (f * kK + kk) * kR + i], Dl = sm[S::FY + ((1 - f) * kK + kk) * kR + i];
-      const float4 eg = *reinterpret_cast<const float4*>(sm + S::CEG + 4 * k);
-      const float ez0 = sm[S::EZ + 4 * k + 2 * f], ez1 = sm[S::EZ + 4 * k + 2 * f + 1];   // Ez[0|1][f] at k
-      const float ex0 = sm[S::EXY + f * kR + i], ex1 = sm[S::EXY + (2 + f) * kR + i];       // Ex[f][0|1] at i
-      const float by = w0 * (sm[S::CL1 + i] + eg.z);
-      float o = (sm[S::CPS + 8 + f] + by) * Cl;
-      o = fmaf(sm[S::CPS + 2 + f], Dl, o);
-      o = fmaf(w0, fmaf(sm[S::CA + i], ez0, fmaf(sm[S::CB + i], ez1, fmaf(eg.x, ex0, eg.y * ex1))), o);
-      o -= sm[S::OY + (f * kK + kk) * kR + i];
-      atomicAdd(v + off + k * n + i, o);
-      dot = fmaf(Cl, o, dot);
-    }
-  }
-  // ---- z-faces at (j, i = lane): the slab's partial condensed sums; the
-  //      primary part of rows j in [jlo, jhi) (a 1 / S share of the rows)
-  const int jrows = (n + nslab - 1) / nslab, jlo = s * jrows, jhi = jlo + jrows;
+  // ---- z-faces, rows j = w + 4 (r & 7)
   const int col0 = (((lane >> 2) ^ (w & 7)) << 2) | (lane & 3);         // swizzled column, rows j = w + 8 t
   const int col1 = (((lane >> 2) ^ ((w + 4) & 7)) << 2) | (lane & 3);   // rows j = w + 4 + 8 t
 #pragma unroll 2
   for (int r = 0; r < 16; ++r) {
-    const int f = r >> 3, j = w + 4 * (r & 7), i = lane;
+    const int f = r >> 3, j = w + 4 * (r & 7);
     const int off = H[4 + f];
-    if (off >= 0 && j < n && lin) {
-      const int pos = j * kR + ((r & 1) ? col1 : col0);
-      const float own = sm[S::FZ + f * kZ + pos];
-      float o = -sm[S::V + f * kZ + pos];
-      if (j >= jlo && j < jhi) {
-        const float opp = sm[S::FZ + (1 - f) * kZ + pos];
-        const float ya = sm[S::EXY + (4 + 2 * f) * kR + j], yb = sm[S::EXY + (5 + 2 * f) * kR + j];   // Ey[0|1][f] at j
-        const float xa = sm[S::EXY + (2 * f) * kR + i], xb = sm[S::EXY + (1 + 2 * f) * kR + i];       // Ex[0|1][f] at i
-        const float2 cd = *reinterpret_cast<const float2*>(sm + S::CCD + 2 * j);
-        o = fmaf(sm[S::CPS + 10 + f] + w0 * (sm[S::CL1 + i] + sm[S::CL2 + j]), own, o);
-        o = fmaf(sm[S::CPS + 4 + f], opp, o);
-        o = fmaf(w0, fmaf(sm[S::CA + i], ya, fmaf(sm[S::CB + i], yb, fmaf(cd.x, xa, cd.y * xb))), o);
-      }
-      atomicAdd(v + off + j * n + i, o);
-      dot = fmaf(own, o, dot);
-    }
+    if (off >= 0 && j < n && lin) atomicAdd(v + off + j * n + lane, sm[S::V + f * kZ + j * kR + ((r & 1) ? col1 : col0)]);
   }
   // ---- x-edges Ex[sb][sc] at i = l (warp q = sb + 2 sc) and y-edges
   //      Ey[sa][sc] at j = l (q = sa + 2 sc): the line sums along k over the
@@ -463,17 +490,22 @@ k_tpt_apply_slab(SemGeom g, SemClassTables<float> tab, const float* __restrict__
   const long long u_begin = units * blockIdx.x / gridDim.x, u_end = units * (blockIdx.x + 1) / gridDim.x;
   int* H = reinterpret_cast<int*>(sm + SlabSm::HDR);
   float dot = 0.f;
+  int e = (int)(u_begin / nslab), s = (int)(u_begin - (long long)e * nslab);   // element and slab of the unit
   for (long long un = u_begin; un < u_end; ++un) {
-    const int e = (int)(un / nslab), s = (int)(un - (long long)e * nslab), k0 = s * kK;
+    const int k0 = s * kK;
     __syncthreads();   // the previous unit is done with the buffers (and ent[] is written)
     if (tid < 27) slab_header(g, tab, ent, e, tid, H);
     __syncthreads();
     slab_gather(g, tab, u, H, k0, sm);
     cp_async_wait<0>();
     __syncthreads();
-    slab_condensed(k0, sm);
+    slab_faces(g, s, nslab, k0, sm, dot);
     __syncthreads();
-    dot += slab_scatter(g, H, s, nslab, k0, sm, v);
+    dot += slab_scatter(g, H, s, k0, sm, v);
+    if (++s == nslab) {
+      s = 0;
+      ++e;
+    }
   }
   if (st != nullptr) {
     double vals[1] = {(double)dot}, tot[1];
@@ -496,12 +528,10 @@ void launch_slab_apply(const SemGeom& g, const SemClassTables<float>& t, const f
     cudaFuncSetAttribute(k_tpt_apply_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_slab, kSlabThreads, smem);
-  if (occ < 1) occ = 1;
+  // one unit per CTA (the block scheduler balances the SMs to within one
+  // unit), or contiguous ranges of units once the grid would pass 65536 CTAs
   const long long units = g.nelem * (long long)((g.n + kK - 1) / kK);
-  long long grid = (long long)sem_num_sms() * occ;
-  if (grid > units) grid = units;
+  long long grid = units < 65536 ? units : 65536;
   if (grid < 1) grid = 1;
   k_tpt_apply_slab<<<(int)grid, kSlabThreads, smem, s>>>(g, t, x, y, partials, st);
   sem_count_launch();

@@ -102,6 +102,31 @@ def test_slab_kernel_many_units_ragged():
     assert _check_f32(ctx, ms, 1.0, 19) <= F32_TOL
 
 
+@pytest.mark.parametrize("p,m,ar", [(32, (8, 8, 8), 128.0), (17, (33, 32, 32), 8.0)])
+def test_slab_kernel_at_scale_matches_fp64_operator(p, m, ar):
+    """The k-slab FP32 operator at the p = 32 benchmark size (2048 units, one
+    per CTA, the launch the bench times) and past 65536 units (p = 17 on
+    33 x 32 x 32 = 67584 units: CTAs take ranges of units), against the FP64
+    operator of the same context on the same FP32-representable input (both
+    checked against the oracle at small sizes): equal to FP32 rounding in the
+    2-norm and entry by entry (floor 1e-3 of the largest entry)."""
+    import torch
+    from paper_1601_08179_gb300 import build, sem
+    build.build()
+    hx, hy, hz, _ = si.graded_widths(*m, ar=ar, grade="x")
+    ctx = sem.sem_setup(p, hx, hy, hz, 0.0, sem.default_opts(precision=sem.PREC_MIXED))
+    assert sem.sem_get_operator_kernel(ctx, sem.PREC_MIXED)[0] == sem.KERNEL_SLAB
+    x32 = torch.tensor(si.random_vector(ctx.nb, 77 + p), dtype=torch.float32, device="cuda")
+    v64 = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+    sem.sem_apply_condensed(ctx, x32.double(), v64, sem.SPACE_TRANSFORMED)
+    v32 = torch.empty(ctx.nb, dtype=torch.float32, device="cuda")
+    sem.sem_apply_condensed_f32(ctx, x32, v32)
+    got, ref = host(v32), host(v64)
+    assert relerr(got, ref) <= F32_TOL
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max())
+    assert float(np.max(np.abs(got - ref) / scale)) <= 1e-3
+
+
 @pytest.mark.parametrize("p,m,lam,ar", [(4, (3, 2, 3), 1.0, 3.0), (6, (2, 3, 2), 0.0, 2.0),
                                         (8, (3, 2, 2), 2.0, 4.0)])
 def test_warp_kernel_vs_oracle(p, m, lam, ar):
