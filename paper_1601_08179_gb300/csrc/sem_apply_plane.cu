@@ -84,10 +84,29 @@ __device__ __forceinline__ void halve(float (&P0)[G], float (&P1)[G], int jl) {
   }
 }
 
+// The first halving step of the sums of cj W[i] and dj W[i] over the lanes
+// (cj, dj the lane's own factors): the selection is made on W, so each lane
+// forms only the products it sends and folds its kept half in with one FMA.
+template <int H, int G>
+__device__ __forceinline__ void halve_w(const float (&W)[G], float cj, float dj, float (&P0)[G], float (&P1)[G],
+                                        int jl) {
+  const bool up = (jl & H) != 0;
+#pragma unroll
+  for (int t = 0; t < H; ++t) {
+    const float ws = up ? W[t] : W[t + H], wk = up ? W[t + H] : W[t];
+    P0[t] = fmaf(cj, wk, __shfl_xor_sync(0xffffffffu, cj * ws, H));
+    P1[t] = fmaf(dj, wk, __shfl_xor_sync(0xffffffffu, dj * ws, H));
+  }
+}
+
+// Sums cj W[i] and dj W[i] over the G lanes of a group; lane jl ends with the
+// sums for i = jl.
 template <int G>
-__device__ __forceinline__ void reduce_scatter(float (&P0)[G], float (&P1)[G], int jl, float* y0, float* y1) {
-  if constexpr (G == 8) halve<4, G>(P0, P1, jl);
-  halve<2, G>(P0, P1, jl);
+__device__ __forceinline__ void reduce_scatter(const float (&W)[G], float cj, float dj, int jl, float* y0,
+                                               float* y1) {
+  float P0[G], P1[G];
+  halve_w<G / 2, G>(W, cj, dj, P0, P1, jl);
+  if constexpr (G == 8) halve<2, G>(P0, P1, jl);
   halve<1, G>(P0, P1, jl);
   *y0 = P0[0];
   *y1 = P1[0];
@@ -207,7 +226,7 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
       load_row<RS>(Fp + 3 * FS + k * RS, Dr);
       const float sjk = sj + l3k;
       float X0 = 0.f, X1 = 0.f;
-      float P0[G], P1[G];
+      float Wr[G];   // D^-1 x along the row
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         float x = a[i] * A;
@@ -221,13 +240,12 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
         X1 = fmaf(b[i], w, X1);
         z4[i] = fmaf(ek, w, z4[i]);
         z5[i] = fmaf(gk, w, z5[i]);
-        P0[i] = cj * w;
-        P1[i] = dj * w;
+        Wr[i] = w;
       }
 #pragma unroll
-      for (int i = N; i < G; ++i) P0[i] = P1[i] = 0.f;
+      for (int i = N; i < G; ++i) Wr[i] = 0.f;
       float Y0, Y1;
-      reduce_scatter<G>(P0, P1, jl, &Y0, &Y1);
+      reduce_scatter<G>(Wr, cj, dj, jl, &Y0, &Y1);
       sx[0] = fmaf(ek, A, sx[0]);
       sx[1] = fmaf(gk, A, sx[1]);
       sx[2] = fmaf(ek, B, sx[2]);
@@ -772,7 +790,7 @@ __device__ __forceinline__ void plane2_element(float* W, const int* H, float* __
     load_row<8>(Fp + 3 * FS + k * RS + i0, Dr);
     const float sjk = sj + l3k;
     float X0 = 0.f, X1 = 0.f;
-    float P0[8], P1[8];
+    float Wr[8], P0[8], P1[8];   // D^-1 x along the half-row; the partial sums of its y-contraction
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       float x = a[t] * A;
@@ -786,12 +804,11 @@ __device__ __forceinline__ void plane2_element(float* W, const int* H, float* __
       X1 = fmaf(b[t], w, X1);
       z4[t] = fmaf(ek, w, z4[t]);
       z5[t] = fmaf(gk, w, z5[t]);
-      P0[t] = cj * w;
-      P1[t] = dj * w;
+      Wr[t] = w;
     }
     X0 += __shfl_xor_sync(0xffffffffu, X0, 16);   // both halves of the row
     X1 += __shfl_xor_sync(0xffffffffu, X1, 16);
-    halve<4, 8>(P0, P1, jj);
+    halve_w<4, 8>(Wr, cj, dj, P0, P1, jj);
     halve<2, 8>(P0, P1, jj);
     halve<1, 8>(P0, P1, jj);
     const float Y0 = P0[0] + __shfl_xor_sync(0xffffffffu, P0[0], 8);
