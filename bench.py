@@ -408,6 +408,10 @@ def our_arm(args, rank, world, local_rank):
                        "operator_frac_fp64_peak": flops / p64["apply_s"] / 1e12 / FP64_PEAK_TFLOPS,
                        "clocks": p64["clocks"]}
         out["speedup_vs_fp64"] = p64["step_s"] / r["step_s"]
+    rec = oracle_record(w) if rank == 0 else None
+    if rec is not None and "mixed" in res:
+        out["error_vs_oracle"] = errors_vs_oracle(sem, ctx, f, u, rec, int(res["mixed"]["info"]["refinements"]),
+                                                  forms[head])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_iters = reference_iterations(w)
         iters = res["fp64"]["info"]["iters"] if "fp64" in res else r["info"]["iters"]
@@ -528,6 +532,43 @@ def adjoint_arm(args, rank, world, local_rank):
                           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                           "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "lambda": w.lam},
                           "clocks": clk.summary()}), flush=True)
+
+
+def oracle_record(w: si.Workload):
+    """The oracle's full-size solve of this workload, as recorded in
+    tests/golden by `python -m oracle.reference_solve` (None if not recorded)."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{w.name}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def errors_vs_oracle(sem, ctx, f, u, rec, refinements: int, form_opts):
+    """Relative error, over the recorded sample nodes, against the oracle's
+    solve (rtol 1e-12) of the FP64 solution and of the mixed-precision
+    solution after each FP64 refinement step (the mixed solve re-run with
+    max_refine = 1, 2, ...).  Outside the timed region."""
+    import torch
+    idx = torch.as_tensor(np.asarray(rec["u_samples"]["index"], dtype=np.int64), device=u.device)
+    want = np.asarray(rec["u_samples"]["value"])
+
+    def err():
+        got = u[idx].cpu().numpy()
+        return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+    out = {"samples": int(want.size), "reference": "oracle Algorithm 4 solve of this workload, rtol %g" % rec["rtol"]}
+    sem.sem_set_opts(ctx, sem.default_opts())
+    sem.sem_solve(ctx, f, u)
+    out["fp64"] = err()
+    steps = []
+    for k in range(1, refinements + 1):
+        sem.sem_set_opts(ctx, sem.default_opts(precision=sem.PREC_MIXED, max_refine=k))
+        sem.sem_solve(ctx, f, u, check=False)
+        steps.append(err())
+    out["mixed_per_refinement_step"] = steps
+    sem.sem_set_opts(ctx, form_opts)
+    return out
 
 
 def reference_iterations(w: si.Workload):
