@@ -81,7 +81,8 @@ def test_batched_workload_heterogeneous_64():
         assert relerr(host(us[k]), host(u1)) <= 1e-10, k
 
 
-@pytest.mark.parametrize("p,m,mixed", [(8, (6, 5, 4), False), (4, (8, 6, 6), False), (8, (6, 5, 4), True)])
+@pytest.mark.parametrize("p,m,mixed", [(8, (6, 5, 4), False), (4, (8, 6, 6), False), (8, (6, 5, 4), True),
+                                      (20, (3, 2, 2), True)])
 def test_autotune_keeps_results(p, m, mixed):
     import torch
     from paper_1601_08179_gb300 import sem
@@ -140,6 +141,34 @@ def test_mixed_batch_matches_oracle_and_single_solves():
         u1 = torch.empty_like(us[k])
         sem.sem_solve(c, fs[k], u1)           # the single (host-looped) mixed solve of the same problem
         assert relerr(host(us[k]), host(u1)) <= 1e-9, k
+
+
+def test_mixed_batch_high_degree_slab_kernel():
+    """Mixed-precision problems whose FP32 operator is the k-slab kernel
+    (p = 17, 20, 24: two and three slabs per element) and a low-degree one in
+    one graph: every solution against the oracle's factorized PCG (rtol 1e-13)
+    within the solve bar, and equal to the single solve of the same problem."""
+    import torch
+    from oracle import solve as osolve
+    from paper_1601_08179_gb300 import sem
+    probs = [(17, (2, 1, 2), 1.0, 2.0, 91), (20, (1, 2, 2), 10.0, 1.0, 92), (24, (2, 2, 1), 0.5, 4.0, 93),
+             (6, (2, 2, 2), 1.0, 2.0, 94)]
+    ctxs, fs, us, refs = [], [], [], []
+    for p, m, lam, ar, seed in probs:
+        ctx, ms = make_pair(p, m, lam, ar, opts=_mixed())
+        assert sem.sem_get_operator_kernel(ctx, sem.PREC_MIXED)[0] == (sem.KERNEL_SLAB if p > 16 else sem.KERNEL_PLANE)
+        f = si.node_noise(ms.n_global, seed)
+        ctxs.append(ctx)
+        fs.append(dev(f))
+        us.append(torch.full((ctx.n_nodes,), np.nan, dtype=torch.float64, device="cuda"))
+        refs.append(osolve.bt_solve(ms, lam, f, rtol=1e-13)[0])
+    st, infos = sem.SemBatch(ctxs, fs, us).solve()
+    for k, (u, ref) in enumerate(zip(us, refs)):
+        assert relerr(host(u), ref) <= 1e-9, k
+        assert infos[k]["rel_res"] <= 1e-10 and infos[k]["refinements"] >= 1, k
+        u1 = torch.empty_like(u)
+        sem.sem_solve(ctxs[k], fs[k], u1)
+        assert relerr(host(u), host(u1)) <= 1e-9, k
 
 
 def test_mixed_batch_heterogeneous_64_beats_fp64():
