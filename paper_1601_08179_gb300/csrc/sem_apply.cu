@@ -696,28 +696,27 @@ k_tpt_apply_warp(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* _
 // ---------------------------------------------------------------------------
 // Thread-per-element variant for p = 2 (n = 1)
 // ---------------------------------------------------------------------------
-// FP32 form.  With one interior node per element every entity carries one
-// value, and the packed skeleton is seven regular arrays with the x index fastest:
-// threads take consecutive elements in x, so each of an element's 26 loads
-// and 26 scatter-adds is one contiguous row across the warp.  A thread holds
-// its element's boundary values and outputs in registers; the coefficient
-// block (the formulas of k_class_coeffs with n = 1) is formed from the class's
-// d0..d3 and the 1D basis in registers, and the entity offsets come from the
-// affine per-slot table.
+// With one interior node per element every entity carries one value, and the
+// packed skeleton is seven regular arrays with the x index fastest: threads
+// take consecutive elements in x, so each of an element's 26 loads and 26
+// scatter-adds is one contiguous row across the warp.  A thread holds its
+// element's boundary values and outputs in registers; the entity offsets come
+// from the affine per-slot table, and the class coefficient block (the
+// formulas of k_class_coeffs with n = 1) from the transposed per-class table,
+// where the consecutive classes of an x-graded row make each coefficient one
+// coalesced load (one broadcast load on a uniform mesh).
 constexpr int kThreadsP2 = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(kThreadsP2, sizeof(T) == 8 ? 3 : 4)
-k_tpt_apply_p2(SemGeom g, SemBasis b, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
+k_tpt_apply_p2(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
                double* __restrict__ partials, PcgState* st) {
   __shared__ EntityAffine ent[26];
   if (st != nullptr && st->done) return;
   if (threadIdx.x < 26) entity_affine(g, threadIdx.x, &ent[threadIdx.x]);
   __syncthreads();
-  const T w0 = (T)b.w0, w02 = w0 * w0;
-  const T k0 = (T)b.k[0][0], k1 = (T)b.k[1][0], lam = (T)b.lam[0];
-  const T K00 = (T)b.K[0][0], K11 = (T)b.K[1][1], K01 = (T)b.K[0][1], K10 = (T)b.K[1][0];
-  const int mx = g.mx, my = g.my, mxy = mx * my;
+  const CoefOffsets co = coef_offsets(1);
+  const int nc = tab.ncls, mx = g.mx, my = g.my, mxy = mx * my;
   T dot = T(0);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (int)g.nelem; e += gridDim.x * blockDim.x) {
     const int ez = e / mxy, rem = e - ez * mxy, ey = rem / mx, ex = rem - ey * mx;
@@ -737,150 +736,30 @@ k_tpt_apply_p2(SemGeom g, SemBasis b, SemClassTables<T> tab, const T* __restrict
 #pragma unroll
     for (int r = 0; r < 8; ++r) Vt[r] = off[18 + r] >= 0 ? u[off[18 + r]] : T(0);
     // the class block: d_{dir+1} k_s (skd), scaled by w0 (skw) and w0^2 (skww);
-    // d_{dir+1} K_{s,1-s} (cO, eO = w0 cO, vO = w0^2 cO); the diagonals
-    const int c = elem_class(g, tab, ex, ey, ez);
-    const T d0 = __ldg(tab.dcoef + 4 * c), d1 = __ldg(tab.dcoef + 4 * c + 1), d2 = __ldg(tab.dcoef + 4 * c + 2),
-            d3 = __ldg(tab.dcoef + 4 * c + 3);
-    const T dd[3] = {d1, d2, d3};
-    T skd[6], cO[6];
-#pragma unroll
-    for (int ds = 0; ds < 6; ++ds) {
-      skd[ds] = dd[ds >> 1] * ((ds & 1) ? k1 : k0);
-      cO[ds] = dd[ds >> 1] * ((ds & 1) ? K10 : K01);
-    }
-    const T ndinv = T(-1) / (d0 + (d1 + d2 + d3) * lam);
-    // condensed part: one eigenspace value
-    T x = skd[0] * F[0];
-#pragma unroll
-    for (int k = 1; k < 6; ++k) x = fma(skd[k], F[k], x);
-    const T vv = ndinv * x;
-    T Fo[6], Eo[12], Vo[8];
-    // faces: diagonal d0 w0 + d K_ss + w0 lambda (d' + d''), opposite face, the four edges
-#pragma unroll
-    for (int slot = 0; slot < 6; ++slot) {
-      const int di = slot >> 1, s = slot & 1;
-      const T Kss = s ? K11 : K00;
-      const T others = di == 0 ? d2 + d3 : (di == 1 ? d1 + d3 : d1 + d2);   // no cancellation at high AR
-      const T diag = d0 * w0 + dd[di] * Kss + w0 * lam * others;
-      T out = fma(diag, F[slot], skd[slot] * vv);
-      out = fma(cO[slot], F[slot ^ 1], out);
-      T pr;
-      if (di == 0) pr = skd[2] * Ed[8 + s] + skd[3] * Ed[10 + s] + skd[4] * Ed[4 + s] + skd[5] * Ed[6 + s];
-      else if (di == 1) pr = skd[0] * Ed[8 + 2 * s] + skd[1] * Ed[9 + 2 * s] + skd[4] * Ed[s] + skd[5] * Ed[2 + s];
-      else pr = skd[0] * Ed[4 + 2 * s] + skd[1] * Ed[5 + 2 * s] + skd[2] * Ed[2 * s] + skd[3] * Ed[1 + 2 * s];
-      Fo[slot] = fma(w0, pr, out);
-    }
-    // edges: diagonal, the two vertices, the two faces, the two parallel edges
-#pragma unroll
-    for (int slot = 0; slot < 12; ++slot) {
-      const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
-      const int t1 = grp == 0 ? 1 : 0, t2 = grp == 2 ? 1 : 2;
-      const T diag = w02 * (d0 + dd[grp] * lam) + w0 * (dd[t1] * (s1 ? K11 : K00) + dd[t2] * (s2 ? K11 : K00));
-      T out = diag * Ed[slot];
-      T vert, face, par;
-      if (grp == 0) {
-        vert = skd[0] * Vt[2 * s1 + 4 * s2] + skd[1] * Vt[1 + 2 * s1 + 4 * s2];
-        face = skd[2 + s1] * F[4 + s2] + skd[4 + s2] * F[2 + s1];
-        par = cO[2 + s1] * Ed[(1 - s1) + 2 * s2] + cO[4 + s2] * Ed[s1 + 2 * (1 - s2)];
-      } else if (grp == 1) {
-        vert = skd[2] * Vt[s1 + 4 * s2] + skd[3] * Vt[s1 + 2 + 4 * s2];
-        face = skd[s1] * F[4 + s2] + skd[4 + s2] * F[s1];
-        par = cO[s1] * Ed[4 + (1 - s1) + 2 * s2] + cO[4 + s2] * Ed[4 + s1 + 2 * (1 - s2)];
-      } else {
-        vert = skd[4] * Vt[s1 + 2 * s2] + skd[5] * Vt[s1 + 2 * s2 + 4];
-        face = skd[s1] * F[2 + s2] + skd[2 + s2] * F[s1];
-        par = cO[s1] * Ed[8 + (1 - s1) + 2 * s2] + cO[2 + s2] * Ed[8 + s1 + 2 * (1 - s2)];
-      }
-      out = fma(w02, vert, out);
-      out = fma(w0, face + par, out);
-      Eo[slot] = out;
-    }
-    // vertices: diagonal, the three edges, the three neighbouring vertices
-#pragma unroll
-    for (int slot = 0; slot < 8; ++slot) {
-      const int sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
-      const T diag = d0 * w02 * w0 + w02 * (d1 * (sa ? K11 : K00) + d2 * (sb ? K11 : K00) + d3 * (sc ? K11 : K00));
-      T out = diag * Vt[slot];
-      const T edg = skd[sa] * Ed[sb + 2 * sc] + skd[2 + sb] * Ed[4 + sa + 2 * sc] + skd[4 + sc] * Ed[8 + sa + 2 * sb];
-      const T nb = cO[sa] * Vt[slot ^ 1] + cO[2 + sb] * Vt[slot ^ 2] + cO[4 + sc] * Vt[slot ^ 4];
-      Vo[slot] = fma(w02, edg + nb, out);
-    }
-    // scatter R and the element share of x^T (A x)
-#pragma unroll
-    for (int r = 0; r < 6; ++r)
-      if (off[r] >= 0) { atomicAdd(v + off[r], Fo[r]); dot = fma(F[r], Fo[r], dot); }
-#pragma unroll
-    for (int r = 0; r < 12; ++r)
-      if (off[6 + r] >= 0) { atomicAdd(v + off[6 + r], Eo[r]); dot = fma(Ed[r], Eo[r], dot); }
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-      if (off[18 + r] >= 0) { atomicAdd(v + off[18 + r], Vo[r]); dot = fma(Vt[r], Vo[r], dot); }
-  }
-  if (st != nullptr) {
-    double vals[1] = {(double)dot}, tot[1];
-    if (reduce_grid<1>(vals, partials, &st->counter[0], tot) && threadIdx.x == 0) {
-      const double pq = tot[0];
-      st->pq = pq;
-      if (!(pq > 0.0) || !isfinite(pq)) st->done = 2;
-      else st->alpha = st->rho / pq;
-    }
-  }
-}
-
-// The same operator with the class coefficient block read from the per-class
-// table, elements in the visiting order of elem_visit (the lanes of a warp
-// share a class): the FP64 form, where forming the block in registers would
-// double the FP64 arithmetic.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_tpt_apply_p2_tab(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
-               double* __restrict__ partials, PcgState* st) {
-  if (st != nullptr && st->done) return;
-  const CoefOffsets co = coef_offsets(1);
-  T dot = T(0);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.nelem;
-       e += (long long)gridDim.x * blockDim.x) {
-    int ex, ey, ez;
-    elem_visit(g, e, &ex, &ey, &ez);
-    int off[26];
-    T F[6], Ed[12], Vt[8];
-#pragma unroll
-    for (int r = 0; r < 26; ++r) {
-      bool dir;
-      long long o;
-      if (r < 6) o = face_base(g, ex, ey, ez, r, &dir);
-      else if (r < 18) o = edge_base(g, ex, ey, ez, r - 6, &dir);
-      else o = vert_index(g, ex, ey, ez, r - 18, &dir);
-      off[r] = dir ? -1 : (int)o;
-    }
-#pragma unroll
-    for (int r = 0; r < 6; ++r) F[r] = off[r] >= 0 ? u[off[r]] : T(0);
-#pragma unroll
-    for (int r = 0; r < 12; ++r) Ed[r] = off[6 + r] >= 0 ? u[off[6 + r]] : T(0);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) Vt[r] = off[18 + r] >= 0 ? u[off[18 + r]] : T(0);
-    const T* cb = tab.coef + (long long)elem_class(g, tab, ex, ey, ez) * co.stride;
+    // d_{dir+1} K_{s,1-s} (cO, eO = w0 cO, vO = w0^2 cO); the diagonals; -D^-1
+    const T* cb = tab.coef_soa + elem_class(g, tab, ex, ey, ez);
+    auto C = [&](int r) { return __ldg(cb + r * nc); };
     T skd[6], skw[6], skww[6], cO[6], eO[6], vO[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      skd[k] = __ldg(cb + k);
-      skw[k] = __ldg(cb + 6 + k);
-      skww[k] = __ldg(cb + 12 + k);
-      cO[k] = __ldg(cb + 18 + k);
-      eO[k] = __ldg(cb + 24 + k);
-      vO[k] = __ldg(cb + 30 + k);
+      skd[k] = C(k);
+      skw[k] = C(6 + k);
+      skww[k] = C(12 + k);
+      cO[k] = C(18 + k);
+      eO[k] = C(24 + k);
+      vO[k] = C(30 + k);
     }
     // condensed part: one eigenspace value
     T x = skd[0] * F[0];
 #pragma unroll
     for (int k = 1; k < 6; ++k) x = fma(skd[k], F[k], x);
-    const T vv = __ldg(cb + co.ndinv) * x;
+    const T vv = C(co.ndinv) * x;
     T Fo[6], Eo[12], Vo[8];
     // faces: primary part + condensed contraction
 #pragma unroll
     for (int slot = 0; slot < 6; ++slot) {
       const int dd = slot >> 1, s = slot & 1;
-      T out = fma(__ldg(cb + co.fdiag + slot), F[slot], skd[slot] * vv);
+      T out = fma(C(co.fdiag + slot), F[slot], skd[slot] * vv);
       out = fma(cO[slot], F[slot ^ 1], out);
       if (dd == 0) {
         out = fma(skw[2], Ed[8 + s], out);
@@ -900,11 +779,11 @@ k_tpt_apply_p2_tab(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T*
       }
       Fo[slot] = out;
     }
-    // edges
+    // edges: diagonal, the two vertices, the two faces, the two parallel edges
 #pragma unroll
     for (int slot = 0; slot < 12; ++slot) {
       const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
-      T out = __ldg(cb + co.ediag + slot) * Ed[slot];
+      T out = C(co.ediag + slot) * Ed[slot];
       if (grp == 0) {
         out = fma(skww[0], Vt[2 * s1 + 4 * s2], out);
         out = fma(skww[1], Vt[1 + 2 * s1 + 4 * s2], out);
@@ -929,11 +808,11 @@ k_tpt_apply_p2_tab(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T*
       }
       Eo[slot] = out;
     }
-    // vertices
+    // vertices: diagonal, the three edges, the three neighbouring vertices
 #pragma unroll
     for (int slot = 0; slot < 8; ++slot) {
       const int sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
-      T out = __ldg(cb + co.vdiag + slot) * Vt[slot];
+      T out = C(co.vdiag + slot) * Vt[slot];
       out = fma(skww[sa], Ed[sb + 2 * sc], out);
       out = fma(skww[2 + sb], Ed[4 + sa + 2 * sc], out);
       out = fma(skww[4 + sc], Ed[8 + sa + 2 * sb], out);
@@ -965,24 +844,24 @@ k_tpt_apply_p2_tab(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T*
 }
 
 template <typename T>
-void launch_p2(const SemGeom& g, const SemBasis& b, const SemClassTables<T>& t, const T* x, T* y, double* partials,
-               PcgState* st, cudaStream_t s) {
-  int occ = 1;
-  if constexpr (sizeof(T) == 8) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_p2_tab<T>, kThreads, 0);
-    if (occ < 1) occ = 1;
-    long long grid = (long long)num_sms_cached() * occ;
-    const long long need = (g.nelem + kThreads - 1) / kThreads;
-    if (grid > need) grid = need;
-    k_tpt_apply_p2_tab<T><<<(int)grid, kThreads, 0, s>>>(g, t, x, y, partials, st);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_p2<T>, kThreadsP2, 0);
-    if (occ < 1) occ = 1;
-    long long grid = (long long)num_sms_cached() * occ;
-    const long long need = (g.nelem + kThreadsP2 - 1) / kThreadsP2;
-    if (grid > need) grid = need;
-    k_tpt_apply_p2<T><<<(int)grid, kThreadsP2, 0, s>>>(g, b, t, x, y, partials, st);
+__global__ void k_coef_soa(const T* __restrict__ coef, T* __restrict__ soa, int ncls, int stride) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)ncls * stride;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / stride), r = (int)(t - (long long)c * stride);
+    soa[(long long)r * ncls + c] = coef[t];
   }
+}
+
+template <typename T>
+void launch_p2(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, double* partials, PcgState* st,
+               cudaStream_t s) {
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_p2<T>, kThreadsP2, 0);
+  if (occ < 1) occ = 1;
+  long long grid = (long long)num_sms_cached() * occ;
+  const long long need = (g.nelem + kThreadsP2 - 1) / kThreadsP2;
+  if (grid > need) grid = need;
+  k_tpt_apply_p2<T><<<(int)grid, kThreadsP2, 0, s>>>(g, t, x, y, partials, st);
   sem_count_launch();
 }
 
@@ -1125,7 +1004,7 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
     }
   }
   if (kind == kApplyElement) {
-    launch_p2<T>(g, b, t, x, y, partials, st, s);
+    launch_p2<T>(g, t, x, y, partials, st, s);
     return;
   }
   const ApplyConfig c = (explicit_cfg && cfg->kind == kApplyCta) ? *cfg : sem_apply_config(g.n, sizeof(T));
@@ -1155,6 +1034,18 @@ template void launch_tpt_apply<double>(const SemGeom&, const SemBasis&, const Se
                                        const ApplyConfig*);
 template void launch_tpt_apply<float>(const SemGeom&, const SemBasis&, const SemClassTables<float>&,
                                       const float*, float*, double*, PcgState*, cudaStream_t, const ApplyConfig*);
+template <typename T>
+void launch_coef_soa(const SemGeom& g, const T* coef, T* soa, cudaStream_t s) {
+  const int ncls = g.ux * g.uy * g.uz, stride = (int)coef_offsets(g.n).stride;
+  long long blocks = ((long long)ncls * stride + 255) / 256;
+  if (blocks > (long long)num_sms_cached() * 16) blocks = (long long)num_sms_cached() * 16;
+  if (blocks < 1) blocks = 1;
+  k_coef_soa<T><<<(int)blocks, 256, 0, s>>>(coef, soa, ncls, stride);
+  sem_count_launch();
+}
+
+template void launch_coef_soa<double>(const SemGeom&, const double*, double*, cudaStream_t);
+template void launch_coef_soa<float>(const SemGeom&, const float*, float*, cudaStream_t);
 template void launch_class_coeffs<double>(const SemGeom&, const SemBasis&, const double*, const double*, double*,
                                           cudaStream_t);
 template void launch_class_coeffs<float>(const SemGeom&, const SemBasis&, const double*, const double*, float*,

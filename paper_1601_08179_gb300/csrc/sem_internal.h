@@ -56,6 +56,8 @@ struct SemClassTables {
   long long coef_stride;
   const float* plane = nullptr;   // [ncls][plane_stride] blocks of the plane-per-lane FP32 kernel
   long long plane_stride = 0;     // (sem_apply_plane.cu); null where that kernel does not apply
+  const T* coef_soa = nullptr;    // n = 1: coef transposed, entry r of class c at [r * ncls + c]
+  int ncls = 0;                   // (the thread-per-element kernel); null for n > 1
 };
 
 // One class's coefficient block of the plane-per-lane FP32 operator (units of

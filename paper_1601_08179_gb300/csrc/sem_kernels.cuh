@@ -64,6 +64,11 @@ void launch_slab_apply(const SemGeom& g, const SemClassTables<float>& t, const f
 template <typename T>
 void launch_class_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoef, const double* dinv, T* coef,
                          cudaStream_t s);
+// soa[r * ncls + c] = coef[c * stride + r]: the class blocks transposed, so
+// that threads of consecutive classes read one coefficient with one
+// coalesced load (the thread-per-element kernel, n = 1).
+template <typename T>
+void launch_coef_soa(const SemGeom& g, const T* coef, T* soa, cudaStream_t s);
 
 // y = Hhat~ x on the skeleton (transformed space); y must be zero on entry.
 // If st != nullptr: also x^T y -> st->pq and alpha = rho / pq (CG step).
