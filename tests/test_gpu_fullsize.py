@@ -1,8 +1,10 @@
-"""Full benchmark size (graded p = 8 workload, 32^3 elements, N = 1.68e7)
-against the oracle's own Algorithm-4 solve of the same problem, recorded in
-tests/golden/oracle_<workload>.json by `python -m oracle.reference_solve 8`
-(oracle-only script; seeded samples of the solution, of the transformed
-diagonal and of the nodal condensed load, and the CG iteration count)."""
+"""Full benchmark sizes (graded p = 8 workload, 32^3 elements, N = 1.68e7;
+the mixed-precision workload, p = 16 on 16^3 elements, lambda = 10, aspect
+ratio 16) against the oracle's own Algorithm-4 solve of the same problem,
+recorded in tests/golden/oracle_<workload>.json by
+`python -m oracle.reference_solve 8` and `... mixed16` (oracle-only script;
+seeded samples of the solution, of the transformed diagonal and of the nodal
+condensed load, and the CG iteration count)."""
 import json
 import os
 
@@ -78,3 +80,41 @@ def test_solution_samples_and_iterations(setup, precision):
     assert err <= 1e-8
     if precision == "fp64":
         assert abs(info["iters"] - rec["iterations_to_1e-10"]) <= 2
+
+
+WM = si.MIXED
+GOLD_M = os.path.join(os.path.dirname(__file__), "golden", f"oracle_{WM.name}.json")
+
+
+def test_mixed16_error_per_refinement_step():
+    """The mixed-precision workload at full size: the solution after each FP64
+    refinement step (the solve re-run with max_refine = 1, 2, ...) against the
+    oracle's solve, on the recorded sample nodes.  The error falls at every
+    step and the final solution at the benchmark tolerance (FP64 residual
+    1e-10) is within 1e-9 of the oracle's."""
+    import torch
+    from paper_1601_08179_gb300 import build, sem
+    if not os.path.exists(GOLD_M):
+        pytest.fail(f"missing {GOLD_M}: run python -m oracle.reference_solve mixed16")
+    rec = json.load(open(GOLD_M))
+    build.build()
+    hx, hy, hz = WM.widths()
+    ms = Mesh(WM.p, hx, hy, hz)
+    X, Y, Z = ms.coords()
+    f = dev((si.manufactured_f(X, Y, Z, WM.lam) + si.node_noise(X.size, WM.seed).reshape(X.shape)).ravel())
+    ctx = sem.sem_setup(WM.p, hx, hy, hz, WM.lam, sem.default_opts(precision=sem.PREC_MIXED))
+    u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+    info = sem.sem_solve(ctx, f, u)
+    assert info["rel_res"] <= 1e-10
+    idx = np.array(rec["u_samples"]["index"])
+    want = np.array(rec["u_samples"]["value"])
+    final = _sampled_rel(host(u)[idx], want)
+    errs = []
+    for k in range(1, info["refinements"] + 1):
+        sem.sem_set_opts(ctx, sem.default_opts(precision=sem.PREC_MIXED, max_refine=k))
+        sem.sem_solve(ctx, f, u, check=False)
+        errs.append(_sampled_rel(host(u)[idx], want))
+    print("error vs the oracle per refinement step:", " ".join(f"{e:.2e}" for e in errs), f"final {final:.2e}")
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] == pytest.approx(final, rel=1e-3, abs=1e-12)
+    assert final <= 1e-9
