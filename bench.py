@@ -180,6 +180,8 @@ TRAFFIC_BYTES = {
     ("k_tpt_apply_plane<7>", "graded_p8_m32_ar128_lam0"): 43237888 + 0,
     ("k_tpt_apply<double, 7> (epb 5, ks 7)", "graded_p8_m32_ar128_lam0"): 86415872 + 4352000,
     ("k_tpt_apply_slab", "graded_p32_m8_ar128_lam0"): 10743040 + 0,
+    ("k_tpt_apply_p2<float>", "graded_p2_m128_ar128_lam0"): 117041408 + 12317952,
+    ("k_tpt_apply_p2<double>", "graded_p2_m128_ar128_lam0"): 234106368 + 70302208,
 }
 
 
