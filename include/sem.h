@@ -75,7 +75,7 @@ typedef enum {
   SEM_ECUDA = 3,      /* a CUDA call or kernel launch failed */
   SEM_ENOCONV = 4,    /* solver hit maxit; the best iterate is still written */
   SEM_EBREAKDOWN = 5, /* CG breakdown: p^T A p <= 0 or not finite (e.g. NaN input) */
-  SEM_ENOTSUP = 6     /* option not supported by this build */
+  SEM_ENOTSUP = 6     /* valid request the library does not serve (N_B >= 2^31; batched scheme-0 mixed solves) */
 } sem_status;
 
 typedef enum { SEM_SPACE_NODAL = 0, SEM_SPACE_TRANSFORMED = 1 } sem_space;
