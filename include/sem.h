@@ -282,7 +282,7 @@ sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const d
  *                        lanes per element for 2 <= n <= 8, one warp per
  *                        element (two lanes per plane, each a half row) for
  *                        9 <= n <= 15 (FP32)
- *   SEM_KERNEL_ELEMENT   one thread per element (p = 2)
+ *   SEM_KERNEL_ELEMENT   one thread per element (p = 2; FP32 also p = 3, 4)
  *   SEM_KERNEL_SLAB      a CTA works on one element and a slab of 8 planes k
  *                        of its eigenspace cube at a time (FP32,
  *                        16 <= n <= 31)

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsemgb.so")
 SOURCES = ["sem_host.cpp", "sem_kernels.cu", "sem_apply.cu", "sem_apply_plane.cu", "sem_apply_slab.cu",
-           "sem_api.cu"]
+           "sem_apply_elem.cu", "sem_api.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -72,6 +72,7 @@ struct sem_ctx {
   float* d_plane = nullptr;            // class blocks of the plane-per-lane FP32 kernel
   double* d_coef_soa = nullptr;        // n = 1: the class blocks transposed (FP64, FP32)
   float* d_coef_soa_f = nullptr;
+  float* d_plane_soa = nullptr;        // n = 2, 3: the plane blocks transposed
   double* d_mats = nullptr;            // 4 n*n: S_II, V, V^T M_II, M_II V
   double* d_mass = nullptr;            // [Nx + Ny + Nz] assembled 1D lumped masses
   double* d_h = nullptr;               // [mx + my + mz] element widths
@@ -173,7 +174,7 @@ sem_status compute_tables(sem_ctx* c, cudaStream_t s) {
   launch_class_tables(g, c->h1.basis, c->d_uw, c->d_uw + g.ux, c->d_uw + g.ux + g.uy, c->lambda, c->d_dcoef,
                       c->d_dinv, s);
   launch_class_coeffs<double>(g, c->h1.basis, c->d_dcoef, c->d_dinv, c->d_coef, s);
-  if (c->d_coef_soa != nullptr) launch_coef_soa<double>(g, c->d_coef, c->d_coef_soa, s);
+  if (c->d_coef_soa != nullptr) launch_coef_soa<double>(g, c->d_coef, c->d_coef_soa, coef_offsets(1).stride, s);
   SEM_CUDA(cudaGetLastError());
   SEM_CUDA(cudaMemsetAsync(c->d_t1, 0, sizeof(double) * g.nb, s));
   launch_precond_diag(g, c->h1.basis, c->tab, c->d_t1, s);
@@ -189,8 +190,9 @@ sem_status cast_tables_f32(sem_ctx* c, cudaStream_t s) {
   launch_cast_f32(ncls * 4, c->d_dcoef, c->d_dcoef_f, s);
   launch_cast_f32(ncls * (long long)g.n * g.n * g.n, c->d_dinv, c->d_dinv_f, s);
   launch_class_coeffs<float>(g, c->h1.basis, c->d_dcoef, c->d_dinv, c->d_coef_f, s);
-  if (c->d_coef_soa_f != nullptr) launch_coef_soa<float>(g, c->d_coef_f, c->d_coef_soa_f, s);
+  if (c->d_coef_soa_f != nullptr) launch_coef_soa<float>(g, c->d_coef_f, c->d_coef_soa_f, coef_offsets(1).stride, s);
   if (c->d_plane != nullptr) launch_plane_coeffs(g, c->h1.basis, c->d_dcoef, c->d_plane, s);
+  if (c->d_plane_soa != nullptr) launch_coef_soa<float>(g, c->d_plane, c->d_plane_soa, plane_layout(g.n).stride, s);
   launch_cast_f32(g.nb, c->d_P, c->d_P32, s);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
@@ -208,7 +210,8 @@ sem_status ensure_mixed(sem_ctx* c) {
             dalloc(&c->d_st32, 1) == cudaSuccess &&
             dalloc(&c->d_coef_f, ncls * coef_offsets(g.n).stride) == cudaSuccess &&
             (!plane_table_used(g.n) || dalloc(&c->d_plane, ncls * plane_layout(g.n).stride) == cudaSuccess) &&
-            (g.n != 1 || dalloc(&c->d_coef_soa_f, ncls * coef_offsets(1).stride) == cudaSuccess);
+            (g.n != 1 || dalloc(&c->d_coef_soa_f, ncls * coef_offsets(1).stride) == cudaSuccess) &&
+            (!elem_supported(g.n) || dalloc(&c->d_plane_soa, ncls * plane_layout(g.n).stride) == cudaSuccess);
   if (!ok) return fail(SEM_ENOMEM, "cannot allocate mixed-precision buffers");
   SEM_CUDA(cudaMemsetAsync(c->d_st32, 0, sizeof(PcgState), c->stream));
   c->tab_f.cls_x = c->tab.cls_x;
@@ -220,6 +223,7 @@ sem_status ensure_mixed(sem_ctx* c) {
   c->tab_f.coef_stride = coef_offsets(g.n).stride;
   c->tab_f.plane = c->d_plane;
   c->tab_f.coef_soa = c->d_coef_soa_f;
+  c->tab_f.plane_soa = c->d_plane_soa;
   c->tab_f.ncls = (int)ncls;
   c->tab_f.plane_stride = plane_table_used(g.n) ? plane_layout(g.n).stride : 0;
   sem_status st = cast_tables_f32(c, c->stream);
@@ -655,7 +659,8 @@ void free_ctx(sem_ctx* c) {
   if (c->graph32) cudaGraphExecDestroy(c->graph32);
   if (c->graph32m) cudaGraphExecDestroy(c->graph32m);
   void* ptrs32[] = {c->d_dcoef_f, c->d_dinv_f, c->d_P32, c->d_b32, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_st32,
-                    c->d_coef_f, c->d_coef, c->d_plane, c->d_ctl, c->d_stg, c->d_coef_soa, c->d_coef_soa_f};
+                    c->d_coef_f, c->d_coef, c->d_plane, c->d_ctl, c->d_stg, c->d_coef_soa, c->d_coef_soa_f,
+                    c->d_plane_soa};
   for (void* p : ptrs32)
     if (p) cudaFree(p);
   for (cudaEvent_t ev : c->pev32) cudaEventDestroy(ev);

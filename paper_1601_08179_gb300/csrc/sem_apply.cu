@@ -960,7 +960,7 @@ bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
     case kApplyPlane:
       return elem_bytes == 4 && plane_supported(n);
     case kApplyElement:
-      return n == 1;
+      return n == 1 || (elem_bytes == 4 && elem_supported(n));
     case kApplySlab:
       return elem_bytes == 4 && slab_supported(n);
     default:
@@ -969,10 +969,12 @@ bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
 }
 
 // Measured on GB300: FP64 is bound by the FP64 pipe and runs best with the
-// CTA tile; FP32 at 2 <= n <= 15 with the plane kernels and at 16 <= n <= 31
-// with the k-slab kernel; n = 1 with one thread per element.
+// CTA tile; FP32 at 3 <= n <= 15 with the plane kernels and at 16 <= n <= 31
+// with the k-slab kernel; n = 1, and n = 2 in FP32, with one thread per
+// element (at n = 3 its 254 registers leave too few warps: 150 against the
+// plane kernel's 125 us at p = 4).
 int sem_apply_default_kind(int n, size_t elem_bytes) {
-  if (n == 1) return kApplyElement;
+  if (n == 1 || (elem_bytes == 4 && n == 2)) return kApplyElement;
   if (elem_bytes == 4 && plane_supported(n)) return kApplyPlane;
   if (elem_bytes == 4 && slab_supported(n)) return kApplySlab;
   return kApplyCta;
@@ -1004,8 +1006,19 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
     }
   }
   if (kind == kApplyElement) {
-    launch_p2<T>(g, t, x, y, partials, st, s);
-    return;
+    if constexpr (sizeof(T) == 4) {
+      if (g.n != 1) {
+        if (t.plane_soa != nullptr) {
+          launch_elem_apply(g, t, x, y, partials, st, s);
+          return;
+        }
+        kind = kApplyCta;   // tables not built (cannot happen via the API)
+      }
+    }
+    if (kind == kApplyElement) {
+      launch_p2<T>(g, t, x, y, partials, st, s);
+      return;
+    }
   }
   const ApplyConfig c = (explicit_cfg && cfg->kind == kApplyCta) ? *cfg : sem_apply_config(g.n, sizeof(T));
   switch (g.n) {
@@ -1035,8 +1048,8 @@ template void launch_tpt_apply<double>(const SemGeom&, const SemBasis&, const Se
 template void launch_tpt_apply<float>(const SemGeom&, const SemBasis&, const SemClassTables<float>&,
                                       const float*, float*, double*, PcgState*, cudaStream_t, const ApplyConfig*);
 template <typename T>
-void launch_coef_soa(const SemGeom& g, const T* coef, T* soa, cudaStream_t s) {
-  const int ncls = g.ux * g.uy * g.uz, stride = (int)coef_offsets(g.n).stride;
+void launch_coef_soa(const SemGeom& g, const T* coef, T* soa, long long stride_ll, cudaStream_t s) {
+  const int ncls = g.ux * g.uy * g.uz, stride = (int)stride_ll;
   long long blocks = ((long long)ncls * stride + 255) / 256;
   if (blocks > (long long)num_sms_cached() * 16) blocks = (long long)num_sms_cached() * 16;
   if (blocks < 1) blocks = 1;
@@ -1044,8 +1057,8 @@ void launch_coef_soa(const SemGeom& g, const T* coef, T* soa, cudaStream_t s) {
   sem_count_launch();
 }
 
-template void launch_coef_soa<double>(const SemGeom&, const double*, double*, cudaStream_t);
-template void launch_coef_soa<float>(const SemGeom&, const float*, float*, cudaStream_t);
+template void launch_coef_soa<double>(const SemGeom&, const double*, double*, long long, cudaStream_t);
+template void launch_coef_soa<float>(const SemGeom&, const float*, float*, long long, cudaStream_t);
 template void launch_class_coeffs<double>(const SemGeom&, const SemBasis&, const double*, const double*, double*,
                                           cudaStream_t);
 template void launch_class_coeffs<float>(const SemGeom&, const SemBasis&, const double*, const double*, float*,

@@ -58,6 +58,7 @@ struct SemClassTables {
   long long plane_stride = 0;     // (sem_apply_plane.cu); null where that kernel does not apply
   const T* coef_soa = nullptr;    // n = 1: coef transposed, entry r of class c at [r * ncls + c]
   int ncls = 0;                   // (the thread-per-element kernel); null for n > 1
+  const float* plane_soa = nullptr;   // n = 2, 3: plane blocks transposed (the FP32 thread-per-element kernel)
 };
 
 // One class's coefficient block of the plane-per-lane FP32 operator (units of
@@ -91,6 +92,9 @@ inline __host__ __device__ PlaneLayout plane_layout(int n) {
 inline __host__ __device__ bool plane_supported(int n) { return n >= 2 && n <= 15; }
 // Degrees served by the k-slab kernel (sem_apply_slab.cu): 16 <= n <= 31.
 inline __host__ __device__ bool slab_supported(int n) { return n >= 16 && n <= 31; }
+// Degrees served by the FP32 thread-per-element kernel beyond n = 1
+// (sem_apply_elem.cu): n = 2, 3.
+inline __host__ __device__ bool elem_supported(int n) { return n == 2 || n == 3; }
 // Whether the FP32 tables include the class blocks of plane_layout(n).
 inline __host__ __device__ bool plane_table_used(int n) { return plane_supported(n) || slab_supported(n); }
 

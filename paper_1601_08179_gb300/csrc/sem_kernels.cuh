@@ -11,7 +11,7 @@ enum ApplyKind {
   kApplyWarp = 2,      // one warp per element (FP32, 3 <= n <= 7)
   kApplyPlane = 3,     // lanes per y-plane: 32/G elements per warp (FP32, 2 <= n <= 8) or
                        // one element per warp, half rows (FP32, 9 <= n <= 15)
-  kApplyElement = 4,   // one thread per element (n = 1)
+  kApplyElement = 4,   // one thread per element (n = 1; FP32 also n = 2, 3)
   kApplySlab = 5       // element x slab of 8 planes k per CTA (FP32, 16 <= n <= 31)
 };
 
@@ -68,7 +68,11 @@ void launch_class_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoe
 // that threads of consecutive classes read one coefficient with one
 // coalesced load (the thread-per-element kernel, n = 1).
 template <typename T>
-void launch_coef_soa(const SemGeom& g, const T* coef, T* soa, cudaStream_t s);
+void launch_coef_soa(const SemGeom& g, const T* coef, T* soa, long long stride, cudaStream_t s);
+// y += Hhat~ x with the FP32 thread-per-element kernel (elem_supported(n),
+// transposed class blocks of plane_layout(n)); same contract as launch_tpt_apply.
+void launch_elem_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
+                       double* partials, PcgState* st, cudaStream_t s);
 
 // y = Hhat~ x on the skeleton (transformed space); y must be zero on entry.
 // If st != nullptr: also x^T y -> st->pq and alpha = rho / pq (CG step).

@@ -93,6 +93,45 @@ def test_slab_kernel_vs_oracle(p, m, lam, ar):
     assert err <= F32_TOL
 
 
+ELEM_CASES = [  # p (n = p - 1 in 2, 3), elements, lambda, aspect ratio
+    (3, (3, 2, 3), 1.0, 3.0),
+    (3, (2, 2, 2), 10.0, 1.0),
+    (4, (3, 3, 2), 0.0, 4.0),
+    (4, (2, 3, 3), 2.5, 16.0),
+    (4, (37, 5, 3), 1.0, 8.0),    # 555 elements: several per thread, ragged last warp
+]
+
+
+@pytest.mark.parametrize("p,m,lam,ar", ELEM_CASES)
+def test_element_kernel_fp32_vs_oracle(p, m, lam, ar):
+    """The FP32 thread-per-element kernel at n = 2, 3 (boundary values,
+    eigenspace points and contractions of an element in one thread)."""
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, lam, ar)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_ELEMENT)
+    assert sem.sem_get_operator_kernel(ctx, sem.PREC_MIXED)[0] == sem.KERNEL_ELEMENT
+    err = _check_f32(ctx, ms, lam, 800 + p)
+    print(f"element p={p}: {err:.2e}")
+    assert err <= F32_TOL
+
+
+def test_mixed_solve_with_the_element_kernel():
+    """Mixed-precision solve at p = 4 with the FP32 thread-per-element
+    operator against the dense oracle."""
+    import torch
+    from oracle import dense
+    from paper_1601_08179_gb300 import sem
+    p, m, lam, ar = 4, (3, 2, 3), 1.0, 8.0
+    ctx, ms = make_pair(p, m, lam, ar, opts=sem.default_opts(precision=sem.PREC_MIXED))
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_ELEMENT)
+    X, Y, Z = ms.coords()
+    f = (si.manufactured_f(X, Y, Z, lam) + si.node_noise(X.size, 37).reshape(X.shape)).ravel()
+    u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+    info = sem.sem_solve(ctx, dev(f), u)
+    assert info["refinements"] >= 1
+    assert relerr(host(u), dense.solve_full(ms, lam, f)) <= 1e-9
+
+
 def test_slab_kernel_many_units_ragged():
     """p = 20 on 5 x 3 x 4 = 60 elements x 3 slabs = 180 work units, more than
     one unit per CTA on most CTAs and unequal unit counts, x-graded to aspect
@@ -166,6 +205,11 @@ def test_defaults_and_rejected_variants():
     assert sem.sem_get_operator_kernel(ctx8, sem.PREC_MIXED)[0] == sem.KERNEL_PLANE
     ctx2, _ = make_pair(2, (2, 2, 2), 1.0)
     assert sem.sem_get_operator_kernel(ctx2, sem.PREC_FP64)[0] == sem.KERNEL_ELEMENT
+    ctx3, _ = make_pair(3, (2, 2, 2), 1.0)
+    assert sem.sem_get_operator_kernel(ctx3, sem.PREC_MIXED)[0] == sem.KERNEL_ELEMENT
+    assert sem.sem_get_operator_kernel(ctx3, sem.PREC_FP64)[0] == sem.KERNEL_CTA_TILE
+    ctx4, _ = make_pair(4, (2, 2, 2), 1.0)
+    assert sem.sem_get_operator_kernel(ctx4, sem.PREC_MIXED)[0] == sem.KERNEL_PLANE
     ctx16, _ = make_pair(16, (1, 1, 1), 1.0)
     assert sem.sem_get_operator_kernel(ctx16, sem.PREC_MIXED)[0] == sem.KERNEL_PLANE
     ctx17, _ = make_pair(17, (1, 1, 1), 1.0)
@@ -173,7 +217,8 @@ def test_defaults_and_rejected_variants():
     assert sem.sem_get_operator_kernel(ctx17, sem.PREC_FP64)[0] == sem.KERNEL_CTA_TILE
     bad = [(ctx8, sem.PREC_FP64, sem.KERNEL_PLANE, 0, 0),     # FP32-only variants
            (ctx8, sem.PREC_FP64, sem.KERNEL_WARP, 0, 0),
-           (ctx8, sem.PREC_MIXED, sem.KERNEL_ELEMENT, 0, 0),  # p = 2 only
+           (ctx8, sem.PREC_MIXED, sem.KERNEL_ELEMENT, 0, 0),  # n <= 3 only
+           (ctx3, sem.PREC_FP64, sem.KERNEL_ELEMENT, 0, 0),   # FP64: n = 1 only
            (ctx17, sem.PREC_MIXED, sem.KERNEL_PLANE, 0, 0),   # n = 16 > 15
            (ctx16, sem.PREC_MIXED, sem.KERNEL_WARP, 0, 0),    # n = 15 > 7
            (ctx16, sem.PREC_MIXED, sem.KERNEL_SLAB, 0, 0),    # n = 15 < 16
@@ -241,6 +286,7 @@ def test_fused_cg_iteration_matches_unfused(p, m, lam, ar):
     from oracle import dense
     from paper_1601_08179_gb300 import sem
     ctx, ms = make_pair(p, m, lam, ar, opts=sem.default_opts(precision=sem.PREC_MIXED))
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_PLANE)   # the default at n = 2 is the element kernel
     X, Y, Z = ms.coords()
     f = (si.manufactured_f(X, Y, Z, lam) + si.node_noise(X.size, 31).reshape(X.shape)).ravel()
     ref = dense.solve_full(ms, lam, f)
@@ -270,7 +316,7 @@ def test_fused_cg_only_with_the_plane_kernel():
     assert not sem.sem_cg_fused(ctx0)           # three kernels by default
 
 
-@pytest.mark.parametrize("p", [2, 3, 5, 8, 12, 16, 24, 32])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 8, 12, 16, 24, 32])
 def test_f32_apply_entrywise_high_aspect_ratio(p):
     """FP32 operator on an x-graded mesh of aspect ratio 128 (metric factors
     d_1 : d_2 up to ~1.6e4 within one element), entry by entry (floor 1e-3 of
@@ -280,7 +326,7 @@ def test_f32_apply_entrywise_high_aspect_ratio(p):
     (measured worst entries ~2e-5 at p <= 8, ~3e-4 at p = 12)."""
     import torch
     from paper_1601_08179_gb300 import sem
-    m = {2: (12, 3, 2), 3: (10, 3, 2), 5: (8, 2, 2), 8: (8, 2, 2), 12: (6, 1, 1), 16: (5, 1, 1), 24: (4, 2, 1),
+    m = {2: (12, 3, 2), 3: (10, 3, 2), 4: (9, 2, 2), 5: (8, 2, 2), 8: (8, 2, 2), 12: (6, 1, 1), 16: (5, 1, 1), 24: (4, 2, 1),
          32: (4, 1, 2)}[p]
     ctx, ms = make_pair(p, m, 0.0, 128.0)
     ut = si.random_vector(ms.n_skeleton, 600 + p).astype(np.float32).astype(np.float64)
@@ -291,3 +337,7 @@ def test_f32_apply_entrywise_high_aspect_ratio(p):
     worst = float(np.max(np.abs(got - ref) / scale))
     print(f"p={p}: worst entry-wise error {worst:.2e}")
     assert worst <= (1e-4 if p <= 9 else 1e-3)
+    if p in (3, 4):   # the thread-per-element kernel as well
+        sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_ELEMENT)
+        sem.sem_apply_condensed_f32(ctx, torch.tensor(ut, dtype=torch.float32, device="cuda"), v)
+        assert float(np.max(np.abs(host(v) - ref) / scale)) <= 1e-4
