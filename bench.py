@@ -197,7 +197,7 @@ def kernel_name(sem, ctx, precision: int, p: int) -> str:
     if kind == sem.KERNEL_WARP:
         return f"k_tpt_apply_warp<{t}, {n}>"
     if kind == sem.KERNEL_ELEMENT:
-        return f"k_tpt_apply_p2<{t}>"
+        return f"k_tpt_apply_p2<{t}>" if n == 1 else f"k_tpt_apply_elem<{n}>"
     return f"k_tpt_apply<{t}, {n if n in (1, 3, 7, 15, 31) else 0}> (epb {epb}, ks {ks})"
 
 
