@@ -206,6 +206,30 @@ def test_warm_start_and_set_lambda():
     assert relerr(host(u), ref) <= SOLVE_TOL
 
 
+@pytest.mark.parametrize("p", [2, 3, 4, 8, 17])
+def test_set_lambda_refreshes_every_operator_table(p):
+    """sem_set_lambda rebuilds the class tables of every operator kernel
+    (per-class blocks, their transposed copies for the thread-per-element
+    kernels, the plane and k-slab blocks): FP64 and FP32 applications at the
+    new lambda against the oracle."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    m = {2: (4, 3, 2), 3: (3, 2, 3), 4: (3, 2, 2), 8: (2, 3, 2), 17: (2, 2, 1)}[p]
+    ctx, ms = make_pair(p, m, 1.0, 3.0, opts=sem.default_opts(precision=sem.PREC_MIXED))
+    ut = si.random_vector(ms.n_skeleton, 95).astype(np.float32).astype(np.float64)
+    v32 = torch.empty(ctx.nb, dtype=torch.float32, device="cuda")
+    sem.sem_apply_condensed_f32(ctx, torch.tensor(ut, dtype=torch.float32, device="cuda"), v32)   # tables at lambda = 1
+    sem.sem_set_lambda(ctx, 40.0)
+    free = ms.skeleton_free
+    ref = transform.load_to_transformed(
+        ms, np.where(free, local.apply_condensed(ms, 40.0, transform.solution_from_transformed(ms, np.where(free, ut, 0.0))), 0.0))
+    v = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+    sem.sem_apply_condensed(ctx, dev(ut), v, sem.SPACE_TRANSFORMED)
+    assert relerr(host(v), ref) <= APPLY_TOL
+    sem.sem_apply_condensed_f32(ctx, torch.tensor(ut, dtype=torch.float32, device="cuda"), v32)
+    assert relerr(host(v32), ref) <= 1e-5
+
+
 def test_breakdown_on_nan_input():
     import torch
     from paper_1601_08179_gb300 import sem
