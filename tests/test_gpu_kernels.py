@@ -63,6 +63,19 @@ def test_plane_kernel_vs_oracle(p, m, lam, ar):
     assert err <= F32_TOL
 
 
+@pytest.mark.parametrize("p,m,lam,ar", [(16, (7, 1, 1), 1.0, 4.0), (12, (13, 12, 12), 2.0, 16.0)])
+def test_plane2_kernel_uneven_warp_counts(p, m, lam, ar):
+    """The two-half-row kernel with element counts that do not divide over
+    the warps: 7 elements over 9 warps (two idle), and 1872 elements over the
+    full grid (one or two elements per warp)."""
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, lam, ar)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_PLANE)
+    err = _check_f32(ctx, ms, lam, 900 + p)
+    print(f"plane2 p={p} m={m}: {err:.2e}")
+    assert err <= F32_TOL
+
+
 def test_plane_kernel_many_warps_ragged():
     """p = 8 on 9 x 7 x 5 = 315 elements (79 element groups over many warps,
     the last group one element short), x-graded to aspect ratio 32."""
