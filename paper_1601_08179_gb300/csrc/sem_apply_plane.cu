@@ -744,7 +744,7 @@ __device__ __forceinline__ void plane2_element(float* W, const int* H, float* __
   const int j = actj ? jj : N - 1;
   const int l = i0 + (jj & 7);                // position owned for y-faces and edges
   const bool actl = jj < 8 && l < N;
-  const int lc = actl ? l : N - 1;
+  const int lc = l < N ? l : N - 1;           // (lanes jj and jj ^ 8 share the position)
 
   const float w0 = Cf[PS + 32], w02 = Cf[PS + 33], d0 = Cf[PS + 34];
   float a[8], b[8], l1[8], e4[8], e5[8];
@@ -769,13 +769,22 @@ __device__ __forceinline__ void plane2_element(float* W, const int* H, float* __
     cO[q] = Cf[PS + q];
     fc[q] = Cf[PS + 6 + q];
   }
+  // the walk's face outputs: lane (c, jj) forms the x-face c output at
+  // (k, j) and the y-face jj >> 3 output at (k, l), so every lane forms one
+  // output of each kind
+  const int fy = jj >> 3;
+  const bool actly = l < N;
+  const int ox = H[c], oy = H[2 + fy];
+  const float fcx = c ? fc[1] : fc[0], cOx = c ? cO[1] : cO[0];   // selects keep the arrays in registers
+  const float eyx0 = c ? ey[1] : ey[0], eyx1 = c ? ey[3] : ey[2];
+  const float fcy = fy ? fc[3] : fc[2], cOy = fy ? cO[3] : cO[2];
+  const float exy0 = fy ? ex[1] : ex[0], exy1 = fy ? ex[3] : ex[2];
   float z4[8], z5[8];
 #pragma unroll
   for (int t = 0; t < 8; ++t) z4[t] = z5[t] = 0.f;
   // line sums along k for the edges at l: sx[2 sa + sc] = sum_k (e|g)_k F_sa[k][l],
   // sy[2 sb + sc] = sum_k (e|g)_k F_{2+sb}[k][l]
   float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f};
-  const int ox0 = H[0], ox1 = H[1], oy0 = H[2], oy1 = H[3];
 
 #pragma unroll 1
   for (int k = 0; k < N; ++k) {
@@ -821,44 +830,26 @@ __device__ __forceinline__ void plane2_element(float* W, const int* H, float* __
     sy[1] = fmaf(gk, Cl, sy[1]);
     sy[2] = fmaf(ek, Dl, sy[2]);
     sy[3] = fmaf(gk, Dl, sy[3]);
-    if (c == 0 && actj) {
-      const int kj = k * N + j;
-      const float bx = w0 * (l2j + l3k);
-      float o = (fc[0] + bx) * A;
-      o = fmaf(cO[0], B, o);
-      o = fmaf(w0, fmaf(cj, ezk.x, fmaf(dj, ezk.z, fmaf(ek, ey[0], gk * ey[2]))), o);
-      o -= X0;
-      if (ox0 >= 0) {
-        atomicAdd(v + ox0 + kj, o);
-        dot = fmaf(A, o, dot);
-      }
-      o = (fc[1] + bx) * B;
-      o = fmaf(cO[1], A, o);
-      o = fmaf(w0, fmaf(cj, ezk.y, fmaf(dj, ezk.w, fmaf(ek, ey[1], gk * ey[3]))), o);
-      o -= X1;
-      if (ox1 >= 0) {
-        atomicAdd(v + ox1 + kj, o);
-        dot = fmaf(B, o, dot);
+    if (actj) {      // x-face c at (k, j): diagonal, opposite face, the four edge lines, -condensed
+      const float own = c ? B : A, opp = c ? A : B;
+      float o = (fcx + w0 * (l2j + l3k)) * own;
+      o = fmaf(cOx, opp, o);
+      o = fmaf(w0, fmaf(cj, c ? ezk.y : ezk.x, fmaf(dj, c ? ezk.w : ezk.z, fmaf(ek, eyx0, gk * eyx1))), o);
+      o -= c ? X1 : X0;
+      if (ox >= 0) {
+        atomicAdd(v + ox + k * N + j, o);
+        dot = fmaf(own, o, dot);
       }
     }
-    if (actl) {
-      const int kl = k * N + l;
-      const float by = w0 * (l1l + l3k);
-      float o = (fc[2] + by) * Cl;
-      o = fmaf(cO[2], Dl, o);
-      o = fmaf(w0, fmaf(al, ezk.x, fmaf(bl, ezk.y, fmaf(ek, ex[0], gk * ex[2]))), o);
-      o -= Y0;
-      if (oy0 >= 0) {
-        atomicAdd(v + oy0 + kl, o);
-        dot = fmaf(Cl, o, dot);
-      }
-      o = (fc[3] + by) * Dl;
-      o = fmaf(cO[3], Cl, o);
-      o = fmaf(w0, fmaf(al, ezk.z, fmaf(bl, ezk.w, fmaf(ek, ex[1], gk * ex[3]))), o);
-      o -= Y1;
-      if (oy1 >= 0) {
-        atomicAdd(v + oy1 + kl, o);
-        dot = fmaf(Dl, o, dot);
+    if (actly) {     // y-face jj >> 3 at (k, l)
+      const float own = fy ? Dl : Cl, opp = fy ? Cl : Dl;
+      float o = (fcy + w0 * (l1l + l3k)) * own;
+      o = fmaf(cOy, opp, o);
+      o = fmaf(w0, fmaf(al, fy ? ezk.z : ezk.x, fmaf(bl, fy ? ezk.w : ezk.y, fmaf(ek, exy0, gk * exy1))), o);
+      o -= fy ? Y1 : Y0;
+      if (oy >= 0) {
+        atomicAdd(v + oy + k * N + l, o);
+        dot = fmaf(own, o, dot);
       }
     }
   }
