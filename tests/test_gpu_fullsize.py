@@ -120,33 +120,34 @@ def test_mixed16_error_per_refinement_step():
     assert final <= 1e-9
 
 
-W16 = si.scale_workload(16)
-GOLD_16 = os.path.join(os.path.dirname(__file__), "golden", f"oracle_{W16.name}.json")
+SWEEP_RECORDED = (16,)   # degrees of the graded sweep with an oracle record besides p = 8
 
 
+@pytest.mark.parametrize("p", SWEEP_RECORDED)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_p16_solution_samples_and_iterations(precision):
-    """The graded p = 16 workload (16^3 elements, aspect ratio 128, lambda = 0)
-    at full size against the oracle's solve: FP64 (CTA-tile operator) and
-    mixed (two-half-row plane operator) solutions at the benchmark tolerance
-    on the recorded sample nodes; the FP64 CG takes the oracle's iteration
-    count."""
+def test_sweep_solution_samples_and_iterations(p, precision):
+    """Graded sweep workloads (N ~ 1.68e7, aspect ratio 128, lambda = 0) at
+    full size against the oracle's solve: FP64 and mixed solutions at the
+    benchmark tolerance on the recorded sample nodes; the FP64 CG takes the
+    oracle's iteration count."""
     import torch
     from paper_1601_08179_gb300 import build, sem
-    if not os.path.exists(GOLD_16):
-        pytest.fail(f"missing {GOLD_16}: run python -m oracle.reference_solve 16")
-    rec = json.load(open(GOLD_16))
+    w = si.scale_workload(p)
+    gold = os.path.join(os.path.dirname(__file__), "golden", f"oracle_{w.name}.json")
+    if not os.path.exists(gold):
+        pytest.fail(f"missing {gold}: run python -m oracle.reference_solve {p}")
+    rec = json.load(open(gold))
     build.build()
-    hx, hy, hz = W16.widths()
-    ms = Mesh(W16.p, hx, hy, hz)
+    hx, hy, hz = w.widths()
+    ms = Mesh(w.p, hx, hy, hz)
     X, Y, Z = ms.coords()
-    f = dev((si.manufactured_f(X, Y, Z, W16.lam) + si.node_noise(X.size, W16.seed).reshape(X.shape)).ravel())
+    f = dev((si.manufactured_f(X, Y, Z, w.lam) + si.node_noise(X.size, w.seed).reshape(X.shape)).ravel())
     prec = sem.PREC_FP64 if precision == "fp64" else sem.PREC_MIXED
-    ctx = sem.sem_setup(W16.p, hx, hy, hz, W16.lam, sem.default_opts(precision=prec))
+    ctx = sem.sem_setup(w.p, hx, hy, hz, w.lam, sem.default_opts(precision=prec))
     u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
     info = sem.sem_solve(ctx, f, u)
     err = _sampled_rel(host(u)[np.array(rec["u_samples"]["index"])], np.array(rec["u_samples"]["value"]))
-    print(f"p = 16 {precision}: sampled error {err:.2e}, iterations {info['iters']}")
+    print(f"p = {p} {precision}: sampled error {err:.2e}, iterations {info['iters']}")
     assert err <= 1e-8
     if precision == "fp64":
         assert abs(info["iters"] - rec["iterations_to_1e-10"]) <= 2
