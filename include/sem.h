@@ -286,7 +286,10 @@ sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const d
  *   SEM_KERNEL_SLAB      a CTA works on one element and a slab of 8 planes k
  *                        of its eigenspace cube at a time (FP32,
  *                        16 <= n <= 31)
- * where n = p - 1. */
+ * where n = p - 1.  SEM_KERNEL_AUTO resolves, in FP64, to ELEMENT at p = 2
+ * and CTA_TILE otherwise; in FP32 to ELEMENT at p <= 3, PLANE for
+ * 4 <= p <= 16 and SLAB for 17 <= p <= 32 (the fastest measured on GB300;
+ * sem_autotune ranks the alternatives for a given mesh). */
 enum {
   SEM_KERNEL_AUTO = 0,
   SEM_KERNEL_CTA_TILE = 1,
