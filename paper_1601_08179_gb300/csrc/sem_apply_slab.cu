@@ -9,7 +9,8 @@
 // the work onto the GPU differs.
 //
 // * A work unit is one element and one slab of K = 8 planes k of its n^3
-//   eigenspace cube; a CTA of four warps takes one unit at a time.  The
+//   eigenspace cube; a CTA of four warps takes one unit (a range of units
+//   past 65536 of them).  The
 //   expansion and D^-1 are pointwise in k, so a slab's share of the x- and
 //   y-face outputs is complete (their rows k in the slab) and its share of
 //   the z-face outputs (sums over k) is a partial sum, added by the scatter
@@ -24,9 +25,12 @@
 // * D^-1 = 1 / (d0 + d1 lambda_i + d2 lambda_j + d3 lambda_k) is formed per
 //   point with one reciprocal (as in the plane kernels), from the class block
 //   of plane_layout(n).
-// * Line sums of the primary part that run along k are split over the slabs
-//   in the same way; the rest of the primary part is done once per element
-//   (the z-face rows by a 1 / S share per slab, edges and vertices by slab 0).
+// * The primary part of each face output is formed by the thread that holds
+//   its operands (the walk thread for the x- and z-faces, the y-contraction
+//   thread for the y-faces).  Line sums of the primary part that run along k
+//   are split over the slabs in the same way as the condensed sums; the rest
+//   of the primary part is done once per element (the z-face rows by a 1 / S
+//   share per slab, edges and vertices by slab 0).
 // * Outputs are staged in shared memory and scattered one row per warp
 //   instruction (contiguous red.global.add).
 #include <cuda_runtime.h>
