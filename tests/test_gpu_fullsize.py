@@ -120,7 +120,7 @@ def test_mixed16_error_per_refinement_step():
     assert final <= 1e-9
 
 
-SWEEP_RECORDED = (16,)   # degrees of the graded sweep with an oracle record besides p = 8
+SWEEP_RECORDED = (4, 16)   # degrees of the graded sweep with an oracle record besides p = 8
 
 
 @pytest.mark.parametrize("p", SWEEP_RECORDED)
