@@ -207,7 +207,9 @@ sem_status sem_solve(sem_ctx* ctx, const double* f, double* u, const double* u0,
 
 /* sem_solve on HOST arrays f_host, u_host (full nodal fields): copies f to the
  * device, solves, copies u back, all on `stream`; returns when u_host is
- * written.  Pinned host memory gives the fastest copies. */
+ * written.  Pinned host memory gives the fastest copies.  The two device
+ * fields it copies through are allocated on the first call and kept by the
+ * context (freed by sem_destroy); SEM_ENOMEM if they cannot be allocated. */
 sem_status sem_solve_host(sem_ctx* ctx, const double* f_host, double* u_host,
                           sem_info* info, void* stream);
 

@@ -73,6 +73,8 @@ struct sem_ctx {
   double* d_coef_soa = nullptr;        // n = 1: the class blocks transposed (FP64, FP32)
   float* d_coef_soa_f = nullptr;
   float* d_plane_soa = nullptr;        // n = 2, 3: the plane blocks transposed
+  double* d_hf = nullptr;              // device copies of sem_solve_host's load and solution (first use)
+  double* d_hu = nullptr;
   double* d_mats = nullptr;            // 4 n*n: S_II, V, V^T M_II, M_II V
   double* d_mass = nullptr;            // [Nx + Ny + Nz] assembled 1D lumped masses
   double* d_h = nullptr;               // [mx + my + mz] element widths
@@ -660,7 +662,7 @@ void free_ctx(sem_ctx* c) {
   if (c->graph32m) cudaGraphExecDestroy(c->graph32m);
   void* ptrs32[] = {c->d_dcoef_f, c->d_dinv_f, c->d_P32, c->d_b32, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_st32,
                     c->d_coef_f, c->d_coef, c->d_plane, c->d_ctl, c->d_stg, c->d_coef_soa, c->d_coef_soa_f,
-                    c->d_plane_soa};
+                    c->d_plane_soa, c->d_hf, c->d_hu};
   for (void* p : ptrs32)
     if (p) cudaFree(p);
   for (cudaEvent_t ev : c->pev32) cudaEventDestroy(ev);
@@ -1033,13 +1035,17 @@ sem_status sem_solve_host(sem_ctx* c, const double* f_host, double* u_host, sem_
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   if (f_host == nullptr || u_host == nullptr) return fail(SEM_EINVAL, "null vector");
-  const size_t bytes = sizeof(double) * (size_t)(c->g.Nx * c->g.Ny * c->g.Nz);
+  const long long nn = c->g.Nx * c->g.Ny * c->g.Nz;
+  const size_t bytes = sizeof(double) * (size_t)nn;
   cudaStream_t us = (cudaStream_t)stream;
-  double *df = nullptr, *du = nullptr;
-  if (cudaMalloc((void**)&df, bytes) != cudaSuccess || cudaMalloc((void**)&du, bytes) != cudaSuccess) {
-    if (df) cudaFree(df);
+  // the device copies are kept by the context (no allocation, and no
+  // device-wide synchronization of a free, in the calls after the first)
+  if (c->d_hf == nullptr && (dalloc(&c->d_hf, nn) != cudaSuccess || dalloc(&c->d_hu, nn) != cudaSuccess)) {
+    if (c->d_hf) cudaFree(c->d_hf);
+    c->d_hf = c->d_hu = nullptr;
     return fail(SEM_ENOMEM, "cannot allocate device fields");
   }
+  double *df = c->d_hf, *du = c->d_hu;
   sem_status st = SEM_OK;
   cudaError_t e = cudaMemcpyAsync(df, f_host, bytes, cudaMemcpyHostToDevice, us);
   if (e != cudaSuccess) st = fail(SEM_ECUDA, cudaGetErrorString(e));
@@ -1053,8 +1059,6 @@ sem_status sem_solve_host(sem_ctx* c, const double* f_host, double* u_host, sem_
       keep = t_err;
     }
   }
-  cudaFree(df);
-  cudaFree(du);
   t_err = keep;
   return st;
 }

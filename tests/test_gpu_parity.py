@@ -230,6 +230,26 @@ def test_set_lambda_refreshes_every_operator_table(p):
     assert relerr(host(v32), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_solve_host_buffers(mixed):
+    """sem_solve_host (host load in, host solution out, copies inside): two
+    calls with different loads (the second reuses the context's device
+    fields), each equal to the device-buffer solve and within the solve bar
+    of the dense oracle."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    opts = sem.default_opts(precision=sem.PREC_MIXED) if mixed else None
+    ctx, ms = make_pair(5, (3, 2, 2), 2.0, 3.0, opts=opts)
+    for seed in (41, 42):
+        f = si.node_noise(ms.n_global, seed)
+        u_host = np.zeros(ctx.n_nodes)
+        sem.sem_solve_host(ctx, np.ascontiguousarray(f), u_host)
+        u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+        sem.sem_solve(ctx, dev(f), u)
+        assert relerr(u_host, host(u)) <= 1e-10   # equal up to the order of atomic adds
+        assert relerr(u_host, dense.solve_full(ms, 2.0, f)) <= SOLVE_TOL
+
+
 def test_breakdown_on_nan_input():
     import torch
     from paper_1601_08179_gb300 import sem
