@@ -184,6 +184,7 @@ TRAFFIC_BYTES = {
     ("k_tpt_apply_slab", "graded_p32_m8_ar128_lam0"): 10743040 + 0,
     ("k_tpt_apply_p2<float>", "graded_p2_m128_ar128_lam0"): 117041408 + 12317952,
     ("k_tpt_apply_p2<double>", "graded_p2_m128_ar128_lam0"): 234106368 + 70302208,
+    ("k_tpt_apply<double, 31> (epb 1, ks 8)", "graded_p32_m8_ar128_lam0"): 23709440 + 0,
 }
 
 
