@@ -65,7 +65,23 @@ def test_argument_checks_without_gpu(L):
     L.sem_destroy(None)
 
 
+def test_setup_rejects_a_skeleton_past_int32(L):
+    """Entity offsets inside the kernels are 32-bit: a mesh whose packed
+    skeleton reaches 2^31 entries (p = 32 on 92^3 elements, N_B ~ 2.3e9) is
+    refused with SEM_ENOTSUP before any device work, with the reason."""
+    from paper_1601_08179_gb300 import sem
+    D = sem._D
+    h = ctypes.c_void_p()
+    m = 92
+    hx = np.full(m, 1.0 / m)
+    st = L.sem_setup(ctypes.byref(h), 32, m, m, m, hx.ctypes.data_as(D), hx.ctypes.data_as(D),
+                     hx.ctypes.data_as(D), 1.0, None)
+    assert st == sem.SEM_ENOTSUP
+    assert "2^31" in L.sem_last_error().decode()
+
+
 def test_default_opts(L):
     from paper_1601_08179_gb300 import sem
     o = sem.default_opts()
     assert o.rtol == 1e-10 and o.precision == sem.PREC_FP64 and o.check_every > 0
+    assert o.reliable_delta == 0.0   # automatic, by degree
