@@ -185,6 +185,11 @@ TRAFFIC_BYTES = {
     ("k_tpt_apply_p2<float>", "graded_p2_m128_ar128_lam0"): 117041408 + 12317952,
     ("k_tpt_apply_p2<double>", "graded_p2_m128_ar128_lam0"): 234106368 + 70302208,
     ("k_tpt_apply<double, 31> (epb 1, ks 8)", "graded_p32_m8_ar128_lam0"): 23709440 + 0,
+    ("k_tpt_apply_plane<3>", "graded_p4_m64_ar128_lam0"): 77069824 + 196864,
+    ("k_tpt_apply<double, 3> (epb 28, ks 3)", "graded_p4_m64_ar128_lam0"): 196983552 + 51975424,
+    ("k_tpt_apply_plane2<15>", "graded_p16_m16_ar128_lam0"): 22298624 + 0,
+    ("k_tpt_apply<double, 15> (epb 1, ks 15)", "graded_p16_m16_ar128_lam0"): 45007616 + 6656,
+    ("k_tpt_apply_plane2<15>", "graded_p16_m16_ar16_lam10"): 22293760 + 0,
 }
 
 
