@@ -488,31 +488,6 @@ k_pcg_flush(long long nb, T* __restrict__ x, const T* __restrict__ p, PcgState* 
   }
 }
 
-// Replaces the CG residual by a freshly computed one: rho = r.P r, rr = r.r,
-// done = 0; the search direction and the iteration count are kept.
-// q is cleared for the next operator application; if the CG had stopped
-// (restart != 0) the direction is restarted as p = P r.
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads)
-k_pcg_rebase(long long nb, const T* __restrict__ r, const T* __restrict__ P, T* __restrict__ p, T* __restrict__ q,
-             int restart, double* __restrict__ partials, PcgState* st) {
-  T rz = T(0), rr = T(0);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
-    const T ri = r[i];
-    const T zi = P[i] * ri;
-    if (restart) p[i] = zi;
-    q[i] = T(0);
-    rz = fma(ri, zi, rz);
-    rr = fma(ri, ri, rr);
-  }
-  double v[2] = {(double)rz, (double)rr}, tot[2];
-  if (reduce_grid<2>(v, partials, &st->counter[1], tot) && threadIdx.x == 0) {
-    st->rho = tot[0];
-    st->rr = tot[1];
-    st->done = (isfinite(tot[0]) && isfinite(tot[1])) ? 0 : 2;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Iterative refinement (FP64 outer loop around the FP32 inner CG)
 // ---------------------------------------------------------------------------
@@ -852,12 +827,6 @@ void launch_pcg_flush(long long nb, T* x, const T* p, PcgState* st, cudaStream_t
   template void launch_pcg_flush<T>(long long, T*, const T*, PcgState*, cudaStream_t);
 SEM_INST_VEC(double)
 SEM_INST_VEC(float)
-
-void launch_pcg_rebase_f32(long long nb, const float* r, const float* P, float* p, float* q, int restart,
-                           double* partials, PcgState* st, cudaStream_t s) {
-  k_pcg_rebase<float><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, P, p, q, restart, partials, st);
-  sem_count_launch();
-}
 
 void launch_ir_residual(long long nb, const double* b, const double* Ax, double* r, double* partials,
                         PcgState* st, cudaStream_t s) {

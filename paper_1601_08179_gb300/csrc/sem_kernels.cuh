@@ -149,8 +149,6 @@ void launch_ir_residual(long long nb, const double* b, const double* Ax, double*
 void launch_scale_to_f32(long long n, const double* in, double scale, float* out, cudaStream_t s);
 void launch_ir_update(long long nb, double* x, const float* c, double scale, cudaStream_t s);
 void launch_cast_f32(long long n, const double* in, float* out, cudaStream_t s);
-// Reliable update of the FP32 CG: rho = r.P r and rr = r.r from the new r, q = 0,
-// done = 0; with restart also p = P r.
 // Device-side refinement of a mixed-precision solve (one MixedCtl per
 // problem): start after the FP64 residual r = b (st64) and the FP32 CG
 // initialisation; one step per loop trip (gate, fold x32 into x, FP64
@@ -162,8 +160,6 @@ void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables
                        const double* rhs, double* x, double* q, double* r, float* x32, float* r32, float* p32,
                        float* q32, const float* P32, double* partials, MixedCtl* ctl, PcgState* st32,
                        PcgState* gate, cudaStream_t s);
-void launch_pcg_rebase_f32(long long nb, const float* r, const float* P, float* p, float* q, int restart,
-                           double* partials, PcgState* st, cudaStream_t s);
 
 int sem_vec_blocks();
 
