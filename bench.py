@@ -105,6 +105,25 @@ def whole_job_value(step_s_max: float, dofs_per_rank: int, world: int) -> float:
     return step_s_max / (dofs_per_rank * world)
 
 
+def skeleton_size(p: int, m) -> int:
+    """Length N_B of the packed skeleton vector of an m[0] x m[1] x m[2] mesh of
+    degree p: n^2 values per face, n per edge, one per vertex (n = p - 1),
+    Dirichlet entities included."""
+    n = p - 1
+    mx, my, mz = m
+    faces = (mx + 1) * my * mz + mx * (my + 1) * mz + mx * my * (mz + 1)
+    edges = mx * (my + 1) * (mz + 1) + (mx + 1) * my * (mz + 1) + (mx + 1) * (my + 1) * mz
+    return faces * n * n + edges * n + (mx + 1) * (my + 1) * (mz + 1)
+
+
+def workload_config(w: si.Workload, world: int) -> dict:
+    """The `config` of a solve bench line; both arms print this same dict."""
+    return {"workload": w.name, "p": w.p, "elements": list(w.m), "dofs_per_gpu": w.dofs,
+            "skeleton_unknowns": skeleton_size(w.p, w.m), "lambda": w.lam, "aspect_ratio": w.ar,
+            "rtol": 1e-10, "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (solve working set > 129 MB)"}
+
+
 def max_over_ranks(x: float, world: int) -> float:
     if world == 1:
         return x
@@ -352,6 +371,7 @@ def our_arm(args, rank, world, local_rank):
 
     flops = apply_flops(w)
     nb = ctx.nb
+    assert nb == skeleton_size(w.p, w.m), (nb, w.p, w.m)
     if head == "fp64":
         achieved = flops / r["apply_s"] / 1e12
         roof = {"kernel": kernel_name(sem, ctx, sem.PREC_FP64, w.p), "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
@@ -390,10 +410,8 @@ def our_arm(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "f64" if head == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "dofs_per_gpu": w.dofs,
-                   "skeleton_unknowns": nb, "lambda": w.lam, "aspect_ratio": w.ar, "rtol": 1e-10,
-                   "precision": head, "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (solve working set > 129 MB)"},
+        "precision": head,
+        "config": workload_config(w, world),
         "solve": {"iters": r["info"]["iters"], "refinements": r["info"]["refinements"],
                   "rel_res": r["info"]["rel_res"], "setup_s": setup_s},
         "operator": {"gdof_s": w.dofs / r["apply_s"] / 1e9, "apply_ms": r["apply_s"] * 1e3,
@@ -479,8 +497,9 @@ def batched_arm(args, rank, world, local_rank):
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
            "config": {"workload": "batched64", "problems": len(work), "dofs_total": dofs,
-                      "degrees": sorted(set(w.p for w in work)), "rtol": 1e-10, "precision": head,
+                      "degrees": sorted(set(w.p for w in work)), "rtol": 1e-10,
                       "parallelism": f"replicas{world}"},
+           "precision": head,
            "iters_max": max(i["iters"] for i in r["infos"]), "iters_sum": sum(i["iters"] for i in r["infos"]),
            "rel_res_max": max(i["rel_res"] for i in r["infos"]),
            "gpu_launches": r["launches"], "clocks": r["clocks"]}
@@ -614,8 +633,7 @@ def reference_arm(args, rank, world):
            "ms_per_step": statistics.median(s["sample_s"] for s in samples) * 1e3,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "dofs_per_gpu": w.dofs,
-                      "lambda": w.lam, "aspect_ratio": w.ar, "rtol": 1e-10, "precision": "fp64"},
+           "precision": "fp64", "config": workload_config(w, world),
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                             "sample": last["sample"]},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

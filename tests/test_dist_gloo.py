@@ -82,3 +82,9 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert d["unit"] == "s/DOF" and d["higher_is_better"] is False
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"] == {"value": d["value"], "unit": "s/DOF", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the same workload config as the arm that runs the library, the oracle's precision beside it
+    sys.path.insert(0, ROOT)
+    import bench
+    import sem_inputs as si
+    assert d["config"] == bench.workload_config(si.scale_workload(8), 2)
+    assert d["precision"] == "fp64" and d["dtype"] == "f64"
