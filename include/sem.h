@@ -45,10 +45,14 @@
  * every face, S_II to every edge and 1 to every vertex.
  *
  * Memory and ownership: every vector argument is a caller-owned DEVICE pointer
- * (CUDA global memory of the current device), 8-byte aligned, unless the name
- * says host.  The library never frees caller memory.  A context owns its
- * precomputed tables and solver scratch on the device it was created on.  A
- * context is not thread-safe: use one context per host thread.
+ * (CUDA global memory of the device the context was created on, or managed
+ * memory), aligned to its entry size (8 bytes, 4 for the FP32 vectors), unless
+ * the name says host.  Every entry point checks this of each vector before any
+ * launch (sem_check_vector) and returns SEM_EINVAL otherwise; the length
+ * cannot be checked and is the caller's duty.  The library never frees caller
+ * memory.  A context owns its precomputed tables and solver scratch on the
+ * device it was created on.  A context is not thread-safe: use one context per
+ * host thread.
  *
  * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
  * Operator, load and recovery calls are asynchronous on that stream.  sem_solve
@@ -314,6 +318,11 @@ sem_status sem_set_operator_kernel(sem_ctx* ctx, int precision, int kind, int ep
 /* The kernel in use for one precision, SEM_KERNEL_AUTO resolved: *kind, and
  * for a CTA tile *epb, *ks (else 0; epb, ks may be NULL). */
 sem_status sem_get_operator_kernel(const sem_ctx* ctx, int precision, int* kind, int* epb, int* ks);
+/* The check every entry point makes of a vector argument, without any launch:
+ * SEM_OK if p is not null, is a multiple of elem_bytes (4 or 8) and points to
+ * device memory of the context's device or to managed memory; else SEM_EINVAL
+ * with the reason in sem_last_error(). */
+sem_status sem_check_vector(const sem_ctx* ctx, const void* p, int elem_bytes);
 /* *fused = 1 if the FP32 CG iterations of this context's mixed solves run as
  * one fused kernel each (see sem_opts.fused_cg), else 0. */
 sem_status sem_cg_fused(const sem_ctx* ctx, int* fused);

@@ -690,6 +690,30 @@ sem_status check_ctx(const sem_ctx* c) {
   return SEM_OK;
 }
 
+// A caller vector of `elem`-byte entries: not null, aligned to its entry size,
+// and device memory of the context's device (or managed memory), so that no
+// kernel is launched on a host pointer or on another GPU's memory.
+sem_status check_vec(const sem_ctx* c, const void* p, size_t elem, const char* name) {
+  if (p == nullptr) return fail(SEM_EINVAL, std::string(name) + " is null");
+  if (reinterpret_cast<uintptr_t>(p) % elem != 0)
+    return fail(SEM_EINVAL, std::string(name) + " is not aligned to its entry size");
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // the query's error is not sticky: clear it
+    return fail(SEM_EINVAL, std::string(name) + " is not a CUDA address");
+  }
+  if (a.type == cudaMemoryTypeManaged) return SEM_OK;
+  if (a.type != cudaMemoryTypeDevice) return fail(SEM_EINVAL, std::string(name) + " is not device memory");
+  if (a.device != c->device) return fail(SEM_EINVAL, std::string(name) + " is on another device than the context");
+  return SEM_OK;
+}
+
+#define SEM_CHECK_VEC(p, T)                                        \
+  do {                                                             \
+    const sem_status st_ = check_vec(c, (p), sizeof(T), #p);        \
+    if (st_ != SEM_OK) return st_;                                 \
+  } while (0)
+
 }  // namespace
 
 extern "C" {
@@ -932,7 +956,8 @@ sem_status sem_get_basis(const sem_ctx* c, double* gx, double* gw, double* lam, 
 sem_status sem_apply_condensed(sem_ctx* c, const double* uB, double* vB, sem_space space, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (uB == nullptr || vB == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(uB, double);
+  SEM_CHECK_VEC(vB, double);
   if (uB == vB) return fail(SEM_EINVAL, "uB and vB must not alias");
   cudaStream_t s = (cudaStream_t)stream;
   if (space == SEM_SPACE_TRANSFORMED) return apply_t(c, uB, vB, s);
@@ -948,7 +973,8 @@ sem_status sem_apply_condensed(sem_ctx* c, const double* uB, double* vB, sem_spa
 sem_status sem_apply_condensed_f32(sem_ctx* c, const float* uB, float* vB, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (uB == nullptr || vB == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(uB, float);
+  SEM_CHECK_VEC(vB, float);
   if ((const void*)uB == (const void*)vB) return fail(SEM_EINVAL, "uB and vB must not alias");
   sem_status st = ensure_mixed(c);
   if (st != SEM_OK) return st;
@@ -964,7 +990,8 @@ sem_status sem_apply_condensed_f32(sem_ctx* c, const float* uB, float* vB, void*
 sem_status sem_condense_rhs(sem_ctx* c, const double* f, double* fB, sem_space space, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (f == nullptr || fB == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(f, double);
+  SEM_CHECK_VEC(fB, double);
   if (space != SEM_SPACE_NODAL && space != SEM_SPACE_TRANSFORMED) return fail(SEM_EINVAL, "unknown space");
   cudaStream_t s = (cudaStream_t)stream;
   sem_status st = condense_rhs_t(c, f, fB, s);
@@ -979,7 +1006,7 @@ sem_status sem_condense_rhs(sem_ctx* c, const double* f, double* fB, sem_space s
 sem_status sem_precond_diag(sem_ctx* c, double* diag, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (diag == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(diag, double);
   cudaStream_t s = (cudaStream_t)stream;
   SEM_CUDA(cudaMemsetAsync(diag, 0, sizeof(double) * c->g.nb, s));
   launch_precond_diag(c->g, c->h1.basis, c->tab, diag, s);
@@ -991,7 +1018,9 @@ sem_status sem_recover_interior(sem_ctx* c, const double* f, const double* uB, s
                                 void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (f == nullptr || uB == nullptr || u == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(f, double);
+  SEM_CHECK_VEC(uB, double);
+  SEM_CHECK_VEC(u, double);
   if (space != SEM_SPACE_NODAL && space != SEM_SPACE_TRANSFORMED) return fail(SEM_EINVAL, "unknown space");
   cudaStream_t s = (cudaStream_t)stream;
   // F~_I for this f (the condensed load itself is discarded)
@@ -1008,7 +1037,9 @@ sem_status sem_recover_interior(sem_ctx* c, const double* f, const double* uB, s
 sem_status sem_solve(sem_ctx* c, const double* f, double* u, const double* u0, sem_info* info, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (f == nullptr || u == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(f, double);
+  SEM_CHECK_VEC(u, double);
+  if (u0 != nullptr) SEM_CHECK_VEC(u0, double);
   const auto t0 = std::chrono::steady_clock::now();
   if (info) std::memset(info, 0, sizeof(*info));
   cudaStream_t us = (cudaStream_t)stream;
@@ -1070,7 +1101,8 @@ sem_status sem_solve_host(sem_ctx* c, const double* f_host, double* u_host, sem_
 sem_status sem_transform_skeleton(sem_ctx* c, const double* in, double* out, int kind, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (in == nullptr || out == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(in, double);
+  SEM_CHECK_VEC(out, double);
   if (kind < 0 || kind > 3) return fail(SEM_EINVAL, "kind must be 0..3");
   static const int mat_of_kind[4] = {2, 1, 0, 3};
   launch_skel_transform(c->g, c->mat(mat_of_kind[kind]), in, out, (cudaStream_t)stream);
@@ -1081,7 +1113,8 @@ sem_status sem_transform_skeleton(sem_ctx* c, const double* in, double* out, int
 sem_status sem_pack_skeleton(sem_ctx* c, const double* u_full, double* uB, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (u_full == nullptr || uB == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(u_full, double);
+  SEM_CHECK_VEC(uB, double);
   launch_pack(c->g, u_full, uB, (cudaStream_t)stream);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
@@ -1090,7 +1123,8 @@ sem_status sem_pack_skeleton(sem_ctx* c, const double* u_full, double* uB, void*
 sem_status sem_unpack_skeleton(sem_ctx* c, const double* uB, double* u_full, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (u_full == nullptr || uB == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(uB, double);
+  SEM_CHECK_VEC(u_full, double);
   launch_unpack(c->g, uB, u_full, 0, (cudaStream_t)stream);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
@@ -1138,7 +1172,8 @@ static sem_status ensure_adjoint(sem_ctx* c) {
 sem_status sem_solve_adjoint(sem_ctx* c, const double* gload, double* w, sem_info* info, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (gload == nullptr || w == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(gload, double);
+  SEM_CHECK_VEC(w, double);
   sem_status st = ensure_adjoint(c);
   if (st != SEM_OK) return st;
   const SemGeom& g = c->g;
@@ -1153,7 +1188,10 @@ sem_status sem_gradients(sem_ctx* c, const double* w, const double* u, const dou
                          double* dlambda, double* dhx, double* dhy, double* dhz, void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (w == nullptr || u == nullptr || f == nullptr || df == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(w, double);
+  SEM_CHECK_VEC(u, double);
+  SEM_CHECK_VEC(f, double);
+  SEM_CHECK_VEC(df, double);
   sem_status st = ensure_adjoint(c);
   if (st != SEM_OK) return st;
   const SemGeom& g = c->g;
@@ -1249,7 +1287,8 @@ extern "C" sem_status sem_condense_rhs_noalloc(sem_ctx* c, const double* f, doub
                                                void* stream) {
   t_err.clear();
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
-  if (f == nullptr || fB == nullptr) return fail(SEM_EINVAL, "null vector");
+  SEM_CHECK_VEC(f, double);
+  SEM_CHECK_VEC(fB, double);
   if (space != SEM_SPACE_NODAL && space != SEM_SPACE_TRANSFORMED) return fail(SEM_EINVAL, "unknown space");
   const SemGeom& g = c->g;
   const long long cube = g.nelem * (long long)g.n * g.n * g.n;
@@ -1437,6 +1476,13 @@ extern "C" sem_status sem_set_operator_kernel(sem_ctx* c, int precision, int kin
   return SEM_OK;
 }
 
+extern "C" sem_status sem_check_vector(const sem_ctx* c, const void* p, int elem_bytes) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (elem_bytes != 4 && elem_bytes != 8) return fail(SEM_EINVAL, "elem_bytes must be 4 or 8");
+  return check_vec(c, p, (size_t)elem_bytes, "vector");
+}
+
 extern "C" sem_status sem_cg_fused(const sem_ctx* c, int* fused) {
   t_err.clear();
   if (c == nullptr || fused == nullptr) return fail(SEM_EINVAL, "null argument");
@@ -1531,7 +1577,12 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
     return fail(SEM_EINVAL, "null argument or empty batch");
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
-    if (ctxs[i] == nullptr || f[i] == nullptr || u[i] == nullptr) return fail(SEM_EINVAL, "null context or field");
+    if (ctxs[i] == nullptr) return fail(SEM_EINVAL, "null context");
+    {
+      const sem_ctx* c = ctxs[i];
+      SEM_CHECK_VEC(f[i], double);
+      SEM_CHECK_VEC(u[i], double);
+    }
     if (ctxs[i]->opts.precision == SEM_PREC_MIXED && ctxs[i]->opts.mixed_scheme != 1)
       return fail(SEM_ENOTSUP, "batched mixed-precision solves use reliable updates (mixed_scheme 1)");
     for (int j = 0; j < i; ++j)

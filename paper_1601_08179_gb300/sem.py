@@ -83,6 +83,7 @@ def lib():
         "sem_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "sem_set_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "sem_cg_fused": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+        "sem_check_vector": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "sem_get_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "sem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -116,7 +117,7 @@ def exported_symbols():
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
             "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_set_operator_kernel",
-            "sem_get_operator_kernel", "sem_cg_fused", "sem_batch_create", "sem_batch_solve",
+            "sem_get_operator_kernel", "sem_cg_fused", "sem_check_vector", "sem_batch_create", "sem_batch_solve",
             "sem_batch_destroy", "sem_solve_batch",
             "sem_profile_enable",
             "sem_profile_read", "sem_launch_count",
@@ -339,6 +340,13 @@ def sem_get_operator_kernel(ctx: SemContext, precision: int):
     _check(lib().sem_get_operator_kernel(ctx.handle, int(precision), ctypes.byref(k), ctypes.byref(e),
                                          ctypes.byref(s)))
     return k.value, e.value, s.value
+
+
+def sem_check_vector(ctx: SemContext, ptr: int, elem_bytes: int) -> int:
+    """Status of the check every entry point makes of a vector address (no
+    launch): SEM_OK for device memory of the context's device (or managed
+    memory) aligned to elem_bytes, else SEM_EINVAL."""
+    return lib().sem_check_vector(ctx.handle, ctypes.c_void_p(ptr), int(elem_bytes))
 
 
 def sem_cg_fused(ctx: SemContext) -> bool:

@@ -61,6 +61,7 @@ def test_argument_checks_without_gpu(L):
     assert st == sem.SEM_EINVAL
     # null context
     assert L.sem_apply_condensed(None, None, None, 0, None) == sem.SEM_EINVAL
+    assert L.sem_check_vector(None, None, 8) == sem.SEM_EINVAL
     assert L.sem_status_string(sem.SEM_ENOCONV) == b"not converged"
     L.sem_destroy(None)
 

@@ -250,6 +250,47 @@ def test_solve_host_buffers(mixed):
         assert relerr(u_host, dense.solve_full(ms, 2.0, f)) <= SOLVE_TOL
 
 
+def test_vector_arguments_are_checked_before_any_launch():
+    """Every entry point checks each device vector as sem_check_vector does
+    (device memory of the context's device, aligned to its entry size).  A
+    host array, pinned host memory and misaligned or null addresses are
+    refused; each is first shown to fail sem_check_vector (which launches
+    nothing) before an entry point is given it, and the entry point then
+    returns SEM_EINVAL with nothing launched."""
+    import ctypes
+    import torch
+    from paper_1601_08179_gb300 import sem
+    L = sem.lib()
+    ctx, ms = make_pair(4, (2, 2, 2), 1.0)
+    uB = torch.zeros(ctx.nb, dtype=torch.float64, device="cuda")
+    vB = torch.zeros(ctx.nb, dtype=torch.float64, device="cuda")
+    u32 = torch.zeros(ctx.nb, dtype=torch.float32, device="cuda")
+    assert sem.sem_check_vector(ctx, uB.data_ptr(), 8) == sem.SEM_OK
+    assert sem.sem_check_vector(ctx, u32.data_ptr(), 4) == sem.SEM_OK
+    assert sem.sem_check_vector(ctx, uB.data_ptr() + 4, 4) == sem.SEM_OK   # a float at a 4-byte offset
+    host_arr = np.zeros(ctx.nb)
+    pinned = torch.zeros(ctx.nb, dtype=torch.float64).pin_memory()
+    bad = {"host": host_arr.ctypes.data, "pinned": pinned.data_ptr(), "misaligned": uB.data_ptr() + 4, "null": 0}
+    for name, ptr in bad.items():
+        assert sem.sem_check_vector(ctx, ptr, 8) == sem.SEM_EINVAL, name
+        assert L.sem_last_error().decode(), name
+    assert sem.sem_check_vector(ctx, uB.data_ptr(), 3) == sem.SEM_EINVAL
+    n0 = sem.sem_launch_count()
+    for name, ptr in bad.items():
+        P = ctypes.c_void_p(ptr)
+        good = ctypes.c_void_p(vB.data_ptr())
+        assert L.sem_apply_condensed(ctx.handle, P, good, sem.SPACE_TRANSFORMED, None) == sem.SEM_EINVAL, name
+        assert L.sem_apply_condensed(ctx.handle, good, P, sem.SPACE_TRANSFORMED, None) == sem.SEM_EINVAL, name
+        assert L.sem_pack_skeleton(ctx.handle, P, good, None) == sem.SEM_EINVAL, name
+        assert L.sem_solve(ctx.handle, P, P, None, None, None) == sem.SEM_EINVAL, name
+    assert sem.sem_launch_count() == n0
+    # the checks pass the context's own vectors through: a normal call still works
+    uB.copy_(torch.randn(ctx.nb, dtype=torch.float64, device="cuda"))
+    sem.sem_apply_condensed(ctx, uB, vB)
+    torch.cuda.synchronize()
+    assert torch.isfinite(vB).all()
+
+
 def test_breakdown_on_nan_input():
     import torch
     from paper_1601_08179_gb300 import sem
