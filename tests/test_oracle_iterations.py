@@ -1,0 +1,69 @@
+"""Pin of the oracle's BT solver against the iteration behaviour of the
+paper's solver tests (Sec. 7): 8^3 elements graded in x1 and x2 with a
+constant expansion factor alpha (alpha = 1: aspect ratio 1; alpha = 2: aspect
+ratio 2^7 = 128), lambda = 0, the Euclidean residual norm reduced by 1e12.
+
+* The iteration count rises with the polynomial degree.
+* Between aspect ratio 1 and 128 it grows by a factor of about 1.5 only.
+* Table 5 prints, for alpha = 2, the BT solver's solution time and iteration
+  time per DOF; their quotient bounds the iteration count from above (the
+  solution time also holds the setup).  At p = 8 it is 4.25 us / 25.6 ns = 166.
+
+The paper's right-hand side is a manufactured solution with inhomogeneous
+Dirichlet data; here the load is seeded noise with homogeneous Dirichlet
+data (the same condensed operator on the free unknowns), so the counts are
+compared within bands, not exactly (the oracle: 86 / 124 iterations at p = 4,
+112 / 156 at p = 8, for aspect ratio 1 / 128).  Planted in a copy of the
+oracle, a preconditioner diagonal without its condensed self term takes 251
+iterations at p = 8, alpha = 2 (outside the Table 5 band), and no
+preconditioner grows 5.7-fold with the aspect ratio (outside the ratio band).
+Test infrastructure; CPU only.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import sem_inputs as si
+from oracle.mesh import Mesh
+from oracle.solve import bt_solve
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table5_bt_times.txt")
+
+
+def _table5():
+    rows = np.loadtxt(GOLDEN, comments="#")
+    return {int(p): (it_ns, solve_us) for p, it_ns, solve_us in rows}
+
+
+def _iterations(p, alpha_ar):
+    hx, hy, hz, r = si.graded_widths(8, 8, 8, ar=alpha_ar, grade="xy")
+    assert r == pytest.approx(alpha_ar ** (1.0 / 7.0))    # constant expansion factor alpha
+    ms = Mesh(p, hx, hy, hz)
+    f = si.node_noise(ms.n_global, 5)
+    _, _, it, hist = bt_solve(ms, 0.0, f, rtol=1e-12)
+    assert hist[-1] <= 1e-12
+    return it
+
+
+@pytest.fixture(scope="module")
+def counts():
+    return {(p, ar): _iterations(p, ar) for p in (4, 8) for ar in (1.0, 128.0)}
+
+
+def test_iterations_rise_with_degree(counts):
+    for ar in (1.0, 128.0):
+        assert counts[(8, ar)] > counts[(4, ar)]
+
+
+def test_aspect_ratio_128_adds_about_half(counts):
+    for p in (4, 8):
+        ratio = counts[(p, 128.0)] / counts[(p, 1.0)]
+        assert 1.2 <= ratio <= 1.8, (p, ratio)
+
+
+def test_table5_bound_at_p8(counts):
+    it_ns, solve_us = _table5()[8]
+    bound = solve_us * 1e3 / it_ns          # iterations + setup, in iteration times
+    assert bound == pytest.approx(166.0, abs=0.5)
+    assert 0.7 * bound <= counts[(8, 128.0)] <= 1.05 * bound
