@@ -198,11 +198,11 @@ def node_field(x, y, z, w: si.Workload, seed: int):
 # the kernel as committed (the kernel summaries under profiles/); a kernel or
 # workload with no capture reports null.
 TRAFFIC_BYTES = {
-    ("k_tpt_apply_plane<7>", "graded_p8_m32_ar128_lam0"): 43237888 + 0,
-    ("k_tpt_apply<double, 7> (epb 5, ks 7)", "graded_p8_m32_ar128_lam0"): 86415872 + 4352000,
-    ("k_tpt_apply_slab", "graded_p32_m8_ar128_lam0"): 10743040 + 0,
-    ("k_tpt_apply_p2<float>", "graded_p2_m128_ar128_lam0"): 117041408 + 12317952,
-    ("k_tpt_apply_p2<double>", "graded_p2_m128_ar128_lam0"): 234106368 + 70302208,
+    ("k_tpt_apply_plane<7>", "graded_p8_m32_ar128_lam0"): 43238400 + 0,
+    ("k_tpt_apply<double, 7> (epb 5, ks 7)", "graded_p8_m32_ar128_lam0"): 86408448 + 3930368,
+    ("k_tpt_apply_slab", "graded_p32_m8_ar128_lam0"): 10740992 + 0,
+    ("k_tpt_apply_p2<float>", "graded_p2_m128_ar128_lam0"): 117048576 + 11867904,
+    ("k_tpt_apply_p2<double>", "graded_p2_m128_ar128_lam0"): 234115840 + 69901824,
     ("k_tpt_apply<double, 31> (epb 1, ks 8)", "graded_p32_m8_ar128_lam0"): 23709440 + 0,
     ("k_tpt_apply_plane<3>", "graded_p4_m64_ar128_lam0"): 77069824 + 196864,
     ("k_tpt_apply<double, 3> (epb 28, ks 3)", "graded_p4_m64_ar128_lam0"): 196983552 + 51975424,
