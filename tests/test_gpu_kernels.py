@@ -354,3 +354,43 @@ def test_f32_apply_entrywise_high_aspect_ratio(p):
         sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_ELEMENT)
         sem.sem_apply_condensed_f32(ctx, torch.tensor(ut, dtype=torch.float32, device="cuda"), v)
         assert float(np.max(np.abs(host(v) - ref) / scale)) <= 1e-4
+
+
+THIN_CASES = [  # kernel, p, elements: one element thick in x, or a single row or column of elements
+    ("ELEMENT", 2, (1, 4, 3)), ("ELEMENT", 2, (7, 1, 1)), ("ELEMENT", 3, (1, 3, 4)), ("ELEMENT", 4, (1, 1, 9)),
+    ("PLANE", 4, (1, 5, 3)), ("PLANE", 4, (11, 1, 2)), ("PLANE", 8, (1, 2, 3)), ("PLANE", 8, (9, 1, 1)),
+    ("PLANE", 12, (1, 2, 2)), ("PLANE", 16, (1, 1, 3)), ("WARP", 6, (1, 2, 3)),
+    ("SLAB", 20, (1, 2, 2)), ("SLAB", 20, (3, 1, 1)), ("SLAB", 32, (1, 1, 2)),
+]
+
+
+@pytest.mark.parametrize("kind,p,m", THIN_CASES)
+def test_f32_kernels_on_thin_meshes(kind, p, m):
+    """Meshes one element thick in x (both x-faces of every element on the
+    Dirichlet boundary) and single rows or columns of elements: the x-fastest
+    element order, the affine entity offsets and the boundary masks of every
+    FP32 kernel, against the oracle (uniform widths where x has one element,
+    else graded in x to aspect ratio 4)."""
+    from paper_1601_08179_gb300 import sem
+    ar = 1.0 if m[0] == 1 else 4.0
+    ctx, ms = make_pair(p, m, 1.5, ar)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, getattr(sem, "KERNEL_" + kind))
+    err = _check_f32(ctx, ms, 1.5, 900 + p)
+    print(f"{kind.lower()} p={p} m={m}: {err:.2e}")
+    assert err <= F32_TOL
+
+
+@pytest.mark.parametrize("p,m", [(2, (1, 3, 4)), (4, (1, 3, 2)), (8, (5, 1, 1)), (8, (1, 1, 4)), (20, (1, 2, 1))])
+def test_f64_kernels_on_thin_meshes(p, m):
+    """The FP64 operator (thread per element at p = 2, CTA tile above) on the
+    same kinds of thin meshes, at the 1e-12 apply bar."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    ar = 1.0 if m[0] == 1 else 4.0
+    ctx, ms = make_pair(p, m, 0.5, ar)
+    ut = si.random_vector(ms.n_skeleton, 950 + p)
+    v = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+    sem.sem_apply_condensed(ctx, dev(ut), v, sem.SPACE_TRANSFORMED)
+    got, ref = host(v), _oracle_apply(ms, 0.5, ut)
+    assert np.all(got[~ms.skeleton_free] == 0.0)
+    assert relerr(got, ref) <= 1e-12
