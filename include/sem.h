@@ -323,6 +323,18 @@ sem_status sem_get_operator_kernel(const sem_ctx* ctx, int precision, int* kind,
  * device memory of the context's device or to managed memory; else SEM_EINVAL
  * with the reason in sem_last_error(). */
 sem_status sem_check_vector(const sem_ctx* ctx, const void* p, int elem_bytes);
+/* Bounds record of a debug build (the library compiled with SEM_DEBUG, see
+ * paper_1601_08179_gb300/build.py): every kernel checks each skeleton entity
+ * offset it forms (and each class index) against its range before any access,
+ * counts the failures, keeps the first offending value and skips the entity.
+ * sem_debug_oob synchronises the device, returns the count since the last call
+ * in *count and the first value in *first (-1 if none), and clears the record.
+ * sem_debug_limit_skeleton lowers the bound the checks of this context's later
+ * launches compare against (0 <= bound <= N_B; N_B restores it), so that a
+ * test can show an offending offset is caught while every access stays inside
+ * the real vectors.  Both return SEM_ENOTSUP in release builds. */
+sem_status sem_debug_oob(long long* count, long long* first);
+sem_status sem_debug_limit_skeleton(sem_ctx* ctx, long long bound);
 /* *fused = 1 if the FP32 CG iterations of this context's mixed solves run as
  * one fused kernel each (see sem_opts.fused_cg), else 0. */
 sem_status sem_cg_fused(const sem_ctx* ctx, int* fused);

@@ -801,6 +801,9 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
   g.off[0] = 0;
   for (int b = 0; b < 7; ++b) g.off[b + 1] = g.off[b] + cnt[b];
   g.nb = g.off[7];
+#ifdef SEM_DEBUG
+  g.dbg_bound = g.nb;
+#endif
   if (g.nb >= (1LL << 31)) {
     delete c;
     return fail(SEM_ENOTSUP, "skeleton too large: N_B must be below 2^31");
@@ -1481,6 +1484,40 @@ extern "C" sem_status sem_check_vector(const sem_ctx* c, const void* p, int elem
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   if (elem_bytes != 4 && elem_bytes != 8) return fail(SEM_EINVAL, "elem_bytes must be 4 or 8");
   return check_vec(c, p, (size_t)elem_bytes, "vector");
+}
+
+extern "C" sem_status sem_debug_oob(long long* count, long long* first) {
+  t_err.clear();
+  if (count == nullptr || first == nullptr) return fail(SEM_EINVAL, "null argument");
+  *count = 0;
+  *first = -1;
+#ifdef SEM_DEBUG
+  SEM_CUDA(cudaDeviceSynchronize());
+  unsigned long long n = 0;
+  long long f = -1;
+  cudaError_t (*const take[])(unsigned long long*, long long*) = {sem_debug_take_kernels, sem_debug_take_apply,
+                                                                 sem_debug_take_plane, sem_debug_take_slab,
+                                                                 sem_debug_take_elem};
+  for (auto fn : take) SEM_CUDA(fn(&n, &f));
+  *count = (long long)n;
+  *first = n != 0 ? f : -1;
+  return SEM_OK;
+#else
+  return fail(SEM_ENOTSUP, "the bounds record is compiled in debug builds only (SEM_DEBUG)");
+#endif
+}
+
+extern "C" sem_status sem_debug_limit_skeleton(sem_ctx* c, long long bound) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+#ifdef SEM_DEBUG
+  if (bound < 0 || bound > c->g.nb) return fail(SEM_EINVAL, "bound must lie in [0, N_B]");
+  c->g.dbg_bound = bound;
+  return SEM_OK;
+#else
+  (void)bound;
+  return fail(SEM_ENOTSUP, "the bounds record is compiled in debug builds only (SEM_DEBUG)");
+#endif
 }
 
 extern "C" sem_status sem_cg_fused(const sem_ctx* c, int* fused) {

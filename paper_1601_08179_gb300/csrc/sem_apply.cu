@@ -726,7 +726,7 @@ k_tpt_apply_p2(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __r
 #pragma unroll
     for (int r = 0; r < 26; ++r) {
       const EntityAffine a = ent[r];
-      off[r] = (bits & a.mask) ? -1 : a.base + ex * a.sx + ey * a.sy + ez * a.sz;
+      off[r] = entity_offset(a, r, bits, ex, ey, ez, g);
     }
     T F[6], Ed[12], Vt[8];
 #pragma unroll
@@ -1063,3 +1063,5 @@ template void launch_class_coeffs<double>(const SemGeom&, const SemBasis&, const
                                           cudaStream_t);
 template void launch_class_coeffs<float>(const SemGeom&, const SemBasis&, const double*, const double*, float*,
                                          cudaStream_t);
+
+SEM_DEBUG_TU(apply)

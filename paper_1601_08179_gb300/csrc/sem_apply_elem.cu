@@ -48,7 +48,7 @@ k_tpt_apply_elem(SemGeom g, SemClassTables<float> tab, const float* __restrict__
 #pragma unroll
     for (int r = 0; r < 26; ++r) {
       const EntityAffine a = ent[r];
-      off[r] = (bits & a.mask) ? -1 : a.base + ex * a.sx + ey * a.sy + ez * a.sz;
+      off[r] = entity_offset(a, r, bits, ex, ey, ez, g);
     }
     // gather R^T: faces F[slot][slow * N + fast] (x-faces (k, j), y-faces
     // (k, i), z-faces (j, i)); edges E[q][l] (x-edges q = sb + 2 sc, y-edges
@@ -273,3 +273,5 @@ void launch_elem_apply(const SemGeom& g, const SemClassTables<float>& t, const f
   if (g.n == 2) launch_elem_n<2>(g, t, x, y, partials, st, s);
   else launch_elem_n<3>(g, t, x, y, partials, st, s);
 }
+
+SEM_DEBUG_TU(elem)

@@ -131,7 +131,7 @@ __device__ __forceinline__ void plane_header(const SemGeom& g, const SemClassTab
       val = live ? elem_class(g, tab, ex, ey, ez) : fallback;
     } else {
       const EntityAffine a = ent[r];
-      val = (!live || (bits & a.mask)) ? -1 : a.base + ex * a.sx + ey * a.sy + ez * a.sz;
+      val = live ? entity_offset(a, r, bits, ex, ey, ez, g) : -1;
     }
     H[r] = val;
   }
@@ -1275,3 +1275,5 @@ void launch_plane_apply(const SemGeom& g, const SemClassTables<float>& t, const 
     default: launch_plane_n<8>(g, t, x, y, partials, st, s); break;
   }
 }
+
+SEM_DEBUG_TU(plane)

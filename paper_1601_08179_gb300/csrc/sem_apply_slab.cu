@@ -107,7 +107,7 @@ __device__ __forceinline__ void slab_header(const SemGeom& g, const SemClassTabl
     const int bits = (ex == 0) | ((ex == g.mx - 1) << 1) | ((ey == 0) << 2) | ((ey == g.my - 1) << 3) |
                      ((ez == 0) << 4) | ((ez == g.mz - 1) << 5);
     const EntityAffine a = ent[r];
-    H[r] = (bits & a.mask) ? -1 : a.base + ex * a.sx + ey * a.sy + ez * a.sz;
+    H[r] = entity_offset(a, r, bits, ex, ey, ez, g);
   }
 }
 
@@ -540,3 +540,5 @@ void launch_slab_apply(const SemGeom& g, const SemClassTables<float>& t, const f
   k_tpt_apply_slab<<<(int)grid, kSlabThreads, smem, s>>>(g, t, x, y, partials, st);
   sem_count_launch();
 }
+
+SEM_DEBUG_TU(slab)

@@ -8,6 +8,43 @@
 namespace semdev {
 
 // ---------------------------------------------------------------------------
+// Debug builds (-DSEM_DEBUG): bounds record of the entity offsets
+// ---------------------------------------------------------------------------
+// Every skeleton access of a kernel is an entity offset (formed by
+// face_base / edge_base / vert_index or entity_offset below) plus a local
+// index that the loops keep inside the entity (n^2 values of a face, n of an
+// edge, one vertex).  A debug build checks each offset it forms, and each class
+// index, against its range before any access; a failing one is counted, the
+// first offending value kept, and the entity treated as absent (no gather, no
+// scatter), so the kernel goes on without touching memory out of range.
+// Release builds compile every check to nothing.  The record is per
+// translation unit; SEM_DEBUG_TU defines its host reader.
+#ifdef SEM_DEBUG
+static __device__ unsigned long long sem_dbg_count;
+static __device__ long long sem_dbg_first;
+
+static __device__ __forceinline__ bool sem_dbg_ok(long long v, long long extent, long long bound) {
+  if (v >= 0 && v + extent <= bound) return true;
+  if (atomicAdd(&sem_dbg_count, 1ull) == 0ull) sem_dbg_first = v;
+  return false;
+}
+#endif
+
+// An entity offset `off` of `extent` values, formed by a kernel: returned as is
+// in release builds; in debug builds a non-Dirichlet offset reaching past the
+// checked bound (N_B, unless lowered by sem_debug_limit_skeleton) is recorded
+// and turned into "Dirichlet" (*dir = true).
+static __device__ __forceinline__ long long sem_dbg_entity(long long off, long long extent, const SemGeom& g,
+                                                           bool* dir) {
+#ifdef SEM_DEBUG
+  if (!*dir && !sem_dbg_ok(off, extent, g.dbg_bound)) *dir = true;
+#else
+  (void)extent; (void)g; (void)dir;
+#endif
+  return off;
+}
+
+// ---------------------------------------------------------------------------
 // Mesh helpers
 // ---------------------------------------------------------------------------
 static __device__ __forceinline__ void elem_coords(const SemGeom& g, long long e, int* ex, int* ey, int* ez) {
@@ -42,16 +79,16 @@ static __device__ __forceinline__ long long face_base(const SemGeom& g, int ex, 
   if (d == 0) {
     const int f = ex + s;
     *dir = (f == 0 || f == g.mx);
-    return g.off[0] + (f + (long long)(g.mx + 1) * (ey + (long long)g.my * ez)) * n2;
+    return sem_dbg_entity(g.off[0] + (f + (long long)(g.mx + 1) * (ey + (long long)g.my * ez)) * n2, n2, g, dir);
   }
   if (d == 1) {
     const int f = ey + s;
     *dir = (f == 0 || f == g.my);
-    return g.off[1] + (ex + (long long)g.mx * (f + (long long)(g.my + 1) * ez)) * n2;
+    return sem_dbg_entity(g.off[1] + (ex + (long long)g.mx * (f + (long long)(g.my + 1) * ez)) * n2, n2, g, dir);
   }
   const int f = ez + s;
   *dir = (f == 0 || f == g.mz);
-  return g.off[2] + (ex + (long long)g.mx * (ey + (long long)g.my * f)) * n2;
+  return sem_dbg_entity(g.off[2] + (ex + (long long)g.mx * (ey + (long long)g.my * f)) * n2, n2, g, dir);
 }
 
 // Edge slot 0..11: group = slot >> 2 (0 x-edges Ex[sb][sc], 1 y-edges Ey[sa][sc],
@@ -61,23 +98,23 @@ static __device__ __forceinline__ long long edge_base(const SemGeom& g, int ex, 
   if (grp == 0) {
     const int vy = ey + s1, vz = ez + s2;
     *dir = (vy == 0 || vy == g.my || vz == 0 || vz == g.mz);
-    return g.off[3] + (ex + (long long)g.mx * (vy + (long long)(g.my + 1) * vz)) * g.n;
+    return sem_dbg_entity(g.off[3] + (ex + (long long)g.mx * (vy + (long long)(g.my + 1) * vz)) * g.n, g.n, g, dir);
   }
   if (grp == 1) {
     const int vx = ex + s1, vz = ez + s2;
     *dir = (vx == 0 || vx == g.mx || vz == 0 || vz == g.mz);
-    return g.off[4] + (vx + (long long)(g.mx + 1) * (ey + (long long)g.my * vz)) * g.n;
+    return sem_dbg_entity(g.off[4] + (vx + (long long)(g.mx + 1) * (ey + (long long)g.my * vz)) * g.n, g.n, g, dir);
   }
   const int vx = ex + s1, vy = ey + s2;
   *dir = (vx == 0 || vx == g.mx || vy == 0 || vy == g.my);
-  return g.off[5] + (vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * ez)) * g.n;
+  return sem_dbg_entity(g.off[5] + (vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * ez)) * g.n, g.n, g, dir);
 }
 
 // Vertex slot 0..7 = sa + 2 sb + 4 sc.
 static __device__ __forceinline__ long long vert_index(const SemGeom& g, int ex, int ey, int ez, int slot, bool* dir) {
   const int vx = ex + (slot & 1), vy = ey + ((slot >> 1) & 1), vz = ez + (slot >> 2);
   *dir = (vx == 0 || vx == g.mx || vy == 0 || vy == g.my || vz == 0 || vz == g.mz);
-  return g.off[6] + vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * vz);
+  return sem_dbg_entity(g.off[6] + vx + (long long)(g.mx + 1) * (vy + (long long)(g.my + 1) * vz), 1, g, dir);
 }
 
 // Entity offsets are affine in the element coordinates: offset of entity
@@ -123,9 +160,29 @@ static __device__ void entity_affine(const SemGeom& g, int r, EntityAffine* out)
   *out = a;
 }
 
+// Offset of entity slot r of an element with boundary flags `bits` from the
+// affine form (-1: Dirichlet entity); debug builds check it as sem_dbg_entity.
+static __device__ __forceinline__ int entity_offset(const EntityAffine& a, int r, int bits, int ex, int ey, int ez,
+                                                    const SemGeom& g) {
+#ifdef SEM_DEBUG
+  bool dir = (bits & a.mask) != 0;
+  const int off = a.base + ex * a.sx + ey * a.sy + ez * a.sz;
+  sem_dbg_entity(off, r < 6 ? (long long)g.n * g.n : (r < 18 ? g.n : 1), g, &dir);
+  return dir ? -1 : off;
+#else
+  (void)r; (void)g;
+  return (bits & a.mask) ? -1 : a.base + ex * a.sx + ey * a.sy + ez * a.sz;
+#endif
+}
+
 template <typename T>
 static __device__ __forceinline__ int elem_class(const SemGeom& g, const SemClassTables<T>& t, int ex, int ey, int ez) {
+#ifdef SEM_DEBUG
+  const int c = t.cls_x[ex] + g.ux * (t.cls_y[ey] + g.uy * t.cls_z[ez]);
+  return sem_dbg_ok(c, 1, (long long)g.ux * g.uy * g.uz) ? c : 0;
+#else
   return t.cls_x[ex] + g.ux * (t.cls_y[ey] + g.uy * t.cls_z[ez]);
+#endif
 }
 
 // Global node (gx, gy, gz) of packed skeleton entry idx.
@@ -322,3 +379,23 @@ template <int K>
 static __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory"); }
 
 }  // namespace semdev
+
+// Host reader of one translation unit's bounds record (debug builds): adds its
+// count to *count, keeps its first offending value in *first if none was kept
+// yet, and clears the record.  Expands to nothing in release builds.
+#ifdef SEM_DEBUG
+#define SEM_DEBUG_TU(tag)                                                                  \
+  cudaError_t sem_debug_take_##tag(unsigned long long* count, long long* first) {          \
+    unsigned long long c = 0;                                                              \
+    long long f = 0;                                                                       \
+    cudaError_t e = cudaMemcpyFromSymbol(&c, semdev::sem_dbg_count, sizeof c);             \
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&f, semdev::sem_dbg_first, sizeof f);   \
+    if (e != cudaSuccess) return e;                                                        \
+    if (c != 0 && *count == 0) *first = f;                                                 \
+    *count += c;                                                                           \
+    const unsigned long long z = 0;                                                        \
+    return cudaMemcpyToSymbol(semdev::sem_dbg_count, &z, sizeof z);                        \
+  }
+#else
+#define SEM_DEBUG_TU(tag)
+#endif

@@ -18,6 +18,9 @@ struct SemGeom {
   long long nelem;
   long long off[8];      // block offsets: xf, yf, zf, xe, ye, ze, v, end(=N_B)
   long long nb;
+#ifdef SEM_DEBUG
+  long long dbg_bound;   // bound of the debug entity-offset checks (N_B unless lowered)
+#endif
   long long Nx, Ny, Nz;  // global nodal grid
 };
 

@@ -1014,3 +1014,5 @@ void launch_lambda_gradient(const SemGeom& g, const double* mxs, const double* m
   k_lambda_gradient<<<sem_vec_blocks(), kVecThreads, 0, s>>>(g, mxs, mys, mzs, w, u, partials, out, counter);
   sem_count_launch();
 }
+
+SEM_DEBUG_TU(kernels)

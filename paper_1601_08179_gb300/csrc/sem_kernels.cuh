@@ -179,3 +179,14 @@ void launch_width_gradient(const SemGeom& g, int axis, const double* hx, const d
 void launch_lambda_gradient(const SemGeom& g, const double* mxs, const double* mys, const double* mzs,
                             const double* w, const double* u, double* partials, double* out, unsigned int* counter,
                             cudaStream_t s);
+
+#ifdef SEM_DEBUG
+// Bounds records of the debug build, one per translation unit (SEM_DEBUG_TU in
+// sem_device.cuh): each adds its count, keeps the first offending value and
+// clears its record.
+cudaError_t sem_debug_take_kernels(unsigned long long* count, long long* first);
+cudaError_t sem_debug_take_apply(unsigned long long* count, long long* first);
+cudaError_t sem_debug_take_plane(unsigned long long* count, long long* first);
+cudaError_t sem_debug_take_slab(unsigned long long* count, long long* first);
+cudaError_t sem_debug_take_elem(unsigned long long* count, long long* first);
+#endif

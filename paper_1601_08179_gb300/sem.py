@@ -17,7 +17,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsemgb.so")
+# SEM_LIB selects another build of the library (the debug build of build.py)
+LIB_PATH = os.environ.get("SEM_LIB") or os.path.join(_HERE, "libsemgb.so")
 
 SEM_OK, SEM_EINVAL, SEM_ENOMEM, SEM_ECUDA, SEM_ENOCONV, SEM_EBREAKDOWN, SEM_ENOTSUP = range(7)
 SPACE_NODAL, SPACE_TRANSFORMED = 0, 1
@@ -84,6 +85,8 @@ def lib():
         "sem_set_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "sem_cg_fused": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
         "sem_check_vector": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+        "sem_debug_oob": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "sem_debug_limit_skeleton": (ctypes.c_int, [_P, ctypes.c_longlong]),
         "sem_get_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "sem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -117,7 +120,8 @@ def exported_symbols():
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
             "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_set_operator_kernel",
-            "sem_get_operator_kernel", "sem_cg_fused", "sem_check_vector", "sem_batch_create", "sem_batch_solve",
+            "sem_get_operator_kernel", "sem_cg_fused", "sem_check_vector", "sem_debug_oob", "sem_debug_limit_skeleton",
+            "sem_batch_create", "sem_batch_solve",
             "sem_batch_destroy", "sem_solve_batch",
             "sem_profile_enable",
             "sem_profile_read", "sem_launch_count",
@@ -347,6 +351,19 @@ def sem_check_vector(ctx: SemContext, ptr: int, elem_bytes: int) -> int:
     launch): SEM_OK for device memory of the context's device (or managed
     memory) aligned to elem_bytes, else SEM_EINVAL."""
     return lib().sem_check_vector(ctx.handle, ctypes.c_void_p(ptr), int(elem_bytes))
+
+
+def sem_debug_oob():
+    """(status, count, first) of the debug build's bounds record since the last
+    call (status SEM_ENOTSUP in a release build); clears the record."""
+    n, f = ctypes.c_longlong(), ctypes.c_longlong()
+    st = lib().sem_debug_oob(ctypes.byref(n), ctypes.byref(f))
+    return st, n.value, f.value
+
+
+def sem_debug_limit_skeleton(ctx: SemContext, bound: int) -> int:
+    """Lowers the bound of the debug build's offset checks (status)."""
+    return lib().sem_debug_limit_skeleton(ctx.handle, int(bound))
 
 
 def sem_cg_fused(ctx: SemContext) -> bool:

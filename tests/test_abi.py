@@ -62,6 +62,10 @@ def test_argument_checks_without_gpu(L):
     # null context
     assert L.sem_apply_condensed(None, None, None, 0, None) == sem.SEM_EINVAL
     assert L.sem_check_vector(None, None, 8) == sem.SEM_EINVAL
+    # the bounds record exists in debug builds only (no CUDA call in a release build)
+    st, n, first = sem.sem_debug_oob()
+    assert (st, n, first) == (sem.SEM_ENOTSUP, 0, -1)
+    assert L.sem_debug_limit_skeleton(None, 0) == sem.SEM_EINVAL
     assert L.sem_status_string(sem.SEM_ENOCONV) == b"not converged"
     L.sem_destroy(None)
 
