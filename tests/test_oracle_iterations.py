@@ -13,7 +13,8 @@ The paper's right-hand side is a manufactured solution with inhomogeneous
 Dirichlet data; here the load is seeded noise with homogeneous Dirichlet
 data (the same condensed operator on the free unknowns), so the counts are
 compared within bands, not exactly (the oracle: 86 / 124 iterations at p = 4,
-112 / 156 at p = 8, for aspect ratio 1 / 128).  Planted in a copy of the
+112 / 156 at p = 8, for aspect ratio 1 / 128; 173 at p = 12 against the bound
+184 for aspect ratio 128).  Planted in a copy of the
 oracle, a preconditioner diagonal without its condensed self term takes 251
 iterations at p = 8, alpha = 2 (outside the Table 5 band), and no
 preconditioner grows 5.7-fold with the aspect ratio (outside the ratio band).
@@ -67,3 +68,12 @@ def test_table5_bound_at_p8(counts):
     bound = solve_us * 1e3 / it_ns          # iterations + setup, in iteration times
     assert bound == pytest.approx(166.0, abs=0.5)
     assert 0.7 * bound <= counts[(8, 128.0)] <= 1.05 * bound
+
+
+def test_table5_bound_at_p12(counts):
+    it_ns, solve_us = _table5()[12]
+    bound = solve_us * 1e3 / it_ns
+    assert bound == pytest.approx(183.7, abs=0.5)
+    it = _iterations(12, 128.0)             # about 40 s of CPU
+    assert it > counts[(8, 128.0)]
+    assert 0.7 * bound <= it <= 1.05 * bound
