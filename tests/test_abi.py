@@ -90,3 +90,18 @@ def test_default_opts(L):
     o = sem.default_opts()
     assert o.rtol == 1e-10 and o.precision == sem.PREC_FP64 and o.check_every > 0
     assert o.reliable_delta == 0.0   # automatic, by degree
+
+
+def test_debug_build_compiles_and_exports_the_same_entry_points():
+    """The SEM_DEBUG build (bounds record) compiles for sm_103a and exports
+    every declared entry point; its debug calls check their arguments before
+    any CUDA call."""
+    from paper_1601_08179_gb300 import build
+    D = ctypes.CDLL(build.build(debug=True))
+    for name in _declared():
+        assert hasattr(D, name), name
+    D.sem_debug_oob.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    D.sem_debug_limit_skeleton.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
+    SEM_EINVAL = 1
+    assert D.sem_debug_oob(None, None) == SEM_EINVAL
+    assert D.sem_debug_limit_skeleton(None, 0) == SEM_EINVAL
