@@ -40,15 +40,17 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def _measured_hbm():
+def measured_hbm(path: str = os.path.join(ROOT, "MEASURED_PEAKS.json")):
+    """(GB/s, source) of the HBM roofline: the measured copy bandwidth of this
+    machine's GPUs, else the fallback figure of a GB300 copy, saying which."""
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        return 6800.0     # fallback figure for a GB300 copy
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 6800.0, "fallback: 6.8 TB/s, an earlier GB300 copy (no measured peak)"
 
 
-HBM_GBS = _measured_hbm()
+HBM_GBS, HBM_SOURCE = measured_hbm()
 L2_BYTES = 129e6
 
 
@@ -396,7 +398,7 @@ def our_arm(args, rank, world, local_rank):
             roof = {"kernel": kernel_name(sem, ctx, sem.PREC_MIXED, w.p), "bound": "hbm", "achieved": achieved, "peak": HBM_GBS,
                     "unit": "GB/s", "frac": achieved / HBM_GBS,
                     "traffic": TRAFFIC_BYTES.get((kernel_name(sem, ctx, sem.PREC_MIXED, w.p), w.name)),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)", "bytes_per_launch": 8.0 * nb}
+                    "peak_source": HBM_SOURCE, "bytes_per_launch": 8.0 * nb}
     out = {
         "metric": METRIC,
         "value": whole_job_value(r["step_s"], w.dofs, world),

@@ -27,3 +27,11 @@ def test_workload_config_of_the_degree_sweep():
 
 def test_whole_job_value_counts_every_rank():
     assert bench.whole_job_value(0.5, 1000, 4) == pytest.approx(0.5 / 4000)
+
+
+def test_hbm_peak_names_its_source(tmp_path):
+    f = tmp_path / "peaks.json"
+    f.write_text('{"hbm_gbs": 7001.5}')
+    assert bench.measured_hbm(str(f)) == (7001.5, "MEASURED_PEAKS.json hbm_gbs (copy)")
+    gbs, src = bench.measured_hbm(str(tmp_path / "missing.json"))
+    assert gbs == 6800.0 and src.startswith("fallback")
