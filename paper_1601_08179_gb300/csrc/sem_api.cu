@@ -10,6 +10,7 @@
 //   3. interior recovery u_I = (V(x)V(x)V) D^-1 (F~_I - H~_IB u~_B) and the
 //      nodal skeleton u_B = T^T u~_B.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <chrono>
 #include <cmath>
@@ -714,6 +715,15 @@ sem_status check_vec(const sem_ctx* c, const void* p, size_t elem, const char* n
     if (st_ != SEM_OK) return st_;                                 \
   } while (0)
 
+// NVTX range over one entry point or phase of it: named in profiler timelines
+// and usable as a profiler filter; without a tool attached it costs a check.
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
 }  // namespace
 
 extern "C" {
@@ -748,6 +758,7 @@ static sem_status check_opts(const sem_opts* o) {
 sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double* hx, const double* hy,
                      const double* hz, double lambda, const sem_opts* opts) {
   t_err.clear();
+  NvtxScope nvtx_("sem_setup");
   if (out == nullptr) return fail(SEM_EINVAL, "out is null");
   *out = nullptr;
   if (p < 2 || p > 32) return fail(SEM_EINVAL, "p must be in [2, 32]");
@@ -958,6 +969,7 @@ sem_status sem_get_basis(const sem_ctx* c, double* gx, double* gw, double* lam, 
 
 sem_status sem_apply_condensed(sem_ctx* c, const double* uB, double* vB, sem_space space, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_apply_condensed");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(uB, double);
   SEM_CHECK_VEC(vB, double);
@@ -975,6 +987,7 @@ sem_status sem_apply_condensed(sem_ctx* c, const double* uB, double* vB, sem_spa
 
 sem_status sem_apply_condensed_f32(sem_ctx* c, const float* uB, float* vB, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_apply_condensed_f32");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(uB, float);
   SEM_CHECK_VEC(vB, float);
@@ -992,6 +1005,7 @@ sem_status sem_apply_condensed_f32(sem_ctx* c, const float* uB, float* vB, void*
 
 sem_status sem_condense_rhs(sem_ctx* c, const double* f, double* fB, sem_space space, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_condense_rhs");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(f, double);
   SEM_CHECK_VEC(fB, double);
@@ -1008,6 +1022,7 @@ sem_status sem_condense_rhs(sem_ctx* c, const double* f, double* fB, sem_space s
 
 sem_status sem_precond_diag(sem_ctx* c, double* diag, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_precond_diag");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(diag, double);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1020,6 +1035,7 @@ sem_status sem_precond_diag(sem_ctx* c, double* diag, void* stream) {
 sem_status sem_recover_interior(sem_ctx* c, const double* f, const double* uB, sem_space space, double* u,
                                 void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_recover_interior");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(f, double);
   SEM_CHECK_VEC(uB, double);
@@ -1039,6 +1055,7 @@ sem_status sem_recover_interior(sem_ctx* c, const double* f, const double* uB, s
 
 sem_status sem_solve(sem_ctx* c, const double* f, double* u, const double* u0, sem_info* info, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_solve");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(f, double);
   SEM_CHECK_VEC(u, double);
@@ -1049,17 +1066,27 @@ sem_status sem_solve(sem_ctx* c, const double* f, double* u, const double* u0, s
   SEM_CUDA(cudaEventRecord(c->ev_in, us));
   SEM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
   cudaStream_t s = c->stream;
-  sem_status st = condense_rhs_t(c, f, c->d_b, s);
+  sem_status st;
+  {
+    NvtxScope phase("condense");
+    st = condense_rhs_t(c, f, c->d_b, s);
+  }
   if (st != SEM_OK) return st;
   if (u0) launch_skel_transform(c->g, c->mat(2), u0, c->d_x, s);
   sem_status cg;
-  if (c->opts.precision == SEM_PREC_MIXED)
-    cg = c->opts.mixed_scheme == 1 ? pcg_mixed_reliable(c, u0 != nullptr, info) : pcg_mixed(c, u0 != nullptr, info);
-  else
-    cg = pcg_fp64(c, u0 != nullptr, info);
+  {
+    NvtxScope phase(c->opts.precision == SEM_PREC_MIXED ? "pcg_mixed" : "pcg_fp64");
+    if (c->opts.precision == SEM_PREC_MIXED)
+      cg = c->opts.mixed_scheme == 1 ? pcg_mixed_reliable(c, u0 != nullptr, info) : pcg_mixed(c, u0 != nullptr, info);
+    else
+      cg = pcg_fp64(c, u0 != nullptr, info);
+  }
   if (cg != SEM_OK && cg != SEM_ENOCONV && cg != SEM_EBREAKDOWN) return cg;
   std::string cg_err = t_err;
-  st = recover_t(c, c->d_x, u, s);
+  {
+    NvtxScope phase("recover");
+    st = recover_t(c, c->d_x, u, s);
+  }
   if (st != SEM_OK) return st;
   SEM_CUDA(cudaEventRecord(c->ev_out, s));
   SEM_CUDA(cudaStreamWaitEvent(us, c->ev_out, 0));
@@ -1071,6 +1098,7 @@ sem_status sem_solve(sem_ctx* c, const double* f, double* u, const double* u0, s
 
 sem_status sem_solve_host(sem_ctx* c, const double* f_host, double* u_host, sem_info* info, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_solve_host");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   if (f_host == nullptr || u_host == nullptr) return fail(SEM_EINVAL, "null vector");
   const long long nn = c->g.Nx * c->g.Ny * c->g.Nz;
@@ -1174,6 +1202,7 @@ static sem_status ensure_adjoint(sem_ctx* c) {
 
 sem_status sem_solve_adjoint(sem_ctx* c, const double* gload, double* w, sem_info* info, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_solve_adjoint");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(gload, double);
   SEM_CHECK_VEC(w, double);
@@ -1190,6 +1219,7 @@ sem_status sem_solve_adjoint(sem_ctx* c, const double* gload, double* w, sem_inf
 sem_status sem_gradients(sem_ctx* c, const double* w, const double* u, const double* f, double* df,
                          double* dlambda, double* dhx, double* dhy, double* dhz, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_gradients");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(w, double);
   SEM_CHECK_VEC(u, double);
@@ -1289,6 +1319,7 @@ sem_status noalloc_scratch(double** out) {
 extern "C" sem_status sem_condense_rhs_noalloc(sem_ctx* c, const double* f, double* fB, sem_space space,
                                                void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_condense_rhs_noalloc");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   SEM_CHECK_VEC(f, double);
   SEM_CHECK_VEC(fB, double);
@@ -1424,6 +1455,7 @@ void drop_graph(sem_ctx* c, bool mixed) {
 
 extern "C" sem_status sem_autotune(sem_ctx* c, double* ms_default, double* ms_best) {
   t_err.clear();
+  NvtxScope nvtx_("sem_autotune");
   if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
   const SemGeom& g = c->g;
   const bool mixed = c->opts.precision == SEM_PREC_MIXED;
@@ -1773,6 +1805,7 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
 
 extern "C" sem_status sem_batch_solve(sem_batch* b, sem_info* infos, void* stream) {
   t_err.clear();
+  NvtxScope nvtx_("sem_batch_solve");
   if (b == nullptr) return fail(SEM_EINVAL, "null batch");
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t us = (cudaStream_t)stream;
