@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstddef>
+#include <cstdint>
 #include <cstring>
 #include <algorithm>
 #include <map>
@@ -709,6 +710,7 @@ sem_status check_vec(const sem_ctx* c, const void* p, size_t elem, const char* n
   return SEM_OK;
 }
 
+// check_vec of vector p (entries of type T) in an entry point whose context is `c`
 #define SEM_CHECK_VEC(p, T)                                        \
   do {                                                             \
     const sem_status st_ = check_vec(c, (p), sizeof(T), #p);        \
