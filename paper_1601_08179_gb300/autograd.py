@@ -39,7 +39,8 @@ def context_for(p, hx, hy, hz, lam, opts=None):
 class HelmholtzSolve(torch.autograd.Function):
     """u = HelmholtzSolve.apply(f, lam, hx, hy, hz, p, opts).
 
-    f: CUDA float64 full nodal field (x fastest); lam: 0-d float64 tensor;
+    f: CUDA float64 full nodal field (x fastest); lam: 0-d float64 tensor
+    (its gradient is returned on its device) or a number (no gradient);
     hx, hy, hz: 1-D float64 tensors of element widths; p: degree; opts:
     sem.sem_opts or None.  Gradients flow to f, lam, hx, hy, hz."""
 
@@ -51,6 +52,8 @@ class HelmholtzSolve(torch.autograd.Function):
         u = torch.empty_like(f)
         sem.sem_solve(sctx, f, u)
         ctx.sctx = sctx
+        # lambda may be a tensor (on any device) or a plain number (no gradient)
+        ctx.lam_device = lam.device if torch.is_tensor(lam) else None
         ctx.save_for_backward(f, u, hx, hy, hz)
         return u
 
@@ -63,8 +66,8 @@ class HelmholtzSolve(torch.autograd.Function):
         df = torch.empty_like(u)
         dl, dhx, dhy, dhz = sem.sem_gradients(sctx, w, u, f, df)
         as_t = lambda a, like: torch.as_tensor(a, dtype=torch.float64, device=like.device)
-        return (df, torch.tensor(dl, dtype=torch.float64), as_t(dhx, hx), as_t(dhy, hy), as_t(dhz, hz),
-                None, None)
+        dlam = None if ctx.lam_device is None else torch.tensor(dl, dtype=torch.float64, device=ctx.lam_device)
+        return (df, dlam, as_t(dhx, hx), as_t(dhy, hy), as_t(dhz, hz), None, None)
 
 
 def helmholtz_solve(f, lam, hx, hy, hz, p, opts=None):
