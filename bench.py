@@ -71,6 +71,9 @@ def parse():
                     help="scale: graded N~1.68e7 workload of degree --p (default); mixed16: p = 16 on 16^3, "
                          "lambda = 10, AR 16; batched: 64 heterogeneous problems in one graph launch; "
                          "adjoint: forward + backward of the differentiable solve (p = 8 on 16^3)")
+    ap.add_argument("--oracle-one-core", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--one-core-iters", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--one-core-target", type=float, default=8.0, help=argparse.SUPPRESS)
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
                     help="'both': time the plain FP64 solve and the mixed-precision solve (the headline)")
     return ap.parse_args()
@@ -255,6 +258,7 @@ def oracle_sample(w: si.Workload, iterations: int, target_s: float = 12.0):
         X, Y, Z = ms.coords()
         f = si.manufactured_f(X, Y, Z, w.lam).ravel()
         uB = si.random_vector(ms.n_skeleton, 1)
+        c0 = time.process_time()
         t0 = time.perf_counter()
         fh = local.condensed_rhs(ms, w.lam, f)
         t1 = time.perf_counter()
@@ -266,6 +270,7 @@ def oracle_sample(w: si.Workload, iterations: int, target_s: float = 12.0):
         t2 = time.perf_counter()
         local.recover_interior(ms, w.lam, f, uB2)
         t3 = time.perf_counter()
+        cpu_s = time.process_time() - c0
         t_est = (t1 - t0, t2 - t1, t3 - t2)
         total = sum(t_est)
         if total * 2 > target_s or mz_s >= w.m[2]:
@@ -274,12 +279,44 @@ def oracle_sample(w: si.Workload, iterations: int, target_s: float = 12.0):
     scale = w.m[2] / mz_s
     t_full = scale * (t_est[0] + t_est[2] + iterations * t_est[1])
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": t_full / w.dofs, "unit": UNIT, "cores": cores, "kind": "oracle",
+    # threads the sample kept busy on average: process CPU time (all threads) over wall time
+    threads = cpu_s / max(sum(t_est), 1e-9)
+    return {"value": t_full / w.dofs, "unit": UNIT, "cores": cores, "threads": round(threads, 2), "kind": "oracle",
             "sample": (f"NumPy FP64 oracle (element-local tier) on the {w.m[0]}x{w.m[1]}x{mz_s} slab of the "
                        f"{w.m[0]}x{w.m[1]}x{w.m[2]} mesh: condensed load {t_est[0]:.2f}s, one CG iteration "
                        f"{t_est[1]:.2f}s, recovery {t_est[2]:.2f}s; scaled x{scale:g} to the full mesh and to "
                        f"{iterations} CG iterations"),
             "sample_s": sum(t_est)}
+
+
+BLAS_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def oracle_sample_one_core(w: si.Workload, iterations: int, target_s: float = 8.0):
+    """oracle_sample in a child process pinned to one host core with one BLAS
+    thread (the like-for-like figure for the paper's single-core timings).
+    The BLAS thread counts are set in the child's environment, so they hold
+    from the moment NumPy loads; None if the child fails."""
+    env = dict(os.environ)
+    env.update({k: "1" for k in BLAS_THREAD_VARS})
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-one-core", "--p", str(w.p), "--ar", repr(w.ar),
+           "--lam", repr(w.lam), "--one-core-iters", str(iterations), "--one-core-target", repr(target_s)]
+    try:
+        res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+        return json.loads(lines[-1]) if res.returncode == 0 and lines else None
+    except (OSError, ValueError, subprocess.TimeoutExpired):
+        return None
+
+
+def one_core_child(args):
+    """Body of the one-core child: pins itself to one core of its affinity
+    set, then prints oracle_sample's result as JSON."""
+    if hasattr(os, "sched_setaffinity"):
+        os.sched_setaffinity(0, {min(os.sched_getaffinity(0))})
+    w = si.scale_workload(args.p, ar=args.ar, lam=args.lam)
+    out = oracle_sample(w, args.one_core_iters, target_s=args.one_core_target)
+    print(json.dumps(out), flush=True)
 
 
 # --------------------------------------------------------------------------
@@ -444,9 +481,14 @@ def our_arm(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_iters = reference_iterations(w)
         iters = res["fp64"]["info"]["iters"] if "fp64" in res else r["info"]["iters"]
-        out["cpu_baseline"] = oracle_sample(w, ref_iters if ref_iters is not None else iters)
+        cb_iters = ref_iters if ref_iters is not None else iters
+        out["cpu_baseline"] = oracle_sample(w, cb_iters, target_s=8.0)
         if ref_iters is None:
             out["cpu_baseline"]["sample"] += " (iteration count of this GPU FP64 solve; no oracle solve recorded)"
+        one = oracle_sample_one_core(w, cb_iters) if args.workload == "scale" else None
+        out["cpu_baseline"]["one_core"] = (
+            {"value": one["value"], "unit": UNIT, "cores": 1, "threads": one["threads"], "sample": one["sample"]}
+            if one else None)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -636,14 +678,17 @@ def reference_arm(args, rank, world):
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "precision": "fp64", "config": workload_config(w, world),
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                            "sample": last["sample"]},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "threads": last["threads"],
+                            "kind": "oracle", "sample": last["sample"]},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 def main():
     args = parse()
+    if args.oracle_one_core:
+        one_core_child(args)
+        return
     rank, world, local_rank = dist_setup()
     try:
         if args.impl == "reference":

@@ -109,13 +109,6 @@ typedef struct {
                          recursive residual has fallen by this factor since the
                          previous step; 0 = automatic (default): 0.03 at p = 2,
                          0.01 otherwise (the fastest measured on GB300) */
-  int fused_cg;       /* MIXED: 1 = each FP32 CG iteration of a single solve is one
-                         cooperative kernel (operator, vector updates, dot products,
-                         stopping tests) when the FP32 operator kernel is
-                         SEM_KERNEL_PLANE and the device supports cooperative
-                         launches; 0 = three kernels (default: faster on GB300 at
-                         p = 4 and 8, where the operator's 12 warps per SM limit the
-                         fused kernel's streaming phases) */
 } sem_opts;
 
 /* Result of a solve. */
@@ -236,14 +229,15 @@ sem_status sem_unpack_skeleton(sem_ctx* ctx, const double* uB, double* u_full, v
 /* sem_condense_rhs without any memory allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory at the time of the call -- for example code
- * running while a CUDA stream is being captured into a graph (where
- * cudaMalloc is not part of the capture), or applications whose device memory
- * is fully reserved by their own pool.  sem_condense_rhs allocates its
- * element-interior scratch with cudaMalloc on first use; this variant calls no
- * cudaMalloc, cudaFree or other allocating routine and instead uses a fixed
- * scratch array compiled into the library (12 MiB, held by every GPU that
- * loads the library until the process exits).
+ * cannot allocate device memory at the time of the call -- an application
+ * whose own pool allocator has reserved the device memory up front (where a
+ * cudaMalloc fails or eats into the pool), or a latency-bound loop that must
+ * not take the device-wide synchronisation that cudaFree (and at times
+ * cudaMalloc) makes.  sem_condense_rhs allocates its element-interior scratch
+ * with cudaMalloc on first use; this variant calls no cudaMalloc, cudaFree or
+ * other allocating routine and instead uses a fixed scratch array compiled
+ * into the library (12 MiB, held by every GPU that loads the library until
+ * the process exits).
  *   ctx, f, fB, space, stream: as for sem_condense_rhs (same result).
  *   Limit: elements * (p-1)^3 <= 524288 (e.g. p = 8 on 8^3 elements, p = 4 on
  *   16^3); larger meshes are rejected with SEM_EINVAL and a message.
@@ -335,10 +329,6 @@ sem_status sem_check_vector(const sem_ctx* ctx, const void* p, int elem_bytes);
  * the real vectors.  Both return SEM_ENOTSUP in release builds. */
 sem_status sem_debug_oob(long long* count, long long* first);
 sem_status sem_debug_limit_skeleton(sem_ctx* ctx, long long bound);
-/* *fused = 1 if the FP32 CG iterations of this context's mixed solves run as
- * one fused kernel each (see sem_opts.fused_cg), else 0. */
-sem_status sem_cg_fused(const sem_ctx* ctx, int* fused);
-
 /* Autotuner: times the operator kernel for this context's degree, mesh and
  * precision (FP32 when opts.precision is MIXED, else FP64) over the variants
  * that exist for it and a set of CTA-tile shapes (elements per CTA,

@@ -103,9 +103,3 @@ def load_to_transformed(mesh: Mesh, vB):
     _, V = eigenbasis(mesh.p)
     return _apply_entitywise(mesh, vB, V.T)
 
-
-def load_from_transformed(mesh: Mesh, vt):
-    """F = T^-1 F~; per direction S_II^-1 = M_II V."""
-    _, V = eigenbasis(mesh.p)
-    M, _ = mass_stiffness(mesh.p)
-    return _apply_entitywise(mesh, vt, M[1:-1, 1:-1] @ V)

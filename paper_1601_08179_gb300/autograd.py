@@ -20,16 +20,21 @@ _CACHE: "OrderedDict[tuple, sem.SemContext]" = OrderedDict()
 _CACHE_SIZE = 4
 
 
-def context_for(p, hx, hy, hz, lam, opts=None):
-    """Library context for (p, widths, lambda), cached (LRU of 4)."""
+def context_for(p, hx, hy, hz, lam, opts=None, device=None):
+    """Library context for (p, widths, lambda) on a CUDA device (index or
+    torch.device; default: the current one), cached (LRU of 4)."""
     hx = np.ascontiguousarray(np.asarray(hx, dtype=np.float64))
     hy = np.ascontiguousarray(np.asarray(hy, dtype=np.float64))
     hz = np.ascontiguousarray(np.asarray(hz, dtype=np.float64))
-    key = (int(p), hx.tobytes(), hy.tobytes(), hz.tobytes(), float(lam),
+    d = None if device is None else (torch.device("cuda", device) if isinstance(device, int)
+                                     else torch.device(device))
+    dev = torch.cuda.current_device() if d is None or d.index is None else d.index
+    key = (dev, int(p), hx.tobytes(), hy.tobytes(), hz.tobytes(), float(lam),
            None if opts is None else bytes(opts))
     ctx = _CACHE.pop(key, None)
     if ctx is None:
-        ctx = sem.sem_setup(p, hx, hy, hz, float(lam), opts)
+        with torch.cuda.device(dev):        # a context lives on the device current at setup
+            ctx = sem.sem_setup(p, hx, hy, hz, float(lam), opts)
     _CACHE[key] = ctx
     while len(_CACHE) > _CACHE_SIZE:
         _CACHE.popitem(last=False)
@@ -47,10 +52,11 @@ class HelmholtzSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, f, lam, hx, hy, hz, p, opts=None):
         sctx = context_for(p, hx.detach().cpu().numpy(), hy.detach().cpu().numpy(),
-                           hz.detach().cpu().numpy(), float(lam), opts)
+                           hz.detach().cpu().numpy(), float(lam), opts, device=f.device)
         f = f.detach().contiguous()
         u = torch.empty_like(f)
-        sem.sem_solve(sctx, f, u)
+        with torch.cuda.device(f.device):   # the library runs on the context's (f's) device
+            sem.sem_solve(sctx, f, u)
         ctx.sctx = sctx
         # lambda may be a tensor (on any device) or a plain number (no gradient)
         ctx.lam_device = lam.device if torch.is_tensor(lam) else None
@@ -62,9 +68,10 @@ class HelmholtzSolve(torch.autograd.Function):
         f, u, hx, hy, hz = ctx.saved_tensors
         sctx = ctx.sctx
         w = torch.empty_like(u)
-        sem.sem_solve_adjoint(sctx, gu.detach().contiguous(), w)
         df = torch.empty_like(u)
-        dl, dhx, dhy, dhz = sem.sem_gradients(sctx, w, u, f, df)
+        with torch.cuda.device(u.device):
+            sem.sem_solve_adjoint(sctx, gu.detach().contiguous(), w)
+            dl, dhx, dhy, dhz = sem.sem_gradients(sctx, w, u, f, df)
         as_t = lambda a, like: torch.as_tensor(a, dtype=torch.float64, device=like.device)
         dlam = None if ctx.lam_device is None else torch.tensor(dl, dtype=torch.float64, device=ctx.lam_device)
         return (df, dlam, as_t(dhx, hx), as_t(dhy, hy), as_t(dhz, hz), None, None)

@@ -108,7 +108,6 @@ struct sem_ctx {
   PcgState* d_st32 = nullptr;
   MixedCtl* d_ctl = nullptr;           // device-side refinement control (graph-replayed mixed solves)
   MixedCtl h_ctl{};                    // host copy of it
-  bool coop = false;                   // the device supports cooperative launches
   cudaGraphExec_t graph32m = nullptr;  // one loop trip of the reliable-update mixed solve
   int graph32m_iters = 0;
   bool graph32m_prof = false;
@@ -235,7 +234,6 @@ sem_status ensure_mixed(sem_ctx* c) {
   // operator kernel attributes outside any capture
   SEM_CUDA(cudaMemsetAsync(c->d_q32, 0, sizeof(float) * g.nb, c->stream));
   launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_P32, c->d_q32, nullptr, nullptr, c->stream);
-  if (c->d_plane != nullptr && plane_supported(g.n)) prepare_cg_plane(g);   // kernel attributes outside any capture
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -299,28 +297,12 @@ sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
   return SEM_OK;
 }
 
-// Whether the FP32 CG iterations run as one fused cooperative kernel (single
-// solves; a batch's parallel branches keep the three-kernel form, so that no
-// two cooperative grids compete for residency).
-bool fused_f32(const sem_ctx* c) {
-  if (!c->opts.fused_cg || !c->coop || c->g.n < 2 || c->g.n > 8) return false;   // one-row plane kernel only
-  const int kind = c->op32.kind == kApplyAuto ? sem_apply_default_kind(c->g.n, 4) : c->op32.kind;
-  return kind == kApplyPlane;
-}
-
-// One FP32 CG iteration on the context's FP32 vectors (st32), as one fused
-// kernel or as operator + update + direction; e0/e1 (may be null) become
-// event nodes around the operator (the fused kernel when fused).
-sem_status cg_iter_f32(sem_ctx* c, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, bool allow_fused = true) {
+// One FP32 CG iteration on the context's FP32 vectors (st32): operator,
+// update, direction; e0/e1 (may be null) become event nodes around the
+// operator.
+sem_status cg_iter_f32(sem_ctx* c, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   const SemGeom& g = c->g;
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
-  if (allow_fused && fused_f32(c)) {
-    const cudaError_t e = launch_cg_plane(g, c->tab_f, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32,
-                                          c->d_partials, c->d_st32, s);
-    if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("fused CG iteration: ") + cudaGetErrorString(e));
-    if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
-    return SEM_OK;
-  }
   launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, s, &c->op32);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
   launch_pcg_update<float>(g.nb, c->d_r32, c->d_q32, c->d_P32, c->d_partials, c->d_st32, s);
@@ -687,8 +669,19 @@ void free_ctx(sem_ctx* c) {
   delete c;
 }
 
+// A context and the current device: kernels launch on the current device and
+// read the context's tables and the caller's vectors on c->device, so an entry
+// point that launches refuses to run while another device is current.
 sem_status check_ctx(const sem_ctx* c) {
   if (c == nullptr) return fail(SEM_EINVAL, "null context");
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SEM_EINVAL, "cannot query the current device");
+  }
+  if (cur != c->device)
+    return fail(SEM_EINVAL, "the current device (" + std::to_string(cur) + ") is not the context's device (" +
+                                std::to_string(c->device) + ")");
   return SEM_OK;
 }
 
@@ -740,7 +733,6 @@ void sem_default_opts(sem_opts* o) {
   o->max_refine = 40;
   o->mixed_scheme = 1;
   o->reliable_delta = 0.0;   // automatic (by degree)
-  o->fused_cg = 0;
 }
 
 static sem_status check_opts(const sem_opts* o) {
@@ -753,7 +745,6 @@ static sem_status check_opts(const sem_opts* o) {
   if (o->mixed_scheme != 0 && o->mixed_scheme != 1) return fail(SEM_EINVAL, "mixed_scheme must be 0 or 1");
   if (!(o->reliable_delta == 0.0 || (o->reliable_delta > 0.0 && o->reliable_delta < 1.0)))
     return fail(SEM_EINVAL, "reliable_delta must be 0 (automatic) or in (0, 1)");
-  if (o->fused_cg != 0 && o->fused_cg != 1) return fail(SEM_EINVAL, "fused_cg must be 0 or 1");
   return SEM_OK;
 }
 
@@ -776,11 +767,6 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
 
   sem_ctx* c = new sem_ctx();
   cudaGetDevice(&c->device);
-  {
-    int coop = 0;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
-    c->coop = coop != 0;
-  }
   c->opts = o;
   c->lambda = lambda;
   std::string err;
@@ -929,12 +915,6 @@ sem_status sem_set_opts(sem_ctx* c, const sem_opts* opts) {
   if (opts) o = *opts;
   sem_status vs = check_opts(&o);
   if (vs != SEM_OK) return vs;
-  if (o.fused_cg != c->opts.fused_cg) {   // the FP32 CG graphs hold the iteration's kernels
-    if (c->graph32) cudaGraphExecDestroy(c->graph32);
-    if (c->graph32m) cudaGraphExecDestroy(c->graph32m);
-    c->graph32 = nullptr;
-    c->graph32m = nullptr;
-  }
   c->opts = o;
   return SEM_OK;
 }
@@ -1554,13 +1534,6 @@ extern "C" sem_status sem_debug_limit_skeleton(sem_ctx* c, long long bound) {
 #endif
 }
 
-extern "C" sem_status sem_cg_fused(const sem_ctx* c, int* fused) {
-  t_err.clear();
-  if (c == nullptr || fused == nullptr) return fail(SEM_EINVAL, "null argument");
-  *fused = fused_f32(c) ? 1 : 0;
-  return SEM_OK;
-}
-
 extern "C" sem_status sem_get_operator_kernel(const sem_ctx* c, int precision, int* kind, int* epb, int* ks) {
   t_err.clear();
   if (c == nullptr || kind == nullptr) return fail(SEM_EINVAL, "null argument");
@@ -1648,7 +1621,7 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
     return fail(SEM_EINVAL, "null argument or empty batch");
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
-    if (ctxs[i] == nullptr) return fail(SEM_EINVAL, "null context");
+    if (check_ctx(ctxs[i]) != SEM_OK) return SEM_EINVAL;
     {
       const sem_ctx* c = ctxs[i];
       SEM_CHECK_VEC(f[i], double);
@@ -1778,7 +1751,7 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
         launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32,
                           c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, si);
         for (int it = 0; it < check; ++it) {
-          const sem_status st = cg_iter_f32(c, si, nullptr, nullptr, false);
+          const sem_status st = cg_iter_f32(c, si, nullptr, nullptr);
           if (st != SEM_OK) return st;
         }
         return SEM_OK;
@@ -1809,6 +1782,13 @@ extern "C" sem_status sem_batch_solve(sem_batch* b, sem_info* infos, void* strea
   t_err.clear();
   NvtxScope nvtx_("sem_batch_solve");
   if (b == nullptr) return fail(SEM_EINVAL, "null batch");
+  {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != b->device) {
+      cudaGetLastError();
+      return fail(SEM_EINVAL, "the current device is not the batch's device");
+    }
+  }
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t us = (cudaStream_t)stream;
   cudaStream_t s0 = b->streams[0];

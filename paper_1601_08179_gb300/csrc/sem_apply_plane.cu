@@ -536,144 +536,6 @@ k_tpt_apply_plane(SemGeom g, SemClassTables<float> tab, const float* __restrict_
   }
 }
 
-// One whole FP32 CG iteration (launched cooperatively: every block is
-// resident, so the grid barriers of grid_sum complete):
-//   q = Hhat~ p (the plane kernel)                        -> p^T q, alpha
-//   x += alpha p, r -= alpha q, q = 0                      -> r^T P r, r^T r
-//   the stopping tests of k_pcg_update, identical in every block
-//   p = P r + beta p
-// q and p are still in L2 from the operator when they are reread.  A barrier
-// that times out stops the solve with a breakdown.
-template <int N>
-__global__ void __launch_bounds__(kPlaneThreads, 4)
-k_cg_plane(SemGeom g, SemClassTables<float> tab, float* __restrict__ x, float* __restrict__ r,
-           float* __restrict__ p, float* __restrict__ q, const float* __restrict__ P, double* __restrict__ partials,
-           PcgState* st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ EntityAffine ent[26];
-  __shared__ double red[2 * 33];
-  if (st->done) return;
-  const double rho = st->rho;
-  const int iter0 = st->iter;
-  if (threadIdx.x < 26) entity_affine(g, threadIdx.x, &ent[threadIdx.x]);
-  __syncthreads();
-  const float dot = plane_apply_all<N>(g, tab, ent, p, q, smem_raw);
-  const bool first = blockIdx.x == 0 && threadIdx.x == 0;
-  const unsigned G = gridDim.x;
-  double v1[1] = {(double)dot}, t1[1];
-  if (!grid_sum<1>(v1, partials, &st->bar_count, &st->bar_gen, &st->bar_timeout, red, t1)) {
-    if (threadIdx.x == 0) st->done = 2;
-    return;
-  }
-  const double pq = t1[0];
-  if (!(pq > 0.0) || !isfinite(pq)) {
-    if (first) {
-      st->pq = pq;
-      st->done = 2;
-    }
-    return;
-  }
-  const double alpha = rho / pq;
-  const float af = (float)alpha;
-  const long long nb = g.nb, nv = nb / 4;
-  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long long)G * blockDim.x;
-  float4* __restrict__ x4 = reinterpret_cast<float4*>(x);
-  float4* __restrict__ r4 = reinterpret_cast<float4*>(r);
-  float4* __restrict__ p4 = reinterpret_cast<float4*>(p);
-  float4* __restrict__ q4 = reinterpret_cast<float4*>(q);
-  const float4* __restrict__ P4 = reinterpret_cast<const float4*>(P);
-  constexpr int U = 4;   // packs per thread in flight
-  float rz = 0.f, rr = 0.f;
-  for (long long i0 = t0; i0 < nv; i0 += U * ts) {
-    float4 xv[U], rv[U], pv[U], qv[U], Pv[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const long long i = i0 + k * ts;
-      if (i < nv) {
-        xv[k] = x4[i];
-        rv[k] = r4[i];
-        pv[k] = p4[i];
-        qv[k] = __ldcg(q4 + i);
-        Pv[k] = P4[i];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const long long i = i0 + k * ts;
-      if (i < nv) {
-        float4 xo = xv[k], ro = rv[k];
-        xo.x = fmaf(af, pv[k].x, xo.x); xo.y = fmaf(af, pv[k].y, xo.y);
-        xo.z = fmaf(af, pv[k].z, xo.z); xo.w = fmaf(af, pv[k].w, xo.w);
-        ro.x = fmaf(-af, qv[k].x, ro.x); ro.y = fmaf(-af, qv[k].y, ro.y);
-        ro.z = fmaf(-af, qv[k].z, ro.z); ro.w = fmaf(-af, qv[k].w, ro.w);
-        rz = fmaf(ro.x, Pv[k].x * ro.x, rz); rz = fmaf(ro.y, Pv[k].y * ro.y, rz);
-        rz = fmaf(ro.z, Pv[k].z * ro.z, rz); rz = fmaf(ro.w, Pv[k].w * ro.w, rz);
-        rr = fmaf(ro.x, ro.x, rr); rr = fmaf(ro.y, ro.y, rr); rr = fmaf(ro.z, ro.z, rr); rr = fmaf(ro.w, ro.w, rr);
-        x4[i] = xo;
-        r4[i] = ro;
-        q4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-  }
-  for (long long i = nv * 4 + t0; i < nb; i += ts) {
-    x[i] = fmaf(af, p[i], x[i]);
-    const float ri = fmaf(-af, __ldcg(q + i), r[i]);
-    r[i] = ri;
-    q[i] = 0.f;
-    rz = fmaf(ri, P[i] * ri, rz);
-    rr = fmaf(ri, ri, rr);
-  }
-  double v2[2] = {(double)rz, (double)rr}, t2[2];
-  if (!grid_sum<2>(v2, partials + G, &st->bar_count, &st->bar_gen, &st->bar_timeout, red, t2)) {
-    if (threadIdx.x == 0) st->done = 2;
-    return;
-  }
-  const int it = iter0 + 1;
-  int done = 0;
-  if (!isfinite(t2[0]) || !isfinite(t2[1])) done = 2;
-  else if (t2[1] <= st->tol2) done = 1;
-  else if (it >= st->maxit) done = 3;
-  else if (st->trig2 > 0.0 && t2[1] <= st->trig2) done = 4;   // refinement due: rho is kept
-  if (first) {
-    st->pq = pq;
-    st->alpha = alpha;
-    st->iter = it;
-    st->rho_new = t2[0];
-    st->rr = t2[1];
-    if (done == 0) {
-      st->beta = t2[0] / rho;
-      st->rho = t2[0];
-    }
-    st->xpend = 0;                 // x was updated above
-    st->done = done;
-  }
-  if (done != 0) return;
-  const float bf = (float)(t2[0] / rho);
-  for (long long i0 = t0; i0 < nv; i0 += U * ts) {
-    float4 rv[U], Pv[U], pv[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const long long i = i0 + k * ts;
-      if (i < nv) {
-        rv[k] = r4[i];
-        Pv[k] = P4[i];
-        pv[k] = p4[i];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const long long i = i0 + k * ts;
-      if (i < nv) {
-        float4 po = pv[k];
-        po.x = fmaf(bf, po.x, Pv[k].x * rv[k].x); po.y = fmaf(bf, po.y, Pv[k].y * rv[k].y);
-        po.z = fmaf(bf, po.z, Pv[k].z * rv[k].z); po.w = fmaf(bf, po.w, Pv[k].w * rv[k].w);
-        p4[i] = po;
-      }
-    }
-  }
-  for (long long i = nv * 4 + t0; i < nb; i += ts) p[i] = fmaf(bf, p[i], P[i] * r[i]);
-}
-
 // ---------------------------------------------------------------------------
 // Two-chunk variant for 9 <= n <= 15: one element per warp, lane (c, j) owns
 // the half-row i in [8c, 8c + 8) of y-plane j (16 lanes per half).  The
@@ -1138,35 +1000,6 @@ void launch_plane_n(const SemGeom& g, const SemClassTables<float>& t, const floa
   sem_count_launch();
 }
 
-template <int N>
-void prepare_cg_plane_n() {
-  cudaFuncSetAttribute(k_cg_plane<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem<N>());
-}
-
-template <int N>
-cudaError_t launch_cg_plane_n(const SemGeom& g, const SemClassTables<float>& t, float* x, float* r, float* p,
-                              float* q, const float* P, double* partials, PcgState* st, cudaStream_t s) {
-  const size_t smem = plane_smem<N>();
-  int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_plane<N>, kPlaneThreads, smem);
-  if (occ < 1) occ = 1;
-  // one co-resident wave: the grid barriers need every block resident
-  const int grid = sem_num_sms() * occ;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kPlaneThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;
-  at[0].val.cooperative = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_cg_plane<N>, g, t, x, r, p, q, P, partials, st);
-  sem_count_launch();
-  return e;
-}
-
 // Class blocks in the layout of plane_layout(n), from the metric
 // coefficients d0..d3 of each class and the 1D basis (FP64, stored in FP32).
 __global__ void k_plane_coeffs(SemGeom g, SemBasis b, const double* __restrict__ dcoef, float* __restrict__ out) {
@@ -1226,31 +1059,6 @@ void launch_plane_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoe
   if (blocks < 1) blocks = 1;
   k_plane_coeffs<<<(int)blocks, 256, 0, s>>>(g, b, dcoef, plane);
   sem_count_launch();
-}
-
-void prepare_cg_plane(const SemGeom& g) {
-  switch (g.n) {
-    case 2: prepare_cg_plane_n<2>(); break;
-    case 3: prepare_cg_plane_n<3>(); break;
-    case 4: prepare_cg_plane_n<4>(); break;
-    case 5: prepare_cg_plane_n<5>(); break;
-    case 6: prepare_cg_plane_n<6>(); break;
-    case 7: prepare_cg_plane_n<7>(); break;
-    default: prepare_cg_plane_n<8>(); break;
-  }
-}
-
-cudaError_t launch_cg_plane(const SemGeom& g, const SemClassTables<float>& t, float* x, float* r, float* p,
-                            float* q, const float* P, double* partials, PcgState* st, cudaStream_t s) {
-  switch (g.n) {
-    case 2: return launch_cg_plane_n<2>(g, t, x, r, p, q, P, partials, st, s);
-    case 3: return launch_cg_plane_n<3>(g, t, x, r, p, q, P, partials, st, s);
-    case 4: return launch_cg_plane_n<4>(g, t, x, r, p, q, P, partials, st, s);
-    case 5: return launch_cg_plane_n<5>(g, t, x, r, p, q, P, partials, st, s);
-    case 6: return launch_cg_plane_n<6>(g, t, x, r, p, q, P, partials, st, s);
-    case 7: return launch_cg_plane_n<7>(g, t, x, r, p, q, P, partials, st, s);
-    default: return launch_cg_plane_n<8>(g, t, x, r, p, q, P, partials, st, s);
-  }
 }
 
 void launch_plane_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,

@@ -287,74 +287,6 @@ static __device__ bool reduce_grid(double (&v)[NV], double* partials, unsigned i
   return true;
 }
 
-// Grid-wide barrier for kernels launched cooperatively (all blocks
-// resident).  The wait is bounded: after ~2-3 s a block gives up, records it in
-// *timeout and returns false (callers then stop without touching the
-// vectors).  *count is 0 between barriers; *gen counts completed barriers.
-constexpr long long kBarrierSpins = 50000000;
-static __device__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* timeout) {
-  __shared__ int ok_sh;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = gen;
-    const unsigned int g0 = *vgen;
-    __threadfence();
-    const unsigned int t = atomicAdd(count, 1u);
-    int ok = 1;
-    if (t == gridDim.x - 1) {
-      *count = 0u;
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g0) {
-        if (++spins > kBarrierSpins) {
-          ok = 0;
-          atomicExch(timeout, 1);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    ok_sh = ok;
-  }
-  __syncthreads();
-  return ok_sh != 0;
-}
-
-// Sums NV values over the whole grid in a fixed order; every block ends with
-// the same totals in all its threads.  partials holds NV * gridDim.x doubles;
-// sh is shared scratch of NV * 33 doubles.
-template <int NV>
-static __device__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* count, unsigned int* gen,
-                                int* timeout, double* sh, double (&tot)[NV]) {
-  double* bc = sh + NV * 32;
-  const unsigned G = gridDim.x;
-  block_sum<NV>(v, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) partials[k * G + blockIdx.x] = v[k];
-  }
-  if (!grid_barrier(count, gen, timeout)) return false;
-  double s[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    s[k] = 0.0;
-    for (unsigned i = threadIdx.x; i < G; i += blockDim.x) s[k] += __ldcg(partials + k * G + i);
-  }
-  block_sum<NV>(s, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) bc[k] = s[k];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) tot[k] = bc[k];
-  __syncthreads();
-  return true;
-}
-
 // 1/x to within 1 ulp (FP32, flush-to-zero), one MUFU instruction.
 static __device__ __forceinline__ float rcp_approx(float x) {
   float r;

@@ -141,9 +141,6 @@ struct PcgState {
   int maxit;
   int pad;
   unsigned int counter[4];  // last-block reduction tickets
-  unsigned int bar_count;   // grid barrier of the fused CG iteration kernel
-  unsigned int bar_gen;
-  int bar_timeout;          // set when a barrier wait gave up (the solve reports a breakdown)
   int xpend;                // 1: the last x += alpha p is still owed (the update stopped the CG)
   unsigned int flush_ticket;
   int pad2;

@@ -366,8 +366,6 @@ k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restri
     st->maxit = maxit;
     st->alpha = st->beta = 0.0;
     st->trig2 = 0.0;
-    st->bar_count = 0u;
-    st->bar_timeout = 0;
     st->xpend = 0;
     st->flush_ticket = 0u;
     if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) st->done = 2;

@@ -38,15 +38,6 @@ int sem_apply_default_kind(int n, size_t elem_bytes);
 // Number of SMs of the current device.
 int sem_num_sms();
 
-// One whole FP32 CG iteration with the plane-per-lane operator in one
-// cooperative launch (operator, update, stopping tests, direction; the
-// arithmetic of launch_tpt_apply + launch_pcg_update + launch_pcg_dir).
-// partials must hold 3 x (SMs x resident blocks) doubles.
-cudaError_t launch_cg_plane(const SemGeom& g, const SemClassTables<float>& t, float* x, float* r, float* p,
-                            float* q, const float* P, double* partials, PcgState* st, cudaStream_t s);
-// Sets the fused kernel's attributes (call once outside stream capture).
-void prepare_cg_plane(const SemGeom& g);
-
 // Per-class coefficient blocks of the plane-per-lane kernel (layout
 // plane_layout(n) in sem_internal.h), computed in FP64, stored in FP32.
 void launch_plane_coeffs(const SemGeom& g, const SemBasis& b, const double* dcoef, float* plane, cudaStream_t s);

@@ -36,8 +36,7 @@ class SemError(RuntimeError):
 class sem_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double),
-                ("fused_cg", ctypes.c_int)]
+                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double)]
 
 
 class sem_info(ctypes.Structure):
@@ -83,7 +82,6 @@ def lib():
         "sem_solve_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(sem_info), _P]),
         "sem_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "sem_set_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-        "sem_cg_fused": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
         "sem_check_vector": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "sem_debug_oob": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "sem_debug_limit_skeleton": (ctypes.c_int, [_P, ctypes.c_longlong]),
@@ -120,7 +118,7 @@ def exported_symbols():
             "sem_precond_diag", "sem_recover_interior", "sem_solve", "sem_solve_host",
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
             "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_set_operator_kernel",
-            "sem_get_operator_kernel", "sem_cg_fused", "sem_check_vector", "sem_debug_oob", "sem_debug_limit_skeleton",
+            "sem_get_operator_kernel", "sem_check_vector", "sem_debug_oob", "sem_debug_limit_skeleton",
             "sem_batch_create", "sem_batch_solve",
             "sem_batch_destroy", "sem_solve_batch",
             "sem_profile_enable",
@@ -364,13 +362,6 @@ def sem_debug_oob():
 def sem_debug_limit_skeleton(ctx: SemContext, bound: int) -> int:
     """Lowers the bound of the debug build's offset checks (status)."""
     return lib().sem_debug_limit_skeleton(ctx.handle, int(bound))
-
-
-def sem_cg_fused(ctx: SemContext) -> bool:
-    """Whether the FP32 CG iterations of mixed solves run as one fused kernel each."""
-    f = ctypes.c_int()
-    _check(lib().sem_cg_fused(ctx.handle, ctypes.byref(f)))
-    return bool(f.value)
 
 
 def sem_autotune(ctx: SemContext):

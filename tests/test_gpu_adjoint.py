@@ -93,3 +93,41 @@ def test_gradient_vs_finite_differences_full_size():
         hm[axis][i] -= eps
         fdv = dJ(sol(f, w.lam, *hp), sol(f, w.lam, *hm)) / (2 * eps)
         assert g[i] == pytest.approx(fdv, rel=1e-6), axis
+
+
+def test_lambda_as_number_and_as_cuda_tensor():
+    """lambda passed as a plain number gets no gradient (None) and leaves the
+    other gradients unchanged; passed as a CUDA 0-d tensor its gradient lands
+    on that device and equals the one returned for a CPU tensor."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    from paper_1601_08179_gb300.autograd import helmholtz_solve
+    p, m, lam = 3, (2, 2, 3), 2.0
+    hx, hy, hz, _ = si.graded_widths(*m, ar=2.0)
+    ms = Mesh(p, hx, hy, hz)
+    X, Y, Z = ms.coords()
+    f = (si.manufactured_f(X, Y, Z, lam) + si.node_noise(X.size, 54).reshape(X.shape)).ravel()
+    ut = torch.tensor(si.smooth_target(X, Y, Z, 55).ravel(), device="cuda")
+    opts = sem.default_opts(rtol=1e-13)
+
+    def run(lam_arg):
+        fd = torch.tensor(f, dtype=torch.float64, device="cuda", requires_grad=True)
+        hs = [torch.tensor(h, dtype=torch.float64, requires_grad=True) for h in (hx, hy, hz)]
+        u = helmholtz_solve(fd, lam_arg, *hs, p, opts)
+        (0.5 * ((u - ut) ** 2).sum()).backward()
+        return fd.grad.cpu().numpy(), [h.grad.numpy() for h in hs]
+
+    l_cpu = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+    df_cpu, dh_cpu = run(l_cpu)
+    l_cuda = torch.tensor(lam, dtype=torch.float64, device="cuda", requires_grad=True)
+    df_cuda, dh_cuda = run(l_cuda)
+    assert l_cuda.grad is not None and l_cuda.grad.is_cuda
+    # the runs repeat the same solves; atomics in arrival order make them equal
+    # to rounding, so they are compared at the solve bar
+    assert float(l_cuda.grad) == pytest.approx(float(l_cpu.grad), rel=1e-9)
+    df_num, dh_num = run(lam)
+    for got in (df_cuda, df_num):
+        assert np.linalg.norm(got - df_cpu) <= 1e-9 * np.linalg.norm(df_cpu)
+    for dh in (dh_cuda, dh_num):
+        for got, want in zip(dh, dh_cpu):
+            np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-12 * np.abs(want).max())

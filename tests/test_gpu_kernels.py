@@ -289,46 +289,6 @@ def test_mixed_solve_with_the_slab_kernel():
     assert relerr(host(u), ref) <= 1e-9
 
 
-@pytest.mark.parametrize("p,m,lam,ar", [(8, (3, 3, 2), 1.0, 4.0), (4, (5, 3, 3), 0.0, 8.0), (3, (3, 2, 3), 10.0, 2.0)])
-def test_fused_cg_iteration_matches_unfused(p, m, lam, ar):
-    """The fused FP32 CG iteration (one cooperative kernel: operator, updates,
-    dot products, stopping tests, direction) against the three-kernel form and
-    the dense oracle: both mixed solves reach the solve bar, with iteration
-    counts that differ by rounding only."""
-    import torch
-    from oracle import dense
-    from paper_1601_08179_gb300 import sem
-    ctx, ms = make_pair(p, m, lam, ar, opts=sem.default_opts(precision=sem.PREC_MIXED))
-    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_PLANE)   # the default at n = 2 is the element kernel
-    X, Y, Z = ms.coords()
-    f = (si.manufactured_f(X, Y, Z, lam) + si.node_noise(X.size, 31).reshape(X.shape)).ravel()
-    ref = dense.solve_full(ms, lam, f)
-    out = {}
-    for fused in (1, 0):
-        sem.sem_set_opts(ctx, sem.default_opts(precision=sem.PREC_MIXED, fused_cg=fused))
-        assert sem.sem_cg_fused(ctx) == bool(fused)
-        u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
-        info = sem.sem_solve(ctx, dev(f), u)
-        out[fused] = (host(u), info)
-        assert relerr(out[fused][0], ref) <= 1e-9, fused
-    assert abs(out[1][1]["iters"] - out[0][1]["iters"]) <= max(3, out[0][1]["iters"] // 20)
-    assert relerr(out[1][0], out[0][0]) <= 1e-9
-
-
-def test_fused_cg_only_with_the_plane_kernel():
-    from paper_1601_08179_gb300 import sem
-    ctx, ms = make_pair(8, (2, 2, 2), 1.0, opts=sem.default_opts(precision=sem.PREC_MIXED, fused_cg=1))
-    assert sem.sem_cg_fused(ctx)
-    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_WARP)
-    assert not sem.sem_cg_fused(ctx)
-    sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, sem.KERNEL_AUTO)
-    assert sem.sem_cg_fused(ctx)
-    ctx16, _ = make_pair(16, (1, 1, 1), 1.0, opts=sem.default_opts(precision=sem.PREC_MIXED, fused_cg=1))
-    assert not sem.sem_cg_fused(ctx16)          # the two-half-row plane kernel has no fused form
-    ctx0, _ = make_pair(8, (2, 2, 2), 1.0, opts=sem.default_opts(precision=sem.PREC_MIXED))
-    assert not sem.sem_cg_fused(ctx0)           # three kernels by default
-
-
 @pytest.mark.parametrize("p", [2, 3, 4, 5, 8, 12, 16, 24, 32])
 def test_f32_apply_entrywise_high_aspect_ratio(p):
     """FP32 operator on an x-graded mesh of aspect ratio 128 (metric factors

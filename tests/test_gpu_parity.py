@@ -291,6 +291,33 @@ def test_vector_arguments_are_checked_before_any_launch():
     assert torch.isfinite(vB).all()
 
 
+def test_entry_points_refuse_another_current_device():
+    """An entry point that launches refuses to run while a device other than
+    the context's is current (its kernels would launch there and read the
+    context's tables across devices), with nothing launched.  Needs two
+    visible GPUs; skipped otherwise."""
+    import ctypes
+    import torch
+    from paper_1601_08179_gb300 import sem
+    if torch.cuda.device_count() < 2:
+        pytest.skip("one GPU visible")
+    L = sem.lib()
+    with torch.cuda.device(0):
+        ctx, ms = make_pair(3, (2, 2, 2), 1.0)
+        uB = torch.zeros(ctx.nb, dtype=torch.float64, device="cuda:0")
+        vB = torch.zeros(ctx.nb, dtype=torch.float64, device="cuda:0")
+    with torch.cuda.device(1):
+        n0 = sem.sem_launch_count()
+        st = L.sem_apply_condensed(ctx.handle, ctypes.c_void_p(uB.data_ptr()), ctypes.c_void_p(vB.data_ptr()),
+                                   sem.SPACE_TRANSFORMED, None)
+        assert st == sem.SEM_EINVAL
+        assert "current device" in L.sem_last_error().decode()
+        assert sem.sem_launch_count() == n0
+    with torch.cuda.device(0):
+        sem.sem_apply_condensed(ctx, uB, vB)
+        torch.cuda.synchronize()
+
+
 def test_breakdown_on_nan_input():
     import torch
     from paper_1601_08179_gb300 import sem

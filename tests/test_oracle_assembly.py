@@ -155,6 +155,22 @@ def test_transformed_self_blocks_diagonal(p, m, ar):
                                ut, atol=1e-12 * np.abs(ut).max())
 
 
+@pytest.mark.parametrize("p,m,lam,ar,grade", [(3, (3, 2, 2), 0.0, 8.0, "x"), (4, (2, 3, 2), 1.5, 4.0, "xy"),
+                                              (6, (2, 2, 2), 0.3, 3.0, "x")])
+def test_transformed_diagonal_equals_dense(p, m, lam, ar, grade):
+    """local.transformed_diagonal (the BT preconditioner's diagonal, formed by
+    probing each width class with rows of S = diag(1, S_II, 1)) equals the
+    diagonal of T Ahat T^T from the dense Schur-complement assembly entry by
+    entry, and is zero at Dirichlet entries."""
+    hx, hy, hz, _ = si.graded_widths(*m, ar=ar, grade=grade)
+    ms = Mesh(p, hx, hy, hz)
+    A = dense.assemble_condensed(ms, lam)
+    T = transform.T_matrix(ms)
+    dd = np.where(ms.skeleton_free, (T @ A @ T.T).diagonal(), 0.0)
+    dl = local.transformed_diagonal(ms, lam)
+    np.testing.assert_allclose(dl, dd, rtol=0, atol=1e-13 * np.abs(dd).max())
+
+
 def test_pcg_equals_direct():
     rng = np.random.default_rng(0)
     Q = rng.standard_normal((60, 60))

@@ -1,6 +1,7 @@
 """sem_condense_rhs_noalloc: the condensed load for callers that cannot
-allocate device memory during the call (e.g. while a stream is captured into
-a CUDA graph, or when the application's pool holds all device memory).
+allocate device memory during the call (an application whose own pool holds
+the device memory, or a loop that must not take the device-wide
+synchronisation of cudaFree / cudaMalloc).
 
 It must give the same result as the allocating entry point sem_condense_rhs,
 on consecutive calls that reuse the library's fixed scratch array, and must
