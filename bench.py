@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--no-oracle-error", action="store_true",
                     help="skip the solves that measure the error against the oracle's recorded solve")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the other points of the graded grid (degree sweep, aspect ratio 1 and 8, "
+                         "lambda = 1e2, the mixed-precision workload) measured after the headline")
     ap.add_argument("--workload", default="scale", choices=["scale", "mixed16", "batched", "adjoint"],
                     help="scale: graded N~1.68e7 workload of degree --p (default); mixed16: p = 16 on 16^3, "
                          "lambda = 10, AR 16; batched: 64 heterogeneous problems in one graph launch; "
@@ -231,6 +234,85 @@ def kernel_name(sem, ctx, precision: int, p: int) -> str:
     if kind == sem.KERNEL_ELEMENT:
         return f"k_tpt_apply_p2<{t}>" if n == 1 else f"k_tpt_apply_elem<{n}>"
     return f"k_tpt_apply<{t}, {n if n in (1, 3, 7, 15, 31) else 0}> (epb {epb}, ks {ks})"
+
+
+def roofline(sem, ctx, w: si.Workload, apply_s: float, precision: str) -> dict:
+    """Roofline record of one operator launch of `precision` ("fp64" or
+    "mixed", whose operator is FP32) taking `apply_s` seconds."""
+    flops = apply_flops(w)
+    nb = ctx.nb
+    if precision == "fp64":
+        name = kernel_name(sem, ctx, sem.PREC_FP64, w.p)
+        achieved = flops / apply_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES.get((name, w.name)),
+                "peak_source": "FP64 FMA units x SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "flops_per_launch": flops}
+    # FP32 operator: flops and bytes both near their ridge; report the bound
+    # whose floor is larger
+    name = kernel_name(sem, ctx, sem.PREC_MIXED, w.p)
+    t_alu = flops / (FP32_PEAK_TFLOPS * 1e12)
+    t_hbm = 8.0 * nb / (HBM_GBS * 1e9)
+    if t_alu >= t_hbm:
+        achieved = flops / apply_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES.get((name, w.name)),
+                "peak_source": "FP32 FMA units x SM clock (152 SMs x 128 FMA/clk x 2.07 GHz)",
+                "flops_per_launch": flops}
+    achieved = 8.0 * nb / apply_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": HBM_GBS, "unit": "GB/s",
+            "frac": achieved / HBM_GBS, "traffic": TRAFFIC_BYTES.get((name, w.name)), "peak_source": HBM_SOURCE,
+            "bytes_per_launch": 8.0 * nb}
+
+
+def sweep_workloads():
+    """The other points of the graded-mesh grid, measured beside the headline:
+    the degree sweep at aspect ratio 128 and lambda = 0, the p = 8 mesh at
+    aspect ratio 1 and 8 and at lambda = 1e2, and the mixed-precision
+    workload (p = 16 on 16^3 elements, lambda = 10, aspect ratio 16)."""
+    out = [si.scale_workload(p) for p in (2, 4, 16, 32)]
+    out += [si.scale_workload(8, ar=1.0), si.scale_workload(8, ar=8.0), si.scale_workload(8, lam=100.0)]
+    return out + [si.MIXED]
+
+
+def sweep_point(sem, w: si.Workload, seed: int, steps: int = 2) -> dict:
+    """FP64 and mixed-precision solve time, iterations and operator time of
+    one workload (CUDA events; one untimed warm-up solve per form)."""
+    import torch
+    hx, hy, hz = w.widths()
+    ctx = sem.sem_setup(w.p, hx, hy, hz, w.lam)
+    x, y, z = sem.sem_node_coords(ctx)
+    f = torch.from_numpy(node_field(x, y, z, w, seed)).cuda()
+    u = torch.empty_like(f)
+    rec = {"workload": w.name, "p": w.p, "elements": list(w.m), "aspect_ratio": w.ar, "lambda": w.lam,
+           "dofs": w.dofs}
+    for form, opts in (("fp64", sem.default_opts()), ("mixed", sem.default_opts(precision=sem.PREC_MIXED))):
+        sem.sem_set_opts(ctx, opts)
+        sem.sem_profile_enable(ctx, False)
+        sem.sem_solve(ctx, f, u)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            info = sem.sem_solve(ctx, f, u)
+        ev1.record()
+        torch.cuda.synchronize()
+        step_s = ev0.elapsed_time(ev1) / 1e3 / steps
+        sem.sem_profile_enable(ctx, True)
+        sem.sem_profile_read(ctx, reset=True)
+        sem.sem_solve(ctx, f, u)
+        apply_ms, apply_n = sem.sem_profile_read(ctx, reset=True)
+        sem.sem_profile_enable(ctx, False)
+        apply_s = apply_ms / 1e3 / max(apply_n, 1)
+        roof = roofline(sem, ctx, w, apply_s, form)
+        rec[form] = {"solve_ms": step_s * 1e3, "s_per_dof": step_s / w.dofs, "iters": info["iters"],
+                     "refinements": info["refinements"], "rel_res": info["rel_res"],
+                     "operator_us": apply_s * 1e6, "operator_kernel": roof["kernel"],
+                     "operator_bound": roof["bound"], "operator_frac": roof["frac"]}
+    rec["speedup_mixed_vs_fp64"] = rec["fp64"]["solve_ms"] / rec["mixed"]["solve_ms"]
+    del ctx, f, u
+    torch.cuda.empty_cache()
+    return rec
 
 
 def apply_flops(w: si.Workload) -> float:
@@ -411,31 +493,7 @@ def our_arm(args, rank, world, local_rank):
     flops = apply_flops(w)
     nb = ctx.nb
     assert nb == skeleton_size(w.p, w.m), (nb, w.p, w.m)
-    if head == "fp64":
-        achieved = flops / r["apply_s"] / 1e12
-        roof = {"kernel": kernel_name(sem, ctx, sem.PREC_FP64, w.p), "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": TRAFFIC_BYTES.get((kernel_name(sem, ctx, sem.PREC_FP64, w.p), w.name)),
-                "peak_source": "FP64 FMA units x SM clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-                "flops_per_launch": flops}
-    else:
-        # FP32 operator: flops and bytes both near their ridge; report the
-        # bound whose floor is larger
-        t_alu = flops / (FP32_PEAK_TFLOPS * 1e12)
-        t_hbm = 8.0 * nb / (HBM_GBS * 1e9)
-        if t_alu >= t_hbm:
-            achieved = flops / r["apply_s"] / 1e12
-            roof = {"kernel": kernel_name(sem, ctx, sem.PREC_MIXED, w.p), "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                    "traffic": TRAFFIC_BYTES.get((kernel_name(sem, ctx, sem.PREC_MIXED, w.p), w.name)),
-                    "peak_source": "FP32 FMA units x SM clock (152 SMs x 128 FMA/clk x 2.07 GHz)",
-                    "flops_per_launch": flops}
-        else:
-            achieved = 8.0 * nb / r["apply_s"] / 1e9
-            roof = {"kernel": kernel_name(sem, ctx, sem.PREC_MIXED, w.p), "bound": "hbm", "achieved": achieved, "peak": HBM_GBS,
-                    "unit": "GB/s", "frac": achieved / HBM_GBS,
-                    "traffic": TRAFFIC_BYTES.get((kernel_name(sem, ctx, sem.PREC_MIXED, w.p), w.name)),
-                    "peak_source": HBM_SOURCE, "bytes_per_launch": 8.0 * nb}
+    roof = roofline(sem, ctx, w, r["apply_s"], head)
     out = {
         "metric": METRIC,
         "value": whole_job_value(r["step_s"], w.dofs, world),
@@ -478,6 +536,9 @@ def our_arm(args, rank, world, local_rank):
     if rec is not None and "mixed" in res:
         out["error_vs_oracle"] = errors_vs_oracle(sem, ctx, f, u, rec, int(res["mixed"]["info"]["refinements"]),
                                                   forms[head])
+    if world == 1 and args.workload == "scale" and not args.no_sweep:
+        # every other point of the graded grid, measured in this run after the timed region
+        out["sweep"] = [sweep_point(sem, sw, replica_seed(sw, rank)) for sw in sweep_workloads()]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_iters = reference_iterations(w)
         iters = res["fp64"]["info"]["iters"] if "fp64" in res else r["info"]["iters"]

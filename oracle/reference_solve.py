@@ -1,10 +1,11 @@
 """Writes the oracle's full-size reference record of a benchmark workload.
 
-    python -m oracle.reference_solve [p | mixed16] [--rtol 1e-12]
+    python -m oracle.reference_solve [p | mixed16] [--ar 128] [--lam 0] [--rtol 1e-12]
 
 Runs the oracle's Algorithm 4 (oracle.solve.bt_solve) on the graded workload
-of degree p (N ~ 1.68e7), or on the mixed-precision workload (p = 16 on 16^3
-elements, lambda = 10, aspect ratio 16), with the right-hand side built from
+of degree p (N ~ 1.68e7; x-graded to aspect ratio --ar, Helmholtz parameter
+--lam), or on the mixed-precision workload (p = 16 on 16^3 elements,
+lambda = 10, aspect ratio 16), with the right-hand side built from
 the oracle's own node coordinates, and stores in
 tests/golden/oracle_<workload>.json:
   * the CG iteration count at which ||r|| <= 1e-10 ||b|| (used to scale CPU
@@ -39,8 +40,11 @@ def golden_path(w: si.Workload) -> str:
 
 def main():
     arg = sys.argv[1] if len(sys.argv) > 1 and not sys.argv[1].startswith("-") else "8"
-    rtol = float(sys.argv[sys.argv.index("--rtol") + 1]) if "--rtol" in sys.argv else 1e-12
-    w = si.MIXED if arg == "mixed16" else si.scale_workload(int(arg))
+    def opt(name, default):
+        return float(sys.argv[sys.argv.index(name) + 1]) if name in sys.argv else default
+
+    rtol = opt("--rtol", 1e-12)
+    w = si.MIXED if arg == "mixed16" else si.scale_workload(int(arg), ar=opt("--ar", 128.0), lam=opt("--lam", 0.0))
     hx, hy, hz = w.widths()
     ms = Mesh(w.p, hx, hy, hz)
     X, Y, Z = ms.coords()
