@@ -229,6 +229,8 @@ def kernel_name(sem, ctx, precision: int, p: int) -> str:
         return f"k_tpt_apply_plane<{n}>" if n <= 8 else f"k_tpt_apply_plane2<{n}>"
     if kind == sem.KERNEL_SLAB:
         return "k_tpt_apply_slab"
+    if kind == sem.KERNEL_ROW:
+        return f"k_tpt_apply_row<{n}>"
     if kind == sem.KERNEL_WARP:
         return f"k_tpt_apply_warp<{t}, {n}>"
     if kind == sem.KERNEL_ELEMENT:

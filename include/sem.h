@@ -287,6 +287,13 @@ sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const d
  *   SEM_KERNEL_SLAB      a CTA works on one element and a slab of 8 planes k
  *                        of its eigenspace cube at a time (FP32,
  *                        16 <= n <= 31)
+ *   SEM_KERNEL_ROW       a CTA works on a segment of up to 32 consecutive
+ *                        elements of one x-row: warp w takes plane w of every
+ *                        element's cube, lane l element l; the segment's
+ *                        skeleton ranges move by bulk copies and bulk
+ *                        reduce-adds (FP32, 2 <= n <= 8; vectors whose
+ *                        addresses differ by a multiple of 16 bytes, else it
+ *                        runs as PLANE)
  * where n = p - 1.  SEM_KERNEL_AUTO resolves, in FP64, to ELEMENT at p = 2
  * and CTA_TILE otherwise; in FP32 to ELEMENT at p <= 3, PLANE for
  * 4 <= p <= 16 and SLAB for 17 <= p <= 32 (the fastest measured on GB300;
@@ -297,7 +304,8 @@ enum {
   SEM_KERNEL_WARP = 2,
   SEM_KERNEL_PLANE = 3,
   SEM_KERNEL_ELEMENT = 4,
-  SEM_KERNEL_SLAB = 5
+  SEM_KERNEL_SLAB = 5,
+  SEM_KERNEL_ROW = 6
 };
 
 /* Selects the operator kernel of one precision: SEM_PREC_FP64 (the FP64

@@ -12,7 +12,8 @@ enum ApplyKind {
   kApplyPlane = 3,     // lanes per y-plane: 32/G elements per warp (FP32, 2 <= n <= 8) or
                        // one element per warp, half rows (FP32, 9 <= n <= 15)
   kApplyElement = 4,   // one thread per element (n = 1; FP32 also n = 2, 3)
-  kApplySlab = 5       // element x slab of 8 planes k per CTA (FP32, 16 <= n <= 31)
+  kApplySlab = 5,      // element x slab of 8 planes k per CTA (FP32, 16 <= n <= 31)
+  kApplyRow = 6        // x-row segment of up to 32 elements per CTA, bulk copies (FP32, 2 <= n <= 8)
 };
 
 // Operator launch configuration.
@@ -49,6 +50,18 @@ void launch_plane_apply(const SemGeom& g, const SemClassTables<float>& t, const 
 // plane_layout(n)); same contract as launch_tpt_apply.
 void launch_slab_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
                        double* partials, PcgState* st, cudaStream_t s);
+
+// Degrees served by the row kernel (sem_apply_row.cu).
+inline bool row_supported(int n) { return n >= 2 && n <= 8; }
+// Most row segments one launch takes (bounded by the partial sums of the dot product).
+constexpr long long kRowMaxUnits = 1LL << 17;
+// Whether the row kernel can take this mesh and these vectors: a supported
+// degree, at most kRowMaxUnits segments, and x, y at the same address modulo
+// 16 bytes (its bulk copies keep that alignment).
+bool row_usable(const SemGeom& g, const float* x, const float* y);
+// y += Hhat~ x with the row kernel; same contract as launch_tpt_apply.
+void launch_row_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<float>& t, const float* x, float* y,
+                      double* partials, PcgState* st, cudaStream_t s);
 
 // Per-class operator coefficient blocks (layout in sem_internal.h), computed in
 // FP64 and stored in T.
@@ -180,4 +193,5 @@ cudaError_t sem_debug_take_apply(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_plane(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_slab(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_elem(unsigned long long* count, long long* first);
+cudaError_t sem_debug_take_row(unsigned long long* count, long long* first);
 #endif

@@ -326,9 +326,9 @@ def sem_gradients(ctx: SemContext, w, u, f, df, stream=None):
     return dl.value, dhx, dhy, dhz
 
 
-KERNEL_AUTO, KERNEL_CTA_TILE, KERNEL_WARP, KERNEL_PLANE, KERNEL_ELEMENT, KERNEL_SLAB = 0, 1, 2, 3, 4, 5
+KERNEL_AUTO, KERNEL_CTA_TILE, KERNEL_WARP, KERNEL_PLANE, KERNEL_ELEMENT, KERNEL_SLAB, KERNEL_ROW = 0, 1, 2, 3, 4, 5, 6
 KERNEL_NAMES = {KERNEL_CTA_TILE: "cta_tile", KERNEL_WARP: "warp", KERNEL_PLANE: "plane", KERNEL_ELEMENT: "element",
-                KERNEL_SLAB: "slab"}
+                KERNEL_SLAB: "slab", KERNEL_ROW: "row"}
 
 
 def sem_set_operator_kernel(ctx: SemContext, precision: int, kind: int, epb: int = 0, ks: int = 0):

@@ -34,10 +34,11 @@ def oracle_apply(ms, lam, ut):
 
 out = {"applies": [], "solves": []}
 K = {"AUTO": sem.KERNEL_AUTO, "WARP": sem.KERNEL_WARP, "PLANE": sem.KERNEL_PLANE,
-     "ELEMENT": sem.KERNEL_ELEMENT, "SLAB": sem.KERNEL_SLAB}
+     "ELEMENT": sem.KERNEL_ELEMENT, "SLAB": sem.KERNEL_SLAB, "ROW": sem.KERNEL_ROW}
 # FP64: the built-in kernel (thread per element at p = 2, CTA tile above)
-cases = [(2, (3, 2, 2), ["AUTO"], ["ELEMENT"]), (3, (1, 3, 2), ["AUTO"], ["ELEMENT", "PLANE"]),
-         (4, (3, 2, 2), ["AUTO"], ["PLANE", "ELEMENT", "WARP"]), (8, (2, 2, 3), ["AUTO"], ["PLANE", "WARP"]),
+cases = [(2, (3, 2, 2), ["AUTO"], ["ELEMENT"]), (3, (1, 3, 2), ["AUTO"], ["ELEMENT", "PLANE", "ROW"]),
+         (4, (3, 2, 2), ["AUTO"], ["PLANE", "ELEMENT", "WARP", "ROW"]),
+         (8, (2, 2, 3), ["AUTO"], ["PLANE", "WARP", "ROW"]),
          (12, (2, 1, 2), ["AUTO"], ["PLANE"]), (20, (2, 2, 1), ["AUTO"], ["SLAB"])]
 for p, m, k64, k32 in cases:
     ar = 1.0 if m[0] == 1 else 4.0
@@ -80,7 +81,8 @@ bound = ctx.nb - 27
 ut = si.random_vector(ms.n_skeleton, 3)
 caught = []
 for prec, kind in [(sem.PREC_FP64, sem.KERNEL_AUTO), (sem.PREC_MIXED, sem.KERNEL_PLANE),
-                   (sem.PREC_MIXED, sem.KERNEL_ELEMENT), (sem.PREC_MIXED, sem.KERNEL_WARP)]:
+                   (sem.PREC_MIXED, sem.KERNEL_ELEMENT), (sem.PREC_MIXED, sem.KERNEL_WARP),
+                   (sem.PREC_MIXED, sem.KERNEL_ROW)]:
     assert sem.sem_debug_limit_skeleton(ctx, bound) == sem.SEM_OK
     sem.sem_set_operator_kernel(ctx, prec, kind)
     if prec == sem.PREC_FP64:
