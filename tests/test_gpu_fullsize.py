@@ -120,22 +120,23 @@ def test_mixed16_error_per_refinement_step():
     assert final <= 1e-9
 
 
-SWEEP_RECORDED = (4, 16)   # degrees of the graded sweep with an oracle record besides p = 8
+SWEEP_RECORDED = [(4, 128.0, 0.0), (16, 128.0, 0.0), (8, 128.0, 100.0)]   # besides p = 8, lambda = 0
 
 
-@pytest.mark.parametrize("p", SWEEP_RECORDED)
+@pytest.mark.parametrize("p,ar,lam", SWEEP_RECORDED)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_sweep_solution_samples_and_iterations(p, precision):
-    """Graded sweep workloads (N ~ 1.68e7, aspect ratio 128, lambda = 0) at
-    full size against the oracle's solve: FP64 and mixed solutions at the
-    benchmark tolerance on the recorded sample nodes; the FP64 CG takes the
-    oracle's iteration count."""
+def test_sweep_solution_samples_and_iterations(p, ar, lam, precision):
+    """Graded workloads of the sweep (N ~ 1.68e7, x-graded to aspect ratio
+    ar) at full size against the oracle's solve: the transformed diagonal and
+    the nodal condensed load on the recorded skeleton samples (1e-12), FP64
+    and mixed solutions at the benchmark tolerance on the recorded sample
+    nodes; the FP64 CG takes the oracle's iteration count."""
     import torch
     from paper_1601_08179_gb300 import build, sem
-    w = si.scale_workload(p)
+    w = si.scale_workload(p, ar=ar, lam=lam)
     gold = os.path.join(os.path.dirname(__file__), "golden", f"oracle_{w.name}.json")
     if not os.path.exists(gold):
-        pytest.fail(f"missing {gold}: run python -m oracle.reference_solve {p}")
+        pytest.fail(f"missing {gold}: run python -m oracle.reference_solve {p} --ar {ar:g} --lam {lam:g}")
     rec = json.load(open(gold))
     build.build()
     hx, hy, hz = w.widths()
@@ -144,10 +145,19 @@ def test_sweep_solution_samples_and_iterations(p, precision):
     f = dev((si.manufactured_f(X, Y, Z, w.lam) + si.node_noise(X.size, w.seed).reshape(X.shape)).ravel())
     prec = sem.PREC_FP64 if precision == "fp64" else sem.PREC_MIXED
     ctx = sem.sem_setup(w.p, hx, hy, hz, w.lam, sem.default_opts(precision=prec))
+    if precision == "fp64":
+        d = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+        sem.sem_precond_diag(ctx, d)
+        idx = np.array(rec["diag_samples"]["index"])
+        assert _sampled_rel(host(d)[idx], np.array(rec["diag_samples"]["value"])) <= 1e-12
+        fb = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+        sem.sem_condense_rhs(ctx, f, fb, sem.SPACE_NODAL)
+        idx = np.array(rec["fhat_nodal_samples"]["index"])
+        assert _sampled_rel(host(fb)[idx], np.array(rec["fhat_nodal_samples"]["value"])) <= 1e-12
     u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
     info = sem.sem_solve(ctx, f, u)
     err = _sampled_rel(host(u)[np.array(rec["u_samples"]["index"])], np.array(rec["u_samples"]["value"]))
-    print(f"p = {p} {precision}: sampled error {err:.2e}, iterations {info['iters']}")
+    print(f"{w.name} {precision}: sampled error {err:.2e}, iterations {info['iters']}")
     assert err <= 1e-8
     if precision == "fp64":
         assert abs(info["iters"] - rec["iterations_to_1e-10"]) <= 2
