@@ -44,9 +44,9 @@ namespace {
 constexpr int kRowElems = 32;          // elements per segment (lanes of a warp)
 constexpr int kRowBlocks = 17;         // skeleton ranges of a segment
 constexpr long long kRowSpin = 1LL << 26;   // bound of the mbarrier wait
-// Register cap of the kernel: 96 lets three CTAs of seven warps share an SM at n = 7.
+// Register cap of the kernel (two CTAs of seven warps share an SM at n = 7; fewer registers spill).
 #ifndef SEM_ROW_MAXNREG
-#define SEM_ROW_MAXNREG 96
+#define SEM_ROW_MAXNREG 128
 #endif
 
 // 1-D basis of degree p in FP32 (kernel parameter: read through the constant
@@ -75,6 +75,7 @@ struct RowBlk {
 struct RowCtl {
   unsigned long long hb;
   unsigned whole, first, last;
+  int ex0, Ls, ey, ez;   // the segment: first element, length, row
 };
 
 __host__ __device__ constexpr int row_cap(int len) { return (len + 7) & ~3; }
@@ -108,10 +109,11 @@ struct RowSm {
   __device__ static int ostart(const RowCtl& c, int b) {
     return (b <= 4 ? base(b) : out_base(b)) + (int)((c.hb >> (2 * b)) & 3ull);
   }
-  static constexpr int WB = out_base(kRowBlocks);
-  static constexpr int WBS = N * N * kRowElems;   // floats per plane buffer
-  static constexpr int total = WB + 2 * WBS;      // floats
-  static constexpr size_t bytes = (size_t)total * 4 + kRowBlocks * sizeof(RowBlk) + 32;
+  static constexpr int BUF = out_base(kRowBlocks);   // one segment's buffer: ranges and output staging
+  static constexpr int WB = 2 * BUF;                 // two buffers: the next segment's gather overlaps
+  static constexpr int WBS = N * N * kRowElems;      // floats per plane buffer
+  static constexpr int total = WB + 2 * WBS;         // floats
+  static constexpr size_t bytes = (size_t)total * 4 + 2 * kRowBlocks * sizeof(RowBlk) + 2 * sizeof(RowCtl) + 32;
 };
 
 // ---- asynchronous-proxy helpers (mbarrier, bulk copies, bulk reductions) ----
@@ -151,6 +153,8 @@ __device__ __forceinline__ void bulk_reduce_add(float* dst, const void* src, uns
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Waits until the committed bulk operations of this thread have read their shared-memory sources.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // Makes this thread's shared-memory writes visible to the asynchronous proxy.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void red_add(float* p, float v) {
@@ -235,27 +239,75 @@ __device__ __forceinline__ void row_split(const float* base, long long off, int 
   }
 }
 
-// Gather of the segment's 17 ranges into shared memory: lane b of warp 0
-// issues the bulk copy of range b's aligned middle (all completing on `bar`),
-// every thread takes part in the plain loads of the unaligned ends and in
-// zeroing the ranges on the Dirichlet boundary.  Returns false if the copies
-// did not complete within the wait bound.
+// Describes segment `unit` (warp 0 only, lane b for range b): offsets,
+// lengths and aligned middles of its 17 ranges into blk, the control word into
+// *ctl.  Shared memory keeps each range's global address modulo 16 bytes
+// (input and output vectors agree on it).
 template <int N>
-__device__ __forceinline__ bool row_gather(const float* __restrict__ u, float* S, const RowBlk* blk, const RowCtl& c,
-                                           unsigned long long* bar) {
-  using Sm = RowSm<N>;
-  if (threadIdx.x < 32) {
-    const int b = threadIdx.x;
-    const bool mine = b < kRowBlocks && !((c.whole >> b) & 1u);
-    const unsigned bytes = mine ? 4u * (unsigned)(blk[b].tail - blk[b].head) : 0u;
-    unsigned total = bytes;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-    if (b == 0) mbar_arrive_expect_tx(bar, total);
-    __syncwarp();
-    if (bytes != 0u) bulk_load(S + Sm::start(c, b) + blk[b].head, u + blk[b].off + blk[b].head, bytes, bar);
+__device__ __forceinline__ void row_describe(const SemGeom& g, const RowSeg& seg, long long unit, const float* v,
+                                             RowBlk* blk, RowCtl* ctl) {
+  const int b = threadIdx.x;
+  const int sg = (int)(unit % seg.nseg);
+  const long long r = unit / seg.nseg;
+  const int ey = (int)(r % g.my), ez = (int)(r / g.my);
+  const int ex0 = sg * seg.len;
+  const int Ls = min(seg.len, g.mx - ex0);
+  long long off = 0;
+  int len = 0, flags = 1, h = 0;
+  if (b < kRowBlocks) {
+    row_range(g, b, ex0, Ls, ey, ez, &off, &len, &flags);
+#ifdef SEM_DEBUG
+    // a range reaching past the checked bound is recorded and skipped (treated as Dirichlet)
+    if (!(flags & 1) && !sem_dbg_ok(off, len, g.dbg_bound)) flags = 1;
+#endif
+    h = (int)(((unsigned long long)(v + off) >> 2) & 3ull);
+    RowBlk d;
+    d.off = off;
+    d.len = len;
+    row_split(v, off, len, &d.head, &d.tail);
+    d.pad = 0;
+    blk[b] = d;
   }
-  for (int idx = threadIdx.x; idx < kRowBlocks * 8; idx += blockDim.x) {
+  const unsigned h0 = __ballot_sync(0xffffffffu, h & 1), h1 = __ballot_sync(0xffffffffu, (h >> 1) & 1);
+  const unsigned wh = __ballot_sync(0xffffffffu, b < kRowBlocks && (flags & 1));
+  const unsigned fi = __ballot_sync(0xffffffffu, b < kRowBlocks && (flags & 2));
+  const unsigned la = __ballot_sync(0xffffffffu, b < kRowBlocks && (flags & 4));
+  if (b == 0) {
+    unsigned long long hb = 0;
+    for (int q = 0; q < kRowBlocks; ++q)
+      hb |= (unsigned long long)(((h0 >> q) & 1u) | (((h1 >> q) & 1u) << 1)) << (2 * q);
+    RowCtl cc;
+    cc.hb = hb;
+    cc.whole = wh;
+    cc.first = fi;
+    cc.last = la;
+    cc.ex0 = ex0;
+    cc.Ls = Ls;
+    cc.ey = ey;
+    cc.ez = ez;
+    *ctl = cc;
+  }
+  __syncwarp();
+}
+
+// Gather of a described segment into one buffer (warp 0 only): lane b issues
+// the bulk copy of range b's aligned middle (all completing on `bar`), then
+// the lanes load the unaligned ends and zero the ranges on the Dirichlet
+// boundary.
+template <int N>
+__device__ __forceinline__ void row_prefetch(const float* __restrict__ u, float* S, const RowBlk* blk, const RowCtl& c,
+                                             unsigned long long* bar) {
+  using Sm = RowSm<N>;
+  const int lane = threadIdx.x;
+  const bool mine = lane < kRowBlocks && !((c.whole >> lane) & 1u);
+  const unsigned bytes = mine ? 4u * (unsigned)(blk[lane].tail - blk[lane].head) : 0u;
+  unsigned total = bytes;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+  if (lane == 0) mbar_arrive_expect_tx(bar, total);
+  __syncwarp();
+  if (bytes != 0u) bulk_load(S + Sm::start(c, lane) + blk[lane].head, u + blk[lane].off + blk[lane].head, bytes, bar);
+  for (int idx = lane; idx < kRowBlocks * 8; idx += 32) {
     const int b = idx >> 3, e = idx & 7;
     if ((c.whole >> b) & 1u) continue;
     const int pos = e < 4 ? e : blk[b].tail + (e - 4);
@@ -263,11 +315,15 @@ __device__ __forceinline__ bool row_gather(const float* __restrict__ u, float* S
   }
   for (unsigned m = c.whole; m != 0u; m &= m - 1u) {
     const int b = __ffs(m) - 1, st = Sm::start(c, b), len = blk[b].len;
-    for (int t = threadIdx.x; t < len; t += blockDim.x) S[st + t] = 0.f;
+    for (int t = lane; t < len; t += 32) S[st + t] = 0.f;
   }
+}
+
+// Bounded wait for the bulk copies of one buffer (phase `parity` of its barrier).
+__device__ __forceinline__ bool row_wait(unsigned long long* bar, unsigned parity) {
   long long spins = 0;
-  bool done = mbar_try_wait(bar, 0);
-  while (!done && ++spins < kRowSpin) done = mbar_try_wait(bar, 0);
+  bool done = mbar_try_wait(bar, parity);
+  while (!done && ++spins < kRowSpin) done = mbar_try_wait(bar, parity);
   return done;
 }
 
@@ -287,28 +343,26 @@ __device__ __forceinline__ void row_zero_ends(float* S, const RowBlk* blk, const
   }
 }
 
-// Scatter-add of the segment's outputs: lane b of warp 0 issues the bulk
-// reduce-add of range b's aligned middle, every thread takes part in the
-// red.global.add of the ends; ranges on the Dirichlet boundary are skipped.
-// The caller has fenced its shared-memory writes for the asynchronous proxy
-// and synchronised the CTA.
+// Scatter-add of a segment's outputs: lane b of warp 0 issues the bulk
+// reduce-add of range b's aligned middle and commits it (not waited for
+// here), every thread takes part in the red.global.add of the ends; ranges on
+// the Dirichlet boundary are skipped.  The caller has fenced its
+// shared-memory writes for the asynchronous proxy and synchronised the CTA.
 template <int N>
 __device__ __forceinline__ void row_scatter(float* __restrict__ v, const float* S, const RowBlk* blk, const RowCtl& c) {
   using Sm = RowSm<N>;
-  const bool issuer = threadIdx.x < kRowBlocks && !((c.whole >> threadIdx.x) & 1u);
-  if (issuer) {
+  if (threadIdx.x < kRowBlocks && !((c.whole >> threadIdx.x) & 1u)) {
     const int b = threadIdx.x;
     const int h = blk[b].head, t = blk[b].tail;
     if (t > h) bulk_reduce_add(v + blk[b].off + h, S + Sm::ostart(c, b) + h, 4u * (unsigned)(t - h));
-    bulk_commit();
   }
+  if (threadIdx.x < 32) bulk_commit();
   for (int idx = threadIdx.x; idx < kRowBlocks * 8; idx += blockDim.x) {
     const int b = idx >> 3, e = idx & 7;
     if ((c.whole >> b) & 1u) continue;
     const int pos = e < 4 ? e : blk[b].tail + (e - 4);
     if (e < 4 ? pos < blk[b].head : pos < blk[b].len) red_add(v + blk[b].off + pos, S[Sm::ostart(c, b) + pos]);
   }
-  if (issuer) bulk_wait_all();
 }
 
 // Primary part of the 12 edges of element `el` at position p = warp index
@@ -464,85 +518,25 @@ __device__ __forceinline__ float row_edges(float* S, const RowCtl& c, const RowB
   return dot;
 }
 
-// v += Hhat~ u over one x-row segment per CTA (grid = segments); returns,
-// when st is given, p^T A p and alpha as the other operator kernels do.
+// The element operator of one described, gathered segment (buffer S):
+// edges and vertices, the walk over k, the z-faces; outputs in the buffer.
+// Returns this thread's share of u^T (A u).
 template <int N>
-__global__ void __maxnreg__(SEM_ROW_MAXNREG)
-k_tpt_apply_row(SemGeom g, SemClassTables<float> tab, RowBasis bf, RowSeg seg, const float* __restrict__ u,
-                float* __restrict__ v, double* __restrict__ partials, PcgState* st) {
+__device__ __forceinline__ float row_compute(const SemGeom& g, const SemClassTables<float>& tab, const RowBasis& bf,
+                                             const RowBasis& sbf, float* S, float* WB, const RowCtl& c) {
   using Sm = RowSm<N>;
   constexpr int n2 = N * N;
-  extern __shared__ __align__(16) float S[];
-  RowBlk* blk = reinterpret_cast<RowBlk*>(S + Sm::total);
-  __shared__ RowBasis sbf;   // for indices known at run time only (a kernel parameter indexed so would go to the stack)
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(blk + kRowBlocks);
-  if (st != nullptr && st->done) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long unit = blockIdx.x;
-  const int sg = (int)(unit % seg.nseg);
-  const long long r = unit / seg.nseg;
-  const int ey = (int)(r % g.my), ez = (int)(r / g.my);
-  const int ex0 = sg * seg.len;
-  const int Ls = min(seg.len, g.mx - ex0);
-  __shared__ RowCtl ctl_sh;
-  if (threadIdx.x < 32) {   // warp 0: lane b describes range b
-    const int b = threadIdx.x;
-    long long off = 0;
-    int len = 0, flags = 1, h = 0;
-    if (b < kRowBlocks) {
-      row_range(g, b, ex0, Ls, ey, ez, &off, &len, &flags);
-#ifdef SEM_DEBUG
-      // a range reaching past the checked bound is recorded and skipped (treated as Dirichlet)
-      if (!(flags & 1) && !sem_dbg_ok(off, len, g.dbg_bound)) flags = 1;
-#endif
-      // shared memory keeps the global address modulo 16 bytes (x and y agree on it)
-      h = (int)(((unsigned long long)(v + off) >> 2) & 3ull);
-      RowBlk d;
-      d.off = off;
-      d.len = len;
-      row_split(v, off, len, &d.head, &d.tail);
-      d.pad = 0;
-      blk[b] = d;
-    }
-    const unsigned h0 = __ballot_sync(0xffffffffu, h & 1), h1 = __ballot_sync(0xffffffffu, (h >> 1) & 1);
-    const unsigned wh = __ballot_sync(0xffffffffu, b < kRowBlocks && (flags & 1));
-    const unsigned fi = __ballot_sync(0xffffffffu, b < kRowBlocks && (flags & 2));
-    const unsigned la = __ballot_sync(0xffffffffu, b < kRowBlocks && (flags & 4));
-    if (b == 0) {
-      unsigned long long hb = 0;
-      for (int q = 0; q < kRowBlocks; ++q)
-        hb |= (unsigned long long)(((h0 >> q) & 1u) | (((h1 >> q) & 1u) << 1)) << (2 * q);
-      RowCtl cc;
-      cc.hb = hb;
-      cc.whole = wh;
-      cc.first = fi;
-      cc.last = la;
-      ctl_sh = cc;
-      sbf = bf;
-      mbar_init(bar, 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-  }
-  __syncthreads();
-  const RowCtl c = ctl_sh;
-  const bool ok = row_gather<N>(u, S, blk, c, bar);
-  if (__syncthreads_or(!ok)) {   // the copies did not complete in time: stop the solve
-    if (threadIdx.x == 0 && st != nullptr) st->done = 2;
-    return;
-  }
-  row_zero_ends<N>(S, blk, c, false);
-  __syncthreads();
-
   // element constants: metric coefficients d of the element's width class
-  const bool act = lane < Ls;
+  const bool act = lane < c.Ls;
   const int el = act ? lane : 0;
-  const int cls = elem_class(g, tab, ex0 + el, ey, ez);
+  const int cls = elem_class(g, tab, c.ex0 + el, c.ey, c.ez);
   const float4 dd = __ldg(reinterpret_cast<const float4*>(tab.dcoef) + cls);
   const float d0 = dd.x, d1 = dd.y, d2 = dd.z, d3 = dd.w;
   const float w0 = bf.w0;
 
   float exv[4], eyv[4];
-  float dot = row_edges<N>(S, c, bf, sbf, d0, d1, d2, d3, el, Ls, exv, eyv);
+  float dot = row_edges<N>(S, c, bf, sbf, d0, d1, d2, d3, el, c.Ls, exv, eyv);
   __syncthreads();   // every line sum is taken before the faces are overwritten
 
   // ---- walk the y-plane j = w in k
@@ -556,7 +550,6 @@ k_tpt_apply_row(SemGeom g, SemClassTables<float> tab, RowBasis bf, RowSeg seg, c
   float* YF1 = S + Sm::start(c, 2);
   const float* ZE0 = S + Sm::start(c, 11);
   const float* ZE1 = S + Sm::start(c, 12);
-  float* WB = S + Sm::WB;
   float e4h[N], e5h[N], z4[N], z5[N];
   {
     const float* z0 = S + Sm::start(c, 3) + el * n2 + j * N;
@@ -625,7 +618,7 @@ k_tpt_apply_row(SemGeom g, SemClassTables<float> tab, RowBasis bf, RowSeg seg, c
     __syncwarp();
     if (act) {
       float* t = XF + xo + n2 + k * N;
-      *t = lane + 1 < Ls ? *t + o1 : o1;
+      *t = lane + 1 < c.Ls ? *t + o1 : o1;
     }
     __syncthreads();   // the plane k of D^-1 x is complete; every row k of the y-faces has been read
     // y-faces at (k, i = w): sums over the planes j of D^-1 x
@@ -684,11 +677,78 @@ k_tpt_apply_row(SemGeom g, SemClassTables<float> tab, RowBasis bf, RowSeg seg, c
       }
     }
   }
+  return dot;
+}
+
+// v += Hhat~ u, one x-row segment at a time per CTA (a persistent grid: while
+// a segment is computed, the next one's ranges are on their way into the
+// other buffer); returns, when st is given, p^T A p and alpha as the other
+// operator kernels do.
+template <int N>
+__global__ void __maxnreg__(SEM_ROW_MAXNREG)
+k_tpt_apply_row(SemGeom g, SemClassTables<float> tab, RowBasis bf, RowSeg seg, const float* __restrict__ u,
+                float* __restrict__ v, double* __restrict__ partials, PcgState* st) {
+  using Sm = RowSm<N>;
+  extern __shared__ __align__(16) float S[];
+  RowBlk* blk = reinterpret_cast<RowBlk*>(S + Sm::total);                  // [2][17]
+  RowCtl* ctl = reinterpret_cast<RowCtl*>(blk + 2 * kRowBlocks);           // [2]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(ctl + 2);   // [2]
+  __shared__ RowBasis sbf;   // for indices known at run time only (a kernel parameter indexed so would go to the stack)
+  if (st != nullptr && st->done) return;
+  const long long units = (long long)seg.nseg * g.my * g.mz;
+  const bool warp0 = threadIdx.x < 32;
+  if (threadIdx.x == 0) {
+    sbf = bf;
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
-  row_zero_ends<N>(S, blk, c, true);
-  fence_async_smem();
+  if (warp0 && (long long)blockIdx.x < units) {
+    row_describe<N>(g, seg, blockIdx.x, v, blk, ctl);
+    row_prefetch<N>(u, S, blk, ctl[0], bar);
+  }
   __syncthreads();
-  row_scatter<N>(v, S, blk, c);
+  float dot = 0.f;
+  unsigned phase = 0u;   // bit b: parity of the next completion of bar[b]
+  int t = 0;
+  bool failed = false;
+  for (long long un = blockIdx.x; un < units; un += gridDim.x, ++t) {
+    const int b = t & 1;
+    float* Sb = S + b * Sm::BUF;
+    // the next segment into the other buffer, once the previous scatter from it has read its sources
+    const long long nx = un + gridDim.x;
+    if (warp0) {
+      bulk_wait_read();
+      __syncwarp();
+      if (nx < units) {
+        row_describe<N>(g, seg, nx, v, blk + (b ^ 1) * kRowBlocks, ctl + (b ^ 1));
+        row_prefetch<N>(u, S + (b ^ 1) * Sm::BUF, blk + (b ^ 1) * kRowBlocks, ctl[b ^ 1], bar + (b ^ 1));
+      }
+    }
+    const RowCtl c = ctl[b];
+    const RowBlk* bk = blk + b * kRowBlocks;
+    const bool ok = row_wait(bar + b, (phase >> b) & 1u);
+    phase ^= 1u << b;
+    if (__syncthreads_or(!ok)) {   // the copies did not complete in time: stop the solve
+      failed = true;
+      break;
+    }
+    row_zero_ends<N>(Sb, bk, c, false);
+    __syncthreads();
+    dot += row_compute<N>(g, tab, bf, sbf, Sb, S + Sm::WB, c);
+    __syncthreads();
+    row_zero_ends<N>(Sb, bk, c, true);
+    fence_async_smem();
+    __syncthreads();
+    row_scatter<N>(v, Sb, bk, c);
+    __syncthreads();   // the ends are read before the next gather into this buffer writes them
+  }
+  if (warp0) bulk_wait_all();
+  if (failed) {
+    if (threadIdx.x == 0 && st != nullptr) st->done = 2;
+    return;
+  }
 
   if (st != nullptr) {
     double vals[1] = {(double)dot}, tot[1];
@@ -717,14 +777,18 @@ RowBasis row_basis(const SemBasis& b) {
 template <int N>
 void launch_row_n(const SemGeom& g, const SemBasis& b, const SemClassTables<float>& t, const float* x, float* y,
                   double* partials, PcgState* st, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {   // once per instantiation; the first launch happens outside any capture
+  static int resident = 0;
+  if (resident == 0) {   // once per instantiation; the first launch happens outside any capture
     cudaFuncSetAttribute(k_tpt_apply_row<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RowSm<N>::bytes);
-    attr = true;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_tpt_apply_row<N>, N * 32, RowSm<N>::bytes);
+    if (resident < 1) resident = 1;
   }
   const RowSeg seg = row_segments(g.mx);
   const long long units = (long long)seg.nseg * g.my * g.mz;
-  k_tpt_apply_row<N><<<(unsigned)units, N * 32, RowSm<N>::bytes, s>>>(g, t, row_basis(b), seg, x, y, partials, st);
+  // a persistent grid: every resident CTA walks segments blockIdx.x, + gridDim.x, ...
+  long long grid = (long long)sem_num_sms() * resident;
+  if (grid > units) grid = units;
+  k_tpt_apply_row<N><<<(unsigned)grid, N * 32, RowSm<N>::bytes, s>>>(g, t, row_basis(b), seg, x, y, partials, st);
   sem_count_launch();
 }
 
