@@ -374,6 +374,42 @@ void sem_batch_destroy(sem_batch* batch);
 sem_status sem_solve_batch(sem_ctx* const* ctxs, int count, const double* const* f, double* const* u,
                            sem_info* infos, void* stream);
 
+/* The paper's comparison variants (Sec. 5 and Sec. 8), on the NODAL skeleton
+ * in FP64.  They exist to measure the transformed operator and solver this
+ * library is built on against the alternatives the paper compares them with.
+ * Operators (sem_apply_condensed_variant: vB = Hhat uB, the same operator as
+ * sem_apply_condensed in SEM_SPACE_NODAL, computed another way):
+ *   SEM_OP_TPT  the transformed operator (Table 2) between the skeleton
+ *               transforms: what sem_apply_condensed(NODAL) does
+ *   SEM_OP_TPC  Algorithm 3 with Table 1: the nodal primary part
+ *               (Eq. east_east_primary_part, 12 n^3 multiplications per
+ *               element) and the condensed part through the interior
+ *               eigenspace, the faces mapped in and out with V^T M_II and
+ *               M_II V inside the element loop (37 n^3); p <= 16
+ *   SEM_OP_MMC  Algorithm 2: the nodal primary part and the condensed part as
+ *               a dense 6n^2 x 6n^2 face-to-face matrix per width class,
+ *               applied to all elements of a class with one DGEMM (36 n^4);
+ *               built on first use (O(n^7) per class); p <= 16, at most
+ *               8 GiB of matrices (else SEM_ENOTSUP)
+ * Preconditioners of sem_solve_variant (CG on the nodal condensed system,
+ * stopping at ||r|| <= opts.rtol ||b||, at most opts.maxit iterations):
+ *   SEM_PC_NONE   unpreconditioned (the paper's UC with TPC)
+ *   SEM_PC_DIAG   inverse diagonal of the nodal condensed operator (DC)
+ *   SEM_PC_BLOCK  exact inverse of the face, edge and vertex self blocks (BC),
+ *                 applied in tensor form: transform, the inverse diagonal of
+ *                 the transformed operator, transform back (the blocks are
+ *                 diagonal in the transformed system)
+ * sem_diag_nodal writes the assembled diagonal of the nodal condensed
+ * operator (0 at Dirichlet entries).  Vectors: device, N_B (uB, vB, diag) or
+ * the full nodal grid (f, u).  sem_apply_condensed_variant and sem_diag_nodal
+ * are asynchronous; sem_solve_variant synchronises to read its stopping test
+ * after every iteration and fills info (iters, rel_res, t_solve_s). */
+enum { SEM_OP_TPT = 0, SEM_OP_TPC = 1, SEM_OP_MMC = 2 };
+enum { SEM_PC_NONE = 0, SEM_PC_DIAG = 1, SEM_PC_BLOCK = 2 };
+sem_status sem_apply_condensed_variant(sem_ctx* ctx, int op, const double* uB, double* vB, void* stream);
+sem_status sem_diag_nodal(sem_ctx* ctx, double* diag, void* stream);
+sem_status sem_solve_variant(sem_ctx* ctx, int op, int pc, const double* f, double* u, sem_info* info, void* stream);
+
 /* Residual history of the last MIXED solve: rel_res[k] = ||b - A x_k|| / ||b||
  * (FP64, transformed condensed space) before refinement step k and after the
  * last one; *count = number of entries (up to max_refine + 1).  HOST array of

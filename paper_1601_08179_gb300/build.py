@@ -24,7 +24,7 @@ LIB = os.path.join(HERE, "libsemgb.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libsemgb_debug.so")
 SOURCES = ["sem_host.cpp", "sem_kernels.cu", "sem_apply.cu", "sem_apply_plane.cu", "sem_apply_slab.cu",
-           "sem_apply_elem.cu", "sem_apply_row.cu", "sem_api.cu"]
+           "sem_apply_elem.cu", "sem_apply_row.cu", "sem_compare.cu", "sem_api.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -68,7 +68,7 @@ def build(force: bool = False, debug: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda src: _compile(src, debug), SOURCES))
     tmp = lib + ".tmp"
-    cmd = [nvcc(), ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc(), ARCH, "-shared", "-o", tmp, *objs, "-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -9,6 +9,7 @@
 //      device and the host reads one small status record per batch;
 //   3. interior recovery u_I = (V(x)V(x)V) D^-1 (F~_I - H~_IB u~_B) and the
 //      nodal skeleton u_B = T^T u~_B.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -121,6 +122,20 @@ struct sem_ctx {
   std::vector<cudaEvent_t> pev32;
   std::vector<double> refine_hist;     // ||b - A x_k|| / ||b|| after each refinement step
   ApplyConfig op64{}, op32{};           // operator kernel per precision (kind kApplyAuto: built-in)
+
+  // the paper's comparison variants (nodal skeleton, FP64), allocated on first use
+  double* d_cmpK = nullptr;            // (p+1)^2 stiffness, then the (p+1) GLL weights
+  double* d_cmp = nullptr;             // skeleton vectors of the nodal CG: b, x, r, p, q, z, tmp
+  CmpState* d_cst = nullptr;
+  CmpState h_cst{};
+  double* d_cdiag = nullptr;           // per-class condensed face diagonals
+  double* d_Pdc = nullptr;             // inverse diagonal of the nodal condensed operator (DC)
+  double* d_mmc = nullptr;             // per-class dense condensed face matrices (MMC)
+  int* d_cls_elems = nullptr;          // elements grouped by width class
+  std::vector<long long> cls_start;
+  std::vector<int> cls_count;
+  double *d_mmcU = nullptr, *d_mmcY = nullptr;
+  cublasHandle_t cublas = nullptr;
 
   const double* mat(int k) const { return d_mats + (size_t)k * g.n * g.n; }
 };
@@ -653,6 +668,11 @@ void free_ctx(sem_ctx* c) {
   for (void* p : ptrs32)
     if (p) cudaFree(p);
   for (cudaEvent_t ev : c->pev32) cudaEventDestroy(ev);
+  void* ptrs_cmp[] = {c->d_cmpK, c->d_cmp, c->d_cst, c->d_cdiag, c->d_Pdc, c->d_mmc, c->d_cls_elems, c->d_mmcU,
+                      c->d_mmcY};
+  for (void* p : ptrs_cmp)
+    if (p) cudaFree(p);
+  if (c->cublas) cublasDestroy(c->cublas);
   void* ptrs_adj[] = {c->d_h, c->d_K, c->d_full, c->d_E, c->d_grad};
   for (void* p : ptrs_adj)
     if (p) cudaFree(p);
@@ -1511,7 +1531,8 @@ extern "C" sem_status sem_debug_oob(long long* count, long long* first) {
   long long f = -1;
   cudaError_t (*const take[])(unsigned long long*, long long*) = {sem_debug_take_kernels, sem_debug_take_apply,
                                                                  sem_debug_take_plane, sem_debug_take_slab,
-                                                                 sem_debug_take_elem, sem_debug_take_row};
+                                                                 sem_debug_take_elem, sem_debug_take_row,
+                                                                 sem_debug_take_compare};
   for (auto fn : take) SEM_CUDA(fn(&n, &f));
   *count = (long long)n;
   *first = n != 0 ? f : -1;
@@ -1853,4 +1874,243 @@ extern "C" sem_status sem_solve_batch(sem_ctx* const* ctxs, int count, const dou
   sem_batch_destroy(b);
   t_err = keep;
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// The paper's comparison variants: TPC and MMC operators, DC / BC / UC
+// preconditioning (Sec. 5 and Sec. 8), on the nodal skeleton in FP64
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kMmcMaxBytes = 8ull << 30;   // the per-class dense face matrices MMC may hold
+
+double* cmp_vec(sem_ctx* c, int k) { return c->d_cmp + (size_t)k * c->g.nb; }
+
+sem_status ensure_cmp(sem_ctx* c) {
+  if (c->d_cst != nullptr) return SEM_OK;
+  const SemGeom& g = c->g;
+  std::vector<double> kw(c->h1.K);
+  kw.insert(kw.end(), c->h1.w.begin(), c->h1.w.end());
+  if (dalloc(&c->d_cmpK, kw.size()) != cudaSuccess || dalloc(&c->d_cmp, 7 * (size_t)g.nb) != cudaSuccess ||
+      dalloc(&c->d_cst, 1) != cudaSuccess)
+    return fail(SEM_ENOMEM, "cannot allocate the comparison solver's vectors");
+  SEM_CUDA(cudaMemcpy(c->d_cmpK, kw.data(), kw.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SEM_CUDA(cudaMemset(c->d_cst, 0, sizeof(CmpState)));
+  return SEM_OK;
+}
+
+// Inverse diagonal of the nodal condensed operator (DC).
+sem_status ensure_dc(sem_ctx* c, cudaStream_t s) {
+  if (c->d_Pdc != nullptr) return SEM_OK;
+  const SemGeom& g = c->g;
+  const int ncls = g.ux * g.uy * g.uz;
+  if (dalloc(&c->d_cdiag, (size_t)ncls * 6 * g.n * g.n) != cudaSuccess || dalloc(&c->d_Pdc, g.nb) != cudaSuccess)
+    return fail(SEM_ENOMEM, "cannot allocate the nodal diagonal");
+  double* diag = cmp_vec(c, 6);
+  SEM_CUDA(cudaMemsetAsync(diag, 0, sizeof(double) * g.nb, s));
+  launch_cmp_diag(g, c->h1.basis, c->tab, c->d_cmpK, c->d_cmpK + (g.p + 1) * (g.p + 1), c->mat(2), ncls, c->d_cdiag,
+                  diag, s);
+  launch_invert_diag(g, diag, c->d_Pdc, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+// Dense condensed face matrices of every width class and the elements of
+// each class (MMC).
+sem_status ensure_mmc(sem_ctx* c, cudaStream_t s) {
+  if (c->d_mmc != nullptr) return SEM_OK;
+  const SemGeom& g = c->g;
+  const int ncls = g.ux * g.uy * g.uz;
+  const long long M = 6LL * g.n * g.n;
+  if ((size_t)ncls * M * M * sizeof(double) > kMmcMaxBytes)
+    return fail(SEM_ENOTSUP, "MMC: the dense face matrices of this mesh exceed " +
+                                 std::to_string(kMmcMaxBytes >> 30) + " GiB");
+  std::vector<std::vector<int>> members(ncls);
+  for (long long e = 0; e < g.nelem; ++e) {
+    const int ex = (int)(e % g.mx), ey = (int)((e / g.mx) % g.my), ez = (int)(e / ((long long)g.mx * g.my));
+    members[c->clsx[ex] + g.ux * (c->clsy[ey] + g.uy * c->clsz[ez])].push_back((int)e);
+  }
+  std::vector<int> flat;
+  flat.reserve(g.nelem);
+  c->cls_start.assign(ncls, 0);
+  c->cls_count.assign(ncls, 0);
+  int maxc = 0;
+  for (int k = 0; k < ncls; ++k) {
+    c->cls_start[k] = (long long)flat.size();
+    c->cls_count[k] = (int)members[k].size();
+    maxc = std::max(maxc, c->cls_count[k]);
+    flat.insert(flat.end(), members[k].begin(), members[k].end());
+  }
+  if (dalloc(&c->d_mmc, (size_t)ncls * M * M) != cudaSuccess || dalloc(&c->d_cls_elems, flat.size()) != cudaSuccess ||
+      dalloc(&c->d_mmcU, (size_t)maxc * M) != cudaSuccess || dalloc(&c->d_mmcY, (size_t)maxc * M) != cudaSuccess)
+    return fail(SEM_ENOMEM, "cannot allocate the MMC face matrices");
+  SEM_CUDA(cudaMemcpy(c->d_cls_elems, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice));
+  for (int k = 0; k < ncls; ++k) launch_mmc_build(g, c->h1.basis, c->tab, c->mat(2), k, c->d_mmc + (size_t)k * M * M, s);
+  if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) return fail(SEM_ECUDA, "cublasCreate failed");
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+// v = Hhat u on the nodal skeleton with operator variant op.
+sem_status cmp_apply(sem_ctx* c, int op, const double* u, double* v, cudaStream_t s) {
+  const SemGeom& g = c->g;
+  const double* K = c->d_cmpK;
+  const double* w = K + (g.p + 1) * (g.p + 1);
+  if (op == SEM_OP_TPT) {
+    launch_skel_transform(g, c->mat(2), u, c->d_t1, s);
+    sem_status st = apply_t(c, c->d_t1, c->d_t2, s);
+    if (st != SEM_OK) return st;
+    launch_skel_transform(g, c->mat(3), c->d_t2, v, s);
+    SEM_CUDA(cudaGetLastError());
+    return SEM_OK;
+  }
+  SEM_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * g.nb, s));
+  launch_tpc_apply(g, c->h1.basis, c->tab, K, w, c->mat(2), c->mat(3), u, v, op == SEM_OP_TPC ? 1 : 0, s);
+  if (op == SEM_OP_MMC) {
+    const int M = 6 * g.n * g.n;
+    const double one = 1.0, zero = 0.0;
+    if (cublasSetStream(c->cublas, s) != CUBLAS_STATUS_SUCCESS) return fail(SEM_ECUDA, "cublasSetStream failed");
+    for (size_t k = 0; k < c->cls_count.size(); ++k) {
+      const int cnt = c->cls_count[k];
+      if (cnt == 0) continue;
+      const int* el = c->d_cls_elems + c->cls_start[k];
+      launch_mmc_gather(g, el, cnt, u, c->d_mmcU, s);
+      if (cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, M, cnt, M, &one, c->d_mmc + k * (size_t)M * M, M,
+                      c->d_mmcU, M, &zero, c->d_mmcY, M) != CUBLAS_STATUS_SUCCESS)
+        return fail(SEM_ECUDA, "cublasDgemm failed");
+      launch_mmc_scatter(g, el, cnt, c->d_mmcY, v, s);
+    }
+  }
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+// z = M^-1 r with preconditioner pc (st: skip once the CG has stopped, may be null).
+sem_status cmp_precond(sem_ctx* c, int pc, const double* r, double* z, const CmpState* st, cudaStream_t s) {
+  const SemGeom& g = c->g;
+  if (pc == SEM_PC_NONE) {
+    launch_cmp_diagmul(g.nb, nullptr, r, z, st, s);
+  } else if (pc == SEM_PC_DIAG) {
+    launch_cmp_diagmul(g.nb, c->d_Pdc, r, z, st, s);
+  } else {
+    // block-Jacobi over faces, edges and vertices: T^T diag(T Ahat T^T)^-1 T (the blocks are diagonal in the
+    // transformed system)
+    double* t = cmp_vec(c, 6);
+    launch_skel_transform(g, c->mat(0), r, t, s);
+    launch_cmp_diagmul(g.nb, c->d_P, t, t, nullptr, s);
+    launch_skel_transform(g, c->mat(1), t, z, s);
+  }
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+sem_status check_variant(const sem_ctx* c, int op) {
+  if (op != SEM_OP_TPT && op != SEM_OP_TPC && op != SEM_OP_MMC) return fail(SEM_EINVAL, "unknown operator variant");
+  if (op != SEM_OP_TPT && c->g.p > kCmpMaxP)
+    return fail(SEM_ENOTSUP, "TPC and MMC are built for p <= " + std::to_string(kCmpMaxP));
+  return SEM_OK;
+}
+
+sem_status prepare_variant(sem_ctx* c, int op, cudaStream_t s) {
+  sem_status st = ensure_cmp(c);
+  if (st == SEM_OK && op == SEM_OP_MMC) st = ensure_mmc(c, s);
+  return st;
+}
+
+}  // namespace
+
+extern "C" sem_status sem_apply_condensed_variant(sem_ctx* c, int op, const double* uB, double* vB, void* stream) {
+  t_err.clear();
+  NvtxScope nvtx_("sem_apply_condensed_variant");
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  SEM_CHECK_VEC(uB, double);
+  SEM_CHECK_VEC(vB, double);
+  if (uB == vB) return fail(SEM_EINVAL, "uB and vB must not alias");
+  sem_status st = check_variant(c, op);
+  if (st != SEM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = prepare_variant(c, op, s);
+  if (st != SEM_OK) return st;
+  return cmp_apply(c, op, uB, vB, s);
+}
+
+extern "C" sem_status sem_diag_nodal(sem_ctx* c, double* diag, void* stream) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  SEM_CHECK_VEC(diag, double);
+  cudaStream_t s = (cudaStream_t)stream;
+  sem_status st = ensure_cmp(c);
+  if (st == SEM_OK) st = ensure_dc(c, s);
+  if (st != SEM_OK) return st;
+  // the diagonal is the inverse of the stored inverse (zero stays zero at Dirichlet entries)
+  launch_invert_diag(c->g, c->d_Pdc, diag, s);
+  SEM_CUDA(cudaGetLastError());
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_solve_variant(sem_ctx* c, int op, int pc, const double* f, double* u, sem_info* info,
+                                        void* stream) {
+  t_err.clear();
+  NvtxScope nvtx_("sem_solve_variant");
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  SEM_CHECK_VEC(f, double);
+  SEM_CHECK_VEC(u, double);
+  sem_status st = check_variant(c, op);
+  if (st != SEM_OK) return st;
+  if (pc != SEM_PC_NONE && pc != SEM_PC_DIAG && pc != SEM_PC_BLOCK) return fail(SEM_EINVAL, "unknown preconditioner");
+  const auto t0 = std::chrono::steady_clock::now();
+  if (info) std::memset(info, 0, sizeof(*info));
+  cudaStream_t us = (cudaStream_t)stream;
+  SEM_CUDA(cudaEventRecord(c->ev_in, us));
+  SEM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  cudaStream_t s = c->stream;
+  st = prepare_variant(c, op, s);
+  if (st == SEM_OK && pc == SEM_PC_DIAG) st = ensure_dc(c, s);
+  if (st != SEM_OK) return st;
+  const SemGeom& g = c->g;
+  double *b = cmp_vec(c, 0), *x = cmp_vec(c, 1), *r = cmp_vec(c, 2), *p = cmp_vec(c, 3), *q = cmp_vec(c, 4),
+         *z = cmp_vec(c, 5);
+  // nodal condensed load (Algorithm 1), F~_I kept for the recovery
+  st = condense_rhs_t(c, f, c->d_b, s);
+  if (st != SEM_OK) return st;
+  launch_skel_transform(g, c->mat(3), c->d_b, b, s);
+  st = cmp_precond(c, pc, b, z, nullptr, s);
+  if (st != SEM_OK) return st;
+  launch_cmp_init(g.nb, b, x, r, z, p, c->d_partials, c->d_cst, c->opts.rtol, c->opts.maxit, s);
+  CmpState& h = c->h_cst;
+  // the stopping test is read after every iteration: the operators of this
+  // loop cost milliseconds, the read a few microseconds, and no operator
+  // runs past convergence
+  for (int batch = 0; batch < c->opts.maxit + 2; ++batch) {
+    SEM_CUDA(cudaMemcpyAsync(&h, c->d_cst, sizeof(CmpState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+    if (h.done != 0) break;
+    {
+      st = cmp_apply(c, op, p, q, s);
+      if (st != SEM_OK) return st;
+      launch_cmp_pq(g.nb, p, q, c->d_partials, c->d_cst, s);
+      launch_cmp_xr(g.nb, x, r, p, q, c->d_partials, c->d_cst, s);
+      st = cmp_precond(c, pc, r, z, c->d_cst, s);
+      if (st != SEM_OK) return st;
+      launch_cmp_rz(g.nb, r, z, c->d_partials, c->d_cst, s);
+      launch_cmp_dir(g.nb, z, p, q, c->d_cst, s);
+    }
+  }
+  SEM_CUDA(cudaMemcpyAsync(&h, c->d_cst, sizeof(CmpState), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  // interior recovery from the nodal skeleton solution
+  launch_skel_transform(g, c->mat(2), x, c->d_x, s);
+  st = recover_t(c, c->d_x, u, s);
+  if (st != SEM_OK) return st;
+  SEM_CUDA(cudaEventRecord(c->ev_out, s));
+  SEM_CUDA(cudaStreamWaitEvent(us, c->ev_out, 0));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    info->iters = h.iter;
+    info->rel_res = h.rr0 > 0.0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+    info->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (h.done == 2) return fail(SEM_EBREAKDOWN, "CG breakdown (p^T A p <= 0 or non-finite values)");
+  if (h.done != 1) return fail(SEM_ENOCONV, "CG reached maxit without meeting rtol");
+  return SEM_OK;
 }

@@ -194,4 +194,36 @@ cudaError_t sem_debug_take_plane(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_slab(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_elem(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_row(unsigned long long* count, long long* first);
+cudaError_t sem_debug_take_compare(unsigned long long* count, long long* first);
 #endif
+
+// ---- the paper's comparison variants (sem_compare.cu): nodal skeleton, FP64, p <= 16
+// Device state of the nodal-space CG of the comparison solvers.
+struct CmpState {
+  double rho, pq, rr, rr0, tol2, alpha, beta;
+  int iter, done, maxit, pad;   // done: 1 converged, 2 breakdown, 3 maxit
+  unsigned int counter[4];
+};
+constexpr int kCmpMaxP = 16;
+// v += Hhat u (nodal): primary part, plus the TPC condensed part when condensed != 0.
+void launch_tpc_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t, const double* K,
+                      const double* w, const double* A, const double* B, const double* u, double* v, int condensed,
+                      cudaStream_t s);
+// Dense condensed face-to-face matrix (6n^2 x 6n^2) of one width class.
+void launch_mmc_build(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t, const double* A, int cls,
+                      double* C, cudaStream_t s);
+void launch_mmc_gather(const SemGeom& g, const int* elems, int count, const double* u, double* U, cudaStream_t s);
+void launch_mmc_scatter(const SemGeom& g, const int* elems, int count, const double* Y, double* v, cudaStream_t s);
+// diag += the assembled diagonal of the nodal condensed operator (cd: per-class scratch of ncls * 6n^2).
+void launch_cmp_diag(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t, const double* K,
+                     const double* w, const double* A, int ncls, double* cd, double* diag, cudaStream_t s);
+void launch_cmp_init(long long nb, const double* b, double* x, double* r, const double* z, double* p, double* partials,
+                     CmpState* st, double rtol, int maxit, cudaStream_t s);
+void launch_cmp_pq(long long nb, const double* p, const double* q, double* partials, CmpState* st, cudaStream_t s);
+void launch_cmp_xr(long long nb, double* x, double* r, const double* p, const double* q, double* partials,
+                   CmpState* st, cudaStream_t s);
+void launch_cmp_rz(long long nb, const double* r, const double* z, double* partials, CmpState* st, cudaStream_t s);
+void launch_cmp_dir(long long nb, const double* z, double* p, double* q, const CmpState* st, cudaStream_t s);
+void launch_cmp_diagmul(long long nb, const double* D, const double* r, double* z, const CmpState* st,
+                        cudaStream_t s);
+

@@ -94,6 +94,9 @@ def lib():
         "sem_solve_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                            ctypes.POINTER(sem_info), _P]),
         "sem_gradients": (ctypes.c_int, [_P, _P, _P, _P, _P, _D, _D, _D, _D, _P]),
+        "sem_apply_condensed_variant": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+        "sem_diag_nodal": (ctypes.c_int, [_P, _P, _P]),
+        "sem_solve_variant": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(sem_info), _P]),
         "sem_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
         "sem_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                             ctypes.c_int]),
@@ -121,6 +124,7 @@ def exported_symbols():
             "sem_get_operator_kernel", "sem_check_vector", "sem_debug_oob", "sem_debug_limit_skeleton",
             "sem_batch_create", "sem_batch_solve",
             "sem_batch_destroy", "sem_solve_batch",
+            "sem_apply_condensed_variant", "sem_diag_nodal", "sem_solve_variant",
             "sem_profile_enable",
             "sem_profile_read", "sem_launch_count",
             "sem_destroy", "sem_status_string", "sem_last_error"]
@@ -401,6 +405,33 @@ class SemBatch:
                 self.handle = None
         except Exception:
             pass
+
+
+OP_TPT, OP_TPC, OP_MMC = 0, 1, 2
+PC_NONE, PC_DIAG, PC_BLOCK = 0, 1, 2
+
+
+def sem_apply_condensed_variant(ctx: SemContext, op: int, uB, vB, stream=None):
+    """vB = Hhat uB on the nodal skeleton with the paper's operator variant op
+    (OP_TPT, OP_TPC, OP_MMC)."""
+    _check(lib().sem_apply_condensed_variant(ctx.handle, int(op), _dptr(uB, ctx.nb, "uB"), _dptr(vB, ctx.nb, "vB"),
+                                             _stream(stream, uB)))
+
+
+def sem_diag_nodal(ctx: SemContext, diag, stream=None):
+    """Assembled diagonal of the nodal condensed operator."""
+    _check(lib().sem_diag_nodal(ctx.handle, _dptr(diag, ctx.nb, "diag"), _stream(stream, diag)))
+
+
+def sem_solve_variant(ctx: SemContext, op: int, pc: int, f, u, stream=None, check=True) -> dict:
+    """CG on the nodal condensed system with operator op and preconditioner pc
+    (PC_NONE, PC_DIAG, PC_BLOCK), then interior recovery into u."""
+    info = sem_info()
+    st = lib().sem_solve_variant(ctx.handle, int(op), int(pc), _dptr(f, ctx.n_nodes, "f"), _dptr(u, ctx.n_nodes, "u"),
+                                 ctypes.byref(info), _stream(stream, f))
+    if check:
+        _check(st)
+    return dict(status=st, iters=info.iters, rel_res=info.rel_res, t_solve_s=info.t_solve_s)
 
 
 def sem_refine_history(ctx: SemContext):
