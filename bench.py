@@ -317,6 +317,90 @@ def sweep_point(sem, w: si.Workload, seed: int, steps: int = 2) -> dict:
     return rec
 
 
+# The paper's solver timings (Table 5: one Xeon E5-2690 core, 8^3 elements,
+# expansion factor 2, i.e. aspect ratio 128, lambda = 0, residual reduced by
+# 1e12): iteration time per DOF (ns) and solve time per DOF (us).  Context for
+# the solver comparison below, measured on other hardware.
+PAPER_TABLE5 = {8: {"BT": (25.6, 4.25), "UC": (52.3, 154.0), "DC": (56.2, 15.3), "BC": (75.7, 12.6)},
+                16: {"BT": (17.7, 3.47)}}
+
+
+def _event_time(fn, reps: int) -> float:
+    """Seconds per call of fn (CUDA events, after one untimed call)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def operator_variants(sem, w: si.Workload, reps: int = 10) -> dict:
+    """One application of the condensed operator on the workload's mesh in
+    FP64 by each of the paper's variants (Sec. 5): TPT in the transformed
+    space (the operator of the BT solver), TPT between the nodal skeleton
+    transforms, TPC (Algorithm 3 with Table 1) and MMC (Algorithm 2, its
+    dense face matrices built first, timed separately)."""
+    import torch
+    hx, hy, hz = w.widths()
+    ctx = sem.sem_setup(w.p, hx, hy, hz, w.lam)
+    x = torch.tensor(si.random_vector(ctx.nb, 3000), device="cuda")
+    y = torch.empty_like(x)
+    out = {"workload": w.name, "unit": "us per application, FP64"}
+    out["tpt_transformed"] = _event_time(lambda: sem.sem_apply_condensed(ctx, x, y, sem.SPACE_TRANSFORMED), reps) * 1e6
+    t0 = time.perf_counter()
+    sem.sem_apply_condensed_variant(ctx, sem.OP_MMC, x, y)
+    torch.cuda.synchronize()
+    out["mmc_setup_s"] = time.perf_counter() - t0
+    for name, op in (("tpt_nodal", sem.OP_TPT), ("tpc", sem.OP_TPC), ("mmc", sem.OP_MMC)):
+        out[name] = _event_time(lambda: sem.sem_apply_condensed_variant(ctx, op, x, y), reps) * 1e6
+    del ctx, x, y
+    torch.cuda.empty_cache()
+    return out
+
+
+def paper_solvers(sem, p: int) -> dict:
+    """The solver comparison of Sec. 8 / Table 5 on the paper's own mesh: 8^3
+    elements graded in x and y to aspect ratio 128, lambda = 0, residual
+    reduced by 1e12 (seeded load, homogeneous Dirichlet data).  BT is this
+    library's solve (TPT operator, diagonal of the transformed operator);
+    UC, DC, BC use the TPC operator with no, the nodal diagonal and the
+    block-Jacobi preconditioner, FP64 throughout."""
+    import torch
+    hx, hy, hz, _ = si.graded_widths(8, 8, 8, ar=128.0, grade="xy")
+    ctx = sem.sem_setup(p, hx, hy, hz, 0.0, sem.default_opts(rtol=1e-12))
+    x, y, z = sem.sem_node_coords(ctx)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    f = torch.tensor((si.manufactured_f(X, Y, Z, 0.0) + si.node_noise(X.size, 3100 + p).reshape(X.shape)).ravel(),
+                     device="cuda")
+    u = torch.empty_like(f)
+    dofs = 512 * p ** 3
+    out = {"workload": f"paper_table5_p{p}_m8_xy128_lam0", "dofs": dofs, "rtol": 1e-12}
+    runs = {"BT": lambda: sem.sem_solve(ctx, f, u)}
+    for name, pc in (("UC", sem.PC_NONE), ("DC", sem.PC_DIAG), ("BC", sem.PC_BLOCK)):
+        runs[name] = (lambda pc=pc: sem.sem_solve_variant(ctx, sem.OP_TPC, pc, f, u))
+    for name, fn in runs.items():
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        rec = {"iters": info["iters"], "solve_ms": t * 1e3, "solve_us_per_dof": t / dofs * 1e6,
+               "iteration_ns_per_dof": t / max(info["iters"], 1) / dofs * 1e9}
+        if p in PAPER_TABLE5 and name in PAPER_TABLE5[p]:
+            rec["paper_xeon_core"] = {"iteration_ns_per_dof": PAPER_TABLE5[p][name][0],
+                                      "solve_us_per_dof": PAPER_TABLE5[p][name][1]}
+        out[name] = rec
+    del ctx
+    torch.cuda.empty_cache()
+    return out
+
+
 def apply_flops(w: si.Workload) -> float:
     """Algorithmic FP64 flops of one condensed-operator application: the
     multiplication counts of Table 3 (TPT: 13 n^3 + 68 n^2 per element), each
@@ -541,6 +625,10 @@ def our_arm(args, rank, world, local_rank):
     if world == 1 and args.workload == "scale" and not args.no_sweep:
         # every other point of the graded grid, measured in this run after the timed region
         out["sweep"] = [sweep_point(sem, sw, replica_seed(sw, rank)) for sw in sweep_workloads()]
+        # the paper's comparison operators (Sec. 5) and solvers (Sec. 8, Table 5)
+        if w.p <= 16:
+            out["operator_variants"] = operator_variants(sem, w)
+        out["paper_solvers"] = [paper_solvers(sem, pp) for pp in (8, 16)]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_iters = reference_iterations(w)
         iters = res["fp64"]["info"]["iters"] if "fp64" in res else r["info"]["iters"]

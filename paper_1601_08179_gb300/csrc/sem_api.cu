@@ -109,7 +109,11 @@ struct sem_ctx {
   PcgState* d_st32 = nullptr;
   MixedCtl* d_ctl = nullptr;           // device-side refinement control (graph-replayed mixed solves)
   MixedCtl h_ctl{};                    // host copy of it
-  cudaGraphExec_t graph32m = nullptr;  // one loop trip of the reliable-update mixed solve
+  cudaGraphExec_t graph32m = nullptr;  // one loop trip of the reliable-update mixed solve (or the whole loop)
+  int* d_trips = nullptr;              // trips of the device-side CG loops
+  bool graph_loop = false, graph32m_loop = false;   // the graph holds the whole loop (a while node)
+  long long graph_per_trip = 0, graph32m_per_trip = 0;
+  int graph_cap = 0, graph32m_cap = 0;
   int graph32m_iters = 0;
   bool graph32m_prof = false;
   long long graph32m_launches = 0;
@@ -325,8 +329,74 @@ sem_status cg_iter_f32(sem_ctx* c, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e
   return SEM_OK;
 }
 
+// One thread: another trip of a device-side CG loop while the solve's flag is
+// 0 (running) and fewer than cap trips have run.
+__global__ void k_loop_decide(const int* flag, int* trips, int cap, cudaGraphConditionalHandle handle) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int t = ++(*trips);
+  cudaGraphSetConditional(handle, (*flag == 0 && t < cap) ? 1u : 0u);
+}
+
+// Instantiates *exec from the launches `body` issues on the context stream.
+// loop = false: as they are (one replay runs one batch of CG iterations and
+// the host decides whether to replay).  loop = true: inside a while node whose
+// body ends with k_loop_decide on `flag`, so that one launch runs the whole CG
+// on the device; the caller zeroes d_trips before each launch.  *per_trip:
+// kernel launches of one pass of the body (counted when it runs).
+template <typename F>
+sem_status capture_cg(sem_ctx* c, bool loop, const int* flag, int cap, F body, cudaGraphExec_t* exec,
+                      long long* per_trip) {
+  cudaStream_t s = c->stream;
+  cudaGraph_t main_g = nullptr;
+  sem_status cst = SEM_OK;
+  cudaError_t e = cudaSuccess;
+  const long long before = sem_launch_total();
+  if (!loop) {
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cst = body(s);
+      const cudaError_t e2 = cudaStreamEndCapture(s, &main_g);
+      if (e == cudaSuccess) e = e2;
+    }
+  } else {
+    cudaGraphConditionalHandle handle;
+    e = cudaGraphCreate(&main_g, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, main_g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_loop;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&n_loop, main_g, nullptr, nullptr, 0, &cp);
+    if (e == cudaSuccess) {
+      e = cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cst = body(s);
+        k_loop_decide<<<1, 32, 0, s>>>(flag, c->d_trips, cap, handle);
+        sem_count_launch();
+        cudaGraph_t tmp = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(s, &tmp);
+        if (e == cudaSuccess) e = e2;
+      }
+    }
+  }
+  *per_trip = sem_launch_total() - before;
+  sem_count_launch(-*per_trip);   // counted at replay instead
+  if (e == cudaSuccess && cst == SEM_OK) e = cudaGraphInstantiate(exec, main_g, 0);
+  if (main_g) cudaGraphDestroy(main_g);
+  if (cst != SEM_OK) return cst;
+  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("CG graph: ") + cudaGetErrorString(e));
+  return SEM_OK;
+}
+
+// The FP64 CG's graph: check_every iterations; without profiling, inside a
+// device-side loop over such batches (one launch per solve).
 sem_status build_graph(sem_ctx* c) {
-  if (c->graph != nullptr && c->graph_iters == c->opts.check_every && c->graph_prof == c->prof) return SEM_OK;
+  const int cap = c->opts.maxit / c->opts.check_every + 2;
+  if (c->graph != nullptr && c->graph_iters == c->opts.check_every && c->graph_prof == c->prof && c->graph_cap == cap)
+    return SEM_OK;
   if (c->prof && (int)c->pev.size() < 2 * c->opts.check_every) {
     while ((int)c->pev.size() < 2 * c->opts.check_every) {
       cudaEvent_t ev;
@@ -339,26 +409,39 @@ sem_status build_graph(sem_ctx* c) {
     c->graph = nullptr;
   }
   const SemGeom& g = c->g;
-  cudaGraph_t graph;
-  SEM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  const long long before = sem_launch_total();
-  for (int it = 0; it < c->opts.check_every; ++it) {
-    // external event-record nodes: recorded at every replay, usable for timing
-    if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it], c->stream, cudaEventRecordExternal);
-    launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, c->stream,
-                             &c->op64);
-    if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it + 1], c->stream, cudaEventRecordExternal);
-    launch_pcg_update(g.nb, c->d_r, c->d_q, c->d_P, c->d_partials, c->d_st, c->stream);
-    launch_pcg_dir(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, c->stream);
-  }
-  sem_count_launch(-(sem_launch_total() - before));   // counted at replay instead
-  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&c->graph, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  const bool loop = !c->prof;
+  const int* flag = reinterpret_cast<const int*>(reinterpret_cast<const char*>(c->d_st) + offsetof(PcgState, done));
+  sem_status st = capture_cg(c, loop, flag, cap, [&](cudaStream_t s) -> sem_status {
+    for (int it = 0; it < c->opts.check_every; ++it) {
+      // external event-record nodes: recorded at every replay, usable for timing
+      if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it], s, cudaEventRecordExternal);
+      launch_tpt_apply<double>(g, c->h1.basis, c->tab, c->d_p, c->d_q, c->d_partials, c->d_st, s, &c->op64);
+      if (c->prof) cudaEventRecordWithFlags(c->pev[2 * it + 1], s, cudaEventRecordExternal);
+      launch_pcg_update(g.nb, c->d_r, c->d_q, c->d_P, c->d_partials, c->d_st, s);
+      launch_pcg_dir(g.nb, c->d_x, c->d_r, c->d_p, c->d_q, c->d_P, c->d_st, s);
+    }
+    return SEM_OK;
+  }, &c->graph, &c->graph_per_trip);
+  if (st != SEM_OK) return st;
   c->graph_iters = c->opts.check_every;
   c->graph_prof = c->prof;
+  c->graph_loop = loop;
+  c->graph_cap = cap;
+  return SEM_OK;
+}
+
+// One launch of a device-side CG loop: zero its trip counter, replay, read the
+// state record (and the trips, for the launch count).
+sem_status run_loop(sem_ctx* c, cudaGraphExec_t exec, long long per_trip, void* host_state, const void* dev_state,
+                    size_t state_bytes) {
+  cudaStream_t s = c->stream;
+  int trips = 0;
+  SEM_CUDA(cudaMemsetAsync(c->d_trips, 0, sizeof(int), s));
+  SEM_CUDA(cudaGraphLaunch(exec, s));
+  SEM_CUDA(cudaMemcpyAsync(host_state, dev_state, state_bytes, cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaMemcpyAsync(&trips, c->d_trips, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  sem_count_launch((long long)trips * per_trip);
   return SEM_OK;
 }
 
@@ -375,13 +458,18 @@ sem_status pcg_fp64(sem_ctx* c, bool warm, sem_info* info) {
   SEM_CUDA(cudaGetLastError());
   sem_status st = build_graph(c);
   if (st != SEM_OK) return st;
-  SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-  SEM_CUDA(cudaStreamSynchronize(s));
-  const int max_batches = c->opts.maxit / c->opts.check_every + 2;
+  if (c->graph_loop) {   // the whole CG in one launch, decided on the device
+    st = run_loop(c, c->graph, c->graph_per_trip, c->h_st, c->d_st, sizeof(PcgState));
+    if (st != SEM_OK) return st;
+  } else {
+    SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA(cudaStreamSynchronize(s));
+  }
+  const int max_batches = c->graph_loop ? 0 : c->opts.maxit / c->opts.check_every + 2;
   for (int b = 0; b < max_batches && c->h_st->done == 0; ++b) {
     const int it0 = c->h_st->iter;
     SEM_CUDA(cudaGraphLaunch(c->graph, s));
-    sem_count_launch(3LL * c->graph_iters);
+    sem_count_launch(c->graph_per_trip);
     SEM_CUDA(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
     SEM_CUDA(cudaStreamSynchronize(s));
     if (c->graph_prof) {
@@ -535,7 +623,9 @@ sem_status pcg_mixed(sem_ctx* c, bool warm, sem_info* info) {
 // (when due; every kernel gated on the device) and check_every FP32 CG
 // iterations, with event nodes around the FP32 operator when profiling.
 sem_status build_graph32m(sem_ctx* c) {
-  if (c->graph32m != nullptr && c->graph32m_iters == c->opts.check_every && c->graph32m_prof == c->prof)
+  const int cap = c->opts.maxit / c->opts.check_every + 2 + c->opts.max_refine;
+  if (c->graph32m != nullptr && c->graph32m_iters == c->opts.check_every && c->graph32m_prof == c->prof &&
+      c->graph32m_cap == cap)
     return SEM_OK;
   while (c->prof && (int)c->pev32.size() < 2 * c->opts.check_every) {
     cudaEvent_t ev;
@@ -547,27 +637,22 @@ sem_status build_graph32m(sem_ctx* c) {
     c->graph32m = nullptr;
   }
   const SemGeom& g = c->g;
-  cudaGraph_t graph;
-  SEM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  const long long before = sem_launch_total();
-  launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32, c->d_p32,
-                    c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, c->stream);
-  sem_status cst = SEM_OK;
-  for (int it = 0; it < c->opts.check_every && cst == SEM_OK; ++it)
-    cst = cg_iter_f32(c, c->stream, c->prof ? c->pev32[2 * it] : nullptr, c->prof ? c->pev32[2 * it + 1] : nullptr);
-  c->graph32m_launches = sem_launch_total() - before;
-  sem_count_launch(-c->graph32m_launches);
-  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-  if (cst != SEM_OK) {
-    if (e == cudaSuccess) cudaGraphDestroy(graph);
+  const bool loop = !c->prof;
+  const int* flag = reinterpret_cast<const int*>(reinterpret_cast<const char*>(c->d_ctl) + offsetof(MixedCtl, finished));
+  sem_status st = capture_cg(c, loop, flag, cap, [&](cudaStream_t s) -> sem_status {
+    launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32, c->d_p32,
+                      c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, s);
+    sem_status cst = SEM_OK;
+    for (int it = 0; it < c->opts.check_every && cst == SEM_OK; ++it)
+      cst = cg_iter_f32(c, s, c->prof ? c->pev32[2 * it] : nullptr, c->prof ? c->pev32[2 * it + 1] : nullptr);
     return cst;
-  }
-  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&c->graph32m, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }, &c->graph32m, &c->graph32m_per_trip);
+  if (st != SEM_OK) return st;
+  c->graph32m_launches = c->graph32m_per_trip;
   c->graph32m_iters = c->opts.check_every;
   c->graph32m_prof = c->prof;
+  c->graph32m_loop = loop;
+  c->graph32m_cap = cap;
   return SEM_OK;
 }
 
@@ -612,7 +697,11 @@ sem_status pcg_mixed_reliable(sem_ctx* c, bool warm, sem_info* info) {
   st = mixed_prologue(c, warm, s);
   if (st != SEM_OK) return st;
   MixedCtl* hc = &c->h_ctl;
-  const int cap = c->opts.maxit / c->opts.check_every + 2 + c->opts.max_refine;
+  if (c->graph32m_loop) {   // the whole refinement-and-CG loop in one launch, decided on the device
+    st = run_loop(c, c->graph32m, c->graph32m_per_trip, hc, c->d_ctl, sizeof(MixedCtl));
+    if (st != SEM_OK) return st;
+  }
+  const int cap = c->graph32m_loop ? 0 : c->opts.maxit / c->opts.check_every + 2 + c->opts.max_refine;
   int it0 = 0;
   for (int trip = 0; trip < cap; ++trip) {
     SEM_CUDA(cudaMemcpyAsync(hc, c->d_ctl, sizeof(MixedCtl), cudaMemcpyDeviceToHost, s));
@@ -676,6 +765,7 @@ void free_ctx(sem_ctx* c) {
   void* ptrs_adj[] = {c->d_h, c->d_K, c->d_full, c->d_E, c->d_grad};
   for (void* p : ptrs_adj)
     if (p) cudaFree(p);
+  if (c->d_trips) cudaFree(c->d_trips);
   void* ptrs[] = {c->d_cls, c->d_uw, c->d_dcoef, c->d_dinv, c->d_mats, c->d_mass, c->d_P, c->d_x, c->d_r,
                   c->d_p, c->d_q, c->d_b, c->d_t1, c->d_t2, c->d_c0, c->d_c1, c->d_FtI, c->d_partials, c->d_st};
   for (void* p : ptrs)
@@ -870,6 +960,7 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
             dalloc(&c->d_q, g.nb) == cudaSuccess && dalloc(&c->d_b, g.nb) == cudaSuccess &&
             dalloc(&c->d_t1, g.nb) == cudaSuccess && dalloc(&c->d_t2, g.nb) == cudaSuccess &&
             dalloc(&c->d_partials, kPartials) == cudaSuccess && dalloc(&c->d_st, 1) == cudaSuccess &&
+            dalloc(&c->d_trips, 1) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_st, sizeof(PcgState)) == cudaSuccess;
   if (!ok) {
     free_ctx(c);
