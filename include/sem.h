@@ -109,6 +109,14 @@ typedef struct {
                          recursive residual has fallen by this factor since the
                          previous step; 0 = automatic (default): 0.03 at p = 2,
                          0.01 otherwise (the fastest measured on GB300) */
+  int deterministic;  /* FP64 operator: 1 (default) = the edge and vertex outputs (shared
+                         by 4 and 8 elements) are summed in a fixed element order
+                         through per-element scratch of nelem (12 (p-1) + 8) doubles,
+                         allocated on first use, so FP64 solves (single or batched)
+                         give the same bits and iteration counts on every run;
+                         0 = atomic scatter-adds (arrival order).  Faces (two
+                         elements, added onto zero) are exact either way.  The FP32
+                         operators of MIXED solves always use atomics. */
 } sem_opts;
 
 /* Result of a solve. */

@@ -111,6 +111,7 @@ struct sem_ctx {
   MixedCtl h_ctl{};                    // host copy of it
   cudaGraphExec_t graph32m = nullptr;  // one loop trip of the reliable-update mixed solve (or the whole loop)
   int* d_trips = nullptr;              // trips of the device-side CG loops
+  double* d_ev = nullptr;              // per-element edge/vertex shares (opts.deterministic)
   bool graph_loop = false, graph32m_loop = false;   // the graph holds the whole loop (a while node)
   long long graph_per_trip = 0, graph32m_per_trip = 0;
   int graph_cap = 0, graph32m_cap = 0;
@@ -766,6 +767,7 @@ void free_ctx(sem_ctx* c) {
   for (void* p : ptrs_adj)
     if (p) cudaFree(p);
   if (c->d_trips) cudaFree(c->d_trips);
+  if (c->d_ev) cudaFree(c->d_ev);
   void* ptrs[] = {c->d_cls, c->d_uw, c->d_dcoef, c->d_dinv, c->d_mats, c->d_mass, c->d_P, c->d_x, c->d_r,
                   c->d_p, c->d_q, c->d_b, c->d_t1, c->d_t2, c->d_c0, c->d_c1, c->d_FtI, c->d_partials, c->d_st};
   for (void* p : ptrs)
@@ -843,6 +845,7 @@ void sem_default_opts(sem_opts* o) {
   o->max_refine = 40;
   o->mixed_scheme = 1;
   o->reliable_delta = 0.0;   // automatic (by degree)
+  o->deterministic = 1;
 }
 
 static sem_status check_opts(const sem_opts* o) {
@@ -855,6 +858,26 @@ static sem_status check_opts(const sem_opts* o) {
   if (o->mixed_scheme != 0 && o->mixed_scheme != 1) return fail(SEM_EINVAL, "mixed_scheme must be 0 or 1");
   if (!(o->reliable_delta == 0.0 || (o->reliable_delta > 0.0 && o->reliable_delta < 1.0)))
     return fail(SEM_EINVAL, "reliable_delta must be 0 (automatic) or in (0, 1)");
+  return SEM_OK;
+}
+
+namespace {
+void drop_graph(sem_ctx* c, bool mixed);
+}
+
+// With opts.deterministic the FP64 operator sums the edge and vertex outputs
+// in a fixed order through per-element scratch (allocated here on first use)
+// instead of atomics; its configuration carries the scratch pointer.
+static sem_status sync_deterministic(sem_ctx* c) {
+  if (c->opts.deterministic && c->d_ev == nullptr) {
+    const size_t count = (size_t)c->g.nelem * (12 * (size_t)c->g.n + 8);
+    if (cudaMalloc((void**)&c->d_ev, count * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_ev = nullptr;
+      return fail(SEM_ENOMEM, "cannot allocate the fixed-order edge/vertex scratch");
+    }
+  }
+  c->op64.ev = c->opts.deterministic ? c->d_ev : nullptr;
   return SEM_OK;
 }
 
@@ -989,6 +1012,7 @@ sem_status sem_setup(sem_ctx** out, int p, int mx, int my, int mz, const double*
   c->tab.coef_soa = c->d_coef_soa;
   c->tab.ncls = (int)ncls;
   sem_status st = compute_tables(c, s);
+  if (st == SEM_OK) st = sync_deterministic(c);
   if (st == SEM_OK) {
     // warm the operator kernel's attributes outside any graph capture
     st = apply_t(c, c->d_P, c->d_t2, s);
@@ -1026,8 +1050,13 @@ sem_status sem_set_opts(sem_ctx* c, const sem_opts* opts) {
   if (opts) o = *opts;
   sem_status vs = check_opts(&o);
   if (vs != SEM_OK) return vs;
+  const bool det_changed = (o.deterministic != 0) != (c->opts.deterministic != 0);
   c->opts = o;
-  return SEM_OK;
+  if (det_changed) {   // the captured FP64 operator launches change
+    drop_graph(c, false);
+    drop_graph(c, true);
+  }
+  return sync_deterministic(c);
 }
 
 sem_status sem_skeleton_size(const sem_ctx* c, long long* nb) {
@@ -1579,6 +1608,7 @@ extern "C" sem_status sem_autotune(sem_ctx* c, double* ms_default, double* ms_be
   }
   (mixed ? c->op32 : c->op64) = r.use_default ? ApplyConfig{} : r.cfg;
   drop_graph(c, mixed);
+  if (!mixed) sync_deterministic(c);
   if (ms_default) *ms_default = r.ms_default;
   if (ms_best) *ms_best = r.ms_best;
   return SEM_OK;
@@ -1601,7 +1631,7 @@ extern "C" sem_status sem_set_operator_kernel(sem_ctx* c, int precision, int kin
   }
   (mixed ? c->op32 : c->op64) = cfg;
   drop_graph(c, mixed);
-  return SEM_OK;
+  return mixed ? SEM_OK : sync_deterministic(c);
 }
 
 extern "C" sem_status sem_check_vector(const sem_ctx* c, const void* p, int elem_bytes) {

@@ -112,7 +112,7 @@ __global__ void k_class_coeffs(SemGeom g, SemBasis b, const double* __restrict__
 template <typename T, int NC>
 __global__ void __launch_bounds__(kThreads)
 k_tpt_apply(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v, int epb, int ks,
-            double* __restrict__ partials, PcgState* st) {
+            double* __restrict__ partials, PcgState* st, T* __restrict__ ev) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
   if (st != nullptr && st->done) return;
   const int n = NC > 0 ? NC : g.n;
@@ -399,7 +399,9 @@ k_tpt_apply(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __rest
       if (off < 0) continue;
       const T* E = elems + el * L.size;
       const T o = E[L.Eo + r];
-      atomicAdd(v + off + l, o);
+      // fixed-order mode: the element's share goes to its slot, summed by k_ev_sum
+      if (ev != nullptr) ev[(e0 + el) * (12LL * n + 8) + r] = o;
+      else atomicAdd(v + off + l, o);
       dot = fma(E[L.E + r], o, dot);
     }
     for (int t = tid; t < epb * 8; t += nt) {
@@ -408,7 +410,8 @@ k_tpt_apply(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __rest
       if (off < 0) continue;
       const T* E = elems + el * L.size;
       const T o = E[L.Vo + r];
-      atomicAdd(v + off, o);
+      if (ev != nullptr) ev[(e0 + el) * (12LL * n + 8) + 12 * n + r] = o;
+      else atomicAdd(v + off, o);
       dot = fma(E[L.Vt + r], o, dot);
     }
   }
@@ -710,7 +713,7 @@ constexpr int kThreadsP2 = 128;
 template <typename T>
 __global__ void __launch_bounds__(kThreadsP2, sizeof(T) == 8 ? 3 : 4)
 k_tpt_apply_p2(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __restrict__ v,
-               double* __restrict__ partials, PcgState* st) {
+               double* __restrict__ partials, PcgState* st, T* __restrict__ ev) {
   __shared__ EntityAffine ent[26];
   if (st != nullptr && st->done) return;
   if (threadIdx.x < 26) entity_affine(g, threadIdx.x, &ent[threadIdx.x]);
@@ -827,10 +830,18 @@ k_tpt_apply_p2(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __r
       if (off[r] >= 0) { atomicAdd(v + off[r], Fo[r]); dot = fma(F[r], Fo[r], dot); }
 #pragma unroll
     for (int r = 0; r < 12; ++r)
-      if (off[6 + r] >= 0) { atomicAdd(v + off[6 + r], Eo[r]); dot = fma(Ed[r], Eo[r], dot); }
+      if (off[6 + r] >= 0) {
+        if (ev != nullptr) ev[(long long)e * 20 + r] = Eo[r];   // fixed-order mode: summed by k_ev_sum
+        else atomicAdd(v + off[6 + r], Eo[r]);
+        dot = fma(Ed[r], Eo[r], dot);
+      }
 #pragma unroll
     for (int r = 0; r < 8; ++r)
-      if (off[18 + r] >= 0) { atomicAdd(v + off[18 + r], Vo[r]); dot = fma(Vt[r], Vo[r], dot); }
+      if (off[18 + r] >= 0) {
+        if (ev != nullptr) ev[(long long)e * 20 + 12 + r] = Vo[r];
+        else atomicAdd(v + off[18 + r], Vo[r]);
+        dot = fma(Vt[r], Vo[r], dot);
+      }
   }
   if (st != nullptr) {
     double vals[1] = {(double)dot}, tot[1];
@@ -854,14 +865,14 @@ __global__ void k_coef_soa(const T* __restrict__ coef, T* __restrict__ soa, int 
 
 template <typename T>
 void launch_p2(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, double* partials, PcgState* st,
-               cudaStream_t s) {
+               cudaStream_t s, T* ev = nullptr) {
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tpt_apply_p2<T>, kThreadsP2, 0);
   if (occ < 1) occ = 1;
   long long grid = (long long)num_sms_cached() * occ;
   const long long need = (g.nelem + kThreadsP2 - 1) / kThreadsP2;
   if (grid > need) grid = need;
-  k_tpt_apply_p2<T><<<(int)grid, kThreadsP2, 0, s>>>(g, t, x, y, partials, st);
+  k_tpt_apply_p2<T><<<(int)grid, kThreadsP2, 0, s>>>(g, t, x, y, partials, st, ev);
   sem_count_launch();
 }
 
@@ -892,7 +903,7 @@ void launch_warp(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y,
 
 template <typename T, int NC>
 void launch_nc(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, double* partials, PcgState* st,
-               const ApplyConfig& c, cudaStream_t s) {
+               const ApplyConfig& c, cudaStream_t s, T* ev = nullptr) {
   static bool attr = false;
   if (!attr) {   // once per instantiation; the first launch happens in sem_setup, outside any capture
     cudaFuncSetAttribute(k_tpt_apply<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -904,7 +915,7 @@ void launch_nc(const SemGeom& g, const SemClassTables<T>& t, const T* x, T* y, d
   const long long ntiles = (g.nelem + c.epb - 1) / c.epb;
   long long grid = (long long)num_sms_cached() * o;
   if (grid > ntiles) grid = ntiles;
-  k_tpt_apply<T, NC><<<(int)grid, c.threads, c.smem, s>>>(g, t, x, y, c.epb, c.ks, partials, st);
+  k_tpt_apply<T, NC><<<(int)grid, c.threads, c.smem, s>>>(g, t, x, y, c.epb, c.ks, partials, st, ev);
   sem_count_launch();
 }
 
@@ -975,6 +986,72 @@ bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
 // with the k-slab kernel; n = 1, and n = 2 in FP32, with one thread per
 // element (at n = 3 its 254 registers leave too few warps: 150 against the
 // plane kernel's 125 us at p = 4).
+// Position of element (ex, ey, ez) in the visiting order of elem_visit.
+__device__ __forceinline__ long long elem_visit_index(const SemGeom& g, int ex, int ey, int ez) {
+  if (g.slow == 0) return (long long)ex * g.my * g.mz + (long long)ez * g.my + ey;
+  if (g.slow == 1) return (long long)ey * g.mx * g.mz + (long long)ez * g.mx + ex;
+  return ex + (long long)g.mx * (ey + (long long)g.my * ez);
+}
+
+// Fixed-order assembly of the edge and vertex outputs (the R^T of Sec. 4 for
+// the entities shared by four and eight elements).  ev holds each element's
+// contributions, (12 n + 8) values per element (edge slot q at q n + l,
+// vertex slot r at 12 n + r), at the element's visit position (visit != 0)
+// or its x-fastest index.  Every entity off the Dirichlet boundary has all
+// its neighbours; it is summed by the one that sees it at its upper sides
+// (edge slots 3, 7, 11, vertex slot 7), in the order of the side bits, and
+// added to v: the result does not depend on the order the elements ran in.
+template <typename T>
+__global__ void k_ev_sum(SemGeom g, const T* __restrict__ ev, T* __restrict__ v, int visit) {
+  const int n = g.n, per = 3 * n + 1;
+  const long long stride = 12LL * n + 8;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.nelem * per;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / per;
+    const int r = (int)(t - e * per);
+    int ex, ey, ez;
+    elem_coords(g, e, &ex, &ey, &ez);
+    bool dir;
+    T sum = T(0);
+    if (r < 3 * n) {
+      const int grp = r / n, l = r - grp * n;
+      const long long off = edge_base(g, ex, ey, ez, 4 * grp + 3, &dir);
+      if (dir) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int s1 = q & 1, s2 = q >> 1;
+        int nx = ex, ny = ey, nz = ez;
+        if (grp == 0) { ny += 1 - s1; nz += 1 - s2; }
+        else if (grp == 1) { nx += 1 - s1; nz += 1 - s2; }
+        else { nx += 1 - s1; ny += 1 - s2; }
+        const long long ne = visit ? elem_visit_index(g, nx, ny, nz) : nx + (long long)g.mx * (ny + (long long)g.my * nz);
+        sum += ev[ne * stride + (4 * grp + q) * n + l];
+      }
+      v[off + l] += sum;
+    } else {
+      const long long off = vert_index(g, ex, ey, ez, 7, &dir);
+      if (dir) continue;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int nx = ex + 1 - (q & 1), ny = ey + 1 - ((q >> 1) & 1), nz = ez + 1 - (q >> 2);
+        const long long ne = visit ? elem_visit_index(g, nx, ny, nz) : nx + (long long)g.mx * (ny + (long long)g.my * nz);
+        sum += ev[ne * stride + 12 * n + q];
+      }
+      v[off] += sum;
+    }
+  }
+}
+
+template <typename T>
+void launch_ev_sum(const SemGeom& g, const T* ev, T* v, int visit, cudaStream_t s) {
+  const long long work = g.nelem * (3LL * g.n + 1);
+  long long blocks = (work + 255) / 256;
+  if (blocks > (long long)num_sms_cached() * 16) blocks = (long long)num_sms_cached() * 16;
+  if (blocks < 1) blocks = 1;
+  k_ev_sum<T><<<(int)blocks, 256, 0, s>>>(g, ev, v, visit);
+  sem_count_launch();
+}
+
 int sem_apply_default_kind(int n, size_t elem_bytes) {
   if (n == 1 || (elem_bytes == 4 && n == 2)) return kApplyElement;
   if (elem_bytes == 4 && plane_supported(n)) return kApplyPlane;
@@ -1014,6 +1091,17 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
       }
     }
   }
+  // fixed-order edge and vertex sums: the CTA tile (or, at n = 1, the
+  // element kernel) writes each element's shares to ev, k_ev_sum adds them
+  T* ev = cfg != nullptr ? static_cast<T*>(cfg->ev) : nullptr;
+  if (ev != nullptr) {
+    if (g.n == 1) {
+      launch_p2<T>(g, t, x, y, partials, st, s, ev);
+      launch_ev_sum<T>(g, ev, y, 0, s);
+      return;
+    }
+    kind = kApplyCta;
+  }
   if (kind == kApplyElement) {
     if constexpr (sizeof(T) == 4) {
       if (g.n != 1) {
@@ -1030,6 +1118,17 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
     }
   }
   const ApplyConfig c = (explicit_cfg && cfg->kind == kApplyCta) ? *cfg : sem_apply_config(g.n, sizeof(T));
+  if (ev != nullptr) {
+    switch (g.n) {
+      case 3: launch_nc<T, 3>(g, t, x, y, partials, st, c, s, ev); break;
+      case 7: launch_nc<T, 7>(g, t, x, y, partials, st, c, s, ev); break;
+      case 15: launch_nc<T, 15>(g, t, x, y, partials, st, c, s, ev); break;
+      case 31: launch_nc<T, 31>(g, t, x, y, partials, st, c, s, ev); break;
+      default: launch_nc<T, 0>(g, t, x, y, partials, st, c, s, ev); break;
+    }
+    launch_ev_sum<T>(g, ev, y, 1, s);
+    return;
+  }
   switch (g.n) {
     case 1: launch_nc<T, 1>(g, t, x, y, partials, st, c, s); break;
     case 3: launch_nc<T, 3>(g, t, x, y, partials, st, c, s); break;

@@ -266,34 +266,52 @@ __global__ void k_mode(SemGeom g, const double* __restrict__ A, int axis, const 
 }
 
 // fhat~ faces -= d k_side . (D^-1 Ft_I) along the line into the interior.
+// One thread per face point: the shares of the two elements of the face are
+// added in a fixed order (lower element first), so the condensed load does
+// not depend on the order threads run in.
 __global__ void k_condense_faces(SemGeom g, SemBasis b, SemClassTables<double> tab, const double* __restrict__ FtI,
                                  double* __restrict__ out) {
-  const int n = g.n, n2 = n * n;
+  const int n = g.n, n2 = n * n, mx = g.mx, my = g.my, mz = g.mz;
   const long long n3 = (long long)n2 * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.nelem * 6 * n2; t += (long long)gridDim.x * blockDim.x) {
-    const long long e = t / (6 * n2);
-    const int r = (int)(t - e * 6 * n2);
-    const int slot = r / n2, idx = r - slot * n2, dd = slot >> 1, s = slot & 1;
-    const int slow = idx / n, fast = idx - slow * n;
-    int ex, ey, ez;
-    elem_coords(g, e, &ex, &ey, &ez);
-    bool dir;
-    const long long gi = face_base(g, ex, ey, ez, slot, &dir) + idx;
+  const long long nf0 = (long long)(mx + 1) * my * mz, nf1 = (long long)mx * (my + 1) * mz;
+  const long long nf2 = (long long)mx * my * (mz + 1);
+  const long long total = (nf0 + nf1 + nf2) * n2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    long long f = t / n2;
+    const int idx = (int)(t - f * n2);
+    int dd;
+    if (f < nf0) dd = 0;
+    else if (f < nf0 + nf1) { dd = 1; f -= nf0; }
+    else { dd = 2; f -= nf0 + nf1; }
+    int ex, ey, ez, pos, lim;   // pos: face position along dd (elements pos - 1 and pos)
+    if (dd == 0) { pos = (int)(f % (mx + 1)); const long long q = f / (mx + 1); ey = (int)(q % my); ez = (int)(q / my); ex = pos; lim = mx; }
+    else if (dd == 1) { ex = (int)(f % mx); const long long q = f / mx; pos = (int)(q % (my + 1)); ez = (int)(q / (my + 1)); ey = pos; lim = my; }
+    else { ex = (int)(f % mx); const long long q = f / mx; ey = (int)(q % my); pos = (int)(q / my); ez = pos; lim = mz; }
+    if (pos == 0 || pos == lim) continue;   // Dirichlet face
+    bool dir = false;
+    const long long gi = sem_dbg_entity(g.off[dd] + f * n2, n2, g, &dir) + idx;
     if (dir) continue;
-    const int c = elem_class(g, tab, ex, ey, ez);
-    const double* Dinv = tab.dinv + (long long)c * n3;
-    const double* X = FtI + e * n3;
-    const double* ks = b.k[s];
-    double acc = 0.0;
+    const int slow = idx / n, fast = idx - slow * n;
     long long off0, stride;
     if (dd == 0) { off0 = (long long)(slow * n + fast) * n; stride = 1; }
     else if (dd == 1) { off0 = (long long)slow * n2 + fast; stride = n; }
     else { off0 = (long long)slow * n + fast; stride = n2; }
-    for (int m = 0; m < n; ++m) {
-      const long long q = off0 + m * stride;
-      acc = fma(ks[m], Dinv[q] * X[q], acc);
+    double sum = out[gi];
+    for (int s = 1; s >= 0; --s) {   // the lower element sees the face at its side 1
+      const int lx = ex - (dd == 0 ? s : 0), ly = ey - (dd == 1 ? s : 0), lz = ez - (dd == 2 ? s : 0);
+      const long long e = lx + (long long)mx * (ly + (long long)my * lz);
+      const int c = elem_class(g, tab, lx, ly, lz);
+      const double* Dinv = tab.dinv + (long long)c * n3;
+      const double* X = FtI + e * n3;
+      const double* ks = b.k[s];
+      double acc = 0.0;
+      for (int m = 0; m < n; ++m) {
+        const long long q = off0 + m * stride;
+        acc = fma(ks[m], Dinv[q] * X[q], acc);
+      }
+      sum += -tab.dcoef[c * 4 + 1 + dd] * acc;
     }
-    atomicAdd(out + gi, -tab.dcoef[c * 4 + 1 + dd] * acc);
+    out[gi] = sum;
   }
 }
 
@@ -749,7 +767,9 @@ void launch_mode(const SemGeom& g, const double* A, int axis, const double* in, 
 
 void launch_condense_faces(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,
                            const double* FtI, double* out, cudaStream_t s) {
-  const long long work = g.nelem * 6LL * g.n * g.n;
+  const long long faces = (long long)(g.mx + 1) * g.my * g.mz + (long long)g.mx * (g.my + 1) * g.mz +
+                          (long long)g.mx * g.my * (g.mz + 1);
+  const long long work = faces * g.n * g.n;
   k_condense_faces<<<grid_for(work, 256, 16), 256, 0, s>>>(g, b, t, FtI, out);
   sem_count_launch();
 }

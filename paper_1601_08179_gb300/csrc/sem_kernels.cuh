@@ -23,6 +23,9 @@ struct ApplyConfig {
   int ks = 0;       // CTA tile: eigenspace slab depth (k planes held at once)
   int threads = 0;
   size_t smem = 0;  // CTA tile: dynamic shared memory bytes
+  // Fixed-order edge and vertex sums (bitwise reproducible output): scratch of
+  // nelem (12 n + 8) values of the operator's type, or null for atomics.
+  void* ev = nullptr;
 };
 // Built-in CTA-tile shape for n.
 ApplyConfig sem_apply_config(int n, size_t elem_bytes);

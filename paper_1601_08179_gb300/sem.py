@@ -36,7 +36,7 @@ class SemError(RuntimeError):
 class sem_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double)]
+                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double), ("deterministic", ctypes.c_int)]
 
 
 class sem_info(ctypes.Structure):

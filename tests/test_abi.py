@@ -90,6 +90,21 @@ def test_default_opts(L):
     o = sem.default_opts()
     assert o.rtol == 1e-10 and o.precision == sem.PREC_FP64 and o.check_every > 0
     assert o.reliable_delta == 0.0   # automatic, by degree
+    assert o.deterministic == 1      # fixed-order edge and vertex sums in the FP64 operator
+
+
+def test_opts_struct_matches_the_header():
+    """The binding's sem_opts mirrors include/sem.h field for field (a
+    mismatch would shift every later field)."""
+    import os
+    import re
+    from paper_1601_08179_gb300 import sem
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "sem.h")).read()
+    body = hdr[hdr.index("/* Solver options."):hdr.index("} sem_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(double|int)\s+(\w+);", body)
+    assert [(n, t) for t, n in fields] == [(n, {ctypes.c_double: "double", ctypes.c_int: "int"}[t])
+                                           for n, t in sem.sem_opts._fields_]
 
 
 def test_debug_build_compiles_and_exports_the_same_entry_points():
