@@ -117,6 +117,14 @@ typedef struct {
                          0 = atomic scatter-adds (arrival order).  Faces (two
                          elements, added onto zero) are exact either way.  The FP32
                          operators of MIXED solves always use atomics. */
+  int onepass_step;   /* MIXED single solves: 1 (default) = the FP32 CG's update and
+                         direction are one kernel that reads r, q, P, x, p and writes
+                         r, x, p, q once per iteration (a grid barrier between the two
+                         halves; cooperative launch, one CTA per SM, the barrier's
+                         wait bounded); 0 = two kernels (r, P read twice).  Batched
+                         solves always take two kernels.  Where the device or the
+                         graph cannot take the cooperative launch the solve falls
+                         back to two kernels by itself. */
 } sem_opts;
 
 /* Result of a solve. */
@@ -345,6 +353,15 @@ sem_status sem_check_vector(const sem_ctx* ctx, const void* p, int elem_bytes);
  * the real vectors.  Both return SEM_ENOTSUP in release builds. */
 sem_status sem_debug_oob(long long* count, long long* first);
 sem_status sem_debug_limit_skeleton(sem_ctx* ctx, long long bound);
+/* Failure check of the one-pass CG step's grid barrier (debug builds): runs
+ * one step of the FP32 CG on zeroed vectors with the barrier's arrival count
+ * preset past the grid size, so that no CTA ever completes the barrier; each
+ * CTA's bounded wait (about a second) runs out, and the step stops the CG.
+ * Returns the step's record: *bar_fail (1 when a wait ran out) and *done (2:
+ * stopped as a breakdown).  The context stays usable (its FP32 CG record is
+ * cleared afterwards).  SEM_ENOTSUP in release builds or where the device
+ * cannot take the cooperative launch. */
+sem_status sem_debug_cg_step_timeout(sem_ctx* ctx, int* bar_fail, int* done);
 /* Autotuner: times the operator kernel for this context's degree, mesh and
  * precision (FP32 when opts.precision is MIXED, else FP64) over the variants
  * that exist for it and a set of CTA-tile shapes (elements per CTA,

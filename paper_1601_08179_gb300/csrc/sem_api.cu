@@ -112,6 +112,8 @@ struct sem_ctx {
   cudaGraphExec_t graph32m = nullptr;  // one loop trip of the reliable-update mixed solve (or the whole loop)
   int* d_trips = nullptr;              // trips of the device-side CG loops
   double* d_ev = nullptr;              // per-element edge/vertex shares (opts.deterministic)
+  bool step_ok = false;                // the device runs the one-pass FP32 CG step (cooperative launch)
+  bool step_failed = false;            // a graph with it could not be built: two-pass step from then on
   bool graph_loop = false, graph32m_loop = false;   // the graph holds the whole loop (a while node)
   long long graph_per_trip = 0, graph32m_per_trip = 0;
   int graph_cap = 0, graph32m_cap = 0;
@@ -255,6 +257,7 @@ sem_status ensure_mixed(sem_ctx* c) {
   SEM_CUDA(cudaMemsetAsync(c->d_q32, 0, sizeof(float) * g.nb, c->stream));
   launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_P32, c->d_q32, nullptr, nullptr, c->stream);
   SEM_CUDA(cudaGetLastError());
+  SEM_CUDA(prepare_pcg_step<float>(g.nb, &c->step_ok));
   return SEM_OK;
 }
 
@@ -317,14 +320,23 @@ sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
   return SEM_OK;
 }
 
-// One FP32 CG iteration on the context's FP32 vectors (st32): operator,
-// update, direction; e0/e1 (may be null) become event nodes around the
-// operator.
-sem_status cg_iter_f32(sem_ctx* c, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+// Whether the FP32 CG of a single solve takes the one-pass step.
+bool use_step(const sem_ctx* c) { return c->opts.onepass_step != 0 && c->step_ok && !c->step_failed; }
+
+// One FP32 CG iteration on the context's FP32 vectors (st32): operator, then
+// update and direction, as one pass with a grid barrier (onepass) or as two
+// kernels; e0/e1 (may be null) become event nodes around the operator.
+sem_status cg_iter_f32(sem_ctx* c, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, bool onepass) {
   const SemGeom& g = c->g;
   if (e0) cudaEventRecordWithFlags(e0, s, cudaEventRecordExternal);
   launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_p32, c->d_q32, c->d_partials, c->d_st32, s, &c->op32);
   if (e1) cudaEventRecordWithFlags(e1, s, cudaEventRecordExternal);
+  if (onepass) {
+    const cudaError_t e = launch_pcg_step<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials,
+                                                 c->d_st32, s);
+    if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("one-pass CG step: ") + cudaGetErrorString(e));
+    return SEM_OK;
+  }
   launch_pcg_update<float>(g.nb, c->d_r32, c->d_q32, c->d_P32, c->d_partials, c->d_st32, s);
   launch_pcg_dir<float>(g.nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_st32, s);
   return SEM_OK;
@@ -508,24 +520,33 @@ sem_status build_graph32(sem_ctx* c) {
     cudaGraphExecDestroy(c->graph32);
     c->graph32 = nullptr;
   }
-  const SemGeom& g = c->g;
-  cudaGraph_t graph;
-  SEM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  const long long before = sem_launch_total();
-  sem_status cst = SEM_OK;
-  for (int it = 0; it < c->opts.check_every && cst == SEM_OK; ++it)
-    cst = cg_iter_f32(c, c->stream, c->prof ? c->pev32[2 * it] : nullptr, c->prof ? c->pev32[2 * it + 1] : nullptr);
-  c->graph32_launches = sem_launch_total() - before;
-  sem_count_launch(-c->graph32_launches);
-  cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-  if (cst != SEM_OK) {
-    if (e == cudaSuccess) cudaGraphDestroy(graph);
-    return cst;
+  for (int attempt = 0;; ++attempt) {
+    const bool onepass = use_step(c);
+    cudaGraph_t graph;
+    SEM_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const long long before = sem_launch_total();
+    sem_status cst = SEM_OK;
+    for (int it = 0; it < c->opts.check_every && cst == SEM_OK; ++it)
+      cst = cg_iter_f32(c, c->stream, c->prof ? c->pev32[2 * it] : nullptr, c->prof ? c->pev32[2 * it + 1] : nullptr,
+                        onepass);
+    c->graph32_launches = sem_launch_total() - before;
+    sem_count_launch(-c->graph32_launches);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (e == cudaSuccess && cst == SEM_OK) {
+      e = cudaGraphInstantiate(&c->graph32, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e == cudaSuccess) break;
+    } else if (e == cudaSuccess) {
+      cudaGraphDestroy(graph);
+    }
+    if (onepass && attempt == 0) {   // a graph with the one-pass step could not be built: two passes
+      cudaGetLastError();
+      c->step_failed = true;
+      continue;
+    }
+    if (cst != SEM_OK) return cst;
+    return fail(SEM_ECUDA, std::string("FP32 CG graph: ") + cudaGetErrorString(e));
   }
-  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&c->graph32, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return fail(SEM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   c->graph32_iters = c->opts.check_every;
   c->graph32_prof = c->prof;
   return SEM_OK;
@@ -640,14 +661,22 @@ sem_status build_graph32m(sem_ctx* c) {
   const SemGeom& g = c->g;
   const bool loop = !c->prof;
   const int* flag = reinterpret_cast<const int*>(reinterpret_cast<const char*>(c->d_ctl) + offsetof(MixedCtl, finished));
-  sem_status st = capture_cg(c, loop, flag, cap, [&](cudaStream_t s) -> sem_status {
-    launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32, c->d_p32,
-                      c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, s);
-    sem_status cst = SEM_OK;
-    for (int it = 0; it < c->opts.check_every && cst == SEM_OK; ++it)
-      cst = cg_iter_f32(c, s, c->prof ? c->pev32[2 * it] : nullptr, c->prof ? c->pev32[2 * it + 1] : nullptr);
-    return cst;
-  }, &c->graph32m, &c->graph32m_per_trip);
+  sem_status st = SEM_OK;
+  for (int attempt = 0;; ++attempt) {
+    const bool onepass = use_step(c);
+    st = capture_cg(c, loop, flag, cap, [&](cudaStream_t s) -> sem_status {
+      launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32,
+                        c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, s);
+      sem_status cst = SEM_OK;
+      for (int it = 0; it < c->opts.check_every && cst == SEM_OK; ++it)
+        cst = cg_iter_f32(c, s, c->prof ? c->pev32[2 * it] : nullptr, c->prof ? c->pev32[2 * it + 1] : nullptr,
+                          onepass);
+      return cst;
+    }, &c->graph32m, &c->graph32m_per_trip);
+    if (st == SEM_OK || !onepass || attempt > 0) break;
+    cudaGetLastError();   // a graph with the one-pass step could not be built: two passes
+    c->step_failed = true;
+  }
   if (st != SEM_OK) return st;
   c->graph32m_launches = c->graph32m_per_trip;
   c->graph32m_iters = c->opts.check_every;
@@ -846,6 +875,7 @@ void sem_default_opts(sem_opts* o) {
   o->mixed_scheme = 1;
   o->reliable_delta = 0.0;   // automatic (by degree)
   o->deterministic = 1;
+  o->onepass_step = 1;
 }
 
 static sem_status check_opts(const sem_opts* o) {
@@ -858,6 +888,8 @@ static sem_status check_opts(const sem_opts* o) {
   if (o->mixed_scheme != 0 && o->mixed_scheme != 1) return fail(SEM_EINVAL, "mixed_scheme must be 0 or 1");
   if (!(o->reliable_delta == 0.0 || (o->reliable_delta > 0.0 && o->reliable_delta < 1.0)))
     return fail(SEM_EINVAL, "reliable_delta must be 0 (automatic) or in (0, 1)");
+  if (o->deterministic != 0 && o->deterministic != 1) return fail(SEM_EINVAL, "deterministic must be 0 or 1");
+  if (o->onepass_step != 0 && o->onepass_step != 1) return fail(SEM_EINVAL, "onepass_step must be 0 or 1");
   return SEM_OK;
 }
 
@@ -1050,9 +1082,10 @@ sem_status sem_set_opts(sem_ctx* c, const sem_opts* opts) {
   if (opts) o = *opts;
   sem_status vs = check_opts(&o);
   if (vs != SEM_OK) return vs;
-  const bool det_changed = (o.deterministic != 0) != (c->opts.deterministic != 0);
+  const bool det_changed = (o.deterministic != 0) != (c->opts.deterministic != 0) ||
+                           (o.onepass_step != 0) != (c->opts.onepass_step != 0);
   c->opts = o;
-  if (det_changed) {   // the captured FP64 operator launches change
+  if (det_changed) {   // the captured operator or CG-step launches change
     drop_graph(c, false);
     drop_graph(c, true);
   }
@@ -1676,6 +1709,41 @@ extern "C" sem_status sem_debug_limit_skeleton(sem_ctx* c, long long bound) {
 #endif
 }
 
+extern "C" sem_status sem_debug_cg_step_timeout(sem_ctx* c, int* bar_fail, int* done) {
+  t_err.clear();
+  if (check_ctx(c) != SEM_OK) return SEM_EINVAL;
+  if (bar_fail == nullptr || done == nullptr) return fail(SEM_EINVAL, "null argument");
+#ifdef SEM_DEBUG
+  sem_status st = ensure_mixed(c);
+  if (st != SEM_OK) return st;
+  if (!c->step_ok) return fail(SEM_ENOTSUP, "the device cannot run the one-pass CG step");
+  const long long nb = c->g.nb;
+  cudaStream_t s = c->stream;
+  float* vecs[] = {c->d_x32, c->d_r32, c->d_p32, c->d_q32};
+  for (float* v : vecs) SEM_CUDA(cudaMemsetAsync(v, 0, sizeof(float) * nb, s));
+  // a running CG whose barrier count already holds every arrival it will get:
+  // no CTA is the last to arrive, so every wait runs out
+  PcgState h{};
+  h.rho = 1.0;
+  h.tol2 = 0.0;
+  h.maxit = 1 << 30;
+  h.bar_count = 2u * (unsigned)sem_num_sms();
+  SEM_CUDA(cudaMemcpyAsync(c->d_st32, &h, sizeof(PcgState), cudaMemcpyHostToDevice, s));
+  SEM_CUDA(launch_pcg_step<float>(nb, c->d_x32, c->d_r32, c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_st32, s));
+  SEM_CUDA(cudaMemcpyAsync(&h, c->d_st32, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA(cudaStreamSynchronize(s));
+  *bar_fail = h.bar_fail;
+  *done = h.done;
+  SEM_CUDA(cudaMemsetAsync(c->d_st32, 0, sizeof(PcgState), s));   // a later solve starts from a clean record
+  SEM_CUDA(cudaStreamSynchronize(s));
+  return SEM_OK;
+#else
+  *bar_fail = 0;
+  *done = 0;
+  return fail(SEM_ENOTSUP, "the barrier test is compiled in debug builds only (SEM_DEBUG)");
+#endif
+}
+
 extern "C" sem_status sem_get_operator_kernel(const sem_ctx* c, int precision, int* kind, int* epb, int* ks) {
   t_err.clear();
   if (c == nullptr || kind == nullptr) return fail(SEM_EINVAL, "null argument");
@@ -1893,7 +1961,8 @@ extern "C" sem_status sem_batch_create(sem_ctx* const* ctxs, int count, const do
         launch_mixed_step(g, c->h1.basis, c->tab, &c->op64, c->d_b, c->d_x, c->d_q, c->d_r, c->d_x32, c->d_r32,
                           c->d_p32, c->d_q32, c->d_P32, c->d_partials, c->d_ctl, c->d_st32, c->d_stg, si);
         for (int it = 0; it < check; ++it) {
-          const sem_status st = cg_iter_f32(c, si, nullptr, nullptr);
+          // batched problems run concurrently: the two-pass step (no grid barrier)
+          const sem_status st = cg_iter_f32(c, si, nullptr, nullptr, false);
           if (st != SEM_OK) return st;
         }
         return SEM_OK;

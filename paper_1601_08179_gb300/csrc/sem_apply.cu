@@ -831,14 +831,14 @@ k_tpt_apply_p2(SemGeom g, SemClassTables<T> tab, const T* __restrict__ u, T* __r
 #pragma unroll
     for (int r = 0; r < 12; ++r)
       if (off[6 + r] >= 0) {
-        if (ev != nullptr) ev[(long long)e * 20 + r] = Eo[r];   // fixed-order mode: summed by k_ev_sum
+        if (ev != nullptr) ev[(long long)r * g.nelem + e] = Eo[r];   // fixed-order mode: summed by k_ev_sum
         else atomicAdd(v + off[6 + r], Eo[r]);
         dot = fma(Ed[r], Eo[r], dot);
       }
 #pragma unroll
     for (int r = 0; r < 8; ++r)
       if (off[18 + r] >= 0) {
-        if (ev != nullptr) ev[(long long)e * 20 + 12 + r] = Vo[r];
+        if (ev != nullptr) ev[(12LL + r) * g.nelem + e] = Vo[r];
         else atomicAdd(v + off[18 + r], Vo[r]);
         dot = fma(Vt[r], Vo[r], dot);
       }
@@ -995,22 +995,29 @@ __device__ __forceinline__ long long elem_visit_index(const SemGeom& g, int ex, 
 
 // Fixed-order assembly of the edge and vertex outputs (the R^T of Sec. 4 for
 // the entities shared by four and eight elements).  ev holds each element's
-// contributions, (12 n + 8) values per element (edge slot q at q n + l,
-// vertex slot r at 12 n + r), at the element's visit position (visit != 0)
-// or its x-fastest index.  Every entity off the Dirichlet boundary has all
+// contributions, (12 n + 8) values per element (edge slot q at position
+// q n + l, vertex slot r at 12 n + r): visit != 0, element-major at the
+// element's visit position (the CTA tile writes an element's values
+// together); visit == 0, position-major over the x-fastest element index (the
+// one-thread-per-element kernel writes coalesced).  Every entity off the
+// Dirichlet boundary has all
 // its neighbours; it is summed by the one that sees it at its upper sides
 // (edge slots 3, 7, 11, vertex slot 7), in the order of the side bits, and
 // added to v: the result does not depend on the order the elements ran in.
 template <typename T>
 __global__ void k_ev_sum(SemGeom g, const T* __restrict__ ev, T* __restrict__ v, int visit) {
-  const int n = g.n, per = 3 * n + 1;
-  const long long stride = 12LL * n + 8;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.nelem * per;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long e = t / per;
-    const int r = (int)(t - e * per);
-    int ex, ey, ez;
-    elem_coords(g, e, &ex, &ey, &ez);
+  // 32-bit index arithmetic (nelem (3 n + 1) < 2^31 whenever N_B is); the
+  // thread order follows the layout so that neighbouring threads read
+  // neighbouring values: position fastest for the element-major layout,
+  // element fastest for the position-major one
+  const int n = g.n, per = 3 * n + 1, ne_all = (int)g.nelem, mx = g.mx, my = g.my;
+  const int stride = 12 * n + 8;
+  const int total = ne_all * per;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int e, r;
+    if (visit) { e = t / per; r = t - e * per; }
+    else { r = t / ne_all; e = t - r * ne_all; }
+    const int ez = e / (mx * my), rem = e - ez * (mx * my), ey = rem / mx, ex = rem - ey * mx;
     bool dir;
     T sum = T(0);
     if (r < 3 * n) {
@@ -1024,8 +1031,9 @@ __global__ void k_ev_sum(SemGeom g, const T* __restrict__ ev, T* __restrict__ v,
         if (grp == 0) { ny += 1 - s1; nz += 1 - s2; }
         else if (grp == 1) { nx += 1 - s1; nz += 1 - s2; }
         else { nx += 1 - s1; ny += 1 - s2; }
-        const long long ne = visit ? elem_visit_index(g, nx, ny, nz) : nx + (long long)g.mx * (ny + (long long)g.my * nz);
-        sum += ev[ne * stride + (4 * grp + q) * n + l];
+        const int pos = (4 * grp + q) * n + l;
+        sum += visit ? ev[elem_visit_index(g, nx, ny, nz) * stride + pos]
+                     : ev[(long long)pos * ne_all + nx + mx * (ny + my * nz)];
       }
       v[off + l] += sum;
     } else {
@@ -1034,8 +1042,9 @@ __global__ void k_ev_sum(SemGeom g, const T* __restrict__ ev, T* __restrict__ v,
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int nx = ex + 1 - (q & 1), ny = ey + 1 - ((q >> 1) & 1), nz = ez + 1 - (q >> 2);
-        const long long ne = visit ? elem_visit_index(g, nx, ny, nz) : nx + (long long)g.mx * (ny + (long long)g.my * nz);
-        sum += ev[ne * stride + 12 * n + q];
+        const int pos = 12 * n + q;
+        sum += visit ? ev[elem_visit_index(g, nx, ny, nz) * stride + pos]
+                     : ev[(long long)pos * ne_all + nx + mx * (ny + my * nz)];
       }
       v[off] += sum;
     }

@@ -144,6 +144,10 @@ struct PcgState {
   int xpend;                // 1: the last x += alpha p is still owed (the update stopped the CG)
   unsigned int flush_ticket;
   int pad2;
+  unsigned int bar_count;   // grid barrier of the one-pass CG step: arrivals, generation
+  unsigned int bar_gen;
+  int bar_fail;             // 1: a barrier wait ran out (the CG stopped with done = 2)
+  int pad3;
 };
 
 // Device-side control of one mixed-precision solve (FP32 CG with reliable

@@ -103,19 +103,42 @@ __global__ void k_precond_diag(SemGeom g, SemBasis b, SemClassTables<double> tab
         val = d[0] * w0 + d[3] * b.K[s][s] + w0 * (d[1] * b.lam[fast] + d[2] * b.lam[slow]) - d[3] * d[3] * cond;
       }
     } else if (r < 6 * n2 + 12 * n) {
+      // an edge is shared by four elements: the one that sees it at its upper
+      // sides (slot 4 grp + 3) sums all four shares in a fixed order
       const int q = r - 6 * n2, slot = q / n, l = q - slot * n;
-      const int grp = slot >> 2, s1 = slot & 1, s2 = (slot >> 1) & 1;
+      if ((slot & 3) != 3) continue;
+      const int grp = slot >> 2;
       gi = edge_base(g, ex, ey, ez, slot, &dir) + l;
+      if (dir) continue;
       // along-edge direction gets d w0^2 Lambda; the two transverse directions d w0 K_ss
       const int da = grp, t1 = grp == 0 ? 1 : 0, t2 = grp == 2 ? 1 : 2;
-      val = d[0] * w0 * w0 + d[da + 1] * w0 * w0 * b.lam[l] + d[t1 + 1] * w0 * b.K[s1][s1] +
-            d[t2 + 1] * w0 * b.K[s2][s2];
+      val = 0.0;
+      for (int nq = 0; nq < 4; ++nq) {
+        const int s1 = nq & 1, s2 = nq >> 1;
+        int nx = ex, ny = ey, nz = ez;
+        if (grp == 0) { ny += 1 - s1; nz += 1 - s2; }
+        else if (grp == 1) { nx += 1 - s1; nz += 1 - s2; }
+        else { nx += 1 - s1; ny += 1 - s2; }
+        const double* dn = tab.dcoef + elem_class(g, tab, nx, ny, nz) * 4;
+        val += dn[0] * w0 * w0 + dn[da + 1] * w0 * w0 * b.lam[l] + dn[t1 + 1] * w0 * b.K[s1][s1] +
+               dn[t2 + 1] * w0 * b.K[s2][s2];
+      }
     } else {
+      // a vertex is shared by eight elements: summed by the one that sees it
+      // as its slot 7, in a fixed order
       const int slot = r - 6 * n2 - 12 * n;
-      const int sa = slot & 1, sb = (slot >> 1) & 1, sc = slot >> 2;
+      if (slot != 7) continue;
       gi = vert_index(g, ex, ey, ez, slot, &dir);
-      val = d[0] * w0 * w0 * w0 + w0 * w0 * (d[1] * b.K[sa][sa] + d[2] * b.K[sb][sb] + d[3] * b.K[sc][sc]);
+      if (dir) continue;
+      val = 0.0;
+      for (int nq = 0; nq < 8; ++nq) {
+        const int sa = nq & 1, sb = (nq >> 1) & 1, sc = nq >> 2;
+        const double* dn = tab.dcoef + elem_class(g, tab, ex + 1 - sa, ey + 1 - sb, ez + 1 - sc) * 4;
+        val += dn[0] * w0 * w0 * w0 + w0 * w0 * (dn[1] * b.K[sa][sa] + dn[2] * b.K[sb][sb] + dn[3] * b.K[sc][sc]);
+      }
     }
+    // faces: two shares added onto zero (exact in either order); edges and
+    // vertices: one add of the fixed-order sum
     if (!dir) atomicAdd(diag + gi, val);
   }
 }
@@ -386,6 +409,8 @@ k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restri
     st->trig2 = 0.0;
     st->xpend = 0;
     st->flush_ticket = 0u;
+    st->bar_count = 0u;
+    st->bar_fail = 0;
     if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) st->done = 2;
     else if (tot[1] <= st->tol2) st->done = 1;
     else st->done = 0;
@@ -500,6 +525,182 @@ k_pcg_flush(long long nb, T* __restrict__ x, const T* __restrict__ p, PcgState* 
     if (atomicAdd(&st->flush_ticket, 1u) == gridDim.x - 1) {
       st->xpend = 0;
       st->flush_ticket = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One-pass CG step: update and direction with a grid barrier between them
+// ---------------------------------------------------------------------------
+// After the operator (q = A p, alpha = rho / p.q) one CG step reads r, q, P,
+// x and p once and writes r, x, p and q once: r -= alpha q, z = P r,
+// rho' = r.z and rr = r.r, the stopping tests; then x += alpha p,
+// p = z + beta p, q = 0.  beta needs rho' summed over the whole vector, so a
+// grid barrier separates the two halves.  The grid is one CTA per SM,
+// launched cooperatively (all CTAs resident); CTA b owns the contiguous packs
+// [nv b / G, nv (b + 1) / G) and keeps z of its first zcap packs in shared
+// memory across the barrier (z of the others is formed again from r and P,
+// the same arithmetic).  Every CTA sums the per-CTA partials in the same
+// order, so all take the same decision; CTA 0 records it.  The barrier's wait
+// is bounded (about a second): on timeout the CTA records bar_fail, stops the
+// CG with done = 2 and returns.
+constexpr int kStepThreads = 1024;
+constexpr long long kBarSpin = 1LL << 24;
+
+// Grid barrier over st->bar_count / bar_gen (one use per launch; the last CTA
+// to arrive resets the count).  Returns false in every thread of a CTA whose
+// wait ran out.
+static __device__ bool step_barrier(PcgState* st) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &st->bar_gen;
+    const unsigned int g0 = *gen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+      atomicExch(&st->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g0) {
+        if (++spins > kBarSpin) { good = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStepThreads, 1)
+k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
+           const T* __restrict__ P, double* __restrict__ partials, PcgState* st, long long zcap) {
+  extern __shared__ __align__(16) unsigned char step_smem[];
+  __shared__ double tot_sh[2];
+  __shared__ double red_sh[2 * 32];
+  if (st->done) return;   // read by every CTA before the barrier; written after it
+  constexpr int W = 16 / sizeof(T);
+  using V = Pack<T, W>;
+  V* zs = reinterpret_cast<V*>(step_smem);
+  const T alpha = (T)st->alpha;
+  const double rho = st->rho, tol2 = st->tol2, trig2 = st->trig2;
+  const int it = st->iter + 1, maxit = st->maxit;
+  const unsigned G = gridDim.x;
+  const long long nv = nb / W;
+  const long long c0 = nv * blockIdx.x / G, c1 = nv * (blockIdx.x + 1) / G;
+  const bool tail_cta = blockIdx.x == G - 1;
+
+  // ---- r -= alpha q, z = P r, partial dots
+  T rz = T(0), rr = T(0);
+  for (long long iv = c0 + threadIdx.x; iv < c1; iv += kStepThreads) {
+    V rv = reinterpret_cast<const V*>(r)[iv];
+    const V qv = reinterpret_cast<const V*>(q)[iv];
+    const V Pv = reinterpret_cast<const V*>(P)[iv];
+    V zv;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      const T ri = fma(-alpha, qv.v[c], rv.v[c]);
+      rv.v[c] = ri;
+      zv.v[c] = Pv.v[c] * ri;
+      rz = fma(ri, zv.v[c], rz);
+      rr = fma(ri, ri, rr);
+    }
+    reinterpret_cast<V*>(r)[iv] = rv;
+    if (iv - c0 < zcap) zs[iv - c0] = zv;
+  }
+  if (tail_cta) {
+    for (long long i = nv * W + threadIdx.x; i < nb; i += kStepThreads) {
+      const T ri = fma(-alpha, q[i], r[i]);
+      r[i] = ri;
+      rz = fma(ri, P[i] * ri, rz);
+      rr = fma(ri, ri, rr);
+    }
+  }
+  double v[2] = {(double)rz, (double)rr};
+  block_sum<2>(v, red_sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = v[0];
+    partials[G + blockIdx.x] = v[1];
+  }
+  if (!step_barrier(st)) {
+    if (threadIdx.x == 0) {
+      st->bar_fail = 1;
+      st->done = 2;
+    }
+    return;
+  }
+  // ---- totals in a fixed order (the same in every CTA) and the decision
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0;
+    for (unsigned i = threadIdx.x; i < G; i += 32) {
+      a += __ldcg(partials + i);
+      b += __ldcg(partials + G + i);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (threadIdx.x == 0) {
+      tot_sh[0] = a;
+      tot_sh[1] = b;
+    }
+  }
+  __syncthreads();
+  const double RZ = tot_sh[0], RR = tot_sh[1];
+  int done = 0;
+  if (!isfinite(RZ) || !isfinite(RR)) done = 2;
+  else if (RR <= tol2) done = 1;
+  else if (it >= maxit) done = 3;
+  else if (trig2 > 0.0 && RR <= trig2) done = 4;   // refinement due: rho (of the previous residual) is kept
+  const double beta = done == 0 ? RZ / rho : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->iter = it;
+    st->rho_new = RZ;
+    st->rr = RR;
+    if (done == 0) {
+      st->beta = beta;
+      st->rho = RZ;
+    }
+    st->xpend = done != 0 ? 1 : 0;   // a stopped CG owes x += alpha p (flush or refinement fold)
+    st->done = done;
+  }
+  if (done != 0) return;
+  // ---- x += alpha p, p = z + beta p, q = 0
+  const T bt = (T)beta;
+  V zero;
+#pragma unroll
+  for (int c = 0; c < W; ++c) zero.v[c] = T(0);
+  for (long long iv = c0 + threadIdx.x; iv < c1; iv += kStepThreads) {
+    V xv = reinterpret_cast<const V*>(x)[iv];
+    V pv = reinterpret_cast<const V*>(p)[iv];
+    V zv;
+    if (iv - c0 < zcap) {
+      zv = zs[iv - c0];
+    } else {   // this thread wrote r[iv] above
+      const V rv = reinterpret_cast<const V*>(r)[iv];
+      const V Pv = reinterpret_cast<const V*>(P)[iv];
+#pragma unroll
+      for (int c = 0; c < W; ++c) zv.v[c] = Pv.v[c] * rv.v[c];
+    }
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      xv.v[c] = fma(alpha, pv.v[c], xv.v[c]);
+      pv.v[c] = fma(bt, pv.v[c], zv.v[c]);
+    }
+    reinterpret_cast<V*>(x)[iv] = xv;
+    reinterpret_cast<V*>(p)[iv] = pv;
+    reinterpret_cast<V*>(q)[iv] = zero;
+  }
+  if (tail_cta) {
+    for (long long i = nv * W + threadIdx.x; i < nb; i += kStepThreads) {
+      x[i] = fma(alpha, p[i], x[i]);
+      p[i] = fma(bt, p[i], P[i] * r[i]);
+      q[i] = T(0);
     }
   }
 }
@@ -831,6 +1032,51 @@ void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgS
   sem_count_launch();
 }
 
+// Shared memory of the one-pass step for a vector of nb values: z of
+// ceil(nv / SMs) packs per CTA, at most kStepSmemMax bytes.
+constexpr size_t kStepSmemMax = 200 * 1024;
+template <typename T>
+static size_t step_smem(long long nb) {
+  const long long nv = nb / (16 / (long long)sizeof(T));
+  const long long per = (nv + num_sms() - 1) / num_sms();
+  const size_t bytes = (size_t)per * 16;
+  return bytes < kStepSmemMax ? bytes : kStepSmemMax;
+}
+
+template <typename T>
+cudaError_t prepare_pcg_step(long long nb, bool* usable) {
+  *usable = false;
+  cudaError_t e = cudaFuncSetAttribute(k_pcg_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStepSmemMax);
+  if (e != cudaSuccess) return e;
+  int dev = 0, coop = 0, occ = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_step<T>, kStepThreads, step_smem<T>(nb));
+  if (e != cudaSuccess) return e;
+  *usable = coop != 0 && occ >= 1;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_pcg_step(long long nb, T* x, T* r, T* p, T* q, const T* P, double* partials, PcgState* st,
+                            cudaStream_t s) {
+  const size_t smem = step_smem<T>(nb);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)num_sms());
+  cfg.blockDim = dim3(kStepThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const long long zcap = (long long)(smem / 16);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg_step<T>, nb, x, r, p, q, P, partials, st, zcap);
+  sem_count_launch();
+  return e;
+}
+
 template <typename T>
 void launch_pcg_flush(long long nb, T* x, const T* p, PcgState* st, cudaStream_t s) {
   k_pcg_flush<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, p, st);
@@ -842,7 +1088,9 @@ void launch_pcg_flush(long long nb, T* x, const T* p, PcgState* st, cudaStream_t
                                    int, int, cudaStream_t);                                                   \
   template void launch_pcg_update<T>(long long, T*, const T*, const T*, double*, PcgState*, cudaStream_t);     \
   template void launch_pcg_dir<T>(long long, T*, const T*, T*, T*, const T*, PcgState*, cudaStream_t);         \
-  template void launch_pcg_flush<T>(long long, T*, const T*, PcgState*, cudaStream_t);
+  template void launch_pcg_flush<T>(long long, T*, const T*, PcgState*, cudaStream_t);                     \
+  template cudaError_t prepare_pcg_step<T>(long long, bool*);                                                 \
+  template cudaError_t launch_pcg_step<T>(long long, T*, T*, T*, T*, const T*, double*, PcgState*, cudaStream_t);
 SEM_INST_VEC(double)
 SEM_INST_VEC(float)
 

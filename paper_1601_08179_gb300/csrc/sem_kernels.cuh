@@ -145,6 +145,15 @@ void launch_pcg_update(long long nb, T* r, const T* q, const T* P, double* parti
 // x += alpha p, then p = P r + beta p, q = 0.
 template <typename T>
 void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s);
+// One-pass CG step (k_pcg_step: the update and the direction of one iteration
+// with a grid barrier between them; cooperative launch, one CTA per SM).
+// prepare_pcg_step sets the kernel's shared-memory limit (call outside graph
+// capture) and reports whether the device can run it for vectors of nb.
+template <typename T>
+cudaError_t prepare_pcg_step(long long nb, bool* usable);
+template <typename T>
+cudaError_t launch_pcg_step(long long nb, T* x, T* r, T* p, T* q, const T* P, double* partials, PcgState* st,
+                            cudaStream_t s);
 // Applies an owed x += alpha p (no-op when none is owed; idempotent).
 template <typename T>
 void launch_pcg_flush(long long nb, T* x, const T* p, PcgState* st, cudaStream_t s);

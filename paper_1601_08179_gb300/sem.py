@@ -36,7 +36,8 @@ class SemError(RuntimeError):
 class sem_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("precision", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("max_refine", ctypes.c_int),
-                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double), ("deterministic", ctypes.c_int)]
+                ("mixed_scheme", ctypes.c_int), ("reliable_delta", ctypes.c_double), ("deterministic", ctypes.c_int),
+                ("onepass_step", ctypes.c_int)]
 
 
 class sem_info(ctypes.Structure):
@@ -85,6 +86,7 @@ def lib():
         "sem_check_vector": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "sem_debug_oob": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "sem_debug_limit_skeleton": (ctypes.c_int, [_P, ctypes.c_longlong]),
+        "sem_debug_cg_step_timeout": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "sem_get_operator_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "sem_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
@@ -122,6 +124,7 @@ def exported_symbols():
             "sem_transform_skeleton", "sem_pack_skeleton", "sem_unpack_skeleton", "sem_refine_history",
             "sem_solve_adjoint", "sem_gradients", "sem_autotune", "sem_set_operator_kernel",
             "sem_get_operator_kernel", "sem_check_vector", "sem_debug_oob", "sem_debug_limit_skeleton",
+            "sem_debug_cg_step_timeout",
             "sem_batch_create", "sem_batch_solve",
             "sem_batch_destroy", "sem_solve_batch",
             "sem_apply_condensed_variant", "sem_diag_nodal", "sem_solve_variant",
@@ -366,6 +369,14 @@ def sem_debug_oob():
 def sem_debug_limit_skeleton(ctx: SemContext, bound: int) -> int:
     """Lowers the bound of the debug build's offset checks (status)."""
     return lib().sem_debug_limit_skeleton(ctx.handle, int(bound))
+
+
+def sem_debug_cg_step_timeout(ctx: SemContext):
+    """(status, bar_fail, done) of one one-pass CG step whose grid barrier
+    never completes (debug build; SEM_ENOTSUP in a release build)."""
+    bf, dn = ctypes.c_int(), ctypes.c_int()
+    st = lib().sem_debug_cg_step_timeout(ctx.handle, ctypes.byref(bf), ctypes.byref(dn))
+    return st, bf.value, dn.value
 
 
 def sem_autotune(ctx: SemContext):

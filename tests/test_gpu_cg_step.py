@@ -1,0 +1,73 @@
+"""The one-pass FP32 CG step (update and direction in one kernel, a bounded
+grid barrier between them; sem_opts.onepass_step) against the two-kernel
+step and the dense oracle: mixed-precision solves converge to the same
+tolerance with the same iteration counts up to FP32 rounding order, on
+meshes whose skeleton length is not a multiple of four (scalar tail), on
+the p = 8 benchmark mesh (the whole z = P r of each CTA kept in shared
+memory) and on the p = 4 sweep mesh (N_B = 9.9e6: part of z formed again
+from r and P after the barrier).  The barrier's timeout is covered by the
+debug-build test."""
+import numpy as np
+import pytest
+
+import sem_inputs as si
+from oracle import dense
+from tests.gpu_util import dev, host, make_pair, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(ctx, f, onepass):
+    import torch
+    from paper_1601_08179_gb300 import sem
+    sem.sem_set_opts(ctx, sem.default_opts(precision=sem.PREC_MIXED, onepass_step=onepass))
+    u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+    n0 = sem.sem_launch_count()
+    info = sem.sem_solve(ctx, f, u)
+    return host(u), info, sem.sem_launch_count() - n0
+
+
+@pytest.mark.parametrize("p,m,lam,ar", [(3, (5, 3, 2), 1.0, 4.0), (4, (4, 3, 3), 0.0, 16.0), (6, (3, 4, 2), 10.0, 2.0),
+                                        (8, (3, 3, 3), 0.5, 8.0), (2, (9, 7, 5), 1.0, 1.0), (12, (2, 3, 2), 1.0, 4.0)])
+def test_onepass_step_matches_two_kernels_and_oracle(p, m, lam, ar):
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, lam, ar, opts=sem.default_opts(precision=sem.PREC_MIXED))
+    f = si.node_noise(ms.n_global, 3100 + p)
+    ref = dense.solve_full(ms, lam, f)
+    u1, i1, l1 = _solve(ctx, dev(f), 1)
+    u0, i0, l0 = _solve(ctx, dev(f), 0)
+    print(f"p={p} m={m} N_B={ctx.nb} (mod 4 = {ctx.nb % 4}): iterations {i1['iters']} one-pass / {i0['iters']} "
+          f"two kernels, launches {l1} / {l0}")
+    for u, info in ((u1, i1), (u0, i0)):
+        assert info["rel_res"] <= 1e-10
+        assert relerr(u, ref) <= 1e-9
+    assert abs(i1["iters"] - i0["iters"]) <= 2
+    assert l1 < l0   # one launch fewer per CG iteration
+
+
+def test_some_case_has_a_scalar_tail():
+    from paper_1601_08179_gb300 import sem
+    tails = []
+    for p, m in [(3, (5, 3, 2)), (4, (4, 3, 3)), (6, (3, 4, 2)), (8, (3, 3, 3)), (2, (9, 7, 5)), (12, (2, 3, 2))]:
+        ctx, _ = make_pair(p, m, 1.0, 1.0, opts=sem.default_opts(precision=sem.PREC_MIXED))
+        tails.append(ctx.nb % 4)
+    assert any(t != 0 for t in tails), tails
+
+
+@pytest.mark.parametrize("p", [8, 4])
+def test_onepass_step_at_full_size(p):
+    """The graded sweep workload of degree p (N ~ 1.68e7): the one-pass and
+    two-kernel FP32 CG reach the FP64 residual 1e-10 in iteration counts
+    within 2 % of each other, and their solutions agree to the tolerance."""
+    from paper_1601_08179_gb300 import build, sem
+    build.build()
+    w = si.scale_workload(p)
+    hx, hy, hz = w.widths()
+    ctx = sem.sem_setup(w.p, hx, hy, hz, w.lam, sem.default_opts(precision=sem.PREC_MIXED))
+    f = dev(si.node_noise(ctx.n_nodes, 3200 + p))
+    u1, i1, _ = _solve(ctx, f, 1)
+    u0, i0, _ = _solve(ctx, f, 0)
+    print(f"p={p}: N_B={ctx.nb}, iterations {i1['iters']} one-pass / {i0['iters']} two kernels")
+    assert i1["rel_res"] <= 1e-10 and i0["rel_res"] <= 1e-10
+    assert abs(i1["iters"] - i0["iters"]) <= max(2, 0.02 * i0["iters"])
+    assert relerr(u1, u0) <= 1e-8

@@ -4,8 +4,10 @@ kernels of both precisions, load condensation, preconditioner, solves
 (FP64, mixed, batched) and recovery on regular and thin meshes, the record
 stays empty and the results meet the same bars as the release build; with the
 checked bound lowered below the vertex block, the offsets past it are caught
-(and skipped) while every access stays inside the real vectors.  The work
-runs in a child process that loads the debug library (SEM_LIB)."""
+(and skipped) while every access stays inside the real vectors.  The
+one-pass CG step's grid barrier, made never to complete, gives up after its
+bounded wait and stops the CG, and the context solves normally afterwards.
+The work runs in a child process that loads the debug library (SEM_LIB)."""
 import json
 import os
 import subprocess
@@ -100,6 +102,17 @@ out["bound"] = bound
 out["limit_out_of_range"] = sem.sem_debug_limit_skeleton(ctx, ctx.nb + 1)
 st, n, first = sem.sem_debug_oob()
 out["after"] = [st, n, first]
+
+# the one-pass CG step's grid barrier with its arrival count preset so that
+# it never completes: every CTA's bounded wait runs out, the CG stops as a
+# breakdown, and the context solves normally afterwards
+ctx, ms = make_pair(6, (3, 2, 2), 1.0, 2.0, opts=sem.default_opts(precision=sem.PREC_MIXED))
+f = si.node_noise(ms.n_global, 11)
+u = torch.empty(ctx.n_nodes, dtype=torch.float64, device="cuda")
+sem.sem_solve(ctx, dev(f), u)
+st, bar_fail, done = sem.sem_debug_cg_step_timeout(ctx)
+info = sem.sem_solve(ctx, dev(f), u)
+out["barrier"] = [st, bar_fail, done, info["rel_res"], relerr(host(u), dense.solve_full(ms, 1.0, f))]
 print("RESULT " + json.dumps(out))
 """
 
@@ -124,3 +137,6 @@ def test_debug_build_bounds_record():
         assert st == sem.SEM_OK and n >= 1 and first >= out["bound"] and finite, (prec, kind, st, n, first)
     assert out["limit_out_of_range"] == sem.SEM_EINVAL
     assert out["after"] == [sem.SEM_OK, 0, -1]
+    st, bar_fail, done, rel_res, err = out["barrier"]
+    assert st == sem.SEM_OK and bar_fail == 1 and done == 2, out["barrier"]
+    assert rel_res <= 1e-10 and err <= 1e-9, out["barrier"]
