@@ -120,11 +120,13 @@ typedef struct {
   int onepass_step;   /* MIXED single solves: 1 (default) = the FP32 CG's update and
                          direction are one kernel that reads r, q, P, x, p and writes
                          r, x, p, q once per iteration (a grid barrier between the two
-                         halves; cooperative launch, one CTA per SM, the barrier's
-                         wait bounded); 0 = two kernels (r, P read twice).  Batched
-                         solves always take two kernels.  Where the device or the
-                         graph cannot take the cooperative launch the solve falls
-                         back to two kernels by itself. */
+                         halves; cooperative launch, one CTA per SM holding its
+                         range of z = P r in shared memory, the barrier's wait
+                         bounded); 0 = two kernels (r, P read twice).  The one-pass
+                         step is taken only where z fits (N_B up to 200 KB of FP32
+                         per SM: 7.78e6 on 152 SMs); batched solves, larger N_B, or a
+                         device or graph that cannot take the cooperative launch
+                         run two kernels. */
 } sem_opts;
 
 /* Result of a solve. */

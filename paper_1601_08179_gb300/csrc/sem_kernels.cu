@@ -538,13 +538,14 @@ k_pcg_flush(long long nb, T* __restrict__ x, const T* __restrict__ p, PcgState* 
 // p = z + beta p, q = 0.  beta needs rho' summed over the whole vector, so a
 // grid barrier separates the two halves.  The grid is one CTA per SM,
 // launched cooperatively (all CTAs resident); CTA b owns the contiguous packs
-// [nv b / G, nv (b + 1) / G) and keeps z of its first zcap packs in shared
-// memory across the barrier (z of the others is formed again from r and P,
-// the same arithmetic).  Every CTA sums the per-CTA partials in the same
+// [nv b / G, nv (b + 1) / G) and keeps their z in shared memory across the
+// barrier (the launcher takes this kernel only when z fits).  Every CTA sums
+// the per-CTA partials in the same
 // order, so all take the same decision; CTA 0 records it.  The barrier's wait
 // is bounded (about a second): on timeout the CTA records bar_fail, stops the
 // CG with done = 2 and returns.
 constexpr int kStepThreads = 1024;
+
 constexpr long long kBarSpin = 1LL << 24;
 
 // Grid barrier over st->bar_count / bar_gen (one use per launch; the last CTA
@@ -579,7 +580,7 @@ static __device__ bool step_barrier(PcgState* st) {
 template <typename T>
 __global__ void __launch_bounds__(kStepThreads, 1)
 k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
-           const T* __restrict__ P, double* __restrict__ partials, PcgState* st, long long zcap) {
+           const T* __restrict__ P, double* __restrict__ partials, PcgState* st) {
   extern __shared__ __align__(16) unsigned char step_smem[];
   __shared__ double tot_sh[2];
   __shared__ double red_sh[2 * 32];
@@ -595,23 +596,37 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
   const long long c0 = nv * blockIdx.x / G, c1 = nv * (blockIdx.x + 1) / G;
   const bool tail_cta = blockIdx.x == G - 1;
 
-  // ---- r -= alpha q, z = P r, partial dots
+  // ---- r -= alpha q, z = P r, partial dots (two packs per thread per trip:
+  //      six loads in flight)
   T rz = T(0), rr = T(0);
-  for (long long iv = c0 + threadIdx.x; iv < c1; iv += kStepThreads) {
-    V rv = reinterpret_cast<const V*>(r)[iv];
-    const V qv = reinterpret_cast<const V*>(q)[iv];
-    const V Pv = reinterpret_cast<const V*>(P)[iv];
-    V zv;
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-      const T ri = fma(-alpha, qv.v[c], rv.v[c]);
-      rv.v[c] = ri;
-      zv.v[c] = Pv.v[c] * ri;
-      rz = fma(ri, zv.v[c], rz);
-      rr = fma(ri, ri, rr);
+  for (long long iv = c0 + threadIdx.x; iv < c1; iv += 2 * kStepThreads) {
+    const long long iw = iv + kStepThreads;
+    const bool two = iw < c1;
+    V rv[2], qv[2], Pv[2];
+    rv[0] = reinterpret_cast<const V*>(r)[iv];
+    qv[0] = reinterpret_cast<const V*>(q)[iv];
+    Pv[0] = reinterpret_cast<const V*>(P)[iv];
+    if (two) {
+      rv[1] = reinterpret_cast<const V*>(r)[iw];
+      qv[1] = reinterpret_cast<const V*>(q)[iw];
+      Pv[1] = reinterpret_cast<const V*>(P)[iw];
     }
-    reinterpret_cast<V*>(r)[iv] = rv;
-    if (iv - c0 < zcap) zs[iv - c0] = zv;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !two) break;
+      V zv;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const T ri = fma(-alpha, qv[h].v[c], rv[h].v[c]);
+        rv[h].v[c] = ri;
+        zv.v[c] = Pv[h].v[c] * ri;
+        rz = fma(ri, zv.v[c], rz);
+        rr = fma(ri, ri, rr);
+      }
+      const long long ih = h ? iw : iv;
+      reinterpret_cast<V*>(r)[ih] = rv[h];
+      zs[ih - c0] = zv;
+    }
   }
   if (tail_cta) {
     for (long long i = nv * W + threadIdx.x; i < nb; i += kStepThreads) {
@@ -678,15 +693,7 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
   for (long long iv = c0 + threadIdx.x; iv < c1; iv += kStepThreads) {
     V xv = reinterpret_cast<const V*>(x)[iv];
     V pv = reinterpret_cast<const V*>(p)[iv];
-    V zv;
-    if (iv - c0 < zcap) {
-      zv = zs[iv - c0];
-    } else {   // this thread wrote r[iv] above
-      const V rv = reinterpret_cast<const V*>(r)[iv];
-      const V Pv = reinterpret_cast<const V*>(P)[iv];
-#pragma unroll
-      for (int c = 0; c < W; ++c) zv.v[c] = Pv.v[c] * rv.v[c];
-    }
+    const V zv = zs[iv - c0];
 #pragma unroll
     for (int c = 0; c < W; ++c) {
       xv.v[c] = fma(alpha, pv.v[c], xv.v[c]);
@@ -1033,14 +1040,15 @@ void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgS
 }
 
 // Shared memory of the one-pass step for a vector of nb values: z of
-// ceil(nv / SMs) packs per CTA, at most kStepSmemMax bytes.
+// ceil(nv / SMs) packs per CTA; the step is taken only up to kStepSmemMax.
+// (Where z does not fit, forming it again after the barrier from r and P
+// was measured slower than the two-kernel step, whose re-reads hit L2.)
 constexpr size_t kStepSmemMax = 200 * 1024;
 template <typename T>
 static size_t step_smem(long long nb) {
   const long long nv = nb / (16 / (long long)sizeof(T));
   const long long per = (nv + num_sms() - 1) / num_sms();
-  const size_t bytes = (size_t)per * 16;
-  return bytes < kStepSmemMax ? bytes : kStepSmemMax;
+  return (size_t)(per > 0 ? per : 1) * 16;
 }
 
 template <typename T>
@@ -1051,7 +1059,9 @@ cudaError_t prepare_pcg_step(long long nb, bool* usable) {
   int dev = 0, coop = 0, occ = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_step<T>, kStepThreads, step_smem<T>(nb));
+  const size_t smem = step_smem<T>(nb);
+  if (smem > kStepSmemMax) return cudaSuccess;   // z does not fit: two kernels
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pcg_step<T>, kStepThreads, smem);
   if (e != cudaSuccess) return e;
   *usable = coop != 0 && occ >= 1;
   return cudaSuccess;
@@ -1061,6 +1071,7 @@ template <typename T>
 cudaError_t launch_pcg_step(long long nb, T* x, T* r, T* p, T* q, const T* P, double* partials, PcgState* st,
                             cudaStream_t s) {
   const size_t smem = step_smem<T>(nb);
+  if (smem > kStepSmemMax) return cudaErrorInvalidValue;   // prepare_pcg_step reports it unusable
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)num_sms());
   cfg.blockDim = dim3(kStepThreads);
@@ -1071,8 +1082,7 @@ cudaError_t launch_pcg_step(long long nb, T* x, T* r, T* p, T* q, const T* P, do
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const long long zcap = (long long)(smem / 16);
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg_step<T>, nb, x, r, p, q, P, partials, st, zcap);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg_step<T>, nb, x, r, p, q, P, partials, st);
   sem_count_launch();
   return e;
 }

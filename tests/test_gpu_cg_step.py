@@ -4,9 +4,9 @@ step and the dense oracle: mixed-precision solves converge to the same
 tolerance with the same iteration counts up to FP32 rounding order, on
 meshes whose skeleton length is not a multiple of four (scalar tail), on
 the p = 8 benchmark mesh (the whole z = P r of each CTA kept in shared
-memory) and on the p = 4 sweep mesh (N_B = 9.9e6: part of z formed again
-from r and P after the barrier).  The barrier's timeout is covered by the
-debug-build test."""
+memory) and on the p = 4 sweep mesh (N_B = 9.9e6: z does not fit, the
+solve takes the two-kernel step either way).  The barrier's timeout is
+covered by the debug-build test."""
 import numpy as np
 import pytest
 
