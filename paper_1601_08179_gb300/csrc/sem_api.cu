@@ -320,6 +320,12 @@ sem_status apply_t(sem_ctx* c, const double* x, double* y, cudaStream_t s) {
   return SEM_OK;
 }
 
+// Status message of a solve stopped by a grid-barrier timeout of the one-pass
+// CG step (PcgState::bar_fail) rather than by a breakdown of the iteration.
+constexpr const char* kBarFailMsg =
+    "the one-pass CG step's grid barrier wait ran out (its CTAs were not all resident); "
+    "set opts.onepass_step = 0";
+
 // Whether the FP32 CG of a single solve takes the one-pass step.
 bool use_step(const sem_ctx* c) { return c->opts.onepass_step != 0 && c->step_ok && !c->step_failed; }
 
@@ -630,7 +636,8 @@ sem_status pcg_mixed(sem_ctx* c, bool warm, sem_info* info) {
     info->refinements = refinements;
     info->rel_res = rel;
   }
-  if (result == SEM_EBREAKDOWN) return fail(result, "CG breakdown or non-finite residual in the refinement");
+  if (result == SEM_EBREAKDOWN)
+    return fail(result, c->h_st->bar_fail ? kBarFailMsg : "CG breakdown or non-finite residual in the refinement");
   if (result != SEM_OK) return fail(result, "refinement did not reach rtol (maxit, max_refine or stagnation)");
   return SEM_OK;
 }
@@ -768,7 +775,8 @@ sem_status pcg_mixed_reliable(sem_ctx* c, bool warm, sem_info* info) {
     info->refinements = hc->refinements;
     info->rel_res = hc->hist[last];
   }
-  if (hc->finished == 2) return fail(SEM_EBREAKDOWN, "CG breakdown or non-finite residual in the refinement");
+  if (hc->finished == 2)
+    return fail(SEM_EBREAKDOWN, c->h_st->bar_fail ? kBarFailMsg : "CG breakdown or non-finite residual in the refinement");
   if (hc->finished != 1) return fail(SEM_ENOCONV, "refinement did not reach rtol (maxit, max_refine or stagnation)");
   return SEM_OK;
 }

@@ -1005,7 +1005,8 @@ __device__ __forceinline__ long long elem_visit_index(const SemGeom& g, int ex, 
 // (edge slots 3, 7, 11, vertex slot 7), in the order of the side bits, and
 // added to v: the result does not depend on the order the elements ran in.
 template <typename T>
-__global__ void k_ev_sum(SemGeom g, const T* __restrict__ ev, T* __restrict__ v, int visit) {
+__global__ void k_ev_sum(SemGeom g, const T* __restrict__ ev, T* __restrict__ v, int visit, const PcgState* st) {
+  if (st != nullptr && st->done) return;   // the operator launch before it did not run (stopped CG, closed gate)
   // 32-bit index arithmetic (nelem (3 n + 1) < 2^31 whenever N_B is); the
   // thread order follows the layout so that neighbouring threads read
   // neighbouring values: position fastest for the element-major layout,
@@ -1052,12 +1053,12 @@ __global__ void k_ev_sum(SemGeom g, const T* __restrict__ ev, T* __restrict__ v,
 }
 
 template <typename T>
-void launch_ev_sum(const SemGeom& g, const T* ev, T* v, int visit, cudaStream_t s) {
+void launch_ev_sum(const SemGeom& g, const T* ev, T* v, int visit, const PcgState* st, cudaStream_t s) {
   const long long work = g.nelem * (3LL * g.n + 1);
   long long blocks = (work + 255) / 256;
   if (blocks > (long long)num_sms_cached() * 16) blocks = (long long)num_sms_cached() * 16;
   if (blocks < 1) blocks = 1;
-  k_ev_sum<T><<<(int)blocks, 256, 0, s>>>(g, ev, v, visit);
+  k_ev_sum<T><<<(int)blocks, 256, 0, s>>>(g, ev, v, visit, st);
   sem_count_launch();
 }
 
@@ -1106,7 +1107,7 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
   if (ev != nullptr) {
     if (g.n == 1) {
       launch_p2<T>(g, t, x, y, partials, st, s, ev);
-      launch_ev_sum<T>(g, ev, y, 0, s);
+      launch_ev_sum<T>(g, ev, y, 0, st, s);
       return;
     }
     kind = kApplyCta;
@@ -1135,7 +1136,7 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
       case 31: launch_nc<T, 31>(g, t, x, y, partials, st, c, s, ev); break;
       default: launch_nc<T, 0>(g, t, x, y, partials, st, c, s, ev); break;
     }
-    launch_ev_sum<T>(g, ev, y, 1, s);
+    launch_ev_sum<T>(g, ev, y, 1, st, s);
     return;
   }
   switch (g.n) {
