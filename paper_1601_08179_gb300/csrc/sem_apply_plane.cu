@@ -457,10 +457,14 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
     }
 }
 
-// Two-stage pipeline per warp: while the element groups of quad q are
-// computed from one buffer, the entity offsets of quad q + 1 are formed and
-// its gather is in flight (cp.async) into the other buffer.  v += Hhat~ u over
-// this warp's range of element groups; returns the thread's share of u^T v.
+// Per warp, element group after element group ("quads" of EPW elements):
+// form the entity offsets, gather by cp.async, compute.  One buffer per
+// group slot: a second buffer with the next group's gather in flight
+// (a two-stage pipeline) was measured slower (p = 8: 58.7 against 53.6 us
+// per application; p = 4: 125 against 120 us): it doubles the CTA's shared
+// memory, which the L1 cache gives up, and the other resident warps already
+// cover one warp's gather.  v += Hhat~ u over this warp's range of element
+// groups; returns the thread's share of u^T v.
 template <int N>
 __device__ __forceinline__ float plane_apply_all(const SemGeom& g, const SemClassTables<float>& tab,
                                                  const EntityAffine* ent, const float* __restrict__ u,
@@ -470,46 +474,27 @@ __device__ __forceinline__ float plane_apply_all(const SemGeom& g, const SemClas
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int grp = lane / G, jl = lane - grp * G;
   const int slot_id = wib * EPW + grp, nslots = wpb * EPW;
-  // buffer-major: buffer b of slot s at (b nslots + s); consecutive slots keep
-  // their bank offset
-  int* H0 = reinterpret_cast<int*>(smem_raw) + slot_id * kHdr;                 // buffer b: H0 + b hstep
-  float* W0 = reinterpret_cast<float*>(smem_raw + (size_t)2 * nslots * kHdr * sizeof(int)) +
-              (size_t)slot_id * S::size;                                      // buffer b: W0 + b wstep
-  const int hstep = nslots * kHdr, wstep = nslots * S::size;
-  // element groups ("quads") of EPW consecutive elements, split into equal
-  // contiguous ranges over all warps of the grid
+  int* H = reinterpret_cast<int*>(smem_raw) + slot_id * kHdr;
+  float* W = reinterpret_cast<float*>(smem_raw + (size_t)nslots * kHdr * sizeof(int)) + (size_t)slot_id * S::size;
+  // element groups of EPW consecutive elements, split into equal contiguous
+  // ranges over all warps of the grid
   const long long nq_all = (g.nelem + EPW - 1) / EPW, nw = (long long)gridDim.x * wpb;
   const long long w = (long long)blockIdx.x * wpb + wib;
   const long long q_begin = nq_all * w / nw;
   const int nq = (int)(nq_all * (w + 1) / nw - q_begin);
-  int held0 = -1, held1 = -1;   // class in each buffer's coefficient block (equal over the group)
+  int held = -1;   // class whose coefficient block the slot holds (equal over the group)
   float dot = 0.f;
-
-  auto stage = [&](int qi, int b) {
-    int* H = H0 + b * hstep;
-    float* W = W0 + b * wstep;
-    const int held = b ? held1 : held0;
+  for (int qi = 0; qi < nq; ++qi) {
     const long long e = (q_begin + qi) * EPW + grp;
     plane_header<G>(g, tab, ent, (int)e, e < g.nelem, held >= 0 ? held : 0, jl, H);
     __syncwarp();
     const int cls = H[26];
     plane_gather<N>(u, tab.plane + (long long)cls * tab.plane_stride, cls != held, H, W, jl);
     cp_async_commit();
-    if (b) held1 = cls;
-    else held0 = cls;
-  };
-
-  if (nq > 0) stage(0, 0);
-  for (int qi = 0; qi < nq; ++qi) {
-    const int b = qi & 1;
-    if (qi + 1 < nq) {
-      stage(qi + 1, b ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    held = cls;
+    cp_async_wait<0>();
     __syncwarp();
-    plane_element<N>(W0 + b * wstep, H0 + b * hstep, v, jl, dot);
+    plane_element<N>(W, H, v, jl, dot);
     __syncwarp();
   }
   return dot;
@@ -974,7 +959,7 @@ template <int N>
 size_t plane_smem() {
   using S = PlaneSm<N>;
   const int wpb = kPlaneThreads / 32;
-  return (size_t)wpb * S::EPW * 2 * kHdr * sizeof(int) + (size_t)wpb * S::EPW * 2 * S::size * sizeof(float);
+  return (size_t)wpb * S::EPW * kHdr * sizeof(int) + (size_t)wpb * S::EPW * S::size * sizeof(float);
 }
 
 template <int N>

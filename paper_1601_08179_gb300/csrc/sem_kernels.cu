@@ -544,7 +544,8 @@ k_pcg_flush(long long nb, T* __restrict__ x, const T* __restrict__ p, PcgState* 
 // order, so all take the same decision; CTA 0 records it.  The barrier's wait
 // is bounded (about a second): on timeout the CTA records bar_fail, stops the
 // CG with done = 2 and returns.
-constexpr int kStepThreads = 1024;
+constexpr int kStepThreads = 768;
+constexpr int kStepUnroll = 4;   // packs per thread per trip
 
 constexpr long long kBarSpin = 1LL << 24;
 
@@ -596,24 +597,25 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
   const long long c0 = nv * blockIdx.x / G, c1 = nv * (blockIdx.x + 1) / G;
   const bool tail_cta = blockIdx.x == G - 1;
 
-  // ---- r -= alpha q, z = P r, partial dots (two packs per thread per trip:
-  //      six loads in flight)
+  // ---- r -= alpha q, z = P r, partial dots.  Each thread issues the loads
+  //      of kStepUnroll packs before using any (12 loads in flight): both
+  //      halves are bound by memory latency, not by instruction issue
   T rz = T(0), rr = T(0);
-  for (long long iv = c0 + threadIdx.x; iv < c1; iv += 2 * kStepThreads) {
-    const long long iw = iv + kStepThreads;
-    const bool two = iw < c1;
-    V rv[2], qv[2], Pv[2];
-    rv[0] = reinterpret_cast<const V*>(r)[iv];
-    qv[0] = reinterpret_cast<const V*>(q)[iv];
-    Pv[0] = reinterpret_cast<const V*>(P)[iv];
-    if (two) {
-      rv[1] = reinterpret_cast<const V*>(r)[iw];
-      qv[1] = reinterpret_cast<const V*>(q)[iw];
-      Pv[1] = reinterpret_cast<const V*>(P)[iw];
+  for (long long base = c0 + threadIdx.x; base < c1; base += kStepUnroll * kStepThreads) {
+    V rv[kStepUnroll], qv[kStepUnroll], Pv[kStepUnroll];
+#pragma unroll
+    for (int h = 0; h < kStepUnroll; ++h) {
+      const long long ih = base + (long long)h * kStepThreads;
+      if (ih < c1) {
+        rv[h] = reinterpret_cast<const V*>(r)[ih];
+        qv[h] = reinterpret_cast<const V*>(q)[ih];
+        Pv[h] = reinterpret_cast<const V*>(P)[ih];
+      }
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (h == 1 && !two) break;
+    for (int h = 0; h < kStepUnroll; ++h) {
+      const long long ih = base + (long long)h * kStepThreads;
+      if (ih >= c1) break;
       V zv;
 #pragma unroll
       for (int c = 0; c < W; ++c) {
@@ -623,7 +625,6 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
         rz = fma(ri, zv.v[c], rz);
         rr = fma(ri, ri, rr);
       }
-      const long long ih = h ? iw : iv;
       reinterpret_cast<V*>(r)[ih] = rv[h];
       zs[ih - c0] = zv;
     }
@@ -690,18 +691,30 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
   V zero;
 #pragma unroll
   for (int c = 0; c < W; ++c) zero.v[c] = T(0);
-  for (long long iv = c0 + threadIdx.x; iv < c1; iv += kStepThreads) {
-    V xv = reinterpret_cast<const V*>(x)[iv];
-    V pv = reinterpret_cast<const V*>(p)[iv];
-    const V zv = zs[iv - c0];
+  for (long long base = c0 + threadIdx.x; base < c1; base += kStepUnroll * kStepThreads) {
+    V xv[kStepUnroll], pv[kStepUnroll];
 #pragma unroll
-    for (int c = 0; c < W; ++c) {
-      xv.v[c] = fma(alpha, pv.v[c], xv.v[c]);
-      pv.v[c] = fma(bt, pv.v[c], zv.v[c]);
+    for (int h = 0; h < kStepUnroll; ++h) {
+      const long long ih = base + (long long)h * kStepThreads;
+      if (ih < c1) {
+        xv[h] = reinterpret_cast<const V*>(x)[ih];
+        pv[h] = reinterpret_cast<const V*>(p)[ih];
+      }
     }
-    reinterpret_cast<V*>(x)[iv] = xv;
-    reinterpret_cast<V*>(p)[iv] = pv;
-    reinterpret_cast<V*>(q)[iv] = zero;
+#pragma unroll
+    for (int h = 0; h < kStepUnroll; ++h) {
+      const long long ih = base + (long long)h * kStepThreads;
+      if (ih >= c1) break;
+      const V zv = zs[ih - c0];
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        xv[h].v[c] = fma(alpha, pv[h].v[c], xv[h].v[c]);
+        pv[h].v[c] = fma(bt, pv[h].v[c], zv.v[c]);
+      }
+      reinterpret_cast<V*>(x)[ih] = xv[h];
+      reinterpret_cast<V*>(p)[ih] = pv[h];
+      reinterpret_cast<V*>(q)[ih] = zero;
+    }
   }
   if (tail_cta) {
     for (long long i = nv * W + threadIdx.x; i < nb; i += kStepThreads) {
