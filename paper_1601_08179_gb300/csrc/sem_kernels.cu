@@ -637,6 +637,17 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
       rr = fma(ri, ri, rr);
     }
   }
+  // the second half's first x and p packs do not depend on beta: their
+  // loads are issued before the barrier and land while it is waited for
+  V xv[kStepUnroll], pv[kStepUnroll];
+#pragma unroll
+  for (int h = 0; h < kStepUnroll; ++h) {
+    const long long ih = c0 + threadIdx.x + (long long)h * kStepThreads;
+    if (ih < c1) {
+      xv[h] = reinterpret_cast<const V*>(x)[ih];
+      pv[h] = reinterpret_cast<const V*>(p)[ih];
+    }
+  }
   double v[2] = {(double)rz, (double)rr};
   block_sum<2>(v, red_sh);
   if (threadIdx.x == 0) {
@@ -692,13 +703,14 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
 #pragma unroll
   for (int c = 0; c < W; ++c) zero.v[c] = T(0);
   for (long long base = c0 + threadIdx.x; base < c1; base += kStepUnroll * kStepThreads) {
-    V xv[kStepUnroll], pv[kStepUnroll];
+    if (base != c0 + threadIdx.x) {   // the first trip's packs were loaded before the barrier
 #pragma unroll
-    for (int h = 0; h < kStepUnroll; ++h) {
-      const long long ih = base + (long long)h * kStepThreads;
-      if (ih < c1) {
-        xv[h] = reinterpret_cast<const V*>(x)[ih];
-        pv[h] = reinterpret_cast<const V*>(p)[ih];
+      for (int h = 0; h < kStepUnroll; ++h) {
+        const long long ih = base + (long long)h * kStepThreads;
+        if (ih < c1) {
+          xv[h] = reinterpret_cast<const V*>(x)[ih];
+          pv[h] = reinterpret_cast<const V*>(p)[ih];
+        }
       }
     }
 #pragma unroll
