@@ -55,10 +55,12 @@ def test_argument_checks_without_gpu(L):
     st = L.sem_setup(ctypes.byref(h), 4, 0, 2, 2, ok.ctypes.data_as(D), ok.ctypes.data_as(D),
                      ok.ctypes.data_as(D), 1.0, None)
     assert st == sem.SEM_EINVAL
-    o = sem.default_opts(rtol=2.0)
-    st = L.sem_setup(ctypes.byref(h), 4, 2, 2, 2, ok.ctypes.data_as(D), ok.ctypes.data_as(D),
-                     ok.ctypes.data_as(D), 1.0, ctypes.byref(o))
-    assert st == sem.SEM_EINVAL
+    for o in (sem.default_opts(rtol=2.0), sem.default_opts(deterministic=2), sem.default_opts(onepass_step=-1)):
+        st = L.sem_setup(ctypes.byref(h), 4, 2, 2, 2, ok.ctypes.data_as(D), ok.ctypes.data_as(D),
+                         ok.ctypes.data_as(D), 1.0, ctypes.byref(o))
+        assert st == sem.SEM_EINVAL
+        assert L.sem_last_error().decode()
+    assert L.sem_debug_cg_step_timeout(None, None, None) == sem.SEM_EINVAL
     # null context
     assert L.sem_apply_condensed(None, None, None, 0, None) == sem.SEM_EINVAL
     assert L.sem_check_vector(None, None, 8) == sem.SEM_EINVAL
