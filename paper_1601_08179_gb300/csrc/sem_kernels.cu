@@ -36,6 +36,10 @@ long long sem_launch_total() { return g_launches.load(); }
 namespace {
 
 constexpr int kVecThreads = 256;
+// Packs per thread per trip in the CG update and direction kernels, which run
+// two 256-thread CTAs per SM (up to 128 registers: 4 vectors x 4 packs in
+// flight per thread)
+constexpr int kVecUnroll = 4;
 
 // ---------------------------------------------------------------------------
 // Per-width-class tables: d (Eq. metriccoeffelement) and D^-1 (Eq. hii_diagonal)
@@ -422,7 +426,7 @@ k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restri
 // this kernel stops the CG it is owed (st->xpend) and applied by
 // k_pcg_flush or by the refinement fold.
 template <typename T>
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, 2)
 k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* __restrict__ P,
              double* __restrict__ partials, PcgState* st) {
   if (st->done) return;
@@ -432,18 +436,32 @@ k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* 
   T rz = T(0), rr = T(0);
   const long long nv = nb / W;
   const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
-  for (long long iv = g0; iv < nv; iv += gs) {
-    V rv = reinterpret_cast<const V*>(r)[iv];
-    const V qv = reinterpret_cast<const V*>(q)[iv];
-    const V Pv = reinterpret_cast<const V*>(P)[iv];
+  // kVecUnroll packs per thread per trip, all loads issued first (memory
+  // latency, not bandwidth, bounds a one-pack loop)
+  for (long long base = g0; base < nv; base += kVecUnroll * gs) {
+    V rv[kVecUnroll], qv[kVecUnroll], Pv[kVecUnroll];
 #pragma unroll
-    for (int c = 0; c < W; ++c) {
-      const T ri = fma(-alpha, qv.v[c], rv.v[c]);
-      rv.v[c] = ri;
-      rz = fma(ri, Pv.v[c] * ri, rz);
-      rr = fma(ri, ri, rr);
+    for (int h = 0; h < kVecUnroll; ++h) {
+      const long long iv = base + h * gs;
+      if (iv < nv) {
+        rv[h] = reinterpret_cast<const V*>(r)[iv];
+        qv[h] = reinterpret_cast<const V*>(q)[iv];
+        Pv[h] = reinterpret_cast<const V*>(P)[iv];
+      }
     }
-    reinterpret_cast<V*>(r)[iv] = rv;
+#pragma unroll
+    for (int h = 0; h < kVecUnroll; ++h) {
+      const long long iv = base + h * gs;
+      if (iv >= nv) break;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const T ri = fma(-alpha, qv[h].v[c], rv[h].v[c]);
+        rv[h].v[c] = ri;
+        rz = fma(ri, Pv[h].v[c] * ri, rz);
+        rr = fma(ri, ri, rr);
+      }
+      reinterpret_cast<V*>(r)[iv] = rv[h];
+    }
   }
   for (long long i = nv * W + g0; i < nb; i += gs) {
     const T ri = fma(-alpha, q[i], r[i]);
@@ -477,7 +495,7 @@ k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* 
 
 // x += alpha p (the update of this iteration), then p = P r + beta p and q = 0.
 template <typename T>
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, 2)
 k_pcg_dir(long long nb, T* __restrict__ x, const T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
           const T* __restrict__ P, PcgState* st) {
   if (st->done) return;
@@ -489,19 +507,31 @@ k_pcg_dir(long long nb, T* __restrict__ x, const T* __restrict__ r, T* __restric
   V zero;
 #pragma unroll
   for (int c = 0; c < W; ++c) zero.v[c] = T(0);
-  for (long long iv = g0; iv < nv; iv += gs) {
-    V xv = reinterpret_cast<const V*>(x)[iv];
-    const V rv = reinterpret_cast<const V*>(r)[iv];
-    const V Pv = reinterpret_cast<const V*>(P)[iv];
-    V pv = reinterpret_cast<const V*>(p)[iv];
+  for (long long base = g0; base < nv; base += kVecUnroll * gs) {
+    V xv[kVecUnroll], rv[kVecUnroll], Pv[kVecUnroll], pv[kVecUnroll];
 #pragma unroll
-    for (int c = 0; c < W; ++c) {
-      xv.v[c] = fma(alpha, pv.v[c], xv.v[c]);
-      pv.v[c] = fma(beta, pv.v[c], Pv.v[c] * rv.v[c]);
+    for (int h = 0; h < kVecUnroll; ++h) {
+      const long long iv = base + h * gs;
+      if (iv < nv) {
+        xv[h] = reinterpret_cast<const V*>(x)[iv];
+        rv[h] = reinterpret_cast<const V*>(r)[iv];
+        Pv[h] = reinterpret_cast<const V*>(P)[iv];
+        pv[h] = reinterpret_cast<const V*>(p)[iv];
+      }
     }
-    reinterpret_cast<V*>(x)[iv] = xv;
-    reinterpret_cast<V*>(p)[iv] = pv;
-    reinterpret_cast<V*>(q)[iv] = zero;
+#pragma unroll
+    for (int h = 0; h < kVecUnroll; ++h) {
+      const long long iv = base + h * gs;
+      if (iv >= nv) break;
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        xv[h].v[c] = fma(alpha, pv[h].v[c], xv[h].v[c]);
+        pv[h].v[c] = fma(beta, pv[h].v[c], Pv[h].v[c] * rv[h].v[c]);
+      }
+      reinterpret_cast<V*>(x)[iv] = xv[h];
+      reinterpret_cast<V*>(p)[iv] = pv[h];
+      reinterpret_cast<V*>(q)[iv] = zero;
+    }
   }
   for (long long i = nv * W + g0; i < nb; i += gs) {
     x[i] = fma(alpha, p[i], x[i]);
@@ -1054,13 +1084,13 @@ void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables
 
 template <typename T>
 void launch_pcg_update(long long nb, T* r, const T* q, const T* P, double* partials, PcgState* st, cudaStream_t s) {
-  k_pcg_update<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, q, P, partials, st);
+  k_pcg_update<T><<<num_sms() * 2, kVecThreads, 0, s>>>(nb, r, q, P, partials, st);
   sem_count_launch();
 }
 
 template <typename T>
 void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s) {
-  k_pcg_dir<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, r, p, q, P, st);
+  k_pcg_dir<T><<<num_sms() * 2, kVecThreads, 0, s>>>(nb, x, r, p, q, P, st);
   sem_count_launch();
 }
 
