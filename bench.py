@@ -10,7 +10,11 @@ timed region starts.
 
 Prints one JSON line (rank 0).  `value` is solve time per unknown (s/DOF,
 lower is better) over all ranks; every rank solves its own replica of the
-workload (weak scaling, no collective on the data path).
+workload (weak scaling, no collective on the data path).  On one GPU the
+default line also carries, measured after the timed region: the other
+points of the graded grid (`sweep`), the paper's operator and solver
+comparisons, the 64-problem batch (`batched64`) and the differentiable solve
+(`adjoint`), each with its own CUDA-event timing.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--p 8] [--impl ours|reference]
 """
@@ -630,6 +634,9 @@ def our_arm(args, rank, world, local_rank):
         if w.p <= 16:
             out["operator_variants"] = operator_variants(sem, w)
         out["paper_solvers"] = [paper_solvers(sem, pp) for pp in (8, 16)]
+        # the batched and differentiable workloads, also after the timed region
+        out["batched64"] = measure_batched(2, 1, rank, world, local_rank, ["fp64", "mixed"])
+        out["adjoint"] = measure_adjoint(3, 2, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ref_iters = reference_iterations(w)
         iters = res["fp64"]["info"]["iters"] if "fp64" in res else r["info"]["iters"]
@@ -650,13 +657,22 @@ def batched_arm(args, rank, world, local_rank):
     plain FP64 batch and the mixed-precision batch (FP32 CG with reliable
     updates, FP64 refinement decided on the device), the latter the headline."""
     import torch
-
-    from paper_1601_08179_gb300 import build, sem
+    from paper_1601_08179_gb300 import build
     build.build()
     torch.cuda.set_device(local_rank)
+    forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    out = measure_batched(args.steps, args.warmup, rank, world, local_rank, forms)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def measure_batched(steps, warmup, rank, world, local_rank, forms):
+    """The batched64 line (see batched_arm)."""
+    import torch
+
+    from paper_1601_08179_gb300 import sem
     work = si.batched_problems()
     dofs = sum(w.dofs for w in work)
-    forms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
     res = {}
     for form in forms:
         opts = sem.default_opts(precision=sem.PREC_MIXED) if form == "mixed" else None
@@ -669,7 +685,7 @@ def batched_arm(args, rank, world, local_rank):
             fs.append(torch.from_numpy(si.node_noise(c.n_nodes, replica_seed(w, rank))).cuda())
             us.append(torch.empty(c.n_nodes, dtype=torch.float64, device="cuda"))
         batch = sem.SemBatch(ctxs, fs, us)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             batch.solve()
         torch.cuda.synchronize()
         barrier(world)
@@ -677,19 +693,19 @@ def batched_arm(args, rank, world, local_rank):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local_rank) as clk:
             ev0.record()
-            for _ in range(args.steps):
+            for _ in range(steps):
                 st, infos = batch.solve()
             ev1.record()
             torch.cuda.synchronize()
         barrier(world)
-        res[form] = {"step_s": max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / args.steps, world), "infos": infos,
+        res[form] = {"step_s": max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / steps, world), "infos": infos,
                      "launches": sem.sem_launch_count() - l0, "clocks": clk.summary()}
         del batch, ctxs, fs, us
         torch.cuda.empty_cache()
     head = forms[-1]
     r = res[head]
     out = {"metric": METRIC + " (batched problems)", "value": whole_job_value(r["step_s"], dofs, world), "unit": UNIT,
-           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["step_s"] * 1e3,
+           "n_gpus": world, "steps": steps, "warmup": warmup, "ms_per_step": r["step_s"] * 1e3,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
            "config": {"workload": "batched64", "problems": len(work), "dofs_total": dofs,
@@ -706,19 +722,27 @@ def batched_arm(args, rank, world, local_rank):
         out["fp64"] = {"value": whole_job_value(p64["step_s"], dofs, world), "ms_per_step": p64["step_s"] * 1e3,
                        "iters_max": max(i["iters"] for i in p64["infos"]), "clocks": p64["clocks"]}
         out["speedup_vs_fp64"] = p64["step_s"] / r["step_s"]
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 def adjoint_arm(args, rank, world, local_rank):
     """Forward solve + backward (adjoint solve and gradient kernels) of the
     differentiable solve, J = 1/2 ||u - u_target||^2."""
     import torch
-
-    from paper_1601_08179_gb300 import build, sem
-    from paper_1601_08179_gb300.autograd import context_for, helmholtz_solve
+    from paper_1601_08179_gb300 import build
     build.build()
     torch.cuda.set_device(local_rank)
+    out = measure_adjoint(args.steps, args.warmup, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def measure_adjoint(steps, warmup, rank, world, local_rank):
+    """The adjoint line (see adjoint_arm)."""
+    import torch
+
+    from paper_1601_08179_gb300 import sem
+    from paper_1601_08179_gb300.autograd import context_for, helmholtz_solve
     w = si.ADJOINT
     hx, hy, hz = w.widths()
     ctx = context_for(w.p, hx, hy, hz, w.lam)
@@ -736,26 +760,25 @@ def adjoint_arm(args, rank, world, local_rank):
         J.backward()
         return float(J)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     barrier(world)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
         ev0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         ev1.record()
         torch.cuda.synchronize()
     barrier(world)
-    step_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / args.steps, world)
-    if rank == 0:
-        print(json.dumps({"metric": METRIC + " (forward + adjoint gradient)", "value": whole_job_value(step_s, w.dofs, world),
-                          "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                          "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak",
-                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "lambda": w.lam},
-                          "clocks": clk.summary()}), flush=True)
+    step_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3 / steps, world)
+    return {"metric": METRIC + " (forward + adjoint gradient)", "value": whole_job_value(step_s, w.dofs, world),
+            "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "p": w.p, "elements": list(w.m), "lambda": w.lam},
+            "clocks": clk.summary()}
 
 
 def oracle_record(w: si.Workload):
