@@ -236,6 +236,8 @@ def kernel_name(sem, ctx, precision: int, p: int) -> str:
         return "k_tpt_apply_slab"
     if kind == sem.KERNEL_ROW:
         return f"k_tpt_apply_row<{n}>"
+    if kind == sem.KERNEL_PENCIL:
+        return f"k_tpt_apply_pencil<{n}>"
     if kind == sem.KERNEL_WARP:
         return f"k_tpt_apply_warp<{t}, {n}>"
     if kind == sem.KERNEL_ELEMENT:

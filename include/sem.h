@@ -312,6 +312,11 @@ sem_status sem_gradients(sem_ctx* ctx, const double* w, const double* u, const d
  *                        reduce-adds (FP32, 2 <= n <= 8; vectors whose
  *                        addresses differ by a multiple of 16 bytes, else it
  *                        runs as PLANE)
+ *   SEM_KERNEL_PENCIL    a CTA holds 256 / n^2 elements: one thread per
+ *                        x-pencil (j, k) forms D^-1 x along i and the x-face
+ *                        outputs, then one thread per cube column (i, m)
+ *                        the y- and z-face outputs and the edge and vertex
+ *                        outputs (FP32, 5 <= n <= 8)
  * where n = p - 1.  SEM_KERNEL_AUTO resolves, in FP64, to ELEMENT at p = 2
  * and CTA_TILE otherwise; in FP32 to ELEMENT at p <= 3, PLANE for
  * 4 <= p <= 16 and SLAB for 17 <= p <= 32 (the fastest measured on GB300;
@@ -323,7 +328,8 @@ enum {
   SEM_KERNEL_PLANE = 3,
   SEM_KERNEL_ELEMENT = 4,
   SEM_KERNEL_SLAB = 5,
-  SEM_KERNEL_ROW = 6
+  SEM_KERNEL_ROW = 6,
+  SEM_KERNEL_PENCIL = 7
 };
 
 /* Selects the operator kernel of one precision: SEM_PREC_FP64 (the FP64

@@ -4,7 +4,7 @@ that kernel profiles capture.
     python -m paper_1601_08179_gb300.apply_loop --op plane --p 8 --reps 4
 
 --op names the FP32 mapping of the transformed condensed operator (plane,
-row, slab, elem, warp, cta, auto) or an FP64 form (tpt64, tpc, mmc), --p the degree
+pencil, row, slab, elem, warp, cta, auto) or an FP64 form (tpt64, tpc, mmc), --p the degree
 of the graded workload (the elements per direction follow the degree, as in
 bench.py).  The input is a seeded random vector; nothing is checked.  It
 prints the mean time of one application (CUDA events around the loop, after
@@ -27,7 +27,7 @@ def main(argv=None) -> None:
     from paper_1601_08179_gb300 import build, sem
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--op", default="plane",
-                    choices=["plane", "row", "slab", "elem", "warp", "cta", "auto", "tpt64", "tpc", "mmc"])
+                    choices=["plane", "pencil", "row", "slab", "elem", "warp", "cta", "auto", "tpt64", "tpc", "mmc"])
     ap.add_argument("--p", type=int, default=8, choices=list(si.SCALE_DEGREES))
     ap.add_argument("--reps", type=int, default=4)
     ap.add_argument("--atomic", action="store_true")
@@ -35,12 +35,12 @@ def main(argv=None) -> None:
     build.build()
     w = si.scale_workload(a.p)
     hx, hy, hz = w.widths()
-    f32 = a.op in ("plane", "row", "slab", "elem", "warp", "cta", "auto")
+    f32 = a.op in ("plane", "pencil", "row", "slab", "elem", "warp", "cta", "auto")
     opts = sem.default_opts(precision=sem.PREC_MIXED if f32 else sem.PREC_FP64, deterministic=0 if a.atomic else 1)
     ctx = sem.sem_setup(w.p, hx, hy, hz, w.lam, opts)
     gen = torch.Generator(device="cuda").manual_seed(1234)
     if f32:
-        kern = {"plane": sem.KERNEL_PLANE, "row": sem.KERNEL_ROW, "slab": sem.KERNEL_SLAB, "elem": sem.KERNEL_ELEMENT,
+        kern = {"plane": sem.KERNEL_PLANE, "pencil": sem.KERNEL_PENCIL, "row": sem.KERNEL_ROW, "slab": sem.KERNEL_SLAB, "elem": sem.KERNEL_ELEMENT,
                 "warp": sem.KERNEL_WARP, "cta": sem.KERNEL_CTA_TILE, "auto": sem.KERNEL_AUTO}[a.op]
         sem.sem_set_operator_kernel(ctx, sem.PREC_MIXED, kern)
         x = torch.randn(ctx.nb, dtype=torch.float32, device="cuda", generator=gen)

@@ -24,7 +24,7 @@ LIB = os.path.join(HERE, "libsemgb.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libsemgb_debug.so")
 SOURCES = ["sem_host.cpp", "sem_kernels.cu", "sem_apply.cu", "sem_apply_plane.cu", "sem_apply_slab.cu",
-           "sem_apply_elem.cu", "sem_apply_row.cu", "sem_compare.cu", "sem_api.cu"]
+           "sem_apply_elem.cu", "sem_apply_row.cu", "sem_apply_pencil.cu", "sem_compare.cu", "sem_api.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

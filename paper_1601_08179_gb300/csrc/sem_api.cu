@@ -1576,7 +1576,7 @@ sem_status tune_one(sem_ctx* c, const SemClassTables<T>& tab, const T* x, T* y, 
   };
   // the other work mappings that exist for this degree and precision
   const int def = sem_apply_default_kind(n, sizeof(T));
-  for (int kind : {kApplyWarp, kApplyPlane, kApplySlab, kApplyElement, kApplyRow}) {
+  for (int kind : {kApplyWarp, kApplyPlane, kApplySlab, kApplyElement, kApplyRow, kApplyPencil}) {
     if (kind == def) continue;
     st = consider(sem_apply_config_kind(kind));
     if (st != SEM_OK) return st;
@@ -1694,6 +1694,7 @@ extern "C" sem_status sem_debug_oob(long long* count, long long* first) {
   cudaError_t (*const take[])(unsigned long long*, long long*) = {sem_debug_take_kernels, sem_debug_take_apply,
                                                                  sem_debug_take_plane, sem_debug_take_slab,
                                                                  sem_debug_take_elem, sem_debug_take_row,
+                                                                 sem_debug_take_pencil,
                                                                  sem_debug_take_compare};
   for (auto fn : take) SEM_CUDA(fn(&n, &f));
   *count = (long long)n;

@@ -976,6 +976,8 @@ bool sem_apply_config_valid(int n, size_t elem_bytes, const ApplyConfig& c) {
       return elem_bytes == 4 && slab_supported(n);
     case kApplyRow:
       return elem_bytes == 4 && row_supported(n);
+    case kApplyPencil:
+      return elem_bytes == 4 && pencil_supported(n);
     default:
       return false;
   }
@@ -1076,6 +1078,10 @@ void launch_tpt_apply(const SemGeom& g, const SemBasis& b, const SemClassTables<
   int kind = explicit_cfg ? cfg->kind : sem_apply_default_kind(g.n, sizeof(T));
   if constexpr (sizeof(T) == 4) {
     if ((kind == kApplyPlane || kind == kApplySlab) && t.plane == nullptr) kind = kApplyCta;   // tables not built (cannot happen via the API)
+    if (kind == kApplyPencil && t.plane != nullptr) {
+      launch_pencil_apply(g, t, x, y, partials, st, s);
+      return;
+    }
     if (kind == kApplyRow) {
       if (row_usable(g, x, y)) {
         launch_row_apply(g, b, t, x, y, partials, st, s);

@@ -13,7 +13,8 @@ enum ApplyKind {
                        // one element per warp, half rows (FP32, 9 <= n <= 15)
   kApplyElement = 4,   // one thread per element (n = 1; FP32 also n = 2, 3)
   kApplySlab = 5,      // element x slab of 8 planes k per CTA (FP32, 16 <= n <= 31)
-  kApplyRow = 6        // x-row segment of up to 32 elements per CTA, bulk copies (FP32, 2 <= n <= 8)
+  kApplyRow = 6,       // x-row segment of up to 32 elements per CTA, bulk copies (FP32, 2 <= n <= 8)
+  kApplyPencil = 7     // thread per x-pencil, then per cube column (FP32, 5 <= n <= 8)
 };
 
 // Operator launch configuration.
@@ -53,6 +54,13 @@ void launch_plane_apply(const SemGeom& g, const SemClassTables<float>& t, const 
 // plane_layout(n)); same contract as launch_tpt_apply.
 void launch_slab_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
                        double* partials, PcgState* st, cudaStream_t s);
+
+// Degrees served by the pencil kernel (sem_apply_pencil.cu): 5 <= n <= 8.
+bool pencil_supported(int n);
+// y += Hhat~ x with the pencil kernel (class blocks of plane_layout(n));
+// same contract as launch_tpt_apply.
+void launch_pencil_apply(const SemGeom& g, const SemClassTables<float>& t, const float* x, float* y,
+                         double* partials, PcgState* st, cudaStream_t s);
 
 // Degrees served by the row kernel (sem_apply_row.cu).
 inline bool row_supported(int n) { return n >= 2 && n <= 8; }
@@ -206,6 +214,7 @@ cudaError_t sem_debug_take_plane(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_slab(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_elem(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_row(unsigned long long* count, long long* first);
+cudaError_t sem_debug_take_pencil(unsigned long long* count, long long* first);
 cudaError_t sem_debug_take_compare(unsigned long long* count, long long* first);
 #endif
 

@@ -334,8 +334,9 @@ def sem_gradients(ctx: SemContext, w, u, f, df, stream=None):
 
 
 KERNEL_AUTO, KERNEL_CTA_TILE, KERNEL_WARP, KERNEL_PLANE, KERNEL_ELEMENT, KERNEL_SLAB, KERNEL_ROW = 0, 1, 2, 3, 4, 5, 6
+KERNEL_PENCIL = 7
 KERNEL_NAMES = {KERNEL_CTA_TILE: "cta_tile", KERNEL_WARP: "warp", KERNEL_PLANE: "plane", KERNEL_ELEMENT: "element",
-                KERNEL_SLAB: "slab", KERNEL_ROW: "row"}
+                KERNEL_SLAB: "slab", KERNEL_ROW: "row", KERNEL_PENCIL: "pencil"}
 
 
 def sem_set_operator_kernel(ctx: SemContext, precision: int, kind: int, epb: int = 0, ks: int = 0):

@@ -36,11 +36,11 @@ def oracle_apply(ms, lam, ut):
 
 out = {"applies": [], "solves": []}
 K = {"AUTO": sem.KERNEL_AUTO, "WARP": sem.KERNEL_WARP, "PLANE": sem.KERNEL_PLANE,
-     "ELEMENT": sem.KERNEL_ELEMENT, "SLAB": sem.KERNEL_SLAB, "ROW": sem.KERNEL_ROW}
+     "ELEMENT": sem.KERNEL_ELEMENT, "SLAB": sem.KERNEL_SLAB, "ROW": sem.KERNEL_ROW, "PENCIL": sem.KERNEL_PENCIL}
 # FP64: the built-in kernel (thread per element at p = 2, CTA tile above)
 cases = [(2, (3, 2, 2), ["AUTO"], ["ELEMENT"]), (3, (1, 3, 2), ["AUTO"], ["ELEMENT", "PLANE", "ROW"]),
          (4, (3, 2, 2), ["AUTO"], ["PLANE", "ELEMENT", "WARP", "ROW"]),
-         (8, (2, 2, 3), ["AUTO"], ["PLANE", "WARP", "ROW"]),
+         (8, (2, 2, 3), ["AUTO"], ["PLANE", "WARP", "ROW", "PENCIL"]),
          (12, (2, 1, 2), ["AUTO"], ["PLANE"]), (20, (2, 2, 1), ["AUTO"], ["SLAB"])]
 for p, m, k64, k32 in cases:
     ar = 1.0 if m[0] == 1 else 4.0
