@@ -867,8 +867,10 @@ __device__ __forceinline__ void plane2_element(float* W, const int* H, float* __
   }
 }
 
-// One element per warp; the same two-stage gather pipeline as the one-row
-// kernel.  v += Hhat~ u; returns the thread's share of u^T v.
+// One element per warp; a two-stage gather pipeline: while one element is
+// computed, the next element's offsets are formed and its gather is in flight
+// into a second buffer (measured faster here than one buffer, unlike the
+// one-row kernel above).  v += Hhat~ u; returns the thread's share of u^T v.
 template <int N>
 __device__ __forceinline__ float plane2_apply_all(const SemGeom& g, const SemClassTables<float>& tab,
                                                   const EntityAffine* ent, const float* __restrict__ u,
