@@ -126,7 +126,11 @@ typedef struct {
                          step is taken only where z fits (N_B up to 200 KB of FP32
                          per SM: 7.78e6 on 152 SMs); batched solves, larger N_B, or a
                          device or graph that cannot take the cooperative launch
-                         run two kernels. */
+                         run two kernels.  The step holds every SM: single mixed
+                         solves of several contexts running concurrently on one
+                         GPU should set 0 (otherwise their grids can wait on each
+                         other until the barrier's bounded wait gives up and the
+                         solve fails with SEM_EBREAKDOWN and a message naming it). */
 } sem_opts;
 
 /* Result of a solve. */
