@@ -685,9 +685,11 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
     partials[G + blockIdx.x] = v[1];
   }
   if (!step_barrier(st)) {
+    // the CG stops as a breakdown whatever CTA 0 records after a late barrier
+    // (its record is a compare-and-swap from 0)
     if (threadIdx.x == 0) {
-      st->bar_fail = 1;
-      st->done = 2;
+      atomicExch(&st->bar_fail, 1);
+      atomicExch(&st->done, 2);
     }
     return;
   }
@@ -724,7 +726,7 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
       st->rho = RZ;
     }
     st->xpend = done != 0 ? 1 : 0;   // a stopped CG owes x += alpha p (flush or refinement fold)
-    st->done = done;
+    atomicCAS(&st->done, 0, done);   // a CTA whose barrier wait ran out has already set 2
   }
   if (done != 0) return;
   // ---- x += alpha p, p = z + beta p, q = 0
