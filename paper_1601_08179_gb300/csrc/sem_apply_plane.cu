@@ -112,6 +112,50 @@ __device__ __forceinline__ void reduce_scatter(const float (&W)[G], float cj, fl
   *y1 = P1[0];
 }
 
+// Sums P[i] and sigma_j P[i] over the G lanes of a group (sigma_j = (-1)^j,
+// j = lane), lane jl ending with the two sums for i = jl.  The first halving
+// step pairs lanes of opposite parity and forms P_j + P_{j^1} and
+// P_j - P_{j^1} (the second is the pair's signed sum up to sigma_j); the
+// later steps pair lanes of equal parity, so both sums just add; the sign
+// sigma_jl is applied at the end.
+template <int G>
+__device__ __forceinline__ void reduce_scatter_parity(const float (&P)[G], int jl, float* y0, float* y1) {
+  const bool odd = (jl & 1) != 0;
+  float s[G / 2], d[G / 2];   // index i = 2 t + (jl & 1)
+#pragma unroll
+  for (int t = 0; t < G / 2; ++t) {
+    const float keep = odd ? P[2 * t + 1] : P[2 * t], send = odd ? P[2 * t] : P[2 * t + 1];
+    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+    s[t] = keep + recv;
+    d[t] = keep - recv;
+  }
+  float S, D;
+  if constexpr (G == 8) {
+    const bool up = (jl & 2) != 0;
+    float s2[2], d2[2];   // index i = 4 u + 2 up + (jl & 1)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float ks = up ? s[2 * u + 1] : s[2 * u], ss = up ? s[2 * u] : s[2 * u + 1];
+      const float kd = up ? d[2 * u + 1] : d[2 * u], sd = up ? d[2 * u] : d[2 * u + 1];
+      s2[u] = ks + __shfl_xor_sync(0xffffffffu, ss, 2);
+      d2[u] = kd + __shfl_xor_sync(0xffffffffu, sd, 2);
+    }
+    const bool hi = (jl & 4) != 0;
+    const float ks = hi ? s2[1] : s2[0], ss = hi ? s2[0] : s2[1];
+    const float kd = hi ? d2[1] : d2[0], sd = hi ? d2[0] : d2[1];
+    S = ks + __shfl_xor_sync(0xffffffffu, ss, 4);
+    D = kd + __shfl_xor_sync(0xffffffffu, sd, 4);
+  } else {
+    const bool up = (jl & 2) != 0;
+    const float ks = up ? s[1] : s[0], ss = up ? s[0] : s[1];
+    const float kd = up ? d[1] : d[0], sd = up ? d[0] : d[1];
+    S = ks + __shfl_xor_sync(0xffffffffu, ss, 2);
+    D = kd + __shfl_xor_sync(0xffffffffu, sd, 2);
+  }
+  *y0 = S;
+  *y1 = odd ? -D : D;
+}
+
 // Offsets of the element's 26 entities (-1: Dirichlet entity or no element)
 // and its class (fallback for a missing element) into H[0..26].
 template <int G>
@@ -182,12 +226,23 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
   const int j = act ? jl : N - 1;
     // ---- per-element constants of this lane
     const float w0 = Cf[PS + 32], w02 = Cf[PS + 33], d0 = Cf[PS + 34];
-    float a[RS], b[RS], l1[RS], e4[RS], e5[RS];
+    // The 1D border vectors are centro-symmetric: K~_{Ip}[c] = (-1)^c K~_{I0}[c]
+    // (the GLL points and the interior eigenproblem are symmetric under
+    // x -> -x, so eigenvector c is even or odd with c; canonical signs), hence
+    // b_i = (-1)^i a_i, d_j = (-1)^j c_j and g_k = (-1)^k e_k: each pair of
+    // expansion terms is one term, and each pair of contractions a sum over
+    // the even and one over the odd indices.
+    float a[RS], l1[RS], e45p[RS], e45m[RS];   // e45p/m = z-face rows j: F4 + F5, F4 - F5
     load_row<RS>(Cf + PA, a);
-    load_row<RS>(Cf + PB, b);
     load_row<RS>(Cf + PL1, l1);
-    load_row<RS>(Fp + 4 * FS + j * RS, e4);   // z-face rows j
-    load_row<RS>(Fp + 5 * FS + j * RS, e5);
+    load_row<RS>(Fp + 4 * FS + j * RS, e45p);
+    load_row<RS>(Fp + 5 * FS + j * RS, e45m);
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+      const float f4 = e45p[i], f5 = e45m[i];
+      e45p[i] = f4 + f5;
+      e45m[i] = f4 - f5;
+    }
     const float4 qj = *reinterpret_cast<const float4*>(Cf + PQ + 4 * j);
     const float cj = act ? qj.x : 0.f, dj = act ? qj.y : 0.f;
     const float l2j = Cf[PL2 + j], sj = d0 + l2j;
@@ -198,18 +253,18 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
       ey[q] = W[S::EX + (4 + q) * RS + j];
       ex[q] = W[S::EX + q * RS + j];
     }
-    float fc[6], cO[6];
+    float fc[6], cO[6];   // [4], [5] (z-faces) are read after the walk
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < 4; ++q) {
       cO[q] = Cf[PS + q];
       fc[q] = Cf[PS + 6 + q];
     }
-    float z4[RS], z5[RS];
+    float ze[RS], zo[RS];   // z-contraction over even and over odd k
 #pragma unroll
-    for (int i = 0; i < RS; ++i) z4[i] = z5[i] = 0.f;
-    // line sums along k for the edges: sx[2 sa + sc] = sum_k (e|g)_k F_sa[k][j],
-    // sy[2 sb + sc] = sum_k (e|g)_k F_{2+sb}[k][i = jl]
-    float sx[4] = {0.f, 0.f, 0.f, 0.f}, sy[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = 0; i < RS; ++i) ze[i] = zo[i] = 0.f;
+    // line sums along k for the edges, over even and over odd k:
+    // sx[2 sa + sc] = sum_k (e|g)_k F_sa[k][j], sy[2 sb + sc] = sum_k (e|g)_k F_{2+sb}[k][i = jl]
+    float le[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};   // e_k times A, B, Cl, Dl
     const int ox0 = H[0], ox1 = H[1], oy0 = H[2], oy1 = H[3];
 
     // ---- walk the y-plane j in k: expansion, D^-1, contractions; x- and
@@ -225,35 +280,38 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
       load_row<RS>(Fp + 2 * FS + k * RS, Cr);
       load_row<RS>(Fp + 3 * FS + k * RS, Dr);
       const float sjk = sj + l3k;
-      float X0 = 0.f, X1 = 0.f;
-      float Wr[G];   // D^-1 x along the row
+      const float ABp = A + B, ABm = A - B;   // a_i A + b_i B = a_i (A +- B)
+      float Xe = 0.f, Xo = 0.f;
+      float Pr[G];   // c_j D^-1 x along the row
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        float x = a[i] * A;
-        x = fmaf(b[i], B, x);
+        float x = a[i] * ((i & 1) ? ABm : ABp);
         x = fmaf(cj, Cr[i], x);
         x = fmaf(dj, Dr[i], x);
-        x = fmaf(ek, e4[i], x);
-        x = fmaf(gk, e5[i], x);
+        x = fmaf(ek, (k & 1) ? e45m[i] : e45p[i], x);   // e_k F4 + g_k F5
         const float w = x * rcp_approx(sjk + l1[i]);   // D^-1 x (the sign is applied at the outputs)
-        X0 = fmaf(a[i], w, X0);
-        X1 = fmaf(b[i], w, X1);
-        z4[i] = fmaf(ek, w, z4[i]);
-        z5[i] = fmaf(gk, w, z5[i]);
-        Wr[i] = w;
+        if (i & 1) Xo = fmaf(a[i], w, Xo);
+        else Xe = fmaf(a[i], w, Xe);
+        if (k & 1) zo[i] = fmaf(ek, w, zo[i]);
+        else ze[i] = fmaf(ek, w, ze[i]);
+        Pr[i] = cj * w;
       }
 #pragma unroll
-      for (int i = N; i < G; ++i) Wr[i] = 0.f;
+      for (int i = N; i < G; ++i) Pr[i] = 0.f;
+      const float X0 = Xe + Xo, X1 = Xe - Xo;
       float Y0, Y1;
-      reduce_scatter<G>(Wr, cj, dj, jl, &Y0, &Y1);
-      sx[0] = fmaf(ek, A, sx[0]);
-      sx[1] = fmaf(gk, A, sx[1]);
-      sx[2] = fmaf(ek, B, sx[2]);
-      sx[3] = fmaf(gk, B, sx[3]);
-      sy[0] = fmaf(ek, Cl, sy[0]);
-      sy[1] = fmaf(gk, Cl, sy[1]);
-      sy[2] = fmaf(ek, Dl, sy[2]);
-      sy[3] = fmaf(gk, Dl, sy[3]);
+      reduce_scatter_parity<G>(Pr, jl, &Y0, &Y1);
+      if (k & 1) {
+        lo[0] = fmaf(ek, A, lo[0]);
+        lo[1] = fmaf(ek, B, lo[1]);
+        lo[2] = fmaf(ek, Cl, lo[2]);
+        lo[3] = fmaf(ek, Dl, lo[3]);
+      } else {
+        le[0] = fmaf(ek, A, le[0]);
+        le[1] = fmaf(ek, B, le[1]);
+        le[2] = fmaf(ek, Cl, le[2]);
+        le[3] = fmaf(ek, Dl, le[3]);
+      }
       if (act) {
         const int kj = k * N + j;
         // x-faces at (k, j): diagonal, opposite face, the four edge lines, -condensed
@@ -294,6 +352,26 @@ __device__ __forceinline__ void plane_element(float* W, const int* H, float* __r
         }
       }
     }
+
+    // z-face rows j again, and the even/odd sums combined
+    float b[RS], e4[RS], e5[RS];
+    cO[4] = Cf[PS + 4];
+    cO[5] = Cf[PS + 5];
+    fc[4] = Cf[PS + 10];
+    fc[5] = Cf[PS + 11];
+    load_row<RS>(Cf + PB, b);
+    load_row<RS>(Fp + 4 * FS + j * RS, e4);
+    load_row<RS>(Fp + 5 * FS + j * RS, e5);
+    float (&z4)[RS] = ze;   // in place: z4 = ze + zo, z5 = ze - zo
+    float (&z5)[RS] = zo;
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+      const float t = ze[i];
+      z4[i] = t + zo[i];
+      z5[i] = t - z5[i];
+    }
+    const float sx[4] = {le[0] + lo[0], le[0] - lo[0], le[1] + lo[1], le[1] - lo[1]};
+    const float sy[4] = {le[2] + lo[2], le[2] - lo[2], le[3] + lo[3], le[3] - lo[3]};
 
     // ---- z-faces at (j, i).  The outputs of row j are formed in lane j and
     //      staged in the (no longer needed) z-face rows of shared memory, then
