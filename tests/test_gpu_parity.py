@@ -42,13 +42,14 @@ def test_basis_matches_oracle(p):
     lo, Vo = transform.eigenbasis(p)
     np.testing.assert_allclose(lam, lo, rtol=1e-12)
     np.testing.assert_allclose(V, Vo, atol=1e-11 * np.abs(Vo).max())
-    # the FP32 operator kernels use K~_{Ip}[c] = (-1)^c K~_{I0}[c] (a symmetric
-    # basis with canonical signs): the library's basis has it
+    # the FP32 plane kernel uses K~_{Ip}[c] = (-1)^c K~_{I0}[c] (a symmetric
+    # basis with canonical signs): the library's basis has it, to rounding that
+    # grows with p (the FP64 kernels keep both vectors)
     from oracle.gll import mass_stiffness
     _, K = mass_stiffness(p)
     k0, k1 = V.T @ K[1:p, 0], V.T @ K[1:p, p]
     sign = (-1.0) ** np.arange(p - 1)
-    np.testing.assert_allclose(k1, sign * k0, atol=1e-12 * np.abs(k0).max())
+    np.testing.assert_allclose(k1, sign * k0, rtol=0, atol=3e-11 * np.abs(k0).max())
 
 
 @pytest.mark.parametrize("p,m", [(2, (2, 3, 2)), (3, (1, 2, 3)), (5, (2, 2, 2))])
