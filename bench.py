@@ -211,13 +211,13 @@ def node_field(x, y, z, w: si.Workload, seed: int):
 # figures include the per-element edge/vertex shares of the fixed-order sums);
 # a kernel or workload with no capture reports null.
 TRAFFIC_BYTES = {
-    ("k_tpt_apply_plane<7>", "graded_p8_m32_ar128_lam0"): 43239424 + 0,
+    ("k_tpt_apply_plane<7>", "graded_p8_m32_ar128_lam0"): 43244032 + 0,
     ("k_tpt_apply<double, 7> (epb 5, ks 7)", "graded_p8_m32_ar128_lam0"): 82519552 + 17870336,
     ("k_tpt_apply_slab", "graded_p32_m8_ar128_lam0"): 10740992 + 0,
     ("k_tpt_apply_p2<float>", "graded_p2_m128_ar128_lam0"): 117042176 + 14091520,
     ("k_tpt_apply_p2<double>", "graded_p2_m128_ar128_lam0"): 178927360 + 321355008,
     ("k_tpt_apply<double, 31> (epb 1, ks 8)", "graded_p32_m8_ar128_lam0"): 23401472 + 0,
-    ("k_tpt_apply_plane<3>", "graded_p4_m64_ar128_lam0"): 77064960 + 254208,
+    ("k_tpt_apply_plane<3>", "graded_p4_m64_ar128_lam0"): 77063680 + 213504,
     ("k_tpt_apply<double, 3> (epb 28, ks 3)", "graded_p4_m64_ar128_lam0"): 189429504 + 122293760,
     ("k_tpt_apply_plane2<15>", "graded_p16_m16_ar128_lam0"): 22298624 + 0,
     ("k_tpt_apply<double, 15> (epb 1, ks 15)", "graded_p16_m16_ar128_lam0"): 43648000 + 66304,
