@@ -215,7 +215,8 @@ sem_status sem_recover_interior(sem_ctx* ctx, const double* f, const double* uB,
 
 /* Full solve (Algorithm 4): condense the load, CG with the BT preconditioner
  * to opts.rtol, recover the interior.  With opts.precision = SEM_PREC_MIXED the
- * CG runs in FP32 (FP32 operator, vectors and preconditioner) inside FP64
+ * CG runs in FP32 (FP32 operator and vectors, the preconditioner stored in
+ * BF16) inside FP64
  * iterative refinement: every refinement step adds the FP32 correction to the
  * FP64 iterate x and recomputes the residual r = b - A x with the FP64
  * operator and FP64 dot products (see opts.mixed_scheme); the stopping rule

@@ -104,7 +104,8 @@ struct sem_ctx {
   SemClassTables<double> tab{};
 
   // mixed precision (FP32 inner CG), allocated on first use
-  float *d_dcoef_f = nullptr, *d_dinv_f = nullptr, *d_P32 = nullptr;
+  float *d_dcoef_f = nullptr, *d_dinv_f = nullptr;
+  prec_t<float>* d_P32 = nullptr;     // the FP32 CG's BT preconditioner (BF16)
   float *d_b32 = nullptr, *d_x32 = nullptr, *d_r32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr;
   PcgState* d_st32 = nullptr;
   MixedCtl* d_ctl = nullptr;           // device-side refinement control (graph-replayed mixed solves)
@@ -218,7 +219,7 @@ sem_status cast_tables_f32(sem_ctx* c, cudaStream_t s) {
   if (c->d_coef_soa_f != nullptr) launch_coef_soa<float>(g, c->d_coef_f, c->d_coef_soa_f, coef_offsets(1).stride, s);
   if (c->d_plane != nullptr) launch_plane_coeffs(g, c->h1.basis, c->d_dcoef, c->d_plane, s);
   if (c->d_plane_soa != nullptr) launch_coef_soa<float>(g, c->d_plane, c->d_plane_soa, plane_layout(g.n).stride, s);
-  launch_cast_f32(g.nb, c->d_P, c->d_P32, s);
+  launch_cast_prec32(g.nb, c->d_P, c->d_P32, s);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
 }
@@ -255,7 +256,8 @@ sem_status ensure_mixed(sem_ctx* c) {
   if (st != SEM_OK) return st;
   // operator kernel attributes outside any capture
   SEM_CUDA(cudaMemsetAsync(c->d_q32, 0, sizeof(float) * g.nb, c->stream));
-  launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_P32, c->d_q32, nullptr, nullptr, c->stream);
+  SEM_CUDA(cudaMemsetAsync(c->d_x32, 0, sizeof(float) * g.nb, c->stream));
+  launch_tpt_apply<float>(g, c->h1.basis, c->tab_f, c->d_x32, c->d_q32, nullptr, nullptr, c->stream);
   SEM_CUDA(cudaGetLastError());
   SEM_CUDA(prepare_pcg_step<float>(g.nb, &c->step_ok));
   return SEM_OK;

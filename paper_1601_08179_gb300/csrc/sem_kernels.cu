@@ -382,16 +382,20 @@ struct alignas(sizeof(T) * W) Pack {
   T v[W];
 };
 
+// A preconditioner entry in the arithmetic type of its CG.
+__device__ __forceinline__ double pval(double v) { return v; }
+__device__ __forceinline__ float pval(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restrict__ p,
-           T* __restrict__ q, T* __restrict__ x, const T* __restrict__ P,
+           T* __restrict__ q, T* __restrict__ x, const prec_t<T>* __restrict__ P,
            double* __restrict__ partials, PcgState* st, double rtol, int maxit, int keep_x, int have_q) {
   T rz = T(0), rr = T(0), bb = T(0);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
     const T bi = b[i];
     const T ri = have_q ? bi - q[i] : bi;
-    const T zi = P[i] * ri;
+    const T zi = pval(P[i]) * ri;
     r[i] = ri;
     p[i] = zi;
     q[i] = T(0);
@@ -427,11 +431,12 @@ k_pcg_init(long long nb, const T* __restrict__ b, T* __restrict__ r, T* __restri
 // k_pcg_flush or by the refinement fold.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads, 2)
-k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* __restrict__ P,
+k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const prec_t<T>* __restrict__ P,
              double* __restrict__ partials, PcgState* st) {
   if (st->done) return;
   constexpr int W = 16 / sizeof(T);
   using V = Pack<T, W>;
+  using PV = Pack<prec_t<T>, W>;  // W preconditioner entries (8 bytes in BF16)
   const T alpha = (T)st->alpha;
   T rz = T(0), rr = T(0);
   const long long nv = nb / W;
@@ -439,14 +444,15 @@ k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* 
   // kVecUnroll packs per thread per trip, all loads issued first (memory
   // latency, not bandwidth, bounds a one-pack loop)
   for (long long base = g0; base < nv; base += kVecUnroll * gs) {
-    V rv[kVecUnroll], qv[kVecUnroll], Pv[kVecUnroll];
+    V rv[kVecUnroll], qv[kVecUnroll];
+    PV Pv[kVecUnroll];
 #pragma unroll
     for (int h = 0; h < kVecUnroll; ++h) {
       const long long iv = base + h * gs;
       if (iv < nv) {
         rv[h] = reinterpret_cast<const V*>(r)[iv];
         qv[h] = reinterpret_cast<const V*>(q)[iv];
-        Pv[h] = reinterpret_cast<const V*>(P)[iv];
+        Pv[h] = reinterpret_cast<const PV*>(P)[iv];
       }
     }
 #pragma unroll
@@ -457,7 +463,7 @@ k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* 
       for (int c = 0; c < W; ++c) {
         const T ri = fma(-alpha, qv[h].v[c], rv[h].v[c]);
         rv[h].v[c] = ri;
-        rz = fma(ri, Pv[h].v[c] * ri, rz);
+        rz = fma(ri, pval(Pv[h].v[c]) * ri, rz);
         rr = fma(ri, ri, rr);
       }
       reinterpret_cast<V*>(r)[iv] = rv[h];
@@ -466,7 +472,7 @@ k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* 
   for (long long i = nv * W + g0; i < nb; i += gs) {
     const T ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
-    rz = fma(ri, P[i] * ri, rz);
+    rz = fma(ri, pval(P[i]) * ri, rz);
     rr = fma(ri, ri, rr);
   }
   double v[2] = {(double)rz, (double)rr}, tot[2];
@@ -497,10 +503,11 @@ k_pcg_update(long long nb, T* __restrict__ r, const T* __restrict__ q, const T* 
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads, 2)
 k_pcg_dir(long long nb, T* __restrict__ x, const T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
-          const T* __restrict__ P, PcgState* st) {
+          const prec_t<T>* __restrict__ P, PcgState* st) {
   if (st->done) return;
   constexpr int W = 16 / sizeof(T);
   using V = Pack<T, W>;
+  using PV = Pack<prec_t<T>, W>;  // W preconditioner entries (8 bytes in BF16)
   const T alpha = (T)st->alpha, beta = (T)st->beta;
   const long long nv = nb / W;
   const long long g0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
@@ -508,14 +515,15 @@ k_pcg_dir(long long nb, T* __restrict__ x, const T* __restrict__ r, T* __restric
 #pragma unroll
   for (int c = 0; c < W; ++c) zero.v[c] = T(0);
   for (long long base = g0; base < nv; base += kVecUnroll * gs) {
-    V xv[kVecUnroll], rv[kVecUnroll], Pv[kVecUnroll], pv[kVecUnroll];
+    V xv[kVecUnroll], rv[kVecUnroll], pv[kVecUnroll];
+    PV Pv[kVecUnroll];
 #pragma unroll
     for (int h = 0; h < kVecUnroll; ++h) {
       const long long iv = base + h * gs;
       if (iv < nv) {
         xv[h] = reinterpret_cast<const V*>(x)[iv];
         rv[h] = reinterpret_cast<const V*>(r)[iv];
-        Pv[h] = reinterpret_cast<const V*>(P)[iv];
+        Pv[h] = reinterpret_cast<const PV*>(P)[iv];
         pv[h] = reinterpret_cast<const V*>(p)[iv];
       }
     }
@@ -526,7 +534,7 @@ k_pcg_dir(long long nb, T* __restrict__ x, const T* __restrict__ r, T* __restric
 #pragma unroll
       for (int c = 0; c < W; ++c) {
         xv[h].v[c] = fma(alpha, pv[h].v[c], xv[h].v[c]);
-        pv[h].v[c] = fma(beta, pv[h].v[c], Pv[h].v[c] * rv[h].v[c]);
+        pv[h].v[c] = fma(beta, pv[h].v[c], pval(Pv[h].v[c]) * rv[h].v[c]);
       }
       reinterpret_cast<V*>(x)[iv] = xv[h];
       reinterpret_cast<V*>(p)[iv] = pv[h];
@@ -535,7 +543,7 @@ k_pcg_dir(long long nb, T* __restrict__ x, const T* __restrict__ r, T* __restric
   }
   for (long long i = nv * W + g0; i < nb; i += gs) {
     x[i] = fma(alpha, p[i], x[i]);
-    p[i] = fma(beta, p[i], P[i] * r[i]);
+    p[i] = fma(beta, p[i], pval(P[i]) * r[i]);
     q[i] = T(0);
   }
 }
@@ -611,13 +619,14 @@ static __device__ bool step_barrier(PcgState* st) {
 template <typename T>
 __global__ void __launch_bounds__(kStepThreads, 1)
 k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p, T* __restrict__ q,
-           const T* __restrict__ P, double* __restrict__ partials, PcgState* st) {
+           const prec_t<T>* __restrict__ P, double* __restrict__ partials, PcgState* st) {
   extern __shared__ __align__(16) unsigned char step_smem[];
   __shared__ double tot_sh[2];
   __shared__ double red_sh[2 * 32];
   if (st->done) return;   // read by every CTA before the barrier; written after it
   constexpr int W = 16 / sizeof(T);
   using V = Pack<T, W>;
+  using PV = Pack<prec_t<T>, W>;  // W preconditioner entries (8 bytes in BF16)
   V* zs = reinterpret_cast<V*>(step_smem);
   const T alpha = (T)st->alpha;
   const double rho = st->rho, tol2 = st->tol2, trig2 = st->trig2;
@@ -632,14 +641,15 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
   //      halves are bound by memory latency, not by instruction issue
   T rz = T(0), rr = T(0);
   for (long long base = c0 + threadIdx.x; base < c1; base += kStepUnroll * kStepThreads) {
-    V rv[kStepUnroll], qv[kStepUnroll], Pv[kStepUnroll];
+    V rv[kStepUnroll], qv[kStepUnroll];
+    PV Pv[kStepUnroll];
 #pragma unroll
     for (int h = 0; h < kStepUnroll; ++h) {
       const long long ih = base + (long long)h * kStepThreads;
       if (ih < c1) {
         rv[h] = reinterpret_cast<const V*>(r)[ih];
         qv[h] = reinterpret_cast<const V*>(q)[ih];
-        Pv[h] = reinterpret_cast<const V*>(P)[ih];
+        Pv[h] = reinterpret_cast<const PV*>(P)[ih];
       }
     }
 #pragma unroll
@@ -651,7 +661,7 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
       for (int c = 0; c < W; ++c) {
         const T ri = fma(-alpha, qv[h].v[c], rv[h].v[c]);
         rv[h].v[c] = ri;
-        zv.v[c] = Pv[h].v[c] * ri;
+        zv.v[c] = pval(Pv[h].v[c]) * ri;
         rz = fma(ri, zv.v[c], rz);
         rr = fma(ri, ri, rr);
       }
@@ -663,7 +673,7 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
     for (long long i = nv * W + threadIdx.x; i < nb; i += kStepThreads) {
       const T ri = fma(-alpha, q[i], r[i]);
       r[i] = ri;
-      rz = fma(ri, P[i] * ri, rz);
+      rz = fma(ri, pval(P[i]) * ri, rz);
       rr = fma(ri, ri, rr);
     }
   }
@@ -763,7 +773,7 @@ k_pcg_step(long long nb, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p
   if (tail_cta) {
     for (long long i = nv * W + threadIdx.x; i < nb; i += kStepThreads) {
       x[i] = fma(alpha, p[i], x[i]);
-      p[i] = fma(bt, p[i], P[i] * r[i]);
+      p[i] = fma(bt, p[i], pval(P[i]) * r[i]);
       q[i] = T(0);
     }
   }
@@ -895,14 +905,14 @@ k_mixed_residual(long long nb, const double* __restrict__ b, const double* __res
 // replacement): r32 = r, rho' = r32 . P r32, beta = rho' / rho (0 when the
 // direction restarts), rr, the next trigger delta^2 rr, done = 0.
 __global__ void __launch_bounds__(kVecThreads)
-k_mixed_rebase(long long nb, const double* __restrict__ r, const float* __restrict__ P, float* __restrict__ r32,
+k_mixed_rebase(long long nb, const double* __restrict__ r, const prec_t<float>* __restrict__ P, float* __restrict__ r32,
                double* __restrict__ partials, MixedCtl* ctl, PcgState* st32) {
   if (ctl->phase != 2) return;
   float rz = 0.f, rr = 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
     const float ri = (float)r[i];
     r32[i] = ri;
-    rz = fmaf(ri, P[i] * ri, rz);
+    rz = fmaf(ri, pval(P[i]) * ri, rz);
     rr = fmaf(ri, ri, rr);
   }
   double v[2] = {(double)rz, (double)rr}, tot[2];
@@ -918,13 +928,18 @@ k_mixed_rebase(long long nb, const double* __restrict__ r, const float* __restri
 // Phase 2: p = P r32 + beta p, q = 0 (the direction step of the replaced residual).
 __global__ void __launch_bounds__(kVecThreads)
 k_mixed_dir(long long nb, const float* __restrict__ r32, float* __restrict__ p, float* __restrict__ q,
-            const float* __restrict__ P, const MixedCtl* ctl, const PcgState* st32) {
+            const prec_t<float>* __restrict__ P, const MixedCtl* ctl, const PcgState* st32) {
   if (ctl->phase != 2 || st32->done != 0) return;
   const float beta = (float)st32->beta;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
-    p[i] = fmaf(beta, p[i], P[i] * r32[i]);
+    p[i] = fmaf(beta, p[i], pval(P[i]) * r32[i]);
     q[i] = 0.f;
   }
+}
+
+__global__ void k_to_prec32(long long nb, const double* __restrict__ in, prec_t<float>* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x)
+    out[i] = __double2bfloat16(in[i]);
 }
 
 __global__ void k_scale_to_f32(long long nb, const double* __restrict__ in, double scale, float* __restrict__ out) {
@@ -968,6 +983,11 @@ int sem_vec_blocks() { return num_sms() * 4; }
 // ---------------------------------------------------------------------------
 void launch_cast_f32(long long n, const double* in, float* out, cudaStream_t s) {
   k_scale_to_f32<<<grid_for(n, 256), 256, 0, s>>>(n, in, 1.0, out);
+  sem_count_launch();
+}
+
+void launch_cast_prec32(long long n, const double* in, prec_t<float>* out, cudaStream_t s) {
+  k_to_prec32<<<grid_for(n, 256), 256, 0, s>>>(n, in, out);
   sem_count_launch();
 }
 
@@ -1057,7 +1077,7 @@ void launch_unpack(const SemGeom& g, const double* uB, double* full, int zero_di
 }
 
 template <typename T>
-void launch_pcg_init(long long nb, const T* b, T* r, T* p, T* q, T* x, const T* P, double* partials,
+void launch_pcg_init(long long nb, const T* b, T* r, T* p, T* q, T* x, const prec_t<T>* P, double* partials,
                      PcgState* st, double rtol, int maxit, int keep_x, cudaStream_t s) {
   k_pcg_init<T><<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, b, r, p, q, x, P, partials, st, rtol, maxit, keep_x,
                                                          keep_x);
@@ -1072,7 +1092,7 @@ void launch_mixed_start(MixedCtl* ctl, const PcgState* st64, PcgState* st32, dou
 
 void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& tab, const ApplyConfig* op,
                        const double* rhs, double* x, double* q, double* r, float* x32, float* r32, float* p32,
-                       float* q32, const float* P32, double* partials, MixedCtl* ctl, PcgState* st32,
+                       float* q32, const prec_t<float>* P32, double* partials, MixedCtl* ctl, PcgState* st32,
                        PcgState* gate, cudaStream_t s) {
   const long long nb = g.nb;
   k_mixed_gate<<<1, 32, 0, s>>>(ctl, st32, gate);
@@ -1085,13 +1105,14 @@ void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables
 }
 
 template <typename T>
-void launch_pcg_update(long long nb, T* r, const T* q, const T* P, double* partials, PcgState* st, cudaStream_t s) {
+void launch_pcg_update(long long nb, T* r, const T* q, const prec_t<T>* P, double* partials, PcgState* st,
+                       cudaStream_t s) {
   k_pcg_update<T><<<num_sms() * 2, kVecThreads, 0, s>>>(nb, r, q, P, partials, st);
   sem_count_launch();
 }
 
 template <typename T>
-void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s) {
+void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const prec_t<T>* P, PcgState* st, cudaStream_t s) {
   k_pcg_dir<T><<<num_sms() * 2, kVecThreads, 0, s>>>(nb, x, r, p, q, P, st);
   sem_count_launch();
 }
@@ -1125,7 +1146,7 @@ cudaError_t prepare_pcg_step(long long nb, bool* usable) {
 }
 
 template <typename T>
-cudaError_t launch_pcg_step(long long nb, T* x, T* r, T* p, T* q, const T* P, double* partials, PcgState* st,
+cudaError_t launch_pcg_step(long long nb, T* x, T* r, T* p, T* q, const prec_t<T>* P, double* partials, PcgState* st,
                             cudaStream_t s) {
   const size_t smem = step_smem<T>(nb);
   if (smem > kStepSmemMax) return cudaErrorInvalidValue;   // prepare_pcg_step reports it unusable
@@ -1151,13 +1172,15 @@ void launch_pcg_flush(long long nb, T* x, const T* p, PcgState* st, cudaStream_t
 }
 
 #define SEM_INST_VEC(T)                                                                                       \
-  template void launch_pcg_init<T>(long long, const T*, T*, T*, T*, T*, const T*, double*, PcgState*, double, \
-                                   int, int, cudaStream_t);                                                   \
-  template void launch_pcg_update<T>(long long, T*, const T*, const T*, double*, PcgState*, cudaStream_t);     \
-  template void launch_pcg_dir<T>(long long, T*, const T*, T*, T*, const T*, PcgState*, cudaStream_t);         \
+  template void launch_pcg_init<T>(long long, const T*, T*, T*, T*, T*, const prec_t<T>*, double*, PcgState*,  \
+                                   double, int, int, cudaStream_t);                                           \
+  template void launch_pcg_update<T>(long long, T*, const T*, const prec_t<T>*, double*, PcgState*,           \
+                                     cudaStream_t);                                                           \
+  template void launch_pcg_dir<T>(long long, T*, const T*, T*, T*, const prec_t<T>*, PcgState*, cudaStream_t); \
   template void launch_pcg_flush<T>(long long, T*, const T*, PcgState*, cudaStream_t);                     \
   template cudaError_t prepare_pcg_step<T>(long long, bool*);                                                 \
-  template cudaError_t launch_pcg_step<T>(long long, T*, T*, T*, T*, const T*, double*, PcgState*, cudaStream_t);
+  template cudaError_t launch_pcg_step<T>(long long, T*, T*, T*, T*, const prec_t<T>*, double*, PcgState*,     \
+                                          cudaStream_t);
 SEM_INST_VEC(double)
 SEM_INST_VEC(float)
 

@@ -1,7 +1,26 @@
 // Kernel launchers of the sm_103a condensed spectral-element library.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "sem_internal.h"
+
+// Storage type of the CG's inverse-diagonal (BT) preconditioner: T in the
+// FP64 CG; BF16 in the FP32 inner CG of mixed-precision solves.  The
+// preconditioner is a fixed diagonal scaling, so rounding each entry to BF16
+// (relative change <= 2^-9) moves the spectrum of the preconditioned operator
+// by a factor within 1 +- 2^-8 and keeps it SPD, and every CG step reads
+// half the bytes for it.
+template <typename T>
+struct PrecStore {
+  using type = T;
+};
+template <>
+struct PrecStore<float> {
+  using type = __nv_bfloat16;
+};
+template <typename T>
+using prec_t = typename PrecStore<T>::type;
 
 // Operator kernel variants: one operator, five work mappings (sem_apply.cu,
 // sem_apply_plane.cu, sem_apply_slab.cu).  The numbering is the one of SEM_KERNEL_* in sem.h.
@@ -144,15 +163,16 @@ void launch_unpack(const SemGeom& g, const double* uB, double* full, int zero_di
 // r = b - q (keep_x: q = A x0 on entry) else r = b and x = 0; z = P r; p = z;
 // q = 0; rho = r.z, rr = r.r, rr0 = b.b, tol2 = rtol^2 rr0.
 template <typename T>
-void launch_pcg_init(long long nb, const T* b, T* r, T* p, T* q, T* x, const T* P, double* partials,
+void launch_pcg_init(long long nb, const T* b, T* r, T* p, T* q, T* x, const prec_t<T>* P, double* partials,
                      PcgState* st, double rtol, int maxit, int keep_x, cudaStream_t s);
 // alpha from st: r -= alpha q; rho_new = r.P r, rr = r.r; convergence test.
 // When it stops the CG, the iteration's x += alpha p is owed (st->xpend).
 template <typename T>
-void launch_pcg_update(long long nb, T* r, const T* q, const T* P, double* partials, PcgState* st, cudaStream_t s);
+void launch_pcg_update(long long nb, T* r, const T* q, const prec_t<T>* P, double* partials, PcgState* st,
+                       cudaStream_t s);
 // x += alpha p, then p = P r + beta p, q = 0.
 template <typename T>
-void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgState* st, cudaStream_t s);
+void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const prec_t<T>* P, PcgState* st, cudaStream_t s);
 // One-pass CG step (k_pcg_step: the update and the direction of one iteration
 // with a grid barrier between them; cooperative launch, one CTA per SM).
 // prepare_pcg_step sets the kernel's shared-memory limit (call outside graph
@@ -160,7 +180,7 @@ void launch_pcg_dir(long long nb, T* x, const T* r, T* p, T* q, const T* P, PcgS
 template <typename T>
 cudaError_t prepare_pcg_step(long long nb, bool* usable);
 template <typename T>
-cudaError_t launch_pcg_step(long long nb, T* x, T* r, T* p, T* q, const T* P, double* partials, PcgState* st,
+cudaError_t launch_pcg_step(long long nb, T* x, T* r, T* p, T* q, const prec_t<T>* P, double* partials, PcgState* st,
                             cudaStream_t s);
 // Applies an owed x += alpha p (no-op when none is owed; idempotent).
 template <typename T>
@@ -173,6 +193,8 @@ void launch_ir_residual(long long nb, const double* b, const double* Ax, double*
 void launch_scale_to_f32(long long n, const double* in, double scale, float* out, cudaStream_t s);
 void launch_ir_update(long long nb, double* x, const float* c, double scale, cudaStream_t s);
 void launch_cast_f32(long long n, const double* in, float* out, cudaStream_t s);
+// out = in rounded to the FP32 CG's preconditioner storage type (BF16, nearest even).
+void launch_cast_prec32(long long n, const double* in, prec_t<float>* out, cudaStream_t s);
 // Device-side refinement of a mixed-precision solve (one MixedCtl per
 // problem): start after the FP64 residual r = b (st64) and the FP32 CG
 // initialisation; one step per loop trip (gate, fold x32 into x, FP64
@@ -182,7 +204,7 @@ void launch_mixed_start(MixedCtl* ctl, const PcgState* st64, PcgState* st32, dou
                         int max_refine, cudaStream_t s);
 void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& tab, const ApplyConfig* op,
                        const double* rhs, double* x, double* q, double* r, float* x32, float* r32, float* p32,
-                       float* q32, const float* P32, double* partials, MixedCtl* ctl, PcgState* st32,
+                       float* q32, const prec_t<float>* P32, double* partials, MixedCtl* ctl, PcgState* st32,
                        PcgState* gate, cudaStream_t s);
 
 int sem_vec_blocks();
