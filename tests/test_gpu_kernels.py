@@ -198,6 +198,32 @@ def test_cta_tile_fp32_vs_oracle(p, m, epb, ks):
     assert _check_f32(ctx, ms, 1.0, 500 + p) <= F32_TOL
 
 
+@pytest.mark.parametrize("p,m,epb,ks", [(8, (3, 2, 2), 3, 3),    # n = 7: slabs start at k = 0, 3, 6
+                                        (4, (3, 3, 2), 6, 1),    # n = 3: every slab one plane
+                                        (6, (2, 3, 2), 2, 2),    # n = 5: degree not compiled in
+                                        (9, (2, 2, 2), 2, 5),    # n = 8
+                                        (3, (3, 2, 3), 4, 1),    # n = 2
+                                        (10, (2, 2, 1), 1, 9)])  # n = 9
+def test_cta_tile_fp64_shapes_vs_oracle(p, m, epb, ks):
+    """FP64 CTA tiles of chosen shapes (elements per CTA, k-slab depth: the
+    autotuner's search space) against the oracle at 1e-12, with k-slabs
+    that start at odd planes and degrees served by the run-time-n kernel
+    (Sec. 6 / Table 2)."""
+    import torch
+    from paper_1601_08179_gb300 import sem
+    ctx, ms = make_pair(p, m, 1.5, 8.0)
+    sem.sem_set_operator_kernel(ctx, sem.PREC_FP64, sem.KERNEL_CTA_TILE, epb, ks)
+    assert sem.sem_get_operator_kernel(ctx, sem.PREC_FP64) == (sem.KERNEL_CTA_TILE, epb, ks)
+    ut = si.random_vector(ms.n_skeleton, 650 + p)
+    v = torch.empty(ctx.nb, dtype=torch.float64, device="cuda")
+    sem.sem_apply_condensed(ctx, dev(ut), v, sem.SPACE_TRANSFORMED)
+    got, ref = host(v), _oracle_apply(ms, 1.5, ut)
+    assert np.all(got[~ms.skeleton_free] == 0.0)
+    err = relerr(got, ref)
+    print(f"cta fp64 p={p} epb={epb} ks={ks}: {err:.2e}")
+    assert err <= F64_TOL
+
+
 @pytest.mark.parametrize("kind,epb,ks", [("cta", 1, 1), ("cta", 4, 1), ("element", 0, 0)])
 def test_p2_variants_fp64_vs_oracle(kind, epb, ks):
     import torch
