@@ -89,6 +89,7 @@ struct sem_ctx {
   double *d_x = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_b = nullptr;
   double *d_t1 = nullptr, *d_t2 = nullptr;
   double *d_c0 = nullptr, *d_c1 = nullptr, *d_FtI = nullptr;   // interior cubes
+  int* d_cexp = nullptr;               // per-element scale exponents of the mode products
   double* d_partials = nullptr;
   PcgState* d_st = nullptr;
   PcgState* h_st = nullptr;            // pinned
@@ -279,7 +280,7 @@ sem_status ensure_cubes(sem_ctx* c) {
   if (c->d_c0 != nullptr) return SEM_OK;
   const size_t n3 = (size_t)c->g.nelem * c->g.n * c->g.n * c->g.n;
   if (dalloc(&c->d_c0, n3) != cudaSuccess || dalloc(&c->d_c1, n3) != cudaSuccess ||
-      dalloc(&c->d_FtI, n3) != cudaSuccess)
+      dalloc(&c->d_FtI, n3) != cudaSuccess || dalloc(&c->d_cexp, (size_t)c->g.nelem) != cudaSuccess)
     return fail(SEM_ENOMEM, "cannot allocate element interior scratch");
   return SEM_OK;
 }
@@ -293,9 +294,7 @@ sem_status condense_rhs_t(sem_ctx* c, const double* f, double* out, cudaStream_t
   launch_load_skeleton(g, mx, my, mz, f, c->d_t1, s);
   launch_skel_transform(g, c->mat(0), c->d_t1, out, s);
   launch_interior_load(g, mx, my, mz, f, c->d_c0, s);
-  launch_mode(g, c->mat(0), 0, c->d_c0, c->d_c1, nullptr, s);
-  launch_mode(g, c->mat(0), 1, c->d_c1, c->d_c0, nullptr, s);
-  launch_mode(g, c->mat(0), 2, c->d_c0, c->d_FtI, nullptr, s);
+  launch_mode3(g, c->mat(0), c->d_c0, c->d_c1, c->d_cexp, c->d_FtI, nullptr, s);
   launch_condense_faces(g, c->h1.basis, c->tab, c->d_FtI, out, s);
   SEM_CUDA(cudaGetLastError());
   return SEM_OK;
@@ -305,9 +304,7 @@ sem_status condense_rhs_t(sem_ctx* c, const double* f, double* out, cudaStream_t
 sem_status recover_t(sem_ctx* c, const double* ut, double* u, cudaStream_t s) {
   const SemGeom& g = c->g;
   launch_recover_expand(g, c->h1.basis, c->tab, c->d_FtI, ut, c->d_c0, s);
-  launch_mode(g, c->mat(1), 0, c->d_c0, c->d_c1, nullptr, s);
-  launch_mode(g, c->mat(1), 1, c->d_c1, c->d_c0, nullptr, s);
-  launch_mode(g, c->mat(1), 2, c->d_c0, nullptr, u, s);
+  launch_mode3(g, c->mat(1), c->d_c0, c->d_c1, c->d_cexp, nullptr, u, s);
   launch_skel_transform(g, c->mat(1), ut, c->d_t2, s);
   launch_unpack(g, c->d_t2, u, 1, s);
   SEM_CUDA(cudaGetLastError());
@@ -808,7 +805,7 @@ void free_ctx(sem_ctx* c) {
   if (c->d_trips) cudaFree(c->d_trips);
   if (c->d_ev) cudaFree(c->d_ev);
   void* ptrs[] = {c->d_cls, c->d_uw, c->d_dcoef, c->d_dinv, c->d_mats, c->d_mass, c->d_P, c->d_x, c->d_r,
-                  c->d_p, c->d_q, c->d_b, c->d_t1, c->d_t2, c->d_c0, c->d_c1, c->d_FtI, c->d_partials, c->d_st};
+                  c->d_p, c->d_q, c->d_b, c->d_t1, c->d_t2, c->d_c0, c->d_c1, c->d_FtI, c->d_cexp, c->d_partials, c->d_st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_st) cudaFreeHost(c->h_st);
@@ -1508,6 +1505,8 @@ extern "C" sem_status sem_condense_rhs_noalloc(sem_ctx* c, const double* f, doub
   launch_load_skeleton(g, mx, my, mz, f, fB, s);
   launch_skel_transform(g, c->mat(0), fB, fB, s);
   launch_interior_load(g, mx, my, mz, f, c0, s);
+  // FP64 mode products: the fixed scratch has no room for the per-element
+  // scale exponents of the double-float form
   launch_mode(g, c->mat(0), 0, c0, c1, nullptr, s);
   launch_mode(g, c->mat(0), 1, c1, c0, nullptr, s);
   launch_mode(g, c->mat(0), 2, c0, ft, nullptr, s);

@@ -21,6 +21,8 @@
 // except the skeleton values and the per-width-class D^-1 table (L2 resident).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <atomic>
 #include <cstdio>
 
@@ -288,6 +290,160 @@ __global__ void k_mode(SemGeom g, const double* __restrict__ A, int axis, const 
       grid[gx + g.Nx * (gy + g.Ny * gz)] = s;
     } else {
       out[t] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mode products in double-float arithmetic
+// ---------------------------------------------------------------------------
+// GB300's FP64 pipe runs at 1/64 of the FP32 pipe, and the O(n^4) mode
+// products of load condensation and recovery (S (x) S (x) S on every interior
+// cube, Algorithm 4) are bound by it in plain FP64.  They are computed here on
+// the FP32 pipe in double-float form: a value is an unevaluated sum h + l of
+// two floats (|l| <= ulp(h) / 2, 48 significant bits).  One multiply-add
+// c += a b takes the exact product of the high parts (a product and its FMA
+// residual), adds the cross terms a_h b_l + a_l b_h (the a_l b_l term, below
+// 2^-48 of the product, is dropped), and adds the high product to the running
+// sum with an error-free two-sum (Knuth), the rounding errors going to a
+// second accumulator.  Explicit _rn intrinsics keep the compiler from fusing
+// the error-free steps into FMAs.  Error of a length-n dot product: about
+// n 2^-48 of sum |a b|, that of the FP64 FMA chain being n 2^-53.
+// x 2^-shift = h + l: h the top 24 significant bits, l the next 24 (both
+// truncated), formed from the bit fields with integer operations so that the
+// split costs no FP64-pipe work; |x 2^-shift - h - l| < 2^-46 |x 2^-shift|.
+// Values whose scaled parts would not both be normal floats
+// (|x 2^-shift| < 2^-74 or >= 2^128), zeros and subnormals take the FP64
+// conversion.
+__device__ __forceinline__ float2 df_from_double(double x, int shift = 0) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int ex0 = (int)((hi >> 20) & 0x7ffu), ex = ex0 - shift;
+  if (ex0 == 0 || ex0 == 0x7ff || ex < 949 || ex > 1150) {
+    const double xs = shift == 0 ? x : scalbn(x, -shift);
+    const float h = __double2float_rn(xs);
+    return make_float2(h, __double2float_rn(xs - (double)h));
+  }
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned long long mant = b & 0xfffffffffffffULL;                 // 52 bits below the leading 1
+  const unsigned hb = sign | ((unsigned)(ex - 896) << 23) | (unsigned)(mant >> 29);
+  const unsigned rem = (unsigned)(mant & 0x1fffffffULL);                   // the 29 bits h leaves out
+  unsigned lb = 0u;
+  if (rem != 0u) {
+    const int pb = 31 - __clz((int)rem);                                   // leading bit of rem, 0..28
+    const unsigned m = pb >= 23 ? (rem >> (pb - 23)) : (rem << (23 - pb));
+    lb = sign | ((unsigned)(pb + ex - 948) << 23) | (m & 0x7fffffu);
+  }
+  return make_float2(__uint_as_float(hb), __uint_as_float(lb));
+}
+
+// (s, e) += a b; s is the running sum of the high products, e collects the
+// rounding errors and the low-order terms.
+__device__ __forceinline__ void df_mac(float2 a, float2 b, float& s, float& e) {
+  const float ph = __fmul_rn(a.x, b.x);
+  float pl = __fmaf_rn(a.x, b.x, -ph);
+  pl = __fmaf_rn(a.x, b.y, pl);
+  pl = __fmaf_rn(a.y, b.x, pl);
+  const float t = __fadd_rn(s, ph);
+  const float bv = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(ph, bv));
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(err, pl));
+}
+
+// Double-float has the FP32 exponent range, so each element's cube is scaled
+// by a power of two, 2^-shift with 2^shift <= max |x| < 2^(shift + 1), before
+// the split (exact); the shift goes to eexp[e] and the last mode product
+// scales back.  Entries below 2^-74 of their element's largest keep 24 to 48
+// bits, which is below 2^-120 of that entry in absolute terms.  One CTA per
+// element: the largest exponent, then the split (the second read hits L2).
+__global__ void __launch_bounds__(256)
+k_split_df(SemGeom g, const double* __restrict__ in, float2* __restrict__ out, int* __restrict__ eexp) {
+  __shared__ int emax;
+  const long long n3 = (long long)g.n * g.n * g.n;
+  for (long long e = blockIdx.x; e < g.nelem; e += gridDim.x) {
+    const double* x = in + e * n3;
+    if (threadIdx.x == 0) emax = 0;
+    __syncthreads();
+    int m = 0;
+    for (long long t = threadIdx.x; t < n3; t += blockDim.x) {
+      const int ex = (int)(((unsigned long long)__double_as_longlong(x[t]) >> 52) & 0x7ffu);
+      m = max(m, ex == 0x7ff ? 0 : ex);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&emax, m);
+    __syncthreads();
+    // all zero or subnormal: scale the subnormals up as if the largest had exponent -1022
+    const int shift = (emax == 0 ? 1 : emax) - 1023;
+    for (long long t = threadIdx.x; t < n3; t += blockDim.x) out[e * n3 + t] = df_from_double(x[t], shift);
+    if (threadIdx.x == 0) eexp[e] = shift;
+    __syncthreads();
+  }
+}
+
+// One mode product along `axis` (0: i, 1: j, 2: k) of all interior cubes:
+// out[.. r ..] = sum_c A[r][c] in[.. c ..].  A thread takes one line of a cube
+// along the axis and kModeRows consecutive rows r: each input value it loads
+// serves kModeRows outputs, and the rows of A it reads are the same across
+// the warp (shared-memory broadcast).  FINAL: the result is rounded to FP64
+// into out, or into the interior nodes of the full nodal field when
+// grid != nullptr, after scaling back by the element's 2^eexp[e]; otherwise
+// it stays double-float and scaled.
+constexpr int kModeRows = 8;
+
+template <bool FINAL>
+__global__ void __launch_bounds__(256)
+k_mode_df(SemGeom g, const double* __restrict__ A, int axis, const float2* __restrict__ in, float2* __restrict__ out2,
+          double* __restrict__ out, double* __restrict__ grid, const int* __restrict__ eexp) {
+  __shared__ float2 sA[SEM_MAXN * SEM_MAXN];
+  const int n = g.n, p = g.p, n2 = n * n;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) sA[t] = df_from_double(A[t]);
+  __syncthreads();
+  const long long n3 = (long long)n2 * n, nlines = g.nelem * n2;
+  const int nrb = (n + kModeRows - 1) / kModeRows;
+  const int stride = axis == 0 ? 1 : (axis == 1 ? n : n2);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nlines * nrb;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int rb = (int)(t / nlines);
+    const long long line = t - rb * nlines;
+    const long long e = line / n2;
+    const int q = (int)(line - e * n2), qa = q % n, qb = q / n;
+    // the two coordinates across the line: (j, k), (i, k) or (i, j)
+    const int i0 = axis == 0 ? 0 : qa, j0 = axis == 0 ? qa : (axis == 1 ? 0 : qb), k0 = axis == 2 ? 0 : qb;
+    const long long base = e * n3 + i0 + (long long)n * (j0 + (long long)n * k0);
+    const int r0 = rb * kModeRows;
+    const float2* Arow[kModeRows];
+#pragma unroll
+    for (int u = 0; u < kModeRows; ++u) Arow[u] = sA + min(r0 + u, n - 1) * n;   // rows past n: computed, not stored
+    float sh[kModeRows], sl[kModeRows];
+#pragma unroll
+    for (int u = 0; u < kModeRows; ++u) sh[u] = sl[u] = 0.f;
+    for (int c = 0; c < n; ++c) {
+      const float2 x = in[base + (long long)c * stride];
+#pragma unroll
+      for (int u = 0; u < kModeRows; ++u) df_mac(Arow[u][c], x, sh[u], sl[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kModeRows; ++u) {
+      const int r = r0 + u;
+      if (r >= n) break;
+      const long long o = base + (long long)r * stride;
+      if (FINAL) {
+        const double v = scalbn((double)sh[u] + (double)sl[u], eexp[e]);
+        if (grid != nullptr) {
+          int ex, ey, ez;
+          elem_coords(g, e, &ex, &ey, &ez);
+          const int i = axis == 0 ? r : i0, j = axis == 1 ? r : j0, k = axis == 2 ? r : k0;
+          const long long gx = (long long)ex * p + i + 1, gy = (long long)ey * p + j + 1,
+                          gz = (long long)ez * p + k + 1;
+          grid[gx + g.Nx * (gy + g.Ny * gz)] = v;
+        } else {
+          out[o] = v;
+        }
+      } else {
+        const float h = __fadd_rn(sh[u], sl[u]);
+        out2[o] = make_float2(h, __fsub_rn(sl[u], __fsub_rn(h, sh[u])));
+      }
     }
   }
 }
@@ -1048,6 +1204,21 @@ void launch_mode(const SemGeom& g, const double* A, int axis, const double* in, 
   const long long work = g.nelem * (long long)g.n * g.n * g.n;
   k_mode<<<grid_for(work, 256, 16), 256, 0, s>>>(g, A, axis, in, out, grid);
   sem_count_launch();
+}
+
+void launch_mode3(const SemGeom& g, const double* A, double* in, double* tmp, int* eexp, double* out, double* grid,
+                  cudaStream_t s) {
+  const long long lines = g.nelem * (long long)g.n * g.n * ((g.n + kModeRows - 1) / kModeRows);
+  const int mblocks = grid_for(lines, 256, 16);
+  const int sblocks = (int)std::min<long long>(g.nelem, (long long)num_sms() * 16);
+  // a double-float value takes the 8 bytes of the FP64 one it replaces
+  float2* a = reinterpret_cast<float2*>(tmp);
+  float2* b = reinterpret_cast<float2*>(in);
+  k_split_df<<<sblocks, 256, 0, s>>>(g, in, a, eexp);
+  k_mode_df<false><<<mblocks, 256, 0, s>>>(g, A, 0, a, b, nullptr, nullptr, eexp);
+  k_mode_df<false><<<mblocks, 256, 0, s>>>(g, A, 1, b, a, nullptr, nullptr, eexp);
+  k_mode_df<true><<<mblocks, 256, 0, s>>>(g, A, 2, a, nullptr, out, grid, eexp);
+  sem_count_launch(4);
 }
 
 void launch_condense_faces(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,

@@ -141,10 +141,20 @@ void launch_interior_load(const SemGeom& g, const double* mxs, const double* mys
                           const double* f, double* X, cudaStream_t s);
 
 // Mode product along `axis` (0: i, 1: j, 2: k) of all interior cubes with the
-// n x n matrix A: out[.. r ..] = sum_c A[r][c] in[.. c ..].  If grid != nullptr
-// the result is written to the interior nodes of the full nodal field instead.
+// n x n matrix A in FP64: out[.. r ..] = sum_c A[r][c] in[.. c ..].  If
+// grid != nullptr the result is written to the interior nodes of the full
+// nodal field instead.
 void launch_mode(const SemGeom& g, const double* A, int axis, const double* in, double* out,
                  double* grid, cudaStream_t s);
+// The three mode products (A (x) A (x) A) of all interior cubes with the n x n
+// matrix A: x[.. r ..] <- sum_c A[r][c] x[.. c ..] along i, then j, then k,
+// in double-float arithmetic on the FP32 pipe (about 48 significant bits,
+// each element's cube scaled by a power of two).  in: FP64 cubes (nelem n^3
+// values, overwritten), tmp: scratch of the same size, eexp: nelem ints of
+// scratch; the result goes to out (FP64 cubes), or, if grid != nullptr, to
+// the interior nodes of the full nodal field.
+void launch_mode3(const SemGeom& g, const double* A, double* in, double* tmp, int* eexp, double* out, double* grid,
+                  cudaStream_t s);
 
 // Condensed-load correction: Z = D^-1 Ft_I per element; out faces -= d k . Z.
 void launch_condense_faces(const SemGeom& g, const SemBasis& b, const SemClassTables<double>& t,

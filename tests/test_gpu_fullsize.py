@@ -116,7 +116,12 @@ def test_mixed16_error_per_refinement_step():
         errs.append(_sampled_rel(host(u)[idx], want))
     print("error vs the oracle per refinement step:", " ".join(f"{e:.2e}" for e in errs), f"final {final:.2e}")
     assert all(b < a for a, b in zip(errs, errs[1:]))
-    assert errs[-1] == pytest.approx(final, rel=1e-3, abs=1e-12)
+    # the re-run with the same number of steps reproduces the first run's
+    # error up to the spread of mixed solves, which are reproducible to
+    # rounding only (FP32 atomic adds in the inner operator): two runs stop at
+    # different iterates with the same 1e-10 residual, measured 0.4-1.6e-12
+    # apart in their error against the oracle
+    assert errs[-1] == pytest.approx(final, rel=1e-3, abs=3e-12)
     assert final <= 1e-9
 
 
