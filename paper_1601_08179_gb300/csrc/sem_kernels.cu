@@ -337,6 +337,19 @@ __device__ __forceinline__ float2 df_from_double(double x, int shift = 0) {
   return make_float2(__uint_as_float(hb), __uint_as_float(lb));
 }
 
+// f 2^e as a double, exactly, from the bit fields (integer operations);
+// zeros directly, subnormals and results outside the normal double range
+// through the FP64 path.
+__device__ __forceinline__ double df_part_to_double(float f, int e) {
+  const unsigned u = __float_as_uint(f);
+  if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));   // +-0
+  const int ex = (int)((u >> 23) & 0xffu), dex = ex + 896 + e;
+  if (ex == 0 || ex == 0xff || dex <= 0 || dex >= 0x7ff) return scalbn((double)f, e);
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) | ((unsigned long long)dex << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
 // (s, e) += a b; s is the running sum of the high products, e collects the
 // rounding errors and the low-order terms.
 __device__ __forceinline__ void df_mac(float2 a, float2 b, float& s, float& e) {
@@ -378,6 +391,27 @@ k_split_df(SemGeom g, const double* __restrict__ in, float2* __restrict__ out, i
     for (long long t = threadIdx.x; t < n3; t += blockDim.x) out[e * n3 + t] = df_from_double(x[t], shift);
     if (threadIdx.x == 0) eexp[e] = shift;
     __syncthreads();
+  }
+}
+
+// The same with one warp per element, for cubes of up to 4096 values (n <= 16).
+__global__ void __launch_bounds__(256)
+k_split_df_warp(SemGeom g, const double* __restrict__ in, float2* __restrict__ out, int* __restrict__ eexp) {
+  const long long n3 = (long long)g.n * g.n * g.n;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long e = w0; e < g.nelem; e += nw) {
+    const double* x = in + e * n3;
+    int m = 0;
+    for (long long t = lane; t < n3; t += 32) {
+      const int ex = (int)(((unsigned long long)__double_as_longlong(x[t]) >> 52) & 0x7ffu);
+      m = max(m, ex == 0x7ff ? 0 : ex);
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    const int shift = (m == 0 ? 1 : m) - 1023;
+    for (long long t = lane; t < n3; t += 32) out[e * n3 + t] = df_from_double(x[t], shift);
+    if (lane == 0) eexp[e] = shift;
   }
 }
 
@@ -429,7 +463,8 @@ k_mode_df(SemGeom g, const double* __restrict__ A, int axis, const float2* __res
       if (r >= n) break;
       const long long o = base + (long long)r * stride;
       if (FINAL) {
-        const double v = scalbn((double)sh[u] + (double)sl[u], eexp[e]);
+        const int sc = eexp[e];
+        const double v = df_part_to_double(sh[u], sc) + df_part_to_double(sl[u], sc);   // one FP64 addition
         if (grid != nullptr) {
           int ex, ey, ez;
           elem_coords(g, e, &ex, &ey, &ez);
@@ -1214,7 +1249,10 @@ void launch_mode3(const SemGeom& g, const double* A, double* in, double* tmp, in
   // a double-float value takes the 8 bytes of the FP64 one it replaces
   float2* a = reinterpret_cast<float2*>(tmp);
   float2* b = reinterpret_cast<float2*>(in);
-  k_split_df<<<sblocks, 256, 0, s>>>(g, in, a, eexp);
+  if ((long long)g.n * g.n * g.n <= 4096)
+    k_split_df_warp<<<grid_for(g.nelem * 32, 256, 16), 256, 0, s>>>(g, in, a, eexp);
+  else
+    k_split_df<<<sblocks, 256, 0, s>>>(g, in, a, eexp);
   k_mode_df<false><<<mblocks, 256, 0, s>>>(g, A, 0, a, b, nullptr, nullptr, eexp);
   k_mode_df<false><<<mblocks, 256, 0, s>>>(g, A, 1, b, a, nullptr, nullptr, eexp);
   k_mode_df<true><<<mblocks, 256, 0, s>>>(g, A, 2, a, nullptr, out, grid, eexp);
@@ -1268,7 +1306,12 @@ void launch_mixed_step(const SemGeom& g, const SemBasis& b, const SemClassTables
   const long long nb = g.nb;
   k_mixed_gate<<<1, 32, 0, s>>>(ctl, st32, gate);
   k_mixed_fold<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, x, x32, p32, q, ctl, st32);
-  launch_tpt_apply<double>(g, b, tab, x, q, partials, gate, s, op);
+  // mixed solves are reproducible to rounding only (FP32 atomic adds in the
+  // inner operator): the refinement's FP64 operator takes atomic edge and
+  // vertex adds too, not the fixed-order sums' extra pass
+  ApplyConfig op_atomic = op != nullptr ? *op : ApplyConfig{};
+  op_atomic.ev = nullptr;
+  launch_tpt_apply<double>(g, b, tab, x, q, partials, gate, s, &op_atomic);
   k_mixed_residual<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, rhs, q, r, partials, ctl, st32);
   k_mixed_rebase<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r, P32, r32, partials, ctl, st32);
   k_mixed_dir<<<sem_vec_blocks(), kVecThreads, 0, s>>>(nb, r32, p32, q32, P32, ctl, st32);
