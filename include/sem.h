@@ -197,7 +197,11 @@ sem_status sem_apply_condensed_f32(sem_ctx* ctx, const float* uB, float* vB, voi
 /* Condensed load fhat = sum_e Rhat_e (F_B - H_BI H_II^-1 F_I) (Algorithm 1,
  * first loop; Algorithm 4 in the TRANSFORMED space), with F_e the GLL-quadrature
  * load of the nodal field f: F_e = (h1 h2 h3 / 8) (w (x) w (x) w) o f_e.
- * f: device full nodal field; fB: device skeleton vector.  Asynchronous. */
+ * f: device full nodal field; fB: device skeleton vector.  Asynchronous.
+ * The interior transforms (S (x) S (x) S on every element) are computed in
+ * double-float arithmetic on the FP32 pipe: about 48 significant bits, each
+ * element's values scaled by a power of two first, so the result stays
+ * within about 1e-13 of FP64 arithmetic relative to its norm. */
 sem_status sem_condense_rhs(sem_ctx* ctx, const double* f, double* fB,
                             sem_space space, void* stream);
 
@@ -209,7 +213,9 @@ sem_status sem_precond_diag(sem_ctx* ctx, double* diag, void* stream);
 /* Interior recovery (Algorithm 4, second loop): u_I = H_II^-1 (F_I - H_IB u_B)
  * per element, back-transformed, written with the skeleton values into the
  * full nodal field u.  uB is a skeleton solution in `space`.  f, u: device full
- * nodal fields (u is fully overwritten, Dirichlet nodes with 0).  Asynchronous. */
+ * nodal fields (u is fully overwritten, Dirichlet nodes with 0).  Asynchronous.
+ * The back-transform of the interiors is computed in double-float arithmetic
+ * like the load's (sem_condense_rhs). */
 sem_status sem_recover_interior(sem_ctx* ctx, const double* f, const double* uB,
                                 sem_space space, double* u, void* stream);
 
