@@ -267,7 +267,10 @@ sem_status sem_unpack_skeleton(sem_ctx* ctx, const double* uB, double* u_full, v
  * other allocating routine and instead uses a fixed scratch array compiled
  * into the library (12 MiB, held by every GPU that loads the library until
  * the process exits).
- *   ctx, f, fB, space, stream: as for sem_condense_rhs (same result).
+ *   ctx, f, fB, space, stream: as for sem_condense_rhs (same result to
+ *   about 1e-13: this variant's interior transforms run in FP64, the fixed
+ *   array having no room for the per-element scale exponents of the
+ *   double-float form).
  *   Limit: elements * (p-1)^3 <= 524288 (e.g. p = 8 on 8^3 elements, p = 4 on
  *   16^3); larger meshes are rejected with SEM_EINVAL and a message.
  * The first call on each device looks up the scratch array's device address;
